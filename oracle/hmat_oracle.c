@@ -1,0 +1,963 @@
+/*
+ * hmat_oracle.c -- plain, slow, obviously correct FP64 CPU oracle for the
+ * mixed-precision H-matrix vector product of Ooi, Iwashita, Fukaya, Ida and
+ * Yokota, "Effect of Mixed Precision Computing on H-Matrix Vector
+ * Multiplication in BEM Analysis" (arXiv:1911.00093), and for the BiCG-STAB
+ * solve that repeats it.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package smoke check and
+ * the benchmark's CPU-baseline leg may load this library.  It shares no code
+ * with the GPU path (no headers, no helpers, no tables) and never calls it.
+ *
+ * Build: gcc -O2 -std=c11 -fPIC -shared -ffp-contract=off -fopenmp -lm.
+ * -ffp-contract=off keeps every a*b+c as a rounded product followed by a
+ * rounded sum, which is what the precision emulation of Table 1 relies on.
+ *
+ * What is computed, and where it comes from:
+ *   - collocation kernel a_ij = area_j / (4 pi |c_i - c_j|), a_ii =
+ *     sqrt(area_i / pi) / 2 (single-layer potential of flat panels, unit
+ *     permittivity; the self term is the potential at the centre of a
+ *     uniformly charged disk of the panel's area);
+ *   - cluster tree: longest-axis geometric bisection of the collocation points
+ *     at the bounding-box midpoint, leaf size <= nleaf;
+ *   - block partition M of Section 2, eq. (1)-(2), by standard admissibility
+ *     min(diam tau, diam sigma) <= eta * dist(tau, sigma) with dist > 0;
+ *   - ACA with partial pivoting for the low-rank blocks A|^m ~ V_m W_m, eq. (3)-(4);
+ *   - H-matrix vector product, eq. (5)-(10), (21)-(25), in the precision
+ *     assignments of Table 1 for Methods 1, 2 (eq. 11-16) and 3 (eq. 17-20);
+ *   - BiCG-STAB, Algorithm 1, with the FP64 true-residual acceptance of
+ *     Section 4.1.3 and a restart from the true residual when it fails;
+ *   - dense helpers for pins: full matrix, dense product, Gaussian elimination.
+ *
+ * Readings where the paper is silent are marked READING in the comments.
+ *
+ * Parity unpinned: none of the functions below; every function is pinned by
+ * the not-gpu tests (closed forms, brute force, library routines, invariants).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------- */
+/* precision variants of Table 1 (plus the GPU-native storage forms)           */
+/* ------------------------------------------------------------------------- */
+enum {
+    OR_M1_DOUBLE = 0, /* Method 1-Double, the FP64 baseline                      */
+    OR_M1_SINGLE = 1, /* FP32 matrix x FP32 source -> FP64 result                */
+    OR_M1_MIXED = 2,  /* FP32 matrix x FP64 source -> FP64 result                */
+    OR_M2_DOUBLE = 3, /* V' D W' form, everything FP64                            */
+    OR_M2_SINGLE = 4, /* V' D W' form, FP32 matrix x FP32 source, z FP64          */
+    OR_M2_MIXED = 5,  /* V' D W' form, FP32 matrix x FP64 source, z FP64          */
+    OR_M3 = 6,        /* per-rank FP64/FP32 split by d_i >= d_max 10^-c           */
+    OR_DATA_FP32 = 7, /* panels rounded to FP32, all arithmetic FP64              */
+    OR_DATA_BF16 = 8  /* panels rounded to pow2-scaled BF16, arithmetic FP64      */
+};
+
+/* ------------------------------------------------------------------------- */
+/* kernel                                                                     */
+/* ------------------------------------------------------------------------- */
+/* Entry (i, j) of the collocation matrix, i and j in the ORIGINAL panel order. */
+double or_kernel_entry(const double *c, const double *area, int64_t i, int64_t j)
+{
+    if (i == j)
+        return sqrt(area[i] / OR_PI) / 2.0;
+    double dx = c[3 * i + 0] - c[3 * j + 0];
+    double dy = c[3 * i + 1] - c[3 * j + 1];
+    double dz = c[3 * i + 2] - c[3 * j + 2];
+    double r = sqrt(dx * dx + dy * dy + dz * dz);
+    return area[j] / (4.0 * OR_PI * r);
+}
+
+/* Full dense N x N collocation matrix, row-major, original order. */
+void or_dense_matrix(int64_t n, const double *c, const double *area, double *A)
+{
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = 0; j < n; j++)
+            A[i * n + j] = or_kernel_entry(c, area, i, j);
+}
+
+/* y = A x for a dense row-major matrix. */
+void or_dense_matvec(int64_t n, const double *A, const double *x, double *y)
+{
+    for (int64_t i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int64_t j = 0; j < n; j++)
+            s += A[i * n + j] * x[j];
+        y[i] = s;
+    }
+}
+
+/* Gaussian elimination with partial pivoting, A (row-major, n x n) is copied.
+ * Returns 0, or -1 for an exactly singular pivot. */
+int or_dense_solve(int64_t n, const double *A_in, const double *b, double *x)
+{
+    double *A = (double *)malloc(sizeof(double) * n * n);
+    double *y = (double *)malloc(sizeof(double) * n);
+    if (!A || !y) { free(A); free(y); return -2; }
+    memcpy(A, A_in, sizeof(double) * n * n);
+    memcpy(y, b, sizeof(double) * n);
+    int rc = 0;
+    for (int64_t k = 0; k < n; k++) {
+        int64_t p = k;
+        for (int64_t i = k + 1; i < n; i++)
+            if (fabs(A[i * n + k]) > fabs(A[p * n + k]))
+                p = i;
+        if (A[p * n + k] == 0.0) { rc = -1; break; }
+        if (p != k) {
+            for (int64_t j = 0; j < n; j++) {
+                double t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t;
+            }
+            double t = y[k]; y[k] = y[p]; y[p] = t;
+        }
+        for (int64_t i = k + 1; i < n; i++) {
+            double f = A[i * n + k] / A[k * n + k];
+            if (f == 0.0) continue;
+            for (int64_t j = k; j < n; j++)
+                A[i * n + j] -= f * A[k * n + j];
+            y[i] -= f * y[k];
+        }
+    }
+    if (rc == 0) {
+        for (int64_t i = n - 1; i >= 0; i--) {
+            double s = y[i];
+            for (int64_t j = i + 1; j < n; j++)
+                s -= A[i * n + j] * x[j];
+            x[i] = s / A[i * n + i];
+        }
+    }
+    free(A); free(y);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* cluster tree                                                               */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t begin, end;   /* range [begin, end) of the permuted index space */
+    int64_t child[2];     /* -1 for a leaf */
+    double lo[3], hi[3];  /* bounding box of the member collocation points */
+} or_cluster;
+
+typedef struct {
+    int64_t n;
+    int64_t nleaf;
+    double eta, eps;
+    const double *c, *area;      /* borrowed during the build only */
+    int64_t *perm;               /* perm[p] = original index at permuted position p */
+    or_cluster *cl; int64_t ncl, capcl;
+    /* blocks, in the order the block recursion emits them */
+    int64_t nb, capb;
+    int64_t *bi_s, *bi_e, *bj_s, *bj_e;  /* I_m = [bi_s, bi_e), J_m = [bj_s, bj_e), permuted */
+    int *bkind;                          /* 0 dense, 1 low rank */
+    int64_t *brank;
+    double **bdata;  /* dense: #I x #J row-major A|^m; LR: V_m (#I x r, row-major) then
+                        W_m (r x #J, row-major) -- the paper's V_m, W_m of eq. (3) */
+    int *bforced;    /* 1 if admissible but stored dense because r(#I+#J) >= #I #J */
+} or_hmat;
+
+static void grow_clusters(or_hmat *h)
+{
+    if (h->ncl == h->capcl) {
+        h->capcl = h->capcl ? 2 * h->capcl : 1024;
+        h->cl = (or_cluster *)realloc(h->cl, sizeof(or_cluster) * h->capcl);
+    }
+}
+
+/* comparison key for the median fallback: (coordinate, original index) */
+static const double *g_sort_c;
+static int g_sort_axis;
+static int cmp_coord_index(const void *pa, const void *pb)
+{
+    int64_t a = *(const int64_t *)pa, b = *(const int64_t *)pb;
+    double ca = g_sort_c[3 * a + g_sort_axis], cb = g_sort_c[3 * b + g_sort_axis];
+    if (ca < cb) return -1;
+    if (ca > cb) return 1;
+    return (a < b) ? -1 : (a > b);
+}
+
+/* Build the cluster on idx[begin,end) (original indices, in their current order). */
+static int64_t build_cluster(or_hmat *h, int64_t *idx, int64_t *tmp, int64_t begin, int64_t end)
+{
+    grow_clusters(h);
+    int64_t me = h->ncl++;
+    or_cluster *k = &h->cl[me];
+    k->begin = begin; k->end = end; k->child[0] = k->child[1] = -1;
+    for (int d = 0; d < 3; d++) { k->lo[d] = INFINITY; k->hi[d] = -INFINITY; }
+    for (int64_t p = begin; p < end; p++)
+        for (int d = 0; d < 3; d++) {
+            double v = h->c[3 * idx[p] + d];
+            if (v < k->lo[d]) k->lo[d] = v;
+            if (v > k->hi[d]) k->hi[d] = v;
+        }
+    if (end - begin <= h->nleaf)
+        return me;
+    /* longest axis, ties resolved x < y < z */
+    int axis = 0;
+    double ext = k->hi[0] - k->lo[0];
+    for (int d = 1; d < 3; d++)
+        if (k->hi[d] - k->lo[d] > ext) { ext = k->hi[d] - k->lo[d]; axis = d; }
+    double mid = 0.5 * (k->lo[axis] + k->hi[axis]);
+    /* stable partition: coordinate <= mid goes left */
+    int64_t nl = 0, nr = 0;
+    for (int64_t p = begin; p < end; p++)
+        if (h->c[3 * idx[p] + axis] <= mid) nl++;
+    nr = (end - begin) - nl;
+    int64_t split;
+    if (nl == 0 || nr == 0) {
+        /* READING: degenerate midpoint split -> median by stable (coordinate, index) order */
+        g_sort_c = h->c; g_sort_axis = axis;
+        qsort(idx + begin, (size_t)(end - begin), sizeof(int64_t), cmp_coord_index);
+        split = begin + (end - begin) / 2;
+    } else {
+        int64_t a = begin, b = begin + nl;
+        for (int64_t p = begin; p < end; p++) {
+            if (h->c[3 * idx[p] + axis] <= mid) tmp[a++] = idx[p];
+            else tmp[b++] = idx[p];
+        }
+        memcpy(idx + begin, tmp + begin, sizeof(int64_t) * (end - begin));
+        split = begin + nl;
+    }
+    int64_t l = build_cluster(h, idx, tmp, begin, split);
+    int64_t r = build_cluster(h, idx, tmp, split, end);
+    h->cl[me].child[0] = l;
+    h->cl[me].child[1] = r;
+    return me;
+}
+
+static double box_diam(const or_cluster *k)
+{
+    double s = 0.0;
+    for (int d = 0; d < 3; d++) { double e = k->hi[d] - k->lo[d]; s += e * e; }
+    return sqrt(s);
+}
+
+static double box_dist(const or_cluster *a, const or_cluster *b)
+{
+    double s = 0.0;
+    for (int d = 0; d < 3; d++) {
+        double g = 0.0;
+        if (a->hi[d] < b->lo[d]) g = b->lo[d] - a->hi[d];
+        else if (b->hi[d] < a->lo[d]) g = a->lo[d] - b->hi[d];
+        s += g * g;
+    }
+    return sqrt(s);
+}
+
+/* READING: admissible iff the boxes are apart and min(diam) <= eta * dist. */
+int or_admissible_boxes(const double *alo, const double *ahi, const double *blo,
+                        const double *bhi, double eta)
+{
+    or_cluster a, b;
+    for (int d = 0; d < 3; d++) { a.lo[d] = alo[d]; a.hi[d] = ahi[d]; b.lo[d] = blo[d]; b.hi[d] = bhi[d]; }
+    double dist = box_dist(&a, &b);
+    double da = box_diam(&a), db = box_diam(&b);
+    return dist > 0.0 && (da < db ? da : db) <= eta * dist;
+}
+
+static void push_block(or_hmat *h, int64_t t, int64_t s, int kind)
+{
+    if (h->nb == h->capb) {
+        h->capb = h->capb ? 2 * h->capb : 4096;
+        h->bi_s = (int64_t *)realloc(h->bi_s, sizeof(int64_t) * h->capb);
+        h->bi_e = (int64_t *)realloc(h->bi_e, sizeof(int64_t) * h->capb);
+        h->bj_s = (int64_t *)realloc(h->bj_s, sizeof(int64_t) * h->capb);
+        h->bj_e = (int64_t *)realloc(h->bj_e, sizeof(int64_t) * h->capb);
+        h->bkind = (int *)realloc(h->bkind, sizeof(int) * h->capb);
+        h->brank = (int64_t *)realloc(h->brank, sizeof(int64_t) * h->capb);
+        h->bdata = (double **)realloc(h->bdata, sizeof(double *) * h->capb);
+        h->bforced = (int *)realloc(h->bforced, sizeof(int) * h->capb);
+    }
+    int64_t m = h->nb++;
+    h->bi_s[m] = h->cl[t].begin; h->bi_e[m] = h->cl[t].end;
+    h->bj_s[m] = h->cl[s].begin; h->bj_e[m] = h->cl[s].end;
+    h->bkind[m] = kind; h->brank[m] = 0; h->bdata[m] = NULL; h->bforced[m] = 0;
+}
+
+/* Block recursion.  READING: admissible -> low rank; both leaves -> dense;
+ * otherwise split every non-leaf side (children in order). */
+static void build_blocks(or_hmat *h, int64_t t, int64_t s)
+{
+    const or_cluster *a = &h->cl[t], *b = &h->cl[s];
+    double dist = box_dist(a, b);
+    double da = box_diam(a), db = box_diam(b);
+    if (dist > 0.0 && (da < db ? da : db) <= h->eta * dist) {
+        push_block(h, t, s, 1);
+        return;
+    }
+    int tl = a->child[0] < 0, sl = b->child[0] < 0;
+    if (tl && sl) {
+        push_block(h, t, s, 0);
+        return;
+    }
+    int64_t tc[2] = {t, -1}, sc[2] = {s, -1};
+    int nt = 1, ns = 1;
+    if (!tl) { tc[0] = a->child[0]; tc[1] = a->child[1]; nt = 2; }
+    if (!sl) { sc[0] = b->child[0]; sc[1] = b->child[1]; ns = 2; }
+    for (int i = 0; i < nt; i++)
+        for (int j = 0; j < ns; j++)
+            build_blocks(h, tc[i], sc[j]);
+}
+
+/* entry (p, q) of the matrix in PERMUTED order */
+static double entry_perm(const or_hmat *h, int64_t p, int64_t q)
+{
+    return or_kernel_entry(h->c, h->area, h->perm[p], h->perm[q]);
+}
+
+/* ------------------------------------------------------------------------- */
+/* ACA with partial pivoting (the low-rank method cited in Section 1)          */
+/* ------------------------------------------------------------------------- */
+/* Generic ACA on an m x n block given by an entry callback.  The factors are
+ * returned column by column: *Uc holds r columns of length m, *Vc r columns of
+ * length n (both malloc'ed, caller frees) with block ~ sum_l u_l v_l^T;
+ * returns r <= rmax.
+ * READING (the paper cites ACA without its details): first pivot row 0; the
+ * column pivot is the largest unused |row residual| (lowest index on ties); a
+ * zero residual row is marked used and the lowest unused row is tried next;
+ * the next row pivot is the largest unused |u_k| (lowest index on ties); stop
+ * when ||u_k|| ||v_k|| <= eps ||S_k||_F with the running Frobenius norm of the
+ * approximant S_k = sum_l u_l v_l^T, or when r = rmax. */
+typedef double (*or_entry_fn)(const void *ctx, int64_t i, int64_t j);
+
+int64_t or_aca_generic(int64_t m, int64_t n, or_entry_fn f, const void *ctx, double eps,
+                       int64_t rmax, double **Uc, double **Vc)
+{
+    char *used_row = (char *)calloc((size_t)m, 1);
+    char *used_col = (char *)calloc((size_t)n, 1);
+    double *R = (double *)malloc(sizeof(double) * n);
+    int64_t cap = 8;
+    double *U = (double *)malloc(sizeof(double) * m * cap);
+    double *V = (double *)malloc(sizeof(double) * n * cap);
+    int64_t r = 0;
+    int64_t istar = 0;
+    double normS2 = 0.0;
+    while (r < rmax) {
+        /* row residual R_j = A(i*, j) - sum_l u_l(i*) v_l(j) */
+        for (int64_t j = 0; j < n; j++) {
+            double s = f(ctx, istar, j);
+            for (int64_t l = 0; l < r; l++)
+                s -= U[l * m + istar] * V[l * n + j];
+            R[j] = s;
+        }
+        used_row[istar] = 1;
+        int64_t jstar = -1;
+        double best = -1.0;
+        for (int64_t j = 0; j < n; j++)
+            if (!used_col[j] && fabs(R[j]) > best) { best = fabs(R[j]); jstar = j; }
+        if (jstar < 0)
+            break;
+        if (R[jstar] == 0.0) {
+            int64_t next = -1;
+            for (int64_t i = 0; i < m; i++)
+                if (!used_row[i]) { next = i; break; }
+            if (next < 0)
+                break;
+            istar = next;
+            continue;
+        }
+        if (r == cap) {
+            cap *= 2;
+            U = (double *)realloc(U, sizeof(double) * m * cap);
+            V = (double *)realloc(V, sizeof(double) * n * cap);
+        }
+        double piv = R[jstar];
+        used_col[jstar] = 1;
+        double *u = U + r * m, *v = V + r * n;
+        /* v_r = R / R_j*, u_r = column residual at j* */
+        for (int64_t j = 0; j < n; j++)
+            v[j] = R[j] / piv;
+        for (int64_t i = 0; i < m; i++) {
+            double s = f(ctx, i, jstar);
+            for (int64_t l = 0; l < r; l++)
+                s -= U[l * m + i] * V[l * n + jstar];
+            u[i] = s;
+        }
+        /* ||S_r||^2 = ||S_{r-1}||^2 + ||u||^2 ||v||^2 + 2 sum_l (u_l.u)(v_l.v) */
+        double uu = 0.0, vv = 0.0;
+        for (int64_t i = 0; i < m; i++) uu += u[i] * u[i];
+        for (int64_t j = 0; j < n; j++) vv += v[j] * v[j];
+        double cross = 0.0;
+        for (int64_t l = 0; l < r; l++) {
+            double ul = 0.0, vl = 0.0;
+            for (int64_t i = 0; i < m; i++) ul += U[l * m + i] * u[i];
+            for (int64_t j = 0; j < n; j++) vl += V[l * n + j] * v[j];
+            cross += ul * vl;
+        }
+        normS2 += uu * vv + 2.0 * cross;
+        r++;
+        if (sqrt(uu) * sqrt(vv) <= eps * sqrt(normS2))
+            break;
+        int64_t inext = -1;
+        best = -1.0;
+        for (int64_t i = 0; i < m; i++)
+            if (!used_row[i] && fabs(u[i]) > best) { best = fabs(u[i]); inext = i; }
+        if (inext < 0)
+            break;
+        istar = inext;
+    }
+    free(used_row); free(used_col); free(R);
+    *Uc = U; *Vc = V;
+    return r;
+}
+
+typedef struct { const or_hmat *h; int64_t i0, j0; } or_block_ctx;
+static double block_entry(const void *ctx, int64_t i, int64_t j)
+{
+    const or_block_ctx *b = (const or_block_ctx *)ctx;
+    return entry_perm(b->h, b->i0 + i, b->j0 + j);
+}
+
+/* dense block of an explicit array (used by the ACA pins) */
+typedef struct { const double *A; int64_t ld; } or_array_ctx;
+static double array_entry(const void *ctx, int64_t i, int64_t j)
+{
+    const or_array_ctx *a = (const or_array_ctx *)ctx;
+    return a->A[i * a->ld + j];
+}
+
+/* ACA of an explicit m x n row-major array.  U_out (rmax x m) and V_out (rmax x n)
+ * receive the first r columns u_l, v_l, one after another; returns r. */
+int64_t or_aca_array(int64_t m, int64_t n, const double *A, double eps, int64_t rmax,
+                     double *U_out, double *V_out)
+{
+    or_array_ctx ctx = {A, n};
+    double *U, *V;
+    int64_t r = or_aca_generic(m, n, array_entry, &ctx, eps, rmax, &U, &V);
+    memcpy(U_out, U, sizeof(double) * r * m);
+    memcpy(V_out, V, sizeof(double) * r * n);
+    free(U); free(V);
+    return r;
+}
+
+/* Fill one block: dense entries, or ACA factors (paper's V_m = [u_l], W_m = [v_l]^T). */
+static void fill_block(or_hmat *h, int64_t b)
+{
+    int64_t m = h->bi_e[b] - h->bi_s[b], n = h->bj_e[b] - h->bj_s[b];
+    if (h->bkind[b] == 1) {
+        int64_t rmax = m < n ? m : n;
+        double *U, *V;
+        or_block_ctx ctx = {h, h->bi_s[b], h->bj_s[b]};
+        int64_t r = or_aca_generic(m, n, block_entry, &ctx, h->eps, rmax, &U, &V);
+        if (r * (m + n) >= m * n) {
+            /* READING: a low-rank form that is not smaller than the block is stored dense */
+            h->bkind[b] = 0;
+            h->bforced[b] = 1;
+        } else {
+            double *d = (double *)malloc(sizeof(double) * (r * (m + n) > 0 ? r * (m + n) : 1));
+            /* V_m: #I x r row-major */
+            for (int64_t i = 0; i < m; i++)
+                for (int64_t l = 0; l < r; l++)
+                    d[i * r + l] = U[l * m + i];
+            /* W_m: r x #J row-major, row l is v_l */
+            memcpy(d + m * r, V, sizeof(double) * r * n);
+            h->brank[b] = r;
+            h->bdata[b] = d;
+        }
+        free(U); free(V);
+    }
+    if (h->bkind[b] == 0) {
+        double *d = (double *)malloc(sizeof(double) * m * n);
+        for (int64_t i = 0; i < m; i++)
+            for (int64_t j = 0; j < n; j++)
+                d[i * n + j] = entry_perm(h, h->bi_s[b] + i, h->bj_s[b] + j);
+        h->brank[b] = 0;
+        h->bdata[b] = d;
+    }
+}
+
+/* Build the FP64 H-matrix of the collocation kernel on N panels. */
+or_hmat *or_build(int64_t n, const double *c, const double *area, int64_t nleaf,
+                  double eta, double eps)
+{
+    or_hmat *h = (or_hmat *)calloc(1, sizeof(or_hmat));
+    h->n = n; h->nleaf = nleaf; h->eta = eta; h->eps = eps;
+    h->c = c; h->area = area;
+    h->perm = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    int64_t *tmp = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; i++) h->perm[i] = i;
+    if (n > 0) {
+        build_cluster(h, h->perm, tmp, 0, n);
+        build_blocks(h, 0, 0);
+    }
+    free(tmp);
+    /* blocks are independent: fill them in parallel (results do not depend on
+       the thread count) */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t b = 0; b < h->nb; b++)
+        fill_block(h, b);
+    h->c = NULL; h->area = NULL;
+    return h;
+}
+
+void or_free(or_hmat *h)
+{
+    if (!h) return;
+    for (int64_t b = 0; b < h->nb; b++) free(h->bdata[b]);
+    free(h->bi_s); free(h->bi_e); free(h->bj_s); free(h->bj_e);
+    free(h->bkind); free(h->brank); free(h->bdata); free(h->bforced);
+    free(h->perm); free(h->cl);
+    free(h);
+}
+
+/* ---- accessors (for the tests' serialisation and structural pins) ---- */
+int64_t or_n(const or_hmat *h) { return h->n; }
+int64_t or_nblocks(const or_hmat *h) { return h->nb; }
+int64_t or_nclusters(const or_hmat *h) { return h->ncl; }
+void or_get_perm(const or_hmat *h, int64_t *perm) { memcpy(perm, h->perm, sizeof(int64_t) * h->n); }
+/* per block: i_s, i_e, j_s, j_e, kind, rank, forced-dense flag */
+void or_get_blocks(const or_hmat *h, int64_t *out7)
+{
+    for (int64_t b = 0; b < h->nb; b++) {
+        out7[7 * b + 0] = h->bi_s[b]; out7[7 * b + 1] = h->bi_e[b];
+        out7[7 * b + 2] = h->bj_s[b]; out7[7 * b + 3] = h->bj_e[b];
+        out7[7 * b + 4] = h->bkind[b]; out7[7 * b + 5] = h->brank[b];
+        out7[7 * b + 6] = h->bforced[b];
+    }
+}
+/* per cluster: begin, end, child0, child1 and the box lo[3], hi[3] */
+void or_get_clusters(const or_hmat *h, int64_t *out4, double *box6)
+{
+    for (int64_t k = 0; k < h->ncl; k++) {
+        out4[4 * k + 0] = h->cl[k].begin; out4[4 * k + 1] = h->cl[k].end;
+        out4[4 * k + 2] = h->cl[k].child[0]; out4[4 * k + 3] = h->cl[k].child[1];
+        for (int d = 0; d < 3; d++) { box6[6 * k + d] = h->cl[k].lo[d]; box6[6 * k + 3 + d] = h->cl[k].hi[d]; }
+    }
+}
+/* number of doubles stored for block b (dense m*n, LR r*(m+n)) */
+int64_t or_block_size(const or_hmat *h, int64_t b)
+{
+    int64_t m = h->bi_e[b] - h->bi_s[b], n = h->bj_e[b] - h->bj_s[b];
+    return h->bkind[b] ? h->brank[b] * (m + n) : m * n;
+}
+/* copy block b's data: dense A|^m row-major, or V_m (#I x r) then W_m (r x #J) */
+void or_get_block_data(const or_hmat *h, int64_t b, double *out)
+{
+    memcpy(out, h->bdata[b], sizeof(double) * or_block_size(h, b));
+}
+
+/* ------------------------------------------------------------------------- */
+/* precision helpers                                                         */
+/* ------------------------------------------------------------------------- */
+/* round to the nearest BF16 value (round half to even) from the FP64 value.
+ * A BF16 has the FP32 exponent range and 8 significant bits; scaled values
+ * used here stay far inside the normal range. */
+static double round_bf16(double v)
+{
+    if (v == 0.0 || !isfinite(v)) return v;
+    int e;
+    double m = frexp(v, &e);          /* v = m 2^e, 0.5 <= |m| < 1 */
+    double s = ldexp(m, 8);           /* 8 significant bits before the point */
+    double r = nearbyint(s);          /* default rounding mode: half to even */
+    return ldexp(r, e - 8);
+}
+
+/* the largest power of two not above max|block entries| (1 for an all-zero block) */
+static double pow2_floor_of_max(const double *a, int64_t cnt)
+{
+    double mx = 0.0;
+    for (int64_t k = 0; k < cnt; k++) if (fabs(a[k]) > mx) mx = fabs(a[k]);
+    if (mx == 0.0) return 1.0;
+    int e;
+    frexp(mx, &e);                    /* mx = f 2^e with 0.5 <= f < 1 */
+    return ldexp(1.0, e - 1);
+}
+
+/* READING of the BF16 storage form: each array (a dense block, or a low-rank
+ * factor) is divided by a power of two s (the largest not above its max-abs),
+ * rounded to BF16, and multiplied back by s.  Scaling by a power of two is
+ * exact, so the stored value is s * bf16(a / s). */
+static void round_array_bf16_pow2(const double *a, int64_t cnt, double *out)
+{
+    double s = pow2_floor_of_max(a, cnt);
+    for (int64_t k = 0; k < cnt; k++)
+        out[k] = round_bf16(a[k] / s) * s;
+}
+
+/* Exported for the tests: the BF16 storage rounding of one array. */
+void or_round_bf16_pow2(const double *a, int64_t cnt, double *out)
+{
+    round_array_bf16_pow2(a, cnt, out);
+}
+
+/* ------------------------------------------------------------------------- */
+/* H-matrix vector product, eq. (5)-(10) and (21)-(25), Table 1               */
+/* ------------------------------------------------------------------------- */
+/* Low-rank part of Method 2 (eq. 11-16): from V_m (#I x r) and W_m (r x #J)
+ * form D_V, D_W (max-abs of each column of V_m / row of W_m), V' = V D_V^-1,
+ * W' = D_W^-1 W and d = diag(D_V D_W), all in FP64. */
+static void method2_factors(const double *Vm, const double *Wm, int64_t m, int64_t n, int64_t r,
+                            double *Vp, double *Wp, double *d)
+{
+    for (int64_t l = 0; l < r; l++) {
+        double dv = 0.0, dw = 0.0;
+        for (int64_t i = 0; i < m; i++) if (fabs(Vm[i * r + l]) > dv) dv = fabs(Vm[i * r + l]);
+        for (int64_t j = 0; j < n; j++) if (fabs(Wm[l * n + j]) > dw) dw = fabs(Wm[l * n + j]);
+        for (int64_t i = 0; i < m; i++) Vp[i * r + l] = Vm[i * r + l] / dv;
+        for (int64_t j = 0; j < n; j++) Wp[l * n + j] = Wm[l * n + j] / dw;
+        d[l] = dv * dw;
+    }
+}
+
+/* Exported so the tests can check eq. (16): max-abs of every column of V' and
+ * every row of W' is exactly 1. */
+void or_method2_factors(const or_hmat *h, int64_t b, double *Vp, double *Wp, double *d)
+{
+    int64_t m = h->bi_e[b] - h->bi_s[b], n = h->bj_e[b] - h->bj_s[b], r = h->brank[b];
+    method2_factors(h->bdata[b], h->bdata[b] + m * r, m, n, r, Vp, Wp, d);
+}
+
+/* One product y~ = A~ x in permuted order (xp in, yp out, both FP64 arrays of N).
+ * `variant` selects the precision assignment of Table 1; `c3` is Method 3's c. */
+static void hmatvec_perm(const or_hmat *h, int variant, int c3, const double *xp, double *yp)
+{
+    int64_t N = h->n;
+    float *x32 = (float *)malloc(sizeof(float) * (N > 0 ? N : 1));
+    /* Section 3.5: the FP32 source vector is a fresh copy of the FP64 one */
+    for (int64_t i = 0; i < N; i++) x32[i] = (float)xp[i];
+    for (int64_t i = 0; i < N; i++) yp[i] = 0.0;
+
+    for (int64_t b = 0; b < h->nb; b++) {
+        int64_t is = h->bi_s[b], js = h->bj_s[b];
+        int64_t m = h->bi_e[b] - is, n = h->bj_e[b] - js, r = h->brank[b];
+        const double *xm = xp + js;           /* x_m of eq. (6) */
+        const float *xm32 = x32 + js;
+        double *yhat = (double *)calloc((size_t)(m > 0 ? m : 1), sizeof(double));  /* y^_m, FP64 in every row of Table 1 */
+
+        if (h->bkind[b] == 0) {
+            const double *A = h->bdata[b];
+            double *Ab = NULL;
+            if (variant == OR_DATA_BF16) {
+                Ab = (double *)malloc(sizeof(double) * m * n);
+                round_array_bf16_pow2(A, m * n, Ab);
+            }
+            for (int64_t i = 0; i < m; i++) {
+                for (int64_t j = 0; j < n; j++) {
+                    double a = A[i * n + j];
+                    switch (variant) {
+                    case OR_M1_SINGLE:
+                    case OR_M2_SINGLE: {
+                        float p = (float)a * xm32[j];                          /* FP32 x FP32 -> FP32 */
+                        yhat[i] = yhat[i] + (double)p;                         /* promoted into FP64 y^ */
+                        break;
+                    }
+                    case OR_M1_MIXED:
+                    case OR_M2_MIXED:
+                    case OR_DATA_FP32:
+                        yhat[i] = yhat[i] + (double)(float)a * xm[j];          /* FP32 A promoted, FP64 x */
+                        break;
+                    case OR_DATA_BF16:
+                        yhat[i] = yhat[i] + Ab[i * n + j] * xm[j];
+                        break;
+                    default:                                                   /* M1/M2-Double, M3 */
+                        yhat[i] = yhat[i] + a * xm[j];                         /* eq. (21), FP64 */
+                    }
+                }
+            }
+            free(Ab);
+        } else {
+            const double *Vm = h->bdata[b];          /* #I x r */
+            const double *Wm = h->bdata[b] + m * r;  /* r x #J */
+            if (variant == OR_M1_DOUBLE || variant == OR_DATA_FP32 || variant == OR_DATA_BF16) {
+                const double *V = Vm, *W = Wm;
+                double *Vr = NULL, *Wr = NULL;
+                if (variant == OR_DATA_FP32) {
+                    Vr = (double *)malloc(sizeof(double) * m * r);
+                    Wr = (double *)malloc(sizeof(double) * r * n);
+                    for (int64_t k = 0; k < m * r; k++) Vr[k] = (double)(float)Vm[k];
+                    for (int64_t k = 0; k < r * n; k++) Wr[k] = (double)(float)Wm[k];
+                    V = Vr; W = Wr;
+                } else if (variant == OR_DATA_BF16) {
+                    Vr = (double *)malloc(sizeof(double) * m * r);
+                    Wr = (double *)malloc(sizeof(double) * r * n);
+                    round_array_bf16_pow2(Vm, m * r, Vr);
+                    round_array_bf16_pow2(Wm, r * n, Wr);
+                    V = Vr; W = Wr;
+                }
+                double *z = (double *)calloc((size_t)(r > 0 ? r : 1), sizeof(double));
+                for (int64_t l = 0; l < r; l++)
+                    for (int64_t j = 0; j < n; j++)
+                        z[l] = z[l] + W[l * n + j] * xm[j];                   /* eq. (9)/(22) */
+                for (int64_t i = 0; i < m; i++)
+                    for (int64_t l = 0; l < r; l++)
+                        yhat[i] = yhat[i] + V[i * r + l] * z[l];              /* eq. (10)/(24) */
+                free(z); free(Vr); free(Wr);
+            } else if (variant == OR_M1_SINGLE || variant == OR_M1_MIXED) {
+                float *z32 = (float *)calloc((size_t)(r > 0 ? r : 1), sizeof(float));
+                for (int64_t l = 0; l < r; l++)
+                    for (int64_t j = 0; j < n; j++) {
+                        float w = (float)Wm[l * n + j];
+                        if (variant == OR_M1_SINGLE)
+                            z32[l] = z32[l] + w * xm32[j];                    /* all FP32 */
+                        else
+                            z32[l] = (float)((double)z32[l] + (double)w * xm[j]); /* FP64 op, FP32 z */
+                    }
+                for (int64_t i = 0; i < m; i++)
+                    for (int64_t l = 0; l < r; l++) {
+                        float p = (float)Vm[i * r + l] * z32[l];               /* FP32 x FP32 */
+                        yhat[i] = yhat[i] + (double)p;
+                    }
+                free(z32);
+            } else {
+                /* Methods 2 and 3 on the extended structure V' D W' (eq. 11) */
+                double *Vp = (double *)malloc(sizeof(double) * (m * r > 0 ? m * r : 1));
+                double *Wp = (double *)malloc(sizeof(double) * (r * n > 0 ? r * n : 1));
+                double *d = (double *)malloc(sizeof(double) * (r > 0 ? r : 1));
+                method2_factors(Vm, Wm, m, n, r, Vp, Wp, d);
+                /* Method 3: rank l is FP64 iff d_l >= d_max 10^-c (eq. 17-20);
+                   Method 2-Double is every rank FP64, 2-Single/Mixed every rank FP32 */
+                char *is64 = (char *)malloc((size_t)(r > 0 ? r : 1));
+                double dmax = 0.0;
+                for (int64_t l = 0; l < r; l++) if (d[l] > dmax) dmax = d[l];
+                for (int64_t l = 0; l < r; l++) {
+                    if (variant == OR_M2_DOUBLE) is64[l] = 1;
+                    else if (variant == OR_M3) is64[l] = (d[l] >= dmax * pow(10.0, -(double)c3));
+                    else is64[l] = 0;
+                }
+                double *yhat64 = (double *)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
+                double *yhat32 = (double *)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
+                for (int64_t l = 0; l < r; l++) {
+                    double z = 0.0;                                             /* z_m FP64 (Table 1) */
+                    for (int64_t j = 0; j < n; j++) {
+                        double w = Wp[l * n + j];
+                        if (is64[l])
+                            z = z + w * xm[j];                                  /* eq. (22), FP64 */
+                        else if (variant == OR_M2_SINGLE)
+                            z = z + (double)((float)w * xm32[j]);               /* FP32 product -> FP64 z */
+                        else
+                            z = z + (double)(float)w * xm[j];                   /* FP32 W' promoted */
+                    }
+                    z = z * d[l];                                               /* eq. (23) */
+                    for (int64_t i = 0; i < m; i++) {
+                        double v = Vp[i * r + l];
+                        if (is64[l]) yhat64[i] = yhat64[i] + v * z;             /* eq. (24) */
+                        else yhat32[i] = yhat32[i] + (double)(float)v * z;     /* FP32 V' promoted */
+                    }
+                }
+                /* Section 3.4: the Double and Mixed parts of Method 3 are added */
+                for (int64_t i = 0; i < m; i++) yhat[i] = yhat64[i] + yhat32[i];
+                free(yhat64); free(yhat32); free(is64); free(Vp); free(Wp); free(d);
+            }
+        }
+        for (int64_t i = 0; i < m; i++)
+            yp[is + i] = yp[is + i] + yhat[i];                                 /* eq. (25) */
+        free(yhat);
+    }
+    free(x32);
+}
+
+/* y = A~ x with x, y in ORIGINAL order. */
+void or_matvec(const or_hmat *h, int variant, int c3, const double *x, double *y)
+{
+    int64_t N = h->n;
+    double *xp = (double *)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    double *yp = (double *)malloc(sizeof(double) * (N > 0 ? N : 1));
+    for (int64_t p = 0; p < N; p++) xp[p] = x[h->perm[p]];
+    hmatvec_perm(h, variant, c3, xp, yp);
+    for (int64_t p = 0; p < N; p++) y[h->perm[p]] = yp[p];
+    free(xp); free(yp);
+}
+
+/* Rows `rows[k]` (original order) of A~ x in FP64 (Method 1-Double) -- used to
+ * check sampled outputs of very large products one by one. */
+void or_matvec_rows(const or_hmat *h, const double *x, int64_t nrows, const int64_t *rows, double *out)
+{
+    int64_t N = h->n;
+    int64_t *inv = (int64_t *)malloc(sizeof(int64_t) * (N > 0 ? N : 1));
+    for (int64_t p = 0; p < N; p++) inv[h->perm[p]] = p;
+    for (int64_t k = 0; k < nrows; k++) out[k] = 0.0;
+    for (int64_t b = 0; b < h->nb; b++) {
+        int64_t is = h->bi_s[b], ie = h->bi_e[b], js = h->bj_s[b];
+        int64_t m = ie - is, n = h->bj_e[b] - js, r = h->brank[b];
+        double *z = NULL;
+        for (int64_t k = 0; k < nrows; k++) {
+            int64_t p = inv[rows[k]];
+            if (p < is || p >= ie) continue;
+            int64_t i = p - is;
+            double s = 0.0;
+            if (h->bkind[b] == 0) {
+                for (int64_t j = 0; j < n; j++) s = s + h->bdata[b][i * n + j] * x[h->perm[js + j]];
+            } else {
+                if (!z) {
+                    z = (double *)calloc((size_t)(r > 0 ? r : 1), sizeof(double));
+                    const double *W = h->bdata[b] + m * r;
+                    for (int64_t l = 0; l < r; l++)
+                        for (int64_t j = 0; j < n; j++) z[l] = z[l] + W[l * n + j] * x[h->perm[js + j]];
+                }
+                for (int64_t l = 0; l < r; l++) s = s + h->bdata[b][i * r + l] * z[l];
+            }
+            out[k] = out[k] + s;
+        }
+        free(z);
+    }
+    free(inv);
+}
+
+/* Dense N x N assembly of A~ (original order) for tiny N. */
+void or_hmat_to_dense(const or_hmat *h, double *A)
+{
+    int64_t N = h->n;
+    for (int64_t k = 0; k < N * N; k++) A[k] = 0.0;
+    for (int64_t b = 0; b < h->nb; b++) {
+        int64_t is = h->bi_s[b], js = h->bj_s[b];
+        int64_t m = h->bi_e[b] - is, n = h->bj_e[b] - js, r = h->brank[b];
+        for (int64_t i = 0; i < m; i++)
+            for (int64_t j = 0; j < n; j++) {
+                double v;
+                if (h->bkind[b] == 0) v = h->bdata[b][i * n + j];
+                else {
+                    v = 0.0;
+                    for (int64_t l = 0; l < r; l++)
+                        v = v + h->bdata[b][i * r + l] * h->bdata[b][m * r + l * n + j];
+                }
+                A[h->perm[is + i] * N + h->perm[js + j]] = v;
+            }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* BiCG-STAB, Algorithm 1, with the true-residual acceptance of Section 4.1.3  */
+/* ------------------------------------------------------------------------- */
+typedef void (*or_op_fn)(const void *ctx, const double *x, double *y);
+
+static double dot(int64_t n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; i++) s += a[i] * b[i];
+    return s;
+}
+
+/* status codes */
+enum { OR_OK = 0, OR_BREAKDOWN_RHO = 1, OR_BREAKDOWN_OMEGA = 2, OR_MAXIT = 3, OR_NONFINITE = 4 };
+
+/* info[0] iterations, info[1] true relative residual, info[2] status,
+ * info[3] restarts, info[4] matvecs with `op`, info[5] FP64 true-residual products.
+ * The iteration stops when ||r_i|| <= max(tol ||b||, inner_tol ||r_start||)
+ * where r_start is the true residual the current run started from; inner_tol = 0
+ * is the paper's criterion, inner_tol > 0 makes each run an inner solve of an
+ * iterative refinement.  After each run the true residual b - A64 x decides:
+ * accept, or (READING) restart Algorithm 1 from it. */
+int or_bicgstab_generic(int64_t n, or_op_fn op, const void *opctx, or_op_fn op64, const void *op64ctx,
+                        const double *b, double *x, double tol, double inner_tol, int64_t maxit,
+                        int64_t maxrestart, double *hist, int64_t histcap, double *info)
+{
+    double *r = (double *)malloc(sizeof(double) * n), *rt = (double *)malloc(sizeof(double) * n);
+    double *p = (double *)malloc(sizeof(double) * n), *v = (double *)malloc(sizeof(double) * n);
+    double *s = (double *)malloc(sizeof(double) * n), *t = (double *)malloc(sizeof(double) * n);
+    double *w = (double *)malloc(sizeof(double) * n);
+    int64_t it = 0, restarts = 0, nmv = 0, nmv64 = 0;
+    int status = OR_MAXIT;
+    double bnorm = sqrt(dot(n, b, b));
+    double relres = 0.0;
+    if (bnorm == 0.0) {
+        /* READING: b = 0 has the solution x = 0 and no relative residual */
+        for (int64_t i = 0; i < n; i++) x[i] = 0.0;
+        status = OR_OK;
+        goto done;
+    }
+    /* r_0 = b - A x_0 (an H-matvec, Algorithm 1) */
+    op(opctx, x, w); nmv++;
+    for (int64_t i = 0; i < n; i++) r[i] = b[i] - w[i];
+    for (;;) {
+        double rstart = sqrt(dot(n, r, r));
+        double stop = tol * bnorm;
+        if (inner_tol * rstart > stop) stop = inner_tol * rstart;
+        memcpy(rt, r, sizeof(double) * n);                /* r~ = r_0 */
+        double rho_prev = 0.0, alpha = 0.0, omega = 0.0;
+        int run_done = 0;
+        for (int64_t i = 1; !run_done; i++) {
+            if (it >= maxit) { status = OR_MAXIT; goto final; }
+            it++;
+            double rho = dot(n, rt, r);
+            if (!isfinite(rho)) { status = OR_NONFINITE; goto final; }
+            if (rho == 0.0) { status = OR_BREAKDOWN_RHO; goto final; }
+            if (i == 1) {
+                memcpy(p, r, sizeof(double) * n);
+            } else {
+                double beta = (rho / rho_prev) * (alpha / omega);
+                for (int64_t k = 0; k < n; k++) p[k] = r[k] + beta * (p[k] - omega * v[k]);
+            }
+            op(opctx, p, v); nmv++;                         /* v_i = A p_i */
+            alpha = rho / dot(n, rt, v);
+            for (int64_t k = 0; k < n; k++) s[k] = r[k] - alpha * v[k];
+            double snorm = sqrt(dot(n, s, s));
+            if (hist && it - 1 < histcap) hist[it - 1] = snorm / bnorm;
+            if (!isfinite(snorm)) { status = OR_NONFINITE; goto final; }
+            if (snorm <= stop) {
+                for (int64_t k = 0; k < n; k++) x[k] = x[k] + alpha * p[k];
+                run_done = 1;
+                break;
+            }
+            op(opctx, s, t); nmv++;                         /* t = A s */
+            double tt = dot(n, t, t);
+            omega = (tt == 0.0) ? 0.0 : dot(n, t, s) / tt;
+            for (int64_t k = 0; k < n; k++) x[k] = x[k] + alpha * p[k] + omega * s[k];
+            for (int64_t k = 0; k < n; k++) r[k] = s[k] - omega * t[k];
+            double rnorm = sqrt(dot(n, r, r));
+            if (hist && it - 1 < histcap) hist[it - 1] = rnorm / bnorm;
+            if (!isfinite(rnorm)) { status = OR_NONFINITE; goto final; }
+            if (rnorm <= stop) { run_done = 1; break; }
+            if (omega == 0.0) { status = OR_BREAKDOWN_OMEGA; goto final; }
+            rho_prev = rho;
+        }
+        /* true residual with the FP64 operator (Section 4.1.3) */
+        op64(op64ctx, x, w); nmv64++;
+        for (int64_t k = 0; k < n; k++) r[k] = b[k] - w[k];
+        relres = sqrt(dot(n, r, r)) / bnorm;
+        if (relres <= tol) { status = OR_OK; goto done; }
+        if (restarts >= maxrestart) { status = OR_MAXIT; goto done; }
+        restarts++;
+    }
+final:
+    op64(op64ctx, x, w); nmv64++;
+    for (int64_t k = 0; k < n; k++) r[k] = b[k] - w[k];
+    relres = sqrt(dot(n, r, r)) / bnorm;
+done:
+    info[0] = (double)it; info[1] = relres; info[2] = (double)status;
+    info[3] = (double)restarts; info[4] = (double)nmv; info[5] = (double)nmv64;
+    free(r); free(rt); free(p); free(v); free(s); free(t); free(w);
+    return status;
+}
+
+/* operator wrappers */
+typedef struct { const or_hmat *h; int variant, c3; } or_hop;
+static void hop_apply(const void *ctx, const double *x, double *y)
+{
+    const or_hop *o = (const or_hop *)ctx;
+    hmatvec_perm(o->h, o->variant, o->c3, x, y);
+}
+typedef struct { int64_t n; const double *A; } or_dop;
+static void dop_apply(const void *ctx, const double *x, double *y)
+{
+    const or_dop *o = (const or_dop *)ctx;
+    or_dense_matvec(o->n, o->A, x, y);
+}
+
+/* H-matrix solve A~ x = b (original order; x in: initial guess, out: solution).
+ * `variant` is the precision form of the iterated product; the acceptance test
+ * always uses the FP64 H-matrix (Method 1-Double). */
+int or_bicgstab(const or_hmat *h, int variant, int c3, const double *b, double *x, double tol,
+                double inner_tol, int64_t maxit, int64_t maxrestart, double *hist, int64_t histcap,
+                double *info)
+{
+    int64_t N = h->n;
+    double *bp = (double *)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    double *xp = (double *)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    for (int64_t q = 0; q < N; q++) { bp[q] = b[h->perm[q]]; xp[q] = x[h->perm[q]]; }
+    or_hop op = {h, variant, c3}, op64 = {h, OR_M1_DOUBLE, 0};
+    int st = or_bicgstab_generic(N, hop_apply, &op, hop_apply, &op64, bp, xp, tol, inner_tol, maxit,
+                                 maxrestart, hist, histcap, info);
+    for (int64_t q = 0; q < N; q++) x[h->perm[q]] = xp[q];
+    free(bp); free(xp);
+    return st;
+}
+
+/* Dense solve by the same Algorithm 1 (pinned against LAPACK-style solvers). */
+int or_bicgstab_dense(int64_t n, const double *A, const double *b, double *x, double tol, int64_t maxit,
+                      double *info)
+{
+    or_dop op = {n, A};
+    return or_bicgstab_generic(n, dop_apply, &op, dop_apply, &op, b, x, tol, 0.0, maxit, 0, NULL, 0, info);
+}

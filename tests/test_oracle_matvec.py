@@ -1,0 +1,155 @@
+"""Pins of the oracle's H-matrix vector product (eq. 5-10, 21-25) and of its
+precision variants (Table 1, eq. 11-20)."""
+import numpy as np
+import pytest
+
+import synth
+
+FP32_U = 2.0 ** -24
+
+
+@pytest.mark.parametrize("level", [2, 3, 4])
+def test_hmatvec_vs_dense_brute_force(hcache, oracle_mod, level):
+    mesh = synth.icosphere(level)
+    H = hcache(mesh)
+    A = oracle_mod.dense_matrix(mesh.centroid, mesh.area)
+    rng = np.random.default_rng(level)
+    for x in (np.ones(mesh.n), rng.standard_normal(mesh.n)):
+        y = A @ x
+        yh = H.matvec(x)
+        rel = np.linalg.norm(yh - y) / np.linalg.norm(y)
+        assert rel <= 2 * H.eps, rel      # within the ACA tolerance
+        assert rel > 1e-9                 # and the approximation is really used
+
+
+def test_all_dense_partition_is_the_dense_product(oracle_mod):
+    mesh = synth.icosphere(2)
+    H = oracle_mod.HMatrix(mesh.centroid, mesh.area, eta=0.0)
+    A = oracle_mod.dense_matrix(mesh.centroid, mesh.area)
+    x = np.random.default_rng(0).standard_normal(mesh.n)
+    y = A @ x
+    assert np.linalg.norm(H.matvec(x) - y) <= 1e-15 * np.linalg.norm(y) * 4
+
+
+def test_dense_matvec_helper_matches_numpy(oracle_mod):
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((37, 37)); x = rng.standard_normal(37)
+    assert np.allclose(oracle_mod.dense_matvec(A, x), A @ x, rtol=1e-14, atol=1e-13)
+
+
+def test_linearity_assembly_and_rows(hcache):
+    mesh = synth.icosphere(3)
+    H = hcache(mesh)
+    rng = np.random.default_rng(7)
+    x, z = rng.standard_normal(mesh.n), rng.standard_normal(mesh.n)
+    y = H.matvec(2.0 * x - 3.0 * z)
+    assert np.linalg.norm(y - (2.0 * H.matvec(x) - 3.0 * H.matvec(z))) <= 1e-13 * np.linalg.norm(y)
+    D = H.to_dense()
+    assert np.linalg.norm(D @ x - H.matvec(x)) <= 1e-13 * np.linalg.norm(D @ x)
+    rows = rng.integers(0, mesh.n, 25)
+    assert np.allclose(H.matvec_rows(x, rows), H.matvec(x)[rows], rtol=1e-13, atol=1e-15)
+
+
+def test_method2_scaling_eq16(hcache):
+    mesh = synth.icosphere(3)
+    H = hcache(mesh)
+    blk = H.blocks
+    lr = np.nonzero(blk[:, 4] == 1)[0]
+    for b in lr[:: max(1, len(lr) // 60)]:
+        Vm, Wm = H.block_data(b)
+        Vp, Wp, d = H.method2_factors(b)
+        assert np.array_equal(np.abs(Vp).max(axis=0), np.ones(Vm.shape[1]))   # eq. (16)
+        assert np.array_equal(np.abs(Wp).max(axis=1), np.ones(Wm.shape[0]))
+        assert np.allclose(Vp @ np.diag(d) @ Wp, Vm @ Wm, rtol=1e-14, atol=1e-18)
+        assert np.all(d > 0)
+
+
+def _table1():
+    import os
+    rows = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_precision.txt")
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        f = line.split()
+        rows[f[0]] = f[1:]
+    return rows
+
+
+@pytest.mark.parametrize("name", ["M1_DOUBLE", "M1_SINGLE", "M1_MIXED", "M2_DOUBLE", "M2_SINGLE", "M2_MIXED"])
+def test_variant_precisions_follow_table1(hcache, oracle_mod, name):
+    """The source-vector columns of Table 1 decide whether a perturbation below FP32
+    resolution is seen; the matrix columns decide the error size against FP64."""
+    cols = _table1()[name]
+    x_dense, x_lr, A_dense, W_lr = cols[2], cols[5], cols[1], cols[4]
+    assert x_dense == x_lr
+    mesh = synth.icosphere(3)
+    H = hcache(mesh)
+    v = oracle_mod.VARIANTS[name]
+    rng = np.random.default_rng(11)
+    x = rng.uniform(1.0, 2.0, mesh.n)
+    x32 = x.astype(np.float32).astype(np.float64)
+    # perturb within the FP32 rounding interval of every entry
+    xp = x32 + (x - x32) * 0.5 + x32 * 2.0 ** -30
+    assert np.array_equal(xp.astype(np.float32).astype(np.float64), x32)
+    y, yp = H.matvec(x, v), H.matvec(xp, v)
+    if x_dense == "FP32":
+        assert np.array_equal(y, yp)
+    else:
+        assert not np.array_equal(y, yp)
+    y64 = H.matvec(x, oracle_mod.M1_DOUBLE)
+    rel = np.linalg.norm(y - y64) / np.linalg.norm(y64)
+    if A_dense == "FP64" and W_lr == "FP64":
+        assert rel <= 1e-14
+    else:
+        assert 1e-10 <= rel <= 1e-6       # FP32 rounding is present and within the FP32 bound
+        assert rel <= 40 * FP32_U
+
+
+def test_method3_limits(hcache, oracle_mod):
+    mesh = synth.icosphere(3)
+    H = hcache(mesh)
+    x = np.random.default_rng(4).standard_normal(mesh.n)
+    y64 = H.matvec(x, oracle_mod.M1_DOUBLE)
+    # c large: every rank FP64 -> Method 2-Double
+    y3 = H.matvec(x, oracle_mod.M3, c=30)
+    assert np.array_equal(y3, H.matvec(x, oracle_mod.M2_DOUBLE))
+    assert np.linalg.norm(y3 - y64) <= 1e-14 * np.linalg.norm(y64)
+    # c = -1: every low-rank factor FP32 but dense blocks FP64 (Section 3.3)
+    e = {c: np.linalg.norm(H.matvec(x, oracle_mod.M3, c=c) - y64) / np.linalg.norm(y64) for c in (-1, 0, 1, 2, 4, 7)}
+    e_mixed = np.linalg.norm(H.matvec(x, oracle_mod.M2_MIXED) - y64) / np.linalg.norm(y64)
+    assert 1e-10 < e[-1] < e_mixed        # dense in FP64 removes part of the FP32 error
+    assert e[7] <= e[1] <= e[-1] * 1.01   # more ranks in FP64 as c grows
+
+
+def test_data_rounding_forms(hcache, oracle_mod):
+    mesh = synth.icosphere(3)
+    H = hcache(mesh)
+    x = np.random.default_rng(9).standard_normal(mesh.n)
+    y64 = H.matvec(x)
+    r32 = np.linalg.norm(H.matvec(x, oracle_mod.DATA_FP32) - y64) / np.linalg.norm(y64)
+    rbf = np.linalg.norm(H.matvec(x, oracle_mod.DATA_BF16) - y64) / np.linalg.norm(y64)
+    assert 1e-10 < r32 < 1e-6
+    assert 1e-5 < rbf < 1e-2
+    assert rbf > 1000 * r32
+
+
+def test_bf16_pow2_rounding_matches_torch_bfloat16(oracle_mod):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    for scale in (1e-6, 1.0, 3e4):
+        a = (rng.standard_normal(4000) * scale).astype(np.float32).astype(np.float64)  # FP32-exact
+        got = oracle_mod.round_bf16_pow2(a)
+        mx = np.abs(a).max()
+        s = 2.0 ** (np.floor(np.log2(mx)))
+        ref = (torch.from_numpy(a / s).to(torch.float32).to(torch.bfloat16).to(torch.float64).numpy()) * s
+        assert np.array_equal(got, ref)
+
+
+def test_determinism(hcache, oracle_mod):
+    mesh = synth.icosphere(3)
+    H = hcache(mesh)
+    x = np.random.default_rng(1).standard_normal(mesh.n)
+    for v in range(9):
+        assert np.array_equal(H.matvec(x, v, 2), H.matvec(x, v, 2))
