@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 H-matrix BiCG-STAB solve (arXiv:1911.00093 hot path).
+
+Workload: unit-sphere icosphere level 6 (N = 81,920 flat panels, centroid
+collocation), kernel a_ij = area_j / (4 pi |c_i - c_j|), a_ii = sqrt(area_i/pi)/2,
+bisection cluster tree with leaf 32, eta = 2, ACA eps = 1e-4, right-hand side
+phi_i = 1 + 0.5 z_i, stop at a true relative residual of 1e-8 (FP64 H-matrix).
+
+One step = one whole solve (Algorithm 1 with its two H-matrix products per
+iteration, the FP64 vector work and the FP64 true-residual acceptance) in the
+headline mixed form; the FP64 solve and every other form are measured beside
+it.  `value` is solves per second over all ranks (independent replicas under
+torchrun).  Prints one JSON line on rank 0.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BiCG-STAB time to rel. residual 1e-8 & H-matvec HBM GB/s: mixed vs FP64"
+UNIT = "solves/s"
+FORM_OPTS = {"fp64": {}, "fp64_dfma": {}, "fp32": {"inner_tol": 1e-4}, "bf16": {"inner_tol": 1e-2}}
+CHECK_EVERY = 4  # iterations per graph replay between host reads of the stop flag
+STORE_BYTES = {"fp64": 8, "fp64_dfma": 8, "fp32": 4, "bf16": 2}
+PART_BYTES = {"fp64": 8, "fp64_dfma": 8, "fp32": 4, "bf16": 4}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 50 ms) of SM clock and throttle reasons; summary()
+    keeps the samples whose timestamps fall inside the marked timed window."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+        self.window = None
+
+    def __enter__(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(1.0)  # let the sampler start before the timed region
+        except Exception:
+            self.proc = None
+        return self
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        import datetime
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons, total = [], None, set(), 0
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            total += 1
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                clk, cmax = float(f[2]), float(f[3])
+            except ValueError:
+                continue
+            if self.window and not (self.window[0] - 0.05 <= ts <= self.window[1] + 0.05):
+                continue
+            sm.append(clk)
+            smax = cmax
+            for k, name in enumerate(names):
+                if f[6 + k].lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm), "samples_total": total}
+
+
+def _dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _workload(level):
+    import synth
+    mesh = synth.icosphere(level)
+    return mesh, synth.rhs_one_plus_half_z(mesh)
+
+
+def _config(mesh, args, extra=None):
+    c = {"workload": f"icosphere_L{args.level}_N{mesh.n}_leaf32_eta2_aca1e-4_phi=1+z/2_tol1e-8",
+         "n": mesh.n, "headline_form": args.form, "parallelism": f"replicas{max(1, args.gpus)}",
+         "l2": "inputs larger than L2 (H-matrix panels >> 129 MB; no flush)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def run_reference(args):
+    """The oracle (plain FP64 C, single thread) solving the same workload on the host."""
+    world, rank, _ = _dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+    oracle.build_oracle()
+    mesh, b = _workload(args.level)
+    variant, inner = oracle.M1_DOUBLE, 0.0  # the plain FP64 oracle
+    H = oracle.HMatrix(mesh.centroid, mesh.area)
+    # warm-up: a few products (a CPU program needs no more)
+    for _ in range(max(0, args.warmup)):
+        H.matvec(b, variant)
+    times, infos = [], []
+    budget = 150.0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        x, info = H.bicgstab(b, variant=variant, tol=1e-8, inner_tol=inner)
+        times.append(time.perf_counter() - t0)
+        infos.append(info)
+        if sum(times) > budget:
+            break
+    t = statistics.mean(times)
+    line = {"metric": METRIC, "value": 1.0 / t, "unit": UNIT, "n_gpus": args.gpus, "steps": len(times),
+            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": _config(mesh, args, {"oracle_variant": "fp64"}),
+            "cpu_baseline": {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{len(times)} whole oracle solves of the benchmark workload "
+                                       f"(iters {infos[-1]['iters']}, true relres {infos[-1]['relres']:.2e})"},
+            "e2e": {"value": 1.0 / t, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def cpu_baseline(mesh, b):
+    """The oracle as it stands on this host's cores: one whole FP64 solve of the same workload."""
+    import oracle
+    oracle.build_oracle()
+    H = oracle.HMatrix(mesh.centroid, mesh.area)
+    t0 = time.perf_counter()
+    x, info = H.bicgstab(b, variant=oracle.M1_DOUBLE, tol=1e-8)
+    t = time.perf_counter() - t0
+    return {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one whole FP64 oracle solve of the benchmark workload (iters {info['iters']}, "
+                      f"true relres {info['relres']:.2e}, {t:.1f} s single-threaded; the OpenMP build is untimed)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--level", type=int, default=6)
+    ap.add_argument("--form", default="bf16", choices=list(FORM_OPTS))
+    ap.add_argument("--forms", default="fp64,fp64_dfma,fp32,bf16", help="forms measured beside the headline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--matvec-iters", type=int, default=50)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world, rank, local = _dist_setup(args)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1911_00093_gb300 as P
+    P.load()
+
+    mesh, b_np = _workload(args.level)
+    t0 = time.perf_counter()
+    blob = P.hmat_build(mesh.centroid, mesh.area)
+    build_s = time.perf_counter() - t0
+    stats = P.hmat_blob_stats(blob)
+    forms = [f for f in args.forms.split(",") if f]
+    if args.form not in forms:
+        forms.append(args.form)
+    handles = {}
+    for f in forms:
+        handles[f] = P.hmat_upload(blob, f)
+    stream = torch.cuda.current_stream()
+    b = torch.from_numpy(b_np).cuda()
+    x = torch.zeros_like(b)
+
+    def solve(form):
+        x.zero_()
+        return P.hmat_bicgstab(handles[form], b, x, tol=1e-8, maxit=2000, stream=stream, check_every=CHECK_EVERY,
+                               **FORM_OPTS[form])
+
+    def timed(form, steps, warmup, clk=None):
+        for _ in range(warmup):
+            info = solve(form)
+            if info["status"] != 0:
+                raise RuntimeError(f"{form} solve failed: {info}")
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        w0 = time.time()
+        ev0.record(stream)
+        infos = [solve(form) for _ in range(steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if clk is not None:
+            clk.mark(w0, time.time())
+        ms = ev0.elapsed_time(ev1)
+        if dist:
+            tt = torch.tensor([ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms, infos
+
+    # ---- headline: the mixed-form solve, clocks sampled during the timed region ----
+    with ClockSampler(local) as clk:
+        ms, infos = timed(args.form, args.steps, max(3, args.warmup), clk)
+    clocks = clk.summary()
+    if any(i["status"] != 0 or i["relres_true"] > 1e-8 for i in infos):
+        raise RuntimeError(f"headline solve did not reach the tolerance: {infos[-1]}")
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+    launches = int(sum(i["launches"] for i in infos))
+
+    # ---- every form: solve time and product throughput ----
+    hbm_peak, peak_kind = _peaks()
+    table = {}
+    for f in forms:
+        fms, finf = timed(f, max(3, args.steps // 2), 2)
+        info = P.hmat_info(handles[f])
+        kt = P.hmat_time_matvec(handles[f], args.matvec_iters, False, stream)
+        s = STORE_BYTES[f]
+        p1_bytes = info["phase1_entries"] * s + info["partials"] * PART_BYTES[f]
+        p2_bytes = info["phase2_entries"] * s + 8 * info["n"]
+        table[f] = {"solve_ms": fms / max(3, args.steps // 2), "iters": finf[-1]["iters"],
+                    "restarts": finf[-1]["restarts"], "relres_true": finf[-1]["relres_true"],
+                    "matvec_ms": kt[4], "kernel_ms": {"prep": kt[0], "phase1": kt[1], "reduce": kt[2], "phase2": kt[3]},
+                    "matvec_gbs": (info["stored_entries"] * s) / (kt[4] * 1e-3) / 1e9,
+                    "phase1_gbs": p1_bytes / (kt[1] * 1e-3) / 1e9, "phase2_gbs": p2_bytes / (kt[3] * 1e-3) / 1e9,
+                    "panel_bytes": info["panel_bytes"]}
+    head = table[args.form]
+    dom = "phase2" if head["kernel_ms"]["phase2"] >= head["kernel_ms"]["phase1"] else "phase1"
+    achieved = head[dom + "_gbs"]
+    roofline = {"bound": "hbm", "kernel": f"k_{dom}<{args.form}>", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": None}
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    bh = torch.from_numpy(b_np.copy()).pin_memory()
+    xh = torch.zeros(mesh.n, dtype=torch.float64).pin_memory()
+    P.hmat_bicgstab(handles[args.form], bh, xh, tol=1e-8, maxit=2000, check_every=CHECK_EVERY, **FORM_OPTS[args.form])
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    e2e_steps = args.steps
+    for _ in range(e2e_steps):
+        xh.zero_()
+        P.hmat_bicgstab(handles[args.form], bh, xh, tol=1e-8, maxit=2000, check_every=CHECK_EVERY, **FORM_OPTS[args.form])
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * mesh.n,
+           "d2h_bytes_per_step": 8 * mesh.n}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(mesh, b_np)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"bf16": "bf16+f64", "fp32": "f32+f64", "fp64": "f64", "fp64_dfma": "f64"}[args.form],
+                "data": "synthetic",
+                "config": _config(mesh, args, {"blob_stats": stats, "host_build_s": round(build_s, 3)}),
+                "fp64_solve_ms": table.get("fp64", {}).get("solve_ms"),
+                "speedup_vs_fp64_solve": (table["fp64"]["solve_ms"] / ms_per_step) if "fp64" in table else None,
+                "forms": table, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches,
+                "solve_info": {k: infos[-1][k] for k in ("iters", "restarts", "matvecs", "matvecs_fp64", "relres_true")}}
+        print(json.dumps(line))
+    for h in handles.values():
+        P.hmat_destroy(h)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

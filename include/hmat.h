@@ -1,0 +1,249 @@
+/*
+ * hmat.h -- C ABI of a GB300 (sm_103a) library for the H-matrix vector product
+ * and the BiCG-STAB solve of a collocation BEM system, after Ooi, Iwashita,
+ * Fukaya, Ida, Yokota, "Effect of Mixed Precision Computing on H-Matrix Vector
+ * Multiplication in BEM Analysis" (arXiv:1911.00093).
+ *
+ * The operation (Section 2.1, eq. 5-10 and 21-25): y~ = A~ x, where A~ is a
+ * block partition M of I x J (eq. 1-2) whose blocks are either dense A|^m or
+ * low rank V_m W_m (eq. 3-4); a dense block adds A|^m x_m to y~ (eq. 21), a
+ * low-rank block adds V_m (W_m x_m) (eq. 9-10, 22-24); every block's result
+ * is scattered into y~ (eq. 7-8, 25).  The solver is BiCG-STAB (Algorithm 1),
+ * accepted only when the true residual with the FP64 H-matrix meets the
+ * tolerance (Section 4.1.3).
+ *
+ * Conventions for every function:
+ *   - the return value is an hmat_status; 0 is success; no C++ exception
+ *     crosses this interface;
+ *   - vectors are FP64, length N, in the ORIGINAL panel order (the order of the
+ *     builder's inputs); a block of nrhs vectors is column-major N x nrhs;
+ *   - vector arguments may be device pointers (cudaMalloc, torch tensors) or
+ *     host pointers (pageable or pinned); host data is staged through the
+ *     handle's own device buffers and the call returns after the result is
+ *     back in host memory;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); device work is enqueued on it;
+ *   - a handle is used by one host thread at a time.
+ */
+#ifndef HMAT_H
+#define HMAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hmat_status {
+    HMAT_OK = 0,
+    HMAT_ERR_ARG = 1,              /* null pointer, nrhs < 1, unknown precision, bad option    */
+    HMAT_ERR_BAD_LAYOUT = 2,       /* blob fails validation (magic, sizes, cover of eq. 1-2)   */
+    HMAT_ERR_NOMEM = 3,            /* host or device allocation failed                         */
+    HMAT_ERR_CUDA = 4,             /* a CUDA runtime call failed (hmat_last_cuda_error)        */
+    HMAT_ERR_BREAKDOWN_RHO = 5,    /* Algorithm 1: rho_{i-1} = r~^T r_{i-1} = 0 ("method fails") */
+    HMAT_ERR_BREAKDOWN_OMEGA = 6,  /* Algorithm 1: omega_i = 0 prevents continuation           */
+    HMAT_ERR_MAXIT = 7,            /* iteration or restart budget spent before the tolerance   */
+    HMAT_ERR_NONFINITE = 8,        /* NaN/Inf in a residual norm or an input vector            */
+    HMAT_ERR_RANGE = 9,            /* a panel value cannot be held by the precision form       */
+    HMAT_ERR_UNSUPPORTED = 10      /* valid request outside this build's limits (e.g. leaf>64) */
+} hmat_status;
+
+/*
+ * Precision forms of the uploaded H-matrix.  Every form keeps y~ in FP64.
+ *
+ *  HMAT_FP64       FP64 panels (8 bytes per entry, stored as the exact pair
+ *                  hi = fl32(a), lo = fl32(a - hi)); products and sums run in
+ *                  double-float arithmetic (about 2^-48 relative) on the FP32
+ *                  pipe.  Method 1-Double of Section 3.1 at FP64-class accuracy;
+ *                  relative product error <= 1e-13 against an FP64 evaluation.
+ *  HMAT_FP64_DFMA  IEEE FP64 panels and FP64 FMA arithmetic, literally Method
+ *                  1-Double; on GB300 bound by the FP64 pipe, not by HBM.
+ *  HMAT_FP32       FP32 panels, FP32 copy of the source vector (Section 3.5),
+ *                  FP32 sums over chunks of 8 products, compensated (double-
+ *                  float) sums across chunks, FP64 into y~; <= 1e-6 relative.
+ *  HMAT_BF16       BF16 panels, each dense block and each low-rank factor
+ *                  scaled by a power of two, FP32 source copy, FP32 chunk sums,
+ *                  compensated sums across chunks, FP64 into y~; <= 1e-2
+ *                  relative; meant to be wrapped in FP64 iterative refinement
+ *                  (hmat_solve_opts.inner_tol).
+ *
+ * Every form stores each array (dense block, V_m, W_m) divided by a power of two
+ * (2^floor(log2 max|array|)), which is exact and undone on the fly.
+ */
+typedef enum hmat_precision {
+    HMAT_FP64 = 0,
+    HMAT_FP64_DFMA = 1,
+    HMAT_FP32 = 2,
+    HMAT_BF16 = 3
+} hmat_precision;
+
+typedef struct hmat_t *hmat_handle;
+
+/* ------------------------------------------------------------------------- */
+/* Host builder: collocation BEM kernel -> serialized H-matrix ("blob")        */
+/* ------------------------------------------------------------------------- */
+/*
+ * hmat_build -- build the FP64 H-matrix of the single-layer collocation matrix
+ *   a_ij = area_j / (4 pi |c_i - c_j|)   (i != j),   a_ii = sqrt(area_i / pi) / 2
+ * on n flat panels, on the host (the paper builds it with the HACApK library,
+ * Section 4.1.3; this builder follows the same recipe):
+ *   cluster tree  longest-axis bisection of the collocation points at the
+ *                 bounding-box midpoint (points <= midpoint go left; an empty side
+ *                 falls back to a median split in (coordinate, index) order);
+ *                 clusters with <= leaf points are leaves;
+ *   partition     (tau, sigma) is low rank iff dist(tau, sigma) > 0 and
+ *                 min(diam tau, diam sigma) <= eta dist(tau, sigma) (boxes of the
+ *                 collocation points); two leaves that fail it are dense; otherwise
+ *                 every non-leaf side is split;
+ *   low rank      ACA with partial pivoting to relative accuracy aca_eps; a block
+ *                 whose factors are not smaller than the block is stored dense.
+ * centroids: host, n x 3 row-major FP64 collocation points; areas: host, n FP64.
+ * On success *blob receives a malloc'ed buffer of *blob_bytes bytes owned by the
+ * caller (free it with hmat_blob_free).  Errors: HMAT_ERR_ARG (null, n < 1,
+ * leaf < 1 or > 64, eta < 0, aca_eps <= 0, non-finite input), HMAT_ERR_NOMEM.
+ * Uses OpenMP threads on the host; the result does not depend on their number.
+ */
+int hmat_build(int64_t n, const double *centroids, const double *areas, int32_t leaf, double eta,
+               double aca_eps, void **blob, size_t *blob_bytes);
+
+void hmat_blob_free(void *blob);
+
+/*
+ * Serialized H-matrix, version 1 (all integers little-endian int64, all values
+ * FP64; sections start on 64-byte boundaries; offsets are bytes from the start):
+ *   header (256 bytes): magic "HMATBLB1", u32 version = 1, u32 header bytes = 256,
+ *     n, nclusters, nblocks, ndata, leaf, eta (f64), aca_eps (f64), off_perm,
+ *     off_clusters, off_blocks, off_data, total_bytes, dense_entries,
+ *     lr_entries, rank_sum, rank_max, zero padding;
+ *   perm[n]            perm[p] = original index of the p-th point of the cluster order;
+ *   clusters[nc][4]    begin, end (a range of the cluster order), child0, child1 (-1 for
+ *                      a leaf); cluster 0 is the root [0, n);
+ *   blocks[nb][8]      i_s, i_e, j_s, j_e (ranges of the cluster order), kind (0 dense,
+ *                      1 low rank), rank r, data offset (in values), 0;
+ *   data[ndata]        dense block: A|^m, #I x #J row-major; low-rank block: V_m (#I x r
+ *                      row-major) followed by W_m (r x #J row-major), eq. (3).
+ */
+typedef struct hmat_blob_stats {
+    int64_t n, nclusters, nblocks, nleaves;
+    int64_t dense_blocks, lr_blocks;
+    int64_t dense_entries;   /* sum over dense blocks of #I #J       */
+    int64_t lr_entries;      /* sum over low-rank blocks of r(#I+#J) */
+    int64_t rank_sum, rank_max;
+} hmat_blob_stats;
+
+/* Validate a blob (the same checks as hmat_upload) and report its sizes. */
+int hmat_blob_stats_get(const void *blob, size_t blob_bytes, hmat_blob_stats *out);
+
+/* ------------------------------------------------------------------------- */
+/* Device H-matrix                                                            */
+/* ------------------------------------------------------------------------- */
+/*
+ * hmat_upload -- validate `blob` (host memory, caller-owned, not retained),
+ * convert its panels to `precision` on the host (Section 4.1.3: the FP64
+ * H-matrix is generated first, then each submatrix is converted) and copy the
+ * packed result to the current CUDA device.  Forms other than HMAT_FP64 and
+ * HMAT_FP64_DFMA also keep an HMAT_FP64 copy for the true residual.  The handle
+ * owns every device buffer it allocates.  The call is synchronous.
+ * Errors: HMAT_ERR_ARG, HMAT_ERR_BAD_LAYOUT (bad magic/version/sizes, a non-
+ * permutation, blocks that do not cover I x J exactly once, rank > min(#I,#J),
+ * non-finite values), HMAT_ERR_UNSUPPORTED (a leaf with more than 64 points),
+ * HMAT_ERR_RANGE, HMAT_ERR_NOMEM, HMAT_ERR_CUDA.
+ */
+int hmat_upload(const void *blob, size_t blob_bytes, int32_t precision, hmat_handle *out);
+
+/* Free every device and host resource of the handle (NULL is accepted). */
+int hmat_destroy(hmat_handle h);
+
+/*
+ * hmat_matvec -- y = A~ x (overwrite) for nrhs vectors, column-major N x nrhs,
+ * original panel order, in the handle's precision form.  x and y must not
+ * overlap.  Asynchronous on `stream` for device pointers.
+ * Errors: HMAT_ERR_ARG, HMAT_ERR_CUDA.
+ */
+int hmat_matvec(hmat_handle h, const double *x, double *y, int32_t nrhs, void *stream);
+
+/* Same product with the handle's FP64 copy (the operator of the true residual). */
+int hmat_matvec_fp64(hmat_handle h, const double *x, double *y, int32_t nrhs, void *stream);
+
+typedef struct hmat_solve_opts {
+    double tol;            /* accept when ||b - A~64 x||_2 <= tol ||b||_2 (Section 4.1.3)      */
+    double inner_tol;      /* a run of Algorithm 1 stops at ||r_i|| <= max(tol ||b||,
+                              inner_tol ||r_start||); 0 = the paper's criterion; > 0 turns the
+                              restarts into FP64 iterative refinement of a low-precision solve */
+    int32_t maxit;         /* total Algorithm 1 iterations over all runs                        */
+    int32_t max_restarts;  /* runs after the first one                                          */
+    int32_t check_every;   /* iterations enqueued between host reads of the stop flag (>= 1)    */
+    int32_t use_graph;     /* 1: replay the enqueued iterations as one CUDA graph               */
+} hmat_solve_opts;
+
+typedef struct hmat_solve_info {
+    int32_t status;        /* hmat_status of the solve                                          */
+    int32_t iters;         /* Algorithm 1 iterations (each with up to two products)             */
+    int32_t restarts;      /* runs started from a true residual after the first                 */
+    int32_t matvecs;       /* products in the handle's precision form                           */
+    int32_t matvecs_fp64;  /* FP64 products for true residuals                                  */
+    int32_t launches;      /* kernels this call enqueued (skipped ones inside graph batches too) */
+    double relres_true;    /* ||b - A~64 x||_2 / ||b||_2 at exit                                 */
+    double relres_inner;   /* last recursive ||r_i||_2 / ||b||_2                                */
+} hmat_solve_info;
+
+/* Defaults: tol 1e-8, inner_tol 0, maxit 1000, max_restarts 30, check_every 1, use_graph 1. */
+void hmat_solve_opts_default(hmat_solve_opts *opts);
+
+/*
+ * hmat_bicgstab -- solve A~ x = b by BiCG-STAB (Algorithm 1) with the handle's
+ * precision form for the products v = A~ p and t = A~ s, FP64 for every inner
+ * product, the alpha/beta/omega updates and the vectors, and the FP64 true
+ * residual for acceptance.  x is the initial guess on entry and the solution on
+ * exit (x = 0 on exit when b = 0).  b and x are N vectors in original order.
+ * Returns info->status (also when it is not HMAT_OK).  Synchronises `stream`.
+ * Errors: HMAT_ERR_ARG, HMAT_ERR_CUDA, HMAT_ERR_BREAKDOWN_RHO,
+ * HMAT_ERR_BREAKDOWN_OMEGA, HMAT_ERR_MAXIT, HMAT_ERR_NONFINITE.
+ */
+int hmat_bicgstab(hmat_handle h, const double *b, double *x, double tol, int32_t maxit, void *stream,
+                  hmat_solve_info *info);
+
+/* hmat_bicgstab with every option explicit (opts NULL = defaults). */
+int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const hmat_solve_opts *opts, void *stream,
+                     hmat_solve_info *info);
+
+/* ------------------------------------------------------------------------- */
+/* Introspection                                                              */
+/* ------------------------------------------------------------------------- */
+typedef struct hmat_handle_info {
+    int64_t n;
+    int32_t precision;
+    int32_t nleaves;
+    int64_t panel_bytes;         /* device bytes of the form's panels (algorithmic bytes read per product) */
+    int64_t panel_bytes_fp64;    /* device bytes of the FP64 copy                                           */
+    int64_t index_bytes;         /* device bytes of the packing indices                                     */
+    int64_t stored_entries;      /* dense_entries + lr_entries of the blob                                  */
+    int64_t phase1_entries;      /* entries streamed by the projection t = W x                              */
+    int64_t phase2_entries;      /* entries streamed by the expansion y = D x + V t                         */
+    int64_t partials;            /* partial sums of the projection                                          */
+    int64_t rank_sum;
+} hmat_handle_info;
+
+int hmat_info(hmat_handle h, hmat_handle_info *out);
+
+/*
+ * hmat_time_matvec -- enqueue `iters` products of a fixed internal vector on
+ * `stream` and time each kernel of the product with CUDA events recorded on
+ * that stream; ms_out[0..3] receive the mean milliseconds per launch of the
+ * source-vector preparation, the projection (t = W x), the partial-sum
+ * reduction and the expansion (y = D x + V t); ms_out[4] the mean per whole
+ * product.  `fp64` = 1 times the FP64 copy.  Synchronises `stream`.
+ */
+int hmat_time_matvec(hmat_handle h, int32_t iters, int32_t fp64, void *stream, double *ms_out);
+
+/* Message for a status code (static storage). */
+const char *hmat_strerror(int status);
+
+/* Text of the last CUDA error seen by this library in the calling thread. */
+const char *hmat_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMAT_H */

@@ -1,0 +1,844 @@
+// Device kernels of the H-matrix vector product and of BiCG-STAB (sm_103a).
+//
+// Product (Section 2.1, eq. 5-10 and 21-25), in three launches:
+//   phase 1  one CTA per leaf column cluster kappa: t-partials = Q_kappa^T x_kappa,
+//            Q_kappa the rows of every W_m^T (eq. 9/22) whose column cluster
+//            contains kappa, row-major; each thread owns one 16-byte column vector
+//            and walks the |kappa| rows (coalesced 128-bit loads, x from shared
+//            memory, no cross-thread reduction);
+//   reduce   one warp per low-rank block: t = 2^e sum_kappa partials, in a fixed
+//            order (deterministic, no atomics on values);
+//   phase 2  one CTA per leaf row cluster rho: y_rho = P_rho g_rho with P_rho the
+//            rows of the dense blocks (eq. 21) and of the V_m (eq. 10/24) over rho,
+//            g_rho the matching pieces of x and t staged in shared memory; one warp
+//            per row; each row of y is written once by its owner (eq. 25 without
+//            atomics).
+// Arithmetic per store:
+//   DF    panels are pairs (hi, lo); products and sums in double-float on the
+//         FP32 pipe (the FP64 pipe of GB300 is ~1/60 of FP32);
+//   F64   IEEE FP64 FMA;
+//   F32, BF16  FP32 FMA over chunks of 8 products, chunks summed in double-float.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "hmat.h"
+#include "kernels.h"
+
+namespace hmat_internal {
+
+namespace {
+
+// ------------------------------------------------------------------------
+// double-float helpers (error-free transformations; intrinsics keep the
+// compiler from contracting or reassociating them)
+// ------------------------------------------------------------------------
+struct DF {
+    float s, c;  // value s + c
+};
+
+__device__ __forceinline__ void two_sum_acc(DF &a, float p) {
+    float t = __fadd_rn(a.s, p);
+    float bb = __fsub_rn(t, a.s);
+    float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    a.s = t;
+    a.c = __fadd_rn(a.c, err);
+}
+
+__device__ __forceinline__ void renorm(DF &a) {
+    float t = __fadd_rn(a.s, a.c);
+    a.c = __fsub_rn(a.c, __fsub_rn(t, a.s));
+    a.s = t;
+}
+
+// a += (ah + al) * (xh + xl), the lo*lo term (~2^-48) dropped
+__device__ __forceinline__ void df_fma(DF &a, float ah, float al, float xh, float xl) {
+    float p = __fmul_rn(ah, xh);
+    float e = __fmaf_rn(ah, xh, -p);  // exact error of the product
+    e = __fmaf_rn(ah, xl, e);
+    e = __fmaf_rn(al, xh, e);
+    float t = __fadd_rn(a.s, p);
+    float bb = __fsub_rn(t, a.s);
+    float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    a.s = t;
+    a.c = __fadd_rn(a.c, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    float t = __fadd_rn(a.s, b.s);
+    float bb = __fsub_rn(t, a.s);
+    float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bb)), __fsub_rn(b.s, bb));
+    float c = __fadd_rn(__fadd_rn(a.c, b.c), err);
+    DF r;
+    r.s = __fadd_rn(t, c);
+    r.c = __fsub_rn(c, __fsub_rn(r.s, t));
+    return r;
+}
+
+__device__ __forceinline__ DF df_shfl_xor(DF a, int m) {
+    DF r;
+    r.s = __shfl_xor_sync(0xffffffffu, a.s, m);
+    r.c = __shfl_xor_sync(0xffffffffu, a.c, m);
+    return r;
+}
+
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.s + (double)a.c; }
+
+__device__ __forceinline__ int4 ld_stream(const void *p) { return __ldcs((const int4 *)p); }
+
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+__device__ __forceinline__ float2 split_double(double v) {
+    float hi = __double2float_rn(v);
+    float lo = __double2float_rn(v - (double)hi);
+    return make_float2(hi, lo);
+}
+
+// ------------------------------------------------------------------------
+// store traits
+// ------------------------------------------------------------------------
+// VW = entries per 16-byte vector; Op = operand type of x and t entries.
+template <Store S> struct Tr;
+template <> struct Tr<Store::DF> { static constexpr int VW = 2; using Op = float2; using Part = float2; };
+template <> struct Tr<Store::F64> { static constexpr int VW = 2; using Op = double; using Part = double; };
+template <> struct Tr<Store::F32> { static constexpr int VW = 4; using Op = float; using Part = float; };
+template <> struct Tr<Store::BF16> { static constexpr int VW = 8; using Op = float; using Part = float; };
+
+// per-column / per-row accumulator
+template <Store S> struct Acc;
+template <> struct Acc<Store::DF> {
+    DF a;
+    int n;
+    __device__ void init() { a.s = 0.f; a.c = 0.f; n = 0; }
+};
+template <> struct Acc<Store::F64> {
+    double a;
+    __device__ void init() { a = 0.0; }
+};
+template <> struct Acc<Store::F32> {
+    DF a;
+    float ch;
+    __device__ void init() { a.s = 0.f; a.c = 0.f; ch = 0.f; }
+};
+template <> struct Acc<Store::BF16> {
+    DF a;
+    float ch;
+    __device__ void init() { a.s = 0.f; a.c = 0.f; ch = 0.f; }
+};
+
+// Multiply one 16-byte panel vector by VW operands and accumulate into VW
+// separate accumulators (phase 1: one per column).
+template <Store S> struct Cols;
+template <> struct Cols<Store::DF> {
+    __device__ static void mac(Acc<Store::DF> *acc, int4 raw, float2 x) {
+        float4 v = *reinterpret_cast<float4 *>(&raw);
+        df_fma(acc[0].a, v.x, v.y, x.x, x.y);
+        df_fma(acc[1].a, v.z, v.w, x.x, x.y);
+    }
+};
+template <> struct Cols<Store::F64> {
+    __device__ static void mac(Acc<Store::F64> *acc, int4 raw, double x) {
+        double2 v = *reinterpret_cast<double2 *>(&raw);
+        acc[0].a = fma(v.x, x, acc[0].a);
+        acc[1].a = fma(v.y, x, acc[1].a);
+    }
+};
+template <> struct Cols<Store::F32> {
+    __device__ static void mac(Acc<Store::F32> *acc, int4 raw, float x) {
+        float4 v = *reinterpret_cast<float4 *>(&raw);
+        acc[0].ch = fmaf(v.x, x, acc[0].ch);
+        acc[1].ch = fmaf(v.y, x, acc[1].ch);
+        acc[2].ch = fmaf(v.z, x, acc[2].ch);
+        acc[3].ch = fmaf(v.w, x, acc[3].ch);
+    }
+};
+template <> struct Cols<Store::BF16> {
+    __device__ static void mac(Acc<Store::BF16> *acc, int4 raw, float x) {
+        uint32_t w[4] = {(uint32_t)raw.x, (uint32_t)raw.y, (uint32_t)raw.z, (uint32_t)raw.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            acc[2 * k].ch = fmaf(bf_lo(w[k]), x, acc[2 * k].ch);
+            acc[2 * k + 1].ch = fmaf(bf_hi(w[k]), x, acc[2 * k + 1].ch);
+        }
+    }
+};
+
+// fold a chunk (F32/BF16) or renormalise (DF) -- called every 8 rows / products
+template <Store S> __device__ __forceinline__ void fold(Acc<S> &a);
+template <> __device__ __forceinline__ void fold<Store::DF>(Acc<Store::DF> &a) { renorm(a.a); }
+template <> __device__ __forceinline__ void fold<Store::F64>(Acc<Store::F64> &) {}
+template <> __device__ __forceinline__ void fold<Store::F32>(Acc<Store::F32> &a) { two_sum_acc(a.a, a.ch); a.ch = 0.f; }
+template <> __device__ __forceinline__ void fold<Store::BF16>(Acc<Store::BF16> &a) { two_sum_acc(a.a, a.ch); a.ch = 0.f; }
+
+// partial-sum output of a finished accumulator
+template <Store S> __device__ __forceinline__ typename Tr<S>::Part to_part(Acc<S> &a);
+template <> __device__ __forceinline__ float2 to_part<Store::DF>(Acc<Store::DF> &a) {
+    renorm(a.a);
+    return make_float2(a.a.s, a.a.c);
+}
+template <> __device__ __forceinline__ double to_part<Store::F64>(Acc<Store::F64> &a) { return a.a; }
+template <> __device__ __forceinline__ float to_part<Store::F32>(Acc<Store::F32> &a) {
+    fold<Store::F32>(a);
+    return __fadd_rn(a.a.s, a.a.c);
+}
+template <> __device__ __forceinline__ float to_part<Store::BF16>(Acc<Store::BF16> &a) {
+    fold<Store::BF16>(a);
+    return __fadd_rn(a.a.s, a.a.c);
+}
+
+// skip test of the solver's products: mode 0 never, 1 on a set flag,
+// 2 on a set flag or a stop at the ||s|| check
+__device__ __forceinline__ bool skip_product(const SolverScalars *S, int mode) {
+    if (mode == 0 || S == nullptr) return false;
+    int f = *(volatile const int32_t *)&S->flag;
+    if (f != 0) return true;
+    return mode == 2 && *(volatile const int32_t *)&S->stop_on_s != 0;
+}
+
+// ------------------------------------------------------------------------
+// source-vector operand
+// ------------------------------------------------------------------------
+template <Store S>
+__global__ void k_prep(int n, const double *__restrict__ x, const int32_t *__restrict__ src_perm,
+                       typename Tr<S>::Op *__restrict__ xs) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        double v = x[src_perm ? src_perm[p] : p];
+        if constexpr (S == Store::DF) xs[p] = split_double(v);
+        else if constexpr (S == Store::F64) xs[p] = v;
+        else xs[p] = __double2float_rn(v);
+    }
+}
+
+// ------------------------------------------------------------------------
+// phase 1: per leaf column cluster, projections of x_kappa on the W rows
+// ------------------------------------------------------------------------
+constexpr int kP1Threads = 256;
+constexpr int kP1RunsSmem = 512;
+
+// t operand from a finished partial (scaled by 2^e, exact)
+template <Store S>
+__device__ __forceinline__ typename Tr<S>::Op part_to_op(typename Tr<S>::Part p, int e) {
+    if constexpr (S == Store::DF) return make_float2(ldexpf(p.x, e), ldexpf(p.y, e));
+    else if constexpr (S == Store::F64) return ldexp(p, e);
+    else return ldexpf(p, e);
+}
+
+template <Store S>
+__global__ void __launch_bounds__(kP1Threads) k_phase1(const P1Desc *__restrict__ desc, const Run *__restrict__ runs_g,
+                                                        const void *__restrict__ q1,
+                                                        const typename Tr<S>::Op *__restrict__ xs,
+                                                        typename Tr<S>::Part *__restrict__ part,
+                                                        typename Tr<S>::Op *__restrict__ ts,
+                                                        const SolverScalars *S_, int mode) {
+    using Op = typename Tr<S>::Op;
+    constexpr int VW = Tr<S>::VW;
+    __shared__ Op xk[kMaxLeaf];
+    __shared__ Run runs_s[kP1RunsSmem];
+    if (skip_product(S_, mode)) return;
+    const P1Desc d = desc[blockIdx.x];
+    for (int j = threadIdx.x; j < d.xlen; j += blockDim.x) xk[j] = xs[d.xbeg + j];
+    const bool runs_in_smem = d.rcnt <= kP1RunsSmem;
+    if (runs_in_smem)
+        for (int r = threadIdx.x; r < d.rcnt; r += blockDim.x) runs_s[r] = runs_g[d.rbeg + r];
+    const Run *runs = runs_in_smem ? runs_s : runs_g + d.rbeg;
+    __syncthreads();
+    const int nvec = d.ld / VW;
+    const char *base = (const char *)q1 + (size_t)d.off * (16 / VW);
+    const size_t row_bytes = (size_t)d.ld * (16 / VW);
+    for (int vc = threadIdx.x; vc < nvec; vc += blockDim.x) {
+        Acc<S> acc[VW];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) acc[e].init();
+        const char *col = base + (size_t)vc * 16;
+        int j = 0;
+        for (; j + 8 <= d.xlen; j += 8) {
+            int4 raw[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) raw[u] = ld_stream(col + (size_t)(j + u) * row_bytes);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) Cols<S>::mac(acc, raw[u], xk[j + u]);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) fold<S>(acc[e]);
+        }
+        for (; j < d.xlen; ++j) {
+            int4 raw = ld_stream(col + (size_t)j * row_bytes);
+            Cols<S>::mac(acc, raw, xk[j]);
+        }
+        const int c0 = vc * VW;
+        if (c0 >= d.R) continue;
+        int lo = 0, hi = d.rcnt - 1;  // run holding column c0
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (runs[mid].dst <= c0) lo = mid;
+            else hi = mid - 1;
+        }
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            const int c = c0 + e;
+            if (c < d.R) {
+                while (c >= runs[lo].dst + runs[lo].len) ++lo;
+                const Run rn = runs[lo];
+                const int idx = rn.src + (c - rn.dst);
+                const typename Tr<S>::Part pv = to_part<S>(acc[e]);
+                if ((rn.info & 0xff) == 0) ts[idx] = part_to_op<S>(pv, (rn.info >> 8) - 512);
+                else part[idx] = pv;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// reduce: t_b = 2^e sum_k partial[boff + k r + l] for blocks spanning several
+// leaf clusters; fixed order, contiguous loads
+// ------------------------------------------------------------------------
+template <Store S>
+__global__ void k_reduce(int nlr, const RdDesc *__restrict__ rd, const typename Tr<S>::Part *__restrict__ part,
+                         typename Tr<S>::Op *__restrict__ ts, const SolverScalars *S_, int mode) {
+    if (skip_product(S_, mode)) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= nlr) return;
+    const RdDesc d = rd[warp];
+    for (int l0 = 0; l0 < d.rank; l0 += 32) {
+        const int rr = min(32, d.rank - l0);
+        int rp = 1;
+        while (rp < rr) rp <<= 1;
+        const int G = 32 / rp, g = lane / rp, l = lane % rp;
+        const typename Tr<S>::Part *src = part + d.boff + l0 + l;
+        if constexpr (S == Store::F64) {
+            double a = 0.0;
+            if (l < rr) {
+#pragma unroll 4
+                for (int k = g; k < d.cnt; k += G) a += src[(size_t)k * d.rank];
+            }
+            for (int m = rp; m < 32; m <<= 1) a += __shfl_xor_sync(0xffffffffu, a, m);
+            if (g == 0 && l < rr) ts[d.toff + l0 + l] = ldexp(a, d.scale);
+        } else {
+            DF a{0.f, 0.f};
+            if (l < rr) {
+#pragma unroll 4
+                for (int k = g; k < d.cnt; k += G) {
+                    if constexpr (S == Store::DF) {
+                        float2 pp = src[(size_t)k * d.rank];
+                        a = df_add(a, DF{pp.x, pp.y});
+                    } else {
+                        two_sum_acc(a, src[(size_t)k * d.rank]);
+                    }
+                }
+            }
+            renorm(a);
+            for (int m = rp; m < 32; m <<= 1) a = df_add(a, df_shfl_xor(a, m));
+            if (g == 0 && l < rr) {
+                if constexpr (S == Store::DF) ts[d.toff + l0 + l] = make_float2(ldexpf(a.s, d.scale), ldexpf(a.c, d.scale));
+                else ts[d.toff + l0 + l] = ldexpf(__fadd_rn(a.s, a.c), d.scale);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// phase 2: per leaf row cluster, y_rho = P_rho g_rho
+// ------------------------------------------------------------------------
+constexpr int kP2Threads = 256;
+constexpr int kP2Warps = kP2Threads / 32;
+
+template <Store S>
+__device__ __forceinline__ typename Tr<S>::Op scale_op(typename Tr<S>::Op v, int e) {
+    if constexpr (S == Store::DF) return make_float2(ldexpf(v.x, e), ldexpf(v.y, e));
+    else if constexpr (S == Store::F64) return ldexp(v, e);
+    else return ldexpf(v, e);
+}
+
+// Multiply one 16-byte panel vector by VW consecutive operands (phase 2: one row).
+template <Store S>
+__device__ __forceinline__ void row_mac(Acc<S> &acc, int4 raw, const typename Tr<S>::Op *g);
+template <>
+__device__ __forceinline__ void row_mac<Store::DF>(Acc<Store::DF> &acc, int4 raw, const float2 *g) {
+    float4 v = *reinterpret_cast<float4 *>(&raw);
+    float4 x = *reinterpret_cast<const float4 *>(g);
+    df_fma(acc.a, v.x, v.y, x.x, x.y);
+    df_fma(acc.a, v.z, v.w, x.z, x.w);
+    if (++acc.n == 4) { renorm(acc.a); acc.n = 0; }
+}
+template <>
+__device__ __forceinline__ void row_mac<Store::F64>(Acc<Store::F64> &acc, int4 raw, const double *g) {
+    double2 v = *reinterpret_cast<double2 *>(&raw);
+    double2 x = *reinterpret_cast<const double2 *>(g);
+    acc.a = fma(v.x, x.x, acc.a);
+    acc.a = fma(v.y, x.y, acc.a);
+}
+template <>
+__device__ __forceinline__ void row_mac<Store::F32>(Acc<Store::F32> &acc, int4 raw, const float *g) {
+    float4 v = *reinterpret_cast<float4 *>(&raw);
+    float4 x = *reinterpret_cast<const float4 *>(g);
+    float c = 0.f;
+    c = fmaf(v.x, x.x, c);
+    c = fmaf(v.y, x.y, c);
+    c = fmaf(v.z, x.z, c);
+    c = fmaf(v.w, x.w, c);
+    two_sum_acc(acc.a, c);  // one chunk of 4 products
+}
+template <>
+__device__ __forceinline__ void row_mac<Store::BF16>(Acc<Store::BF16> &acc, int4 raw, const float *g) {
+    float4 x0 = *reinterpret_cast<const float4 *>(g);
+    float4 x1 = *reinterpret_cast<const float4 *>(g + 4);
+    float c = 0.f;
+    c = fmaf(bf_lo((uint32_t)raw.x), x0.x, c);
+    c = fmaf(bf_hi((uint32_t)raw.x), x0.y, c);
+    c = fmaf(bf_lo((uint32_t)raw.y), x0.z, c);
+    c = fmaf(bf_hi((uint32_t)raw.y), x0.w, c);
+    c = fmaf(bf_lo((uint32_t)raw.z), x1.x, c);
+    c = fmaf(bf_hi((uint32_t)raw.z), x1.y, c);
+    c = fmaf(bf_lo((uint32_t)raw.w), x1.z, c);
+    c = fmaf(bf_hi((uint32_t)raw.w), x1.w, c);
+    two_sum_acc(acc.a, c);  // one chunk of 8 products
+}
+
+template <Store S>
+__device__ __forceinline__ DF row_total(Acc<S> &a) {
+    if constexpr (S == Store::F64) return DF{0.f, 0.f};
+    else { renorm(a.a); return a.a; }
+}
+
+template <Store S, int MR>
+__global__ void __launch_bounds__(kP2Threads, MR == 4 ? 4 : 2) k_phase2(const P2Desc *__restrict__ desc, const Run *__restrict__ runs_g,
+                                                        const void *__restrict__ p2,
+                                                        const typename Tr<S>::Op *__restrict__ xs,
+                                                        const typename Tr<S>::Op *__restrict__ ts, int kc,
+                                                        double *__restrict__ y, const int32_t *__restrict__ out_perm,
+                                                        const SolverScalars *S_, int mode, int max_runs_smem) {
+    using Op = typename Tr<S>::Op;
+    constexpr int VW = Tr<S>::VW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Op *g = reinterpret_cast<Op *>(smem_raw);
+    Run *runs_s = reinterpret_cast<Run *>(smem_raw + (size_t)kc * sizeof(Op));
+    if (skip_product(S_, mode)) return;
+    const P2Desc d = desc[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t esz = 16 / VW;
+    const char *base = (const char *)p2 + (size_t)d.off * esz;
+    const size_t row_bytes = (size_t)d.ld * esz;
+
+    // the first vector of each of this warp's rows, in flight while g is staged
+    int4 pre[MR];
+    {
+        const int nv0 = min(kc, d.ld) / VW;
+#pragma unroll
+        for (int rr = 0; rr < MR; ++rr) {
+            const int i = warp + rr * kP2Warps;
+            pre[rr] = (i < d.ylen && lane < nv0) ? ld_stream(base + (size_t)i * row_bytes + (size_t)lane * 16)
+                                                 : make_int4(0, 0, 0, 0);
+        }
+    }
+    const bool runs_in_smem = d.rcnt <= max_runs_smem;
+    if (runs_in_smem)
+        for (int r = threadIdx.x; r < d.rcnt; r += blockDim.x) runs_s[r] = runs_g[d.rbeg + r];
+    const Run *runs = runs_in_smem ? runs_s : runs_g + d.rbeg;
+
+    Acc<S> acc[MR];
+#pragma unroll
+    for (int r = 0; r < MR; ++r) acc[r].init();
+
+    for (int c0 = 0; c0 < d.ld; c0 += kc) {
+        const int cw = min(kc, d.ld - c0);
+        __syncthreads();  // runs visible (first chunk); previous chunk consumed
+        for (int k = threadIdx.x; k < cw; k += blockDim.x) {
+            const int col = c0 + k;
+            Op v;
+            if (col >= d.K) {
+                if constexpr (S == Store::DF) v = make_float2(0.f, 0.f);
+                else v = (Op)0;
+            } else {
+                int lo = 0, hi = d.rcnt - 1;  // last run with dst <= col
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (runs[mid].dst <= col) lo = mid;
+                    else hi = mid - 1;
+                }
+                const Run rn = runs[lo];
+                const int src = rn.src + (col - rn.dst);
+                const int kind = rn.info & 0xff, e = (rn.info >> 8) - 512;
+                v = kind == 0 ? xs[src] : ts[src];
+                if (e != 0) v = scale_op<S>(v, e);
+            }
+            g[k] = v;
+        }
+        __syncthreads();
+        const int nv = cw / VW;
+        const char *chunk = base + (size_t)c0 * esz;
+        int v = lane;
+        if (c0 == 0) {
+            if (v < nv) {
+#pragma unroll
+                for (int rr = 0; rr < MR; ++rr)
+                    if (warp + rr * kP2Warps < d.ylen) row_mac<S>(acc[rr], pre[rr], g + v * VW);
+            }
+            v += 32;
+        }
+        for (; v < nv; v += 32) {
+            int4 raw[MR];
+#pragma unroll
+            for (int rr = 0; rr < MR; ++rr) {
+                const int i = warp + rr * kP2Warps;
+                raw[rr] = i < d.ylen ? ld_stream(chunk + (size_t)i * row_bytes + (size_t)v * 16) : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int rr = 0; rr < MR; ++rr)
+                if (warp + rr * kP2Warps < d.ylen) row_mac<S>(acc[rr], raw[rr], g + v * VW);
+        }
+    }
+    // warp reductions, one output row per (warp, rr)
+#pragma unroll
+    for (int rr = 0; rr < MR; ++rr) {
+        const int i = warp + rr * kP2Warps;
+        if (i < d.ylen) {
+            double out;
+            if constexpr (S == Store::F64) {
+                double a = acc[rr].a;
+                for (int m = 16; m >= 1; m >>= 1) a += __shfl_xor_sync(0xffffffffu, a, m);
+                out = a;
+            } else {
+                DF a = row_total<S>(acc[rr]);
+                for (int m = 16; m >= 1; m >>= 1) a = df_add(a, df_shfl_xor(a, m));
+                out = df_to_double(a);
+            }
+            if (lane == 0) {
+                const int p = d.ybeg + i;
+                y[out_perm ? out_perm[p] : p] = out;
+            }
+        }
+    }
+}
+
+int grid_for(int64_t n, int threads, int cap) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------
+// product launchers
+// ------------------------------------------------------------------------
+#define HMAT_DISPATCH(S, CALL)                                    \
+    switch (S) {                                                  \
+    case Store::DF: { constexpr Store SS = Store::DF; CALL; } break;   \
+    case Store::F64: { constexpr Store SS = Store::F64; CALL; } break; \
+    case Store::F32: { constexpr Store SS = Store::F32; CALL; } break; \
+    case Store::BF16: { constexpr Store SS = Store::BF16; CALL; } break; \
+    }
+
+void launch_prep(Store s, const DevIndex &ix, const double *x, const int32_t *src_perm, void *xs, cudaStream_t st) {
+    int blocks = grid_for(ix.n, 256, 4096);
+    HMAT_DISPATCH(s, (k_prep<SS><<<blocks, 256, 0, st>>>(ix.n, x, src_perm, (typename Tr<SS>::Op *)xs)));
+}
+
+void launch_phase1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
+                   cudaStream_t st) {
+    HMAT_DISPATCH(s, (k_phase1<SS><<<ix.nleaves, kP1Threads, 0, st>>>(
+                         ix.p1, ix.p1_runs, P.q1, (const typename Tr<SS>::Op *)P.xs, (typename Tr<SS>::Part *)P.part,
+                         (typename Tr<SS>::Op *)P.ts, skipS, mode)));
+}
+
+void launch_reduce(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
+                   cudaStream_t st) {
+    if (ix.nlr == 0) return;
+    const int warps_per_block = 8;
+    int blocks = (ix.nlr + warps_per_block - 1) / warps_per_block;
+    HMAT_DISPATCH(s, (k_reduce<SS><<<blocks, 32 * warps_per_block, 0, st>>>(
+                         ix.nlr, ix.rd, (const typename Tr<SS>::Part *)P.part,
+                         (typename Tr<SS>::Op *)P.ts, skipS, mode)));
+}
+
+static int max_runs_smem_for(const DevIndex &ix) { return ix.max_runs < 2048 ? ix.max_runs : 2048; }
+
+size_t phase2_smem_bytes(Store s, const DevIndex &ix) {
+    return (size_t)ix.kc * operand_bytes(s) + (size_t)max_runs_smem_for(ix) * sizeof(Run);
+}
+
+void launch_phase2(Store s, const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm,
+                   const SolverScalars *skipS, int mode, cudaStream_t st) {
+    size_t smem = phase2_smem_bytes(s, ix);
+    int mrs = max_runs_smem_for(ix);
+    if (ix.max_leaf <= 4 * kP2Warps) {
+        HMAT_DISPATCH(s, (k_phase2<SS, 4><<<ix.nleaves, kP2Threads, smem, st>>>(
+                             ix.p2, ix.runs, P.p2, (const typename Tr<SS>::Op *)P.xs,
+                             (const typename Tr<SS>::Op *)P.ts, ix.kc, y, out_perm, skipS, mode, mrs)));
+    } else {
+        HMAT_DISPATCH(s, (k_phase2<SS, kMaxLeaf / kP2Warps><<<ix.nleaves, kP2Threads, smem, st>>>(
+                             ix.p2, ix.runs, P.p2, (const typename Tr<SS>::Op *)P.xs,
+                             (const typename Tr<SS>::Op *)P.ts, ix.kc, y, out_perm, skipS, mode, mrs)));
+    }
+}
+
+// Opt in to large dynamic shared memory for every phase-2 instantiation.
+template <int MR>
+static cudaError_t configure_phase2_mr(size_t max_smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_phase2<Store::DF, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_phase2<Store::F64, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_phase2<Store::F32, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_phase2<Store::BF16, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+}
+
+// Opt in to large dynamic shared memory for every phase-2 instantiation.
+cudaError_t configure_phase2(size_t max_smem) {
+    cudaError_t e = configure_phase2_mr<4>(max_smem);
+    if (e != cudaSuccess) return e;
+    return configure_phase2_mr<kMaxLeaf / kP2Warps>(max_smem);
+}
+
+// ------------------------------------------------------------------------
+// BiCG-STAB vector kernels: FP64 arithmetic, deterministic two-stage
+// reductions (per-block tree, then the last block sums the block partials in
+// block order)
+// ------------------------------------------------------------------------
+namespace {
+
+template <int NV>
+__device__ __forceinline__ void block_reduce(double (&v)[NV], double *sh) {
+    // sh: NV * kVecThreads doubles
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[q * kVecThreads + threadIdx.x] = v[q];
+    __syncthreads();
+    for (int s = kVecThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) sh[q * kVecThreads + threadIdx.x] += sh[q * kVecThreads + threadIdx.x + s];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = sh[q * kVecThreads];
+}
+
+// Block partials -> last block; returns true in the last block, where tot[] holds the totals.
+template <int NV>
+__device__ bool grid_reduce(double (&v)[NV], double *partials, SolverScalars *S, double *sh) {
+    __shared__ bool am_last;
+    block_reduce<NV>(v, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) partials[q * gridDim.x + blockIdx.x] = v[q];
+        __threadfence();
+        unsigned int t = atomicAdd(&S->ticket, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+    double w[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        w[q] = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) w[q] += __ldcg(&partials[q * gridDim.x + b]);
+    }
+    block_reduce<NV>(w, sh);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = w[q];
+    if (threadIdx.x == 0) S->ticket = 0u;
+    return true;
+}
+
+__device__ __forceinline__ bool run_stopped(const SolverScalars *S) {
+    return *(volatile const int32_t *)&S->flag != 0;
+}
+
+// Starts an iteration: the budget test, then the count (an iteration whose rho
+// test fails is counted, one refused by the budget is not).
+__global__ void k_count_iter(SolverScalars *S, int iter_limit) {
+    if (S->flag != 0) return;
+    if (S->iters >= iter_limit) S->flag = HMAT_ERR_MAXIT;
+    else S->iters += 1;
+}
+
+template <Store ST>
+__global__ void __launch_bounds__(kVecThreads) k_update_p(int n, const double *__restrict__ r, double *__restrict__ p,
+                                                          const double *__restrict__ v, typename Tr<ST>::Op *__restrict__ ps,
+                                                          SolverScalars *S) {
+    if (run_stopped(S)) return;
+    const double rho = S->rho;
+    const bool first = S->iter_in_run == 0;
+    if (!isfinite(rho) || rho == 0.0) {  // Algorithm 1: rho_{i-1} = 0 -> the method fails
+        if (blockIdx.x == 0 && threadIdx.x == 0) S->flag = isfinite(rho) ? HMAT_ERR_BREAKDOWN_RHO : HMAT_ERR_NONFINITE;
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) S->nmv += 1;  // v = A p follows
+    const double beta = first ? 0.0 : (rho / S->rho_prev) * (S->alpha / S->omega);
+    const double omega = S->omega;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double pv = first ? r[i] : r[i] + beta * (p[i] - omega * v[i]);
+        p[i] = pv;
+        if constexpr (ST == Store::DF) ps[i] = split_double(pv);
+        else if constexpr (ST == Store::F64) ps[i] = pv;
+        else ps[i] = __double2float_rn(pv);
+    }
+}
+
+__global__ void __launch_bounds__(kVecThreads) k_alpha(int n, const double *__restrict__ rt, const double *__restrict__ v,
+                                                       SolverScalars *S, double *partials) {
+    __shared__ double sh[kVecThreads];
+    if (run_stopped(S)) return;
+    double a[1] = {0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[0] += rt[i] * v[i];
+    if (grid_reduce<1>(a, partials, S, sh) && threadIdx.x == 0) {
+        S->rtv = a[0];
+        S->alpha = S->rho / a[0];
+        if (!isfinite(S->alpha)) S->flag = HMAT_ERR_NONFINITE;
+    }
+}
+
+template <Store ST>
+__global__ void __launch_bounds__(kVecThreads) k_update_s(int n, const double *__restrict__ r, const double *__restrict__ v,
+                                                          double *__restrict__ s, typename Tr<ST>::Op *__restrict__ ss,
+                                                          SolverScalars *S, double *partials) {
+    __shared__ double sh[kVecThreads];
+    if (run_stopped(S)) return;
+    const double alpha = S->alpha;
+    double a[1] = {0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double sv = r[i] - alpha * v[i];
+        s[i] = sv;
+        a[0] += sv * sv;
+        if constexpr (ST == Store::DF) ss[i] = split_double(sv);
+        else if constexpr (ST == Store::F64) ss[i] = sv;
+        else ss[i] = __double2float_rn(sv);
+    }
+    if (grid_reduce<1>(a, partials, S, sh) && threadIdx.x == 0) {
+        S->snorm2 = a[0];
+        if (!isfinite(a[0])) S->flag = HMAT_ERR_NONFINITE;
+        else if (a[0] <= S->stop2) S->stop_on_s = 1;
+        else S->nmv += 1;  // t = A s follows
+    }
+}
+
+__global__ void __launch_bounds__(kVecThreads) k_omega(int n, const double *__restrict__ t, const double *__restrict__ s,
+                                                       SolverScalars *S, double *partials) {
+    __shared__ double sh[2 * kVecThreads];
+    if (run_stopped(S) || S->stop_on_s) return;
+    double a[2] = {0.0, 0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        a[0] += t[i] * s[i];
+        a[1] += t[i] * t[i];
+    }
+    if (grid_reduce<2>(a, partials, S, sh) && threadIdx.x == 0) {
+        S->ts = a[0];
+        S->tt = a[1];
+        S->omega = a[1] == 0.0 ? 0.0 : a[0] / a[1];
+        if (!isfinite(S->omega)) S->flag = HMAT_ERR_NONFINITE;
+    }
+}
+
+__global__ void __launch_bounds__(kVecThreads) k_update_xr(int n, double *__restrict__ x, const double *__restrict__ p,
+                                                           const double *__restrict__ s, const double *__restrict__ t,
+                                                           double *__restrict__ r, const double *__restrict__ rt,
+                                                           SolverScalars *S, double *partials) {
+    __shared__ double sh[2 * kVecThreads];
+    if (run_stopped(S)) return;
+    const bool at_s = S->stop_on_s != 0;
+    const double alpha = S->alpha, omega = at_s ? 0.0 : S->omega;
+    double a[2] = {0.0, 0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double sv = s[i];
+        x[i] = x[i] + alpha * p[i] + omega * sv;
+        double rv = at_s ? sv : sv - omega * t[i];
+        r[i] = rv;
+        a[0] += rt[i] * rv;
+        a[1] += rv * rv;
+    }
+    if (grid_reduce<2>(a, partials, S, sh) && threadIdx.x == 0) {
+        S->rho_prev = S->rho;
+        S->rho = a[0];
+        S->rnorm2 = a[1];
+        S->iter_in_run += 1;
+        if (at_s) {
+            S->rnorm2 = S->snorm2;
+            S->flag = 1;
+        } else if (!isfinite(a[1])) {
+            S->flag = HMAT_ERR_NONFINITE;
+        } else if (a[1] <= S->stop2) {
+            S->flag = 1;
+        } else if (omega == 0.0) {
+            S->flag = HMAT_ERR_BREAKDOWN_OMEGA;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kVecThreads) k_residual(int n, const double *__restrict__ b, const double *__restrict__ y,
+                                                          double *__restrict__ r, double *__restrict__ rt,
+                                                          SolverScalars *S, double *partials) {
+    __shared__ double sh[kVecThreads];
+    double a[1] = {0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double rv = b[i] - (y ? y[i] : 0.0);
+        r[i] = rv;
+        rt[i] = rv;
+        a[0] += rv * rv;
+    }
+    if (grid_reduce<1>(a, partials, S, sh) && threadIdx.x == 0) {
+        S->rnorm2 = a[0];
+        S->rho = a[0];
+        S->iter_in_run = 0;
+        S->stop_on_s = 0;
+        S->flag = isfinite(a[0]) ? 0 : HMAT_ERR_NONFINITE;
+    }
+}
+
+__global__ void k_gather(int n, const int32_t *__restrict__ perm, const double *__restrict__ src, double *__restrict__ dst) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) dst[p] = src[perm[p]];
+}
+__global__ void k_scatter(int n, const int32_t *__restrict__ perm, const double *__restrict__ src, double *__restrict__ dst) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) dst[perm[p]] = src[p];
+}
+
+}  // namespace
+
+int vec_blocks(int64_t n) { return grid_for(n, kVecThreads, 4 * 152); }
+
+void launch_count_iter(SolverScalars *S, int iter_limit, cudaStream_t st) { k_count_iter<<<1, 1, 0, st>>>(S, iter_limit); }
+
+void launch_update_p(Store s, int64_t n, const double *r, double *p, const double *v, void *ps, SolverScalars *S,
+                     cudaStream_t st) {
+    HMAT_DISPATCH(s, (k_update_p<SS><<<vec_blocks(n), kVecThreads, 0, st>>>((int)n, r, p, v,
+                                                                           (typename Tr<SS>::Op *)ps, S)));
+}
+
+void launch_alpha(int64_t n, const double *rt, const double *v, SolverScalars *S, double *partials, cudaStream_t st) {
+    k_alpha<<<vec_blocks(n), kVecThreads, 0, st>>>((int)n, rt, v, S, partials);
+}
+
+void launch_update_s(Store s, int64_t n, const double *r, const double *v, double *svec, void *ss, double *,
+                     const double *, SolverScalars *S, double *partials, cudaStream_t st) {
+    HMAT_DISPATCH(s, (k_update_s<SS><<<vec_blocks(n), kVecThreads, 0, st>>>((int)n, r, v, svec,
+                                                                           (typename Tr<SS>::Op *)ss, S, partials)));
+}
+
+void launch_omega(int64_t n, const double *t, const double *svec, SolverScalars *S, double *partials, cudaStream_t st) {
+    k_omega<<<vec_blocks(n), kVecThreads, 0, st>>>((int)n, t, svec, S, partials);
+}
+
+void launch_update_xr(int64_t n, double *x, const double *p, const double *svec, const double *t, double *r,
+                      const double *rt, SolverScalars *S, double *partials, cudaStream_t st) {
+    k_update_xr<<<vec_blocks(n), kVecThreads, 0, st>>>((int)n, x, p, svec, t, r, rt, S, partials);
+}
+
+void launch_residual(int64_t n, const double *b, const double *y, double *r, double *rt, SolverScalars *S,
+                     double *partials, cudaStream_t st) {
+    k_residual<<<vec_blocks(n), kVecThreads, 0, st>>>((int)n, b, y, r, rt, S, partials);
+}
+
+void launch_gather(int64_t n, const int32_t *perm, const double *src, double *dst_perm, cudaStream_t st) {
+    k_gather<<<grid_for(n, 256, 4096), 256, 0, st>>>((int)n, perm, src, dst_perm);
+}
+
+void launch_scatter(int64_t n, const int32_t *perm, const double *src_perm, double *dst, cudaStream_t st) {
+    k_scatter<<<grid_for(n, 256, 4096), 256, 0, st>>>((int)n, perm, src_perm, dst);
+}
+
+}  // namespace hmat_internal

@@ -1,0 +1,143 @@
+"""GPU BiCG-STAB (Algorithm 1) with the FP64 true-residual acceptance of
+Section 4.1.3, against the oracle's solve and closed-form electrostatics."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from blob_util import dense_blob, oracle_blob
+from gpu_util import lib, need_gpu, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(P, torch, h, b, **kw):
+    bd = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+    xd = torch.zeros_like(bd)
+    info = P.hmat_bicgstab(h, bd, xd, **kw)
+    torch.cuda.synchronize()
+    return xd.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("level", [3, 4])
+def test_fp64_solve_matches_oracle(hcache, oracle_mod, level):
+    torch = need_gpu()
+    P = lib()
+    mesh = synth.icosphere(level)
+    H = hcache(mesh)
+    b = synth.rhs_one_plus_half_z(mesh)
+    h = P.hmat_upload(oracle_blob(H), "fp64")
+    try:
+        x, info = _solve(P, torch, h, b, tol=1e-8)
+        assert info["status"] == 0 and info["relres_true"] <= 1e-8
+        xo, io = H.bicgstab(b, tol=1e-8)
+        assert abs(info["iters"] - io["iters"]) <= 1, (info["iters"], io["iters"])
+        # same algorithm and stop rule: the two 1e-8 solutions agree far below the
+        # discretisation error (their difference is bounded by cond(A) * 2e-8)
+        assert rel(x, xo) <= 1e-5
+        # the oracle's own product confirms the true residual
+        assert np.linalg.norm(b - H.matvec(x)) / np.linalg.norm(b) <= 1.01e-8
+    finally:
+        P.hmat_destroy(h)
+
+
+@pytest.mark.parametrize("form,opts", [("fp64", {}), ("fp64_dfma", {}), ("fp32", {}),
+                                       ("fp32", {"inner_tol": 1e-4}), ("bf16", {"inner_tol": 1e-2})],
+                         ids=["fp64", "fp64_dfma", "fp32", "fp32_refine", "bf16_refine"])
+def test_every_form_reaches_fp64_true_residual(hcache, oracle_mod, form, opts):
+    torch = need_gpu()
+    P = lib()
+    mesh = synth.icosphere(4)
+    H = hcache(mesh)
+    b = synth.rhs_one_plus_half_z(mesh)
+    h = P.hmat_upload(oracle_blob(H), form)
+    try:
+        x, info = _solve(P, torch, h, b, tol=1e-8, **opts)
+        assert info["status"] == 0, info
+        assert info["relres_true"] <= 1e-8
+        assert np.linalg.norm(b - H.matvec(x)) / np.linalg.norm(b) <= 1.01e-8
+        if form == "bf16":
+            assert info["restarts"] >= 2
+    finally:
+        P.hmat_destroy(h)
+
+
+def test_graph_batches_and_host_pointers_agree(hcache):
+    torch = need_gpu()
+    P = lib()
+    mesh = synth.icosphere(4)
+    H = hcache(mesh)
+    b = synth.rhs_one_plus_half_z(mesh)
+    h = P.hmat_upload(oracle_blob(H), "fp32")
+    try:
+        x1, i1 = _solve(P, torch, h, b, tol=1e-8, use_graph=0, check_every=1)
+        x2, i2 = _solve(P, torch, h, b, tol=1e-8, use_graph=1, check_every=1)
+        x3, i3 = _solve(P, torch, h, b, tol=1e-8, use_graph=1, check_every=5)
+        xh = np.zeros(mesh.n)
+        i4 = P.hmat_bicgstab(h, b.copy(), xh, tol=1e-8)
+        for x, i in ((x2, i2), (x3, i3), (xh, i4)):
+            assert np.array_equal(x, x1) and i["iters"] == i1["iters"]
+    finally:
+        P.hmat_destroy(h)
+
+
+def test_status_cases(hcache):
+    torch = need_gpu()
+    P = lib()
+    mesh = synth.icosphere(2)
+    H = hcache(mesh)
+    h = P.hmat_upload(oracle_blob(H), "fp64")
+    try:
+        x, info = _solve(P, torch, h, np.zeros(mesh.n))
+        assert info["status"] == 0 and info["iters"] == 0 and not x.any()
+        x, info = _solve(P, torch, h, np.ones(mesh.n), maxit=1)
+        assert info["status_name"] == "maxit" and info["iters"] == 1
+        bn = np.ones(mesh.n); bn[4] = np.nan
+        x, info = _solve(P, torch, h, bn)
+        assert info["status_name"] == "nonfinite"
+    finally:
+        P.hmat_destroy(h)
+    # exact rho = 0 breakdown (alpha = 1/2, omega = -1 are exact in binary arithmetic)
+    A = np.array([[2.0, 1.0, -1.0], [-1.0, -1.0, 0.0], [-1.0, 1.0, -1.0]])
+    for form in ("fp64", "fp64_dfma"):
+        h = P.hmat_upload(dense_blob(A), form)
+        try:
+            x, info = _solve(P, torch, h, np.array([1.0, 0.0, 0.0]), tol=1e-12)
+            assert info["status_name"] == "breakdown_rho" and info["iters"] == 2, info
+        finally:
+            P.hmat_destroy(h)
+
+
+def test_unit_sphere_total_charge_on_gpu(hcache):
+    torch = need_gpu()
+    P = lib()
+    mesh = synth.icosphere(4)
+    blob = P.hmat_build(mesh.centroid, mesh.area)
+    h = P.hmat_upload(blob, "fp32")
+    try:
+        sigma, info = _solve(P, torch, h, synth.rhs_constant(mesh), tol=1e-8)
+        assert info["status"] == 0
+        q = float(np.dot(sigma, mesh.area)) / (4 * math.pi)
+        assert abs(q - 1.0) <= 3e-2
+    finally:
+        P.hmat_destroy(h)
+
+
+def test_full_size_solve_true_residual(oracle_mod):
+    """Icosphere level 6 (N = 81,920): the FP64 true residual of the GPU solution,
+    recomputed by the oracle's own H-matrix, meets 1e-8."""
+    torch = need_gpu()
+    P = lib()
+    mesh = synth.icosphere(6)
+    blob = P.hmat_build(mesh.centroid, mesh.area)
+    H = oracle_mod.HMatrix(mesh.centroid, mesh.area)
+    b = synth.rhs_one_plus_half_z(mesh)
+    for form, opts in (("fp64", {}), ("bf16", {"inner_tol": 1e-2})):
+        h = P.hmat_upload(blob, form)
+        try:
+            x, info = _solve(P, torch, h, b, tol=1e-8, **opts)
+            assert info["status"] == 0, info
+            assert np.linalg.norm(b - H.matvec(x)) / np.linalg.norm(b) <= 1.05e-8
+        finally:
+            P.hmat_destroy(h)
