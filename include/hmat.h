@@ -221,7 +221,7 @@ typedef struct hmat_handle_info {
     int64_t stored_entries;      /* dense_entries + lr_entries of the blob                                  */
     int64_t phase1_entries;      /* entries streamed by the projection t = W x                              */
     int64_t phase2_entries;      /* entries streamed by the expansion y = D x + V t                         */
-    int64_t partials;            /* partial sums of the projection                                          */
+    int64_t partials;            /* partial sums of blocks spanning several leaf clusters                   */
     int64_t rank_sum;
 } hmat_handle_info;
 
@@ -231,9 +231,9 @@ int hmat_info(hmat_handle h, hmat_handle_info *out);
  * hmat_time_matvec -- enqueue `iters` products of a fixed internal vector on
  * `stream` and time each kernel of the product with CUDA events recorded on
  * that stream; ms_out[0..3] receive the mean milliseconds per launch of the
- * source-vector preparation, the projection (t = W x), the partial-sum
- * reduction and the expansion (y = D x + V t); ms_out[4] the mean per whole
- * product.  `fp64` = 1 times the FP64 copy.  Synchronises `stream`.
+ * source-vector preparation, the projection (t = W x, with its partial-sum
+ * reduction and the operand scatter), 0 (no separate reduction launch) and the
+ * expansion (y = D x + V t); ms_out[4] the mean per whole product.  `fp64` = 1 times the FP64 copy.  Synchronises `stream`.
  */
 int hmat_time_matvec(hmat_handle h, int32_t iters, int32_t fp64, void *stream, double *ms_out);
 

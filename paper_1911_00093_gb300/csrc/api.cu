@@ -117,7 +117,6 @@ void enqueue_product(hmat_t *h, const DevPanels &P, Store s, const double *x_src
                      double *y, const int32_t *out_perm, const SolverScalars *skipS, int mode, cudaStream_t st) {
     if (x_src) launch_prep(s, h->ix, x_src, src_perm, P.xs, st);
     launch_phase1(s, h->ix, P, skipS, mode, st);
-    launch_reduce(s, h->ix, P, skipS, mode, st);
     launch_phase2(s, h->ix, P, y, out_perm, skipS, mode, st);
 }
 
@@ -143,8 +142,12 @@ int alloc_panels(hmat_t *h, const BlobView &v, const Layout &L, Store s, DevPane
     if (st) return st;
     st = h->alloc(&P.part, (size_t)std::max<int64_t>(L.npart, 1) * partial_bytes(s));
     if (st) return st;
-    st = h->alloc(&P.ts, (size_t)std::max<int64_t>(L.tlen, 1) * operand_bytes(s));
+    st = h->alloc(&P.g, (size_t)std::max<int64_t>(L.glen, 1) * operand_bytes(s));
     if (st) return st;
+    CK(cudaMemset(P.g, 0, (size_t)std::max<int64_t>(L.glen, 1) * operand_bytes(s)));  // zero padding columns
+    st = h->alloc(&P.ctr, (size_t)std::max<int32_t>(L.nctr, 1) * sizeof(int32_t));
+    if (st) return st;
+    CK(cudaMemset(P.ctr, 0, (size_t)std::max<int32_t>(L.nctr, 1) * sizeof(int32_t)));
     *bytes_out = (int64_t)(b1 + b2);
     return HMAT_OK;
 }
@@ -181,27 +184,28 @@ extern "C" int hmat_upload(const void *blob, size_t blob_bytes, int32_t precisio
         DevIndex &ix = h->ix;
         ix.n = (int32_t)L.n;
         ix.nleaves = L.nleaves;
-        ix.nlr = (int32_t)L.rd.size();
-        ix.max_runs = L.max_runs;
-        int32_t *perm = nullptr;
-        Run *p1_runs = nullptr;
+        ix.nlr = (int32_t)L.lr.size();
+        ix.nctr = L.nctr;
+        ix.max_leaf = L.max_leaf;
+        int32_t *perm = nullptr, *gdst = nullptr;
         P1Desc *p1 = nullptr;
-        RdDesc *rd = nullptr;
+        P1Run *p1_runs = nullptr;
+        XDst *xdst = nullptr;
+        LrDesc *lr = nullptr;
         P2Desc *p2 = nullptr;
-        Run *runs = nullptr;
         if ((st = h->upload(&perm, L.perm.data(), 4 * L.perm.size())) ||
             (st = h->upload(&p1, L.p1.data(), sizeof(P1Desc) * L.p1.size())) ||
-            (st = h->upload(&rd, L.rd.data(), sizeof(RdDesc) * L.rd.size())) ||
-            (st = h->upload(&p1_runs, L.p1_runs.data(), sizeof(Run) * L.p1_runs.size())) ||
-            (st = h->upload(&p2, L.p2.data(), sizeof(P2Desc) * L.p2.size())) ||
-            (st = h->upload(&runs, L.runs.data(), sizeof(Run) * L.runs.size()))) {
+            (st = h->upload(&p1_runs, L.p1_runs.data(), sizeof(P1Run) * L.p1_runs.size())) ||
+            (st = h->upload(&xdst, L.xdst.data(), sizeof(XDst) * L.xdst.size())) ||
+            (st = h->upload(&lr, L.lr.data(), sizeof(LrDesc) * L.lr.size())) ||
+            (st = h->upload(&gdst, L.gdst.data(), 4 * L.gdst.size())) ||
+            (st = h->upload(&p2, L.p2.data(), sizeof(P2Desc) * L.p2.size()))) {
             return st;
         }
-        ix.perm = perm; ix.p1 = p1; ix.rd = rd; ix.p1_runs = p1_runs; ix.p2 = p2; ix.runs = runs;
-        ix.max_runs1 = L.max_runs1;
-        for (int32_t l = 0; l < L.nleaves; ++l) ix.max_leaf = std::max(ix.max_leaf, L.leaf_begin[l + 1] - L.leaf_begin[l]);
-        h->index_bytes = (int64_t)(4 * L.perm.size() + sizeof(P1Desc) * L.p1.size() + sizeof(RdDesc) * L.rd.size() +
-                                   sizeof(Run) * L.p1_runs.size() + sizeof(P2Desc) * L.p2.size() + sizeof(Run) * L.runs.size());
+        ix.perm = perm; ix.p1 = p1; ix.p1_runs = p1_runs; ix.xdst = xdst; ix.lr = lr; ix.gdst = gdst; ix.p2 = p2;
+        h->index_bytes = (int64_t)(4 * L.perm.size() + sizeof(P1Desc) * L.p1.size() + sizeof(P1Run) * L.p1_runs.size() +
+                                   sizeof(XDst) * L.xdst.size() + sizeof(LrDesc) * L.lr.size() + 4 * L.gdst.size() +
+                                   sizeof(P2Desc) * L.p2.size());
         // phase-2 column chunk: the widest panel if it fits 32 KB of operands
         const int64_t kc_cap = (int64_t)(32768 / operand_bytes(Store::DF));
         ix.kc = (int32_t)std::min<int64_t>(((int64_t)L.max_ld2 + 7) / 8 * 8, kc_cap);
@@ -346,10 +350,9 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = h->ix.n;
     const bool db = is_device_pointer(b), dx = is_device_pointer(x);
-    // kernels per product (source operand, projection, reduction when there are
-    // low-rank blocks, expansion) and per iteration (count, p update, two products
+    // kernels per product (source operand, projection, expansion) and per iteration (count, p update, two products
     // without operand preparation, alpha, s update, omega, x/r update)
-    const int kProductLaunches = h->ix.nlr ? 4 : 3;
+    const int kProductLaunches = 3;
     const int kIterationLaunches = 6 + 2 * (kProductLaunches - 1);
     const double *bsrc = b;
     if (!db) {
@@ -480,7 +483,6 @@ extern "C" int hmat_time_matvec(hmat_handle h, int32_t iters, int32_t fp64, void
         CK(cudaEventRecord(ev[1], st));
         launch_phase1(s, h->ix, P, nullptr, 0, st);
         CK(cudaEventRecord(ev[2], st));
-        launch_reduce(s, h->ix, P, nullptr, 0, st);
         CK(cudaEventRecord(ev[3], st));
         launch_phase2(s, h->ix, P, h->stage_out, nullptr, nullptr, 0, st);
         CK(cudaEventRecord(ev[4], st));

@@ -38,49 +38,63 @@ struct BlobView {
 int parse_blob(const void *blob, size_t bytes, BlobView &view, std::string *why = nullptr);
 
 // ---- packed device layout (host-side description) ----
-// Phase 1 (projection t = W x), one work item per leaf column cluster kappa:
-// a row-major |kappa| x R panel whose column c holds one rank vector of one
-// low-rank block restricted to kappa; its R dot products with x_kappa go, per
-// block (a run of r columns), either straight to t (a block whose column
-// cluster is kappa itself) or to the block's partial sums.
+// The product runs in two launches over leaf clusters.
+//
+// Phase 1, one work item per leaf column cluster kappa: a row-major |kappa| x R
+// panel whose columns are the rank vectors of every W_m (eq. 9/22) whose column
+// cluster contains kappa, restricted to kappa.  Its R dot products with x_kappa
+// are either final (the block's column cluster is kappa) or partial sums that
+// the last phase-1 work item to finish the block adds up in a fixed order.
+// Phase 1 also writes every operand phase 2 needs into per-row-cluster operand
+// buffers g: the slices 2^e x_kappa of the dense blocks over kappa, and each
+// block's 2^e t = 2^e W_m x_m for every leaf row cluster of the block.
+//
+// Phase 2, one work item per leaf row cluster rho: a row-major |rho| x K panel
+// holding the rows over rho of every dense block (eq. 21) and of every V_m
+// (eq. 10/24) whose row cluster contains rho; y_rho = P_rho g_rho.
 struct P1Desc {
-    int64_t off;   // element offset of the panel
-    int32_t R;     // columns
-    int32_t ld;    // row stride (R rounded up to kPadElems)
-    int32_t rbeg;  // first output run (Run: dst = first column, src = first output index,
-                   // info = kind (0 t, 1 partial) | (scale exponent + 512) << 8)
-    int32_t xbeg;  // first row of kappa (cluster order)
-    int32_t xlen;  // rows of kappa
-    int32_t rcnt;  // output runs
+    int64_t off;    // element offset of the panel
+    int32_t R;      // columns
+    int32_t ld;     // row stride (R rounded up to kPadElems)
+    int32_t rbeg;   // first P1Run
+    int32_t rcnt;   // runs (one per low-rank block over kappa)
+    int32_t xbeg;   // first row of kappa (cluster order)
+    int32_t xlen;   // rows of kappa
+    int32_t xdbeg;  // first XDst (dense-block operand slices fed from x_kappa)
+    int32_t xdcnt;
+    int32_t pad[2];
 };
-// Reduction of the partials of one low-rank block spanning several leaf
-// clusters: t[toff + l] = 2^scale sum_k partial[boff + k rank + l].
-struct RdDesc {
-    int32_t boff;   // first partial (block-major: cnt rows of rank values)
-    int32_t cnt;    // number of leaf clusters kappa inside sigma
-    int32_t toff;   // first t entry of the block
+struct P1Run {
+    int32_t col0;   // first panel column of the block
+    int32_t len;    // rank r
+    int32_t q;      // low-rank block index (LrDesc)
+    int32_t poff;   // first partial of this kappa's row of the block, or -1 when final
+};
+struct LrDesc {
+    int32_t boff;   // first partial (block-major: cnt rows of rank values), -1 if single cluster
+    int32_t cnt;    // leaf clusters inside the column cluster
     int32_t rank;
+    int32_t scale;  // exponent e of 2^e t
+    int32_t gbeg;   // first entry of gdst (one per leaf row cluster of the block)
+    int32_t gcnt;
+    int32_t ctr;    // completion counter index (multi-cluster blocks), -1 otherwise
+    int32_t pad;
+};
+struct XDst {
+    int32_t goff;   // operand index of x_kappa[0] in g
     int32_t scale;  // exponent e
-    int32_t pad[3];
 };
-// Phase 2 (expansion y = D x + V t), one work item per leaf row cluster rho:
-// a row-major |rho| x K panel; columns come in runs (dense block slices reading
-// the source vector, then low-rank slices reading t).
 struct P2Desc {
-    int64_t off;
-    int32_t K;
-    int32_t ld;
-    int32_t rbeg;  // first run
-    int32_t rcnt;  // runs
-    int32_t ybeg;  // first row (cluster order)
+    int64_t off;    // element offset of the panel
+    int32_t K;      // columns
+    int32_t ld;     // row stride (K rounded up to kPadElems)
+    int32_t goff;   // first operand of g_rho (ld operands, zero past K)
+    int32_t ybeg;   // first row (cluster order)
     int32_t ylen;
+    int32_t pad;
 };
-struct Run {
-    int32_t dst;    // first column of the run in the panel
-    int32_t src;    // first source index: cluster-order x index (kind 0) or t index (kind 1)
-    int32_t len;
-    int32_t info;   // kind | (scale exponent + 512) << 8
-};
+
+constexpr int kMaxScaleExp = 120;  // |e| of every stored power-of-two scale
 
 struct Layout {
     int64_t n = 0;
@@ -88,13 +102,15 @@ struct Layout {
     std::vector<int32_t> perm;        // perm[p] = original index
     std::vector<int32_t> leaf_begin;  // nleaves + 1
     std::vector<P1Desc> p1;
-    std::vector<RdDesc> rd;
-    std::vector<Run> p1_runs;
+    std::vector<P1Run> p1_runs;
+    std::vector<XDst> xdst;
+    std::vector<LrDesc> lr;
+    std::vector<int32_t> gdst;
     std::vector<P2Desc> p2;
-    std::vector<Run> runs;
     int64_t p1_elems = 0, p2_elems = 0;
-    int64_t npart = 0, tlen = 0;
-    int32_t max_runs = 0, max_ld2 = 0, max_ld1 = 0, max_runs1 = 0;
+    int64_t npart = 0, glen = 0;
+    int32_t nctr = 0;
+    int32_t max_ld2 = 0, max_ld1 = 0, max_runs1 = 0, max_leaf = 0;
     int64_t stored_entries = 0, phase1_entries = 0, phase2_entries = 0, rank_sum = 0;
     // source of each packed entry, used to fill typed panels without
     // materialising an FP64 copy: per P1/P2 work item, the list of block slices

@@ -77,13 +77,6 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
     return r;
 }
 
-__device__ __forceinline__ DF df_shfl_xor(DF a, int m) {
-    DF r;
-    r.s = __shfl_xor_sync(0xffffffffu, a.s, m);
-    r.c = __shfl_xor_sync(0xffffffffu, a.c, m);
-    return r;
-}
-
 __device__ __forceinline__ double df_to_double(DF a) { return (double)a.s + (double)a.c; }
 
 __device__ __forceinline__ int4 ld_stream(const void *p) { return __ldcs((const int4 *)p); }
@@ -126,7 +119,8 @@ template <> struct Acc<Store::F32> {
 template <> struct Acc<Store::BF16> {
     DF a;
     float ch;
-    __device__ void init() { a.s = 0.f; a.c = 0.f; ch = 0.f; }
+    int cnt;
+    __device__ void init() { a.s = 0.f; a.c = 0.f; ch = 0.f; cnt = 0; }
 };
 
 // Multiply one 16-byte panel vector by VW operands and accumulate into VW
@@ -213,38 +207,93 @@ __global__ void k_prep(int n, const double *__restrict__ x, const int32_t *__res
 }
 
 // ------------------------------------------------------------------------
-// phase 1: per leaf column cluster, projections of x_kappa on the W rows
+// exact power-of-two factors (|e| <= 120 is enforced at upload)
+// ------------------------------------------------------------------------
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
+template <Store S>
+__device__ __forceinline__ typename Tr<S>::Op scale_op(typename Tr<S>::Op v, int e) {
+    if constexpr (S == Store::DF) { const float f = pow2f(e); return make_float2(v.x * f, v.y * f); }
+    else if constexpr (S == Store::F64) return v * pow2d(e);
+    else return v * pow2f(e);
+}
+
+// operand from a finished projection (scaled by 2^e, exact)
+template <Store S>
+__device__ __forceinline__ typename Tr<S>::Op part_to_op(typename Tr<S>::Part p, int e) {
+    if constexpr (S == Store::DF) { const float f = pow2f(e); return make_float2(p.x * f, p.y * f); }
+    else if constexpr (S == Store::F64) return p * pow2d(e);
+    else return p * pow2f(e);
+}
+
+// accumulator of the completing work item's fixed-order reduction
+template <Store S> struct RedT { using T = DF; };
+template <> struct RedT<Store::F64> { using T = double; };
+
+template <Store S> __device__ __forceinline__ void red_zero(typename RedT<S>::T &a) {
+    if constexpr (S == Store::F64) a = 0.0; else { a.s = 0.f; a.c = 0.f; }
+}
+template <Store S> __device__ __forceinline__ void red_add_part(typename RedT<S>::T &a, typename Tr<S>::Part p) {
+    if constexpr (S == Store::F64) a += p;
+    else if constexpr (S == Store::DF) a = df_add(a, DF{p.x, p.y});
+    else two_sum_acc(a, p);
+}
+template <Store S> __device__ __forceinline__ void red_add(typename RedT<S>::T &a, typename RedT<S>::T b) {
+    if constexpr (S == Store::F64) a += b; else a = df_add(a, b);
+}
+template <Store S> __device__ __forceinline__ typename Tr<S>::Part red_to_part(typename RedT<S>::T a) {
+    if constexpr (S == Store::F64) return a;
+    else if constexpr (S == Store::DF) { renorm(a); return make_float2(a.s, a.c); }
+    else return __fadd_rn(a.s, a.c);
+}
+
+template <Store S>
+__device__ __forceinline__ typename Tr<S>::Part load_part(const typename Tr<S>::Part *p) {
+    if constexpr (S == Store::DF) return __ldcg(p);
+    else return __ldcg(p);
+}
+
+// ------------------------------------------------------------------------
+// phase 1: per leaf column cluster kappa
 // ------------------------------------------------------------------------
 constexpr int kP1Threads = 256;
 constexpr int kP1RunsSmem = 512;
 
-// t operand from a finished partial (scaled by 2^e, exact)
 template <Store S>
-__device__ __forceinline__ typename Tr<S>::Op part_to_op(typename Tr<S>::Part p, int e) {
-    if constexpr (S == Store::DF) return make_float2(ldexpf(p.x, e), ldexpf(p.y, e));
-    else if constexpr (S == Store::F64) return ldexp(p, e);
-    else return ldexpf(p, e);
-}
-
-template <Store S>
-__global__ void __launch_bounds__(kP1Threads) k_phase1(const P1Desc *__restrict__ desc, const Run *__restrict__ runs_g,
-                                                        const void *__restrict__ q1,
+__global__ void __launch_bounds__(kP1Threads) k_phase1(const P1Desc *__restrict__ desc, const P1Run *__restrict__ runs_g,
+                                                        const XDst *__restrict__ xdst, const LrDesc *__restrict__ lr,
+                                                        const int32_t *__restrict__ gdst, const void *__restrict__ q1,
                                                         const typename Tr<S>::Op *__restrict__ xs,
-                                                        typename Tr<S>::Part *__restrict__ part,
-                                                        typename Tr<S>::Op *__restrict__ ts,
-                                                        const SolverScalars *S_, int mode) {
+                                                        typename Tr<S>::Part *part, typename Tr<S>::Op *__restrict__ g,
+                                                        int32_t *ctr, const SolverScalars *S_, int mode) {
     using Op = typename Tr<S>::Op;
+    using Part = typename Tr<S>::Part;
+    using RT = typename RedT<S>::T;
     constexpr int VW = Tr<S>::VW;
     __shared__ Op xk[kMaxLeaf];
-    __shared__ Run runs_s[kP1RunsSmem];
+    __shared__ P1Run runs_s[kP1RunsSmem];
+    __shared__ int32_t done_q[kP1RunsSmem];
+    __shared__ int32_t ndone;
+    __shared__ RT red[kP1Threads];
     if (skip_product(S_, mode)) return;
     const P1Desc d = desc[blockIdx.x];
     for (int j = threadIdx.x; j < d.xlen; j += blockDim.x) xk[j] = xs[d.xbeg + j];
     const bool runs_in_smem = d.rcnt <= kP1RunsSmem;
     if (runs_in_smem)
         for (int r = threadIdx.x; r < d.rcnt; r += blockDim.x) runs_s[r] = runs_g[d.rbeg + r];
-    const Run *runs = runs_in_smem ? runs_s : runs_g + d.rbeg;
+    const P1Run *runs = runs_in_smem ? runs_s : runs_g + d.rbeg;
+    if (threadIdx.x == 0) ndone = 0;
     __syncthreads();
+
+    // the dense-block operands fed by x_kappa (eq. 21 inputs), scaled by 2^e
+    for (int t = threadIdx.x; t < d.xdcnt * d.xlen; t += blockDim.x) {
+        const int k = t / d.xlen, j = t - k * d.xlen;
+        const XDst x = xdst[d.xdbeg + k];
+        g[x.goff + j] = scale_op<S>(xk[j], x.scale);
+    }
+
+    // projections (eq. 9/22): thread = one 16-byte column vector, walk the rows
     const int nvec = d.ld / VW;
     const char *base = (const char *)q1 + (size_t)d.off * (16 / VW);
     const size_t row_bytes = (size_t)d.ld * (16 / VW);
@@ -272,69 +321,77 @@ __global__ void __launch_bounds__(kP1Threads) k_phase1(const P1Desc *__restrict_
         int lo = 0, hi = d.rcnt - 1;  // run holding column c0
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
-            if (runs[mid].dst <= c0) lo = mid;
+            if (runs[mid].col0 <= c0) lo = mid;
             else hi = mid - 1;
         }
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
             const int c = c0 + e;
             if (c < d.R) {
-                while (c >= runs[lo].dst + runs[lo].len) ++lo;
-                const Run rn = runs[lo];
-                const int idx = rn.src + (c - rn.dst);
-                const typename Tr<S>::Part pv = to_part<S>(acc[e]);
-                if ((rn.info & 0xff) == 0) ts[idx] = part_to_op<S>(pv, (rn.info >> 8) - 512);
-                else part[idx] = pv;
+                while (c >= runs[lo].col0 + runs[lo].len) ++lo;
+                const P1Run rn = runs[lo];
+                const int l = c - rn.col0;
+                const Part pv = to_part<S>(acc[e]);
+                if (rn.poff >= 0) {
+                    part[rn.poff + l] = pv;
+                } else {  // final: 2^e t to every leaf row cluster of the block
+                    const LrDesc ld = lr[rn.q];
+                    const Op o = part_to_op<S>(pv, ld.scale);
+                    for (int k = 0; k < ld.gcnt; ++k) g[gdst[ld.gbeg + k] + l] = o;
+                }
             }
         }
     }
-}
 
-// ------------------------------------------------------------------------
-// reduce: t_b = 2^e sum_k partial[boff + k r + l] for blocks spanning several
-// leaf clusters; fixed order, contiguous loads
-// ------------------------------------------------------------------------
-template <Store S>
-__global__ void k_reduce(int nlr, const RdDesc *__restrict__ rd, const typename Tr<S>::Part *__restrict__ part,
-                         typename Tr<S>::Op *__restrict__ ts, const SolverScalars *S_, int mode) {
-    if (skip_product(S_, mode)) return;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= nlr) return;
-    const RdDesc d = rd[warp];
-    for (int l0 = 0; l0 < d.rank; l0 += 32) {
-        const int rr = min(32, d.rank - l0);
-        int rp = 1;
-        while (rp < rr) rp <<= 1;
-        const int G = 32 / rp, g = lane / rp, l = lane % rp;
-        const typename Tr<S>::Part *src = part + d.boff + l0 + l;
-        if constexpr (S == Store::F64) {
-            double a = 0.0;
-            if (l < rr) {
-#pragma unroll 4
-                for (int k = g; k < d.cnt; k += G) a += src[(size_t)k * d.rank];
+    // blocks spanning several leaf clusters: the work item that completes one
+    // sums its partials in a fixed order (integer ticket; no waiting)
+    __threadfence();
+    for (int r0 = 0; r0 < d.rcnt; r0 += kP1RunsSmem) {
+        __syncthreads();
+        if (threadIdx.x == 0) ndone = 0;
+        __syncthreads();
+        const int r1 = min(d.rcnt, r0 + kP1RunsSmem);
+        for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+            const P1Run rn = runs[r];
+            if (rn.poff >= 0) {
+                const LrDesc ld = lr[rn.q];
+                if (atomicAdd(&ctr[ld.ctr], 1) == ld.cnt - 1) done_q[atomicAdd(&ndone, 1)] = rn.q;
             }
-            for (int m = rp; m < 32; m <<= 1) a += __shfl_xor_sync(0xffffffffu, a, m);
-            if (g == 0 && l < rr) ts[d.toff + l0 + l] = ldexp(a, d.scale);
-        } else {
-            DF a{0.f, 0.f};
-            if (l < rr) {
-#pragma unroll 4
-                for (int k = g; k < d.cnt; k += G) {
-                    if constexpr (S == Store::DF) {
-                        float2 pp = src[(size_t)k * d.rank];
-                        a = df_add(a, DF{pp.x, pp.y});
-                    } else {
-                        two_sum_acc(a, src[(size_t)k * d.rank]);
+        }
+        __syncthreads();
+        const int nd = ndone;  // <= r1 - r0 <= kP1RunsSmem
+        if (nd == 0) continue;
+        __threadfence();
+        for (int i = 0; i < nd; ++i) {
+            const LrDesc ld = lr[done_q[i]];
+            for (int l0 = 0; l0 < ld.rank; l0 += 32) {
+                const int rr = min(32, ld.rank - l0);
+                int rp = 1;
+                while (rp < rr) rp <<= 1;
+                const int G = kP1Threads / rp, gi = threadIdx.x / rp, l = threadIdx.x % rp;
+                RT a;
+                red_zero<S>(a);
+                if (l < rr)
+                    for (int k = gi; k < ld.cnt; k += G)
+                        red_add_part<S>(a, load_part<S>(part + ld.boff + (size_t)k * ld.rank + l0 + l));
+                red[threadIdx.x] = a;
+                __syncthreads();
+                for (int half = G >> 1; half >= 1; half >>= 1) {
+                    if (gi < half) {
+                        RT b = red[threadIdx.x + half * rp];
+                        RT c = red[threadIdx.x];
+                        red_add<S>(c, b);
+                        red[threadIdx.x] = c;
                     }
+                    __syncthreads();
                 }
+                if (gi == 0 && l < rr) {
+                    const Op o = part_to_op<S>(red_to_part<S>(red[l]), ld.scale);
+                    for (int k = 0; k < ld.gcnt; ++k) g[gdst[ld.gbeg + k] + l0 + l] = o;
+                }
+                __syncthreads();
             }
-            renorm(a);
-            for (int m = rp; m < 32; m <<= 1) a = df_add(a, df_shfl_xor(a, m));
-            if (g == 0 && l < rr) {
-                if constexpr (S == Store::DF) ts[d.toff + l0 + l] = make_float2(ldexpf(a.s, d.scale), ldexpf(a.c, d.scale));
-                else ts[d.toff + l0 + l] = ldexpf(__fadd_rn(a.s, a.c), d.scale);
-            }
+            if (threadIdx.x == 0) ctr[ld.ctr] = 0;
         }
     }
 }
@@ -345,14 +402,7 @@ __global__ void k_reduce(int nlr, const RdDesc *__restrict__ rd, const typename 
 constexpr int kP2Threads = 256;
 constexpr int kP2Warps = kP2Threads / 32;
 
-template <Store S>
-__device__ __forceinline__ typename Tr<S>::Op scale_op(typename Tr<S>::Op v, int e) {
-    if constexpr (S == Store::DF) return make_float2(ldexpf(v.x, e), ldexpf(v.y, e));
-    else if constexpr (S == Store::F64) return ldexp(v, e);
-    else return ldexpf(v, e);
-}
-
-// Multiply one 16-byte panel vector by VW consecutive operands (phase 2: one row).
+// Multiply one 16-byte panel vector by VW consecutive operands (one row).
 template <Store S>
 __device__ __forceinline__ void row_mac(Acc<S> &acc, int4 raw, const typename Tr<S>::Op *g);
 template <>
@@ -385,7 +435,7 @@ template <>
 __device__ __forceinline__ void row_mac<Store::BF16>(Acc<Store::BF16> &acc, int4 raw, const float *g) {
     float4 x0 = *reinterpret_cast<const float4 *>(g);
     float4 x1 = *reinterpret_cast<const float4 *>(g + 4);
-    float c = 0.f;
+    float c = acc.ch;
     c = fmaf(bf_lo((uint32_t)raw.x), x0.x, c);
     c = fmaf(bf_hi((uint32_t)raw.x), x0.y, c);
     c = fmaf(bf_lo((uint32_t)raw.y), x0.z, c);
@@ -394,27 +444,34 @@ __device__ __forceinline__ void row_mac<Store::BF16>(Acc<Store::BF16> &acc, int4
     c = fmaf(bf_hi((uint32_t)raw.z), x1.y, c);
     c = fmaf(bf_lo((uint32_t)raw.w), x1.z, c);
     c = fmaf(bf_hi((uint32_t)raw.w), x1.w, c);
-    two_sum_acc(acc.a, c);  // one chunk of 8 products
+    acc.ch = c;
+    if (++acc.cnt == 4) { two_sum_acc(acc.a, acc.ch); acc.ch = 0.f; acc.cnt = 0; }  // chunk of 32
 }
 
+// the lane partial of one row as a reduction accumulator
 template <Store S>
-__device__ __forceinline__ DF row_total(Acc<S> &a) {
-    if constexpr (S == Store::F64) return DF{0.f, 0.f};
-    else { renorm(a.a); return a.a; }
+__device__ __forceinline__ typename RedT<S>::T row_partial(Acc<S> &a) {
+    if constexpr (S == Store::F64) return a.a;
+    else {
+        if constexpr (S == Store::BF16) { two_sum_acc(a.a, a.ch); a.ch = 0.f; }
+        renorm(a.a);
+        return a.a;
+    }
 }
 
 template <Store S, int MR>
-__global__ void __launch_bounds__(kP2Threads, MR == 4 ? 4 : 2) k_phase2(const P2Desc *__restrict__ desc, const Run *__restrict__ runs_g,
-                                                        const void *__restrict__ p2,
-                                                        const typename Tr<S>::Op *__restrict__ xs,
-                                                        const typename Tr<S>::Op *__restrict__ ts, int kc,
-                                                        double *__restrict__ y, const int32_t *__restrict__ out_perm,
-                                                        const SolverScalars *S_, int mode, int max_runs_smem) {
+__global__ void __launch_bounds__(kP2Threads, MR == 4 ? 4 : 2) k_phase2(const P2Desc *__restrict__ desc,
+                                                                       const void *__restrict__ p2,
+                                                                       const typename Tr<S>::Op *__restrict__ g, int kc,
+                                                                       double *__restrict__ y,
+                                                                       const int32_t *__restrict__ out_perm,
+                                                                       const SolverScalars *S_, int mode) {
     using Op = typename Tr<S>::Op;
+    using RT = typename RedT<S>::T;
     constexpr int VW = Tr<S>::VW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Op *g = reinterpret_cast<Op *>(smem_raw);
-    Run *runs_s = reinterpret_cast<Run *>(smem_raw + (size_t)kc * sizeof(Op));
+    Op *gs = reinterpret_cast<Op *>(smem_raw);
+    RT *red = reinterpret_cast<RT *>(smem_raw);  // reused after the last chunk
     if (skip_product(S_, mode)) return;
     const P2Desc d = desc[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -433,38 +490,18 @@ __global__ void __launch_bounds__(kP2Threads, MR == 4 ? 4 : 2) k_phase2(const P2
                                                  : make_int4(0, 0, 0, 0);
         }
     }
-    const bool runs_in_smem = d.rcnt <= max_runs_smem;
-    if (runs_in_smem)
-        for (int r = threadIdx.x; r < d.rcnt; r += blockDim.x) runs_s[r] = runs_g[d.rbeg + r];
-    const Run *runs = runs_in_smem ? runs_s : runs_g + d.rbeg;
-
     Acc<S> acc[MR];
 #pragma unroll
     for (int r = 0; r < MR; ++r) acc[r].init();
 
     for (int c0 = 0; c0 < d.ld; c0 += kc) {
         const int cw = min(kc, d.ld - c0);
-        __syncthreads();  // runs visible (first chunk); previous chunk consumed
-        for (int k = threadIdx.x; k < cw; k += blockDim.x) {
-            const int col = c0 + k;
-            Op v;
-            if (col >= d.K) {
-                if constexpr (S == Store::DF) v = make_float2(0.f, 0.f);
-                else v = (Op)0;
-            } else {
-                int lo = 0, hi = d.rcnt - 1;  // last run with dst <= col
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (runs[mid].dst <= col) lo = mid;
-                    else hi = mid - 1;
-                }
-                const Run rn = runs[lo];
-                const int src = rn.src + (col - rn.dst);
-                const int kind = rn.info & 0xff, e = (rn.info >> 8) - 512;
-                v = kind == 0 ? xs[src] : ts[src];
-                if (e != 0) v = scale_op<S>(v, e);
-            }
-            g[k] = v;
+        if (c0 > 0) __syncthreads();  // previous chunk consumed
+        {
+            const int4 *src = reinterpret_cast<const int4 *>(g + d.goff + c0);
+            int4 *dst = reinterpret_cast<int4 *>(gs);
+            const int nq = cw * (int)sizeof(Op) / 16;
+            for (int k = threadIdx.x; k < nq; k += blockDim.x) dst[k] = __ldcg(src + k);
         }
         __syncthreads();
         const int nv = cw / VW;
@@ -474,7 +511,7 @@ __global__ void __launch_bounds__(kP2Threads, MR == 4 ? 4 : 2) k_phase2(const P2
             if (v < nv) {
 #pragma unroll
                 for (int rr = 0; rr < MR; ++rr)
-                    if (warp + rr * kP2Warps < d.ylen) row_mac<S>(acc[rr], pre[rr], g + v * VW);
+                    if (warp + rr * kP2Warps < d.ylen) row_mac<S>(acc[rr], pre[rr], gs + v * VW);
             }
             v += 32;
         }
@@ -487,29 +524,26 @@ __global__ void __launch_bounds__(kP2Threads, MR == 4 ? 4 : 2) k_phase2(const P2
             }
 #pragma unroll
             for (int rr = 0; rr < MR; ++rr)
-                if (warp + rr * kP2Warps < d.ylen) row_mac<S>(acc[rr], raw[rr], g + v * VW);
+                if (warp + rr * kP2Warps < d.ylen) row_mac<S>(acc[rr], raw[rr], gs + v * VW);
         }
     }
-    // warp reductions, one output row per (warp, rr)
+    // row totals: lane partials through shared memory, summed in lane order
+    __syncthreads();
 #pragma unroll
     for (int rr = 0; rr < MR; ++rr) {
         const int i = warp + rr * kP2Warps;
-        if (i < d.ylen) {
-            double out;
-            if constexpr (S == Store::F64) {
-                double a = acc[rr].a;
-                for (int m = 16; m >= 1; m >>= 1) a += __shfl_xor_sync(0xffffffffu, a, m);
-                out = a;
-            } else {
-                DF a = row_total<S>(acc[rr]);
-                for (int m = 16; m >= 1; m >>= 1) a = df_add(a, df_shfl_xor(a, m));
-                out = df_to_double(a);
-            }
-            if (lane == 0) {
-                const int p = d.ybeg + i;
-                y[out_perm ? out_perm[p] : p] = out;
-            }
-        }
+        if (i < d.ylen) red[i * 32 + lane] = row_partial<S>(acc[rr]);
+    }
+    __syncthreads();
+    if (threadIdx.x < d.ylen) {
+        const int i = threadIdx.x;
+        RT a = red[i * 32];
+        for (int k = 1; k < 32; ++k) red_add<S>(a, red[i * 32 + k]);
+        double out;
+        if constexpr (S == Store::F64) out = a;
+        else out = df_to_double(a);
+        const int p = d.ybeg + i;
+        y[out_perm ? out_perm[p] : p] = out;
     }
 }
 
@@ -541,42 +575,28 @@ void launch_prep(Store s, const DevIndex &ix, const double *x, const int32_t *sr
 void launch_phase1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
                    cudaStream_t st) {
     HMAT_DISPATCH(s, (k_phase1<SS><<<ix.nleaves, kP1Threads, 0, st>>>(
-                         ix.p1, ix.p1_runs, P.q1, (const typename Tr<SS>::Op *)P.xs, (typename Tr<SS>::Part *)P.part,
-                         (typename Tr<SS>::Op *)P.ts, skipS, mode)));
+                         ix.p1, ix.p1_runs, ix.xdst, ix.lr, ix.gdst, P.q1, (const typename Tr<SS>::Op *)P.xs,
+                         (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g, P.ctr, skipS, mode)));
 }
-
-void launch_reduce(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                   cudaStream_t st) {
-    if (ix.nlr == 0) return;
-    const int warps_per_block = 8;
-    int blocks = (ix.nlr + warps_per_block - 1) / warps_per_block;
-    HMAT_DISPATCH(s, (k_reduce<SS><<<blocks, 32 * warps_per_block, 0, st>>>(
-                         ix.nlr, ix.rd, (const typename Tr<SS>::Part *)P.part,
-                         (typename Tr<SS>::Op *)P.ts, skipS, mode)));
-}
-
-static int max_runs_smem_for(const DevIndex &ix) { return ix.max_runs < 2048 ? ix.max_runs : 2048; }
 
 size_t phase2_smem_bytes(Store s, const DevIndex &ix) {
-    return (size_t)ix.kc * operand_bytes(s) + (size_t)max_runs_smem_for(ix) * sizeof(Run);
+    const size_t stage = (size_t)ix.kc * operand_bytes(s);
+    const size_t red = (size_t)ix.max_leaf * 32 * 8;  // row partials of the epilogue (8-byte accumulators)
+    return stage > red ? stage : red;
 }
 
 void launch_phase2(Store s, const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm,
                    const SolverScalars *skipS, int mode, cudaStream_t st) {
     size_t smem = phase2_smem_bytes(s, ix);
-    int mrs = max_runs_smem_for(ix);
     if (ix.max_leaf <= 4 * kP2Warps) {
         HMAT_DISPATCH(s, (k_phase2<SS, 4><<<ix.nleaves, kP2Threads, smem, st>>>(
-                             ix.p2, ix.runs, P.p2, (const typename Tr<SS>::Op *)P.xs,
-                             (const typename Tr<SS>::Op *)P.ts, ix.kc, y, out_perm, skipS, mode, mrs)));
+                             ix.p2, P.p2, (const typename Tr<SS>::Op *)P.g, ix.kc, y, out_perm, skipS, mode)));
     } else {
         HMAT_DISPATCH(s, (k_phase2<SS, kMaxLeaf / kP2Warps><<<ix.nleaves, kP2Threads, smem, st>>>(
-                             ix.p2, ix.runs, P.p2, (const typename Tr<SS>::Op *)P.xs,
-                             (const typename Tr<SS>::Op *)P.ts, ix.kc, y, out_perm, skipS, mode, mrs)));
+                             ix.p2, P.p2, (const typename Tr<SS>::Op *)P.g, ix.kc, y, out_perm, skipS, mode)));
     }
 }
 
-// Opt in to large dynamic shared memory for every phase-2 instantiation.
 template <int MR>
 static cudaError_t configure_phase2_mr(size_t max_smem) {
     cudaError_t e = cudaFuncSetAttribute(k_phase2<Store::DF, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);

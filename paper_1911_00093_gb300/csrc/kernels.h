@@ -10,14 +10,14 @@ namespace hmat_internal {
 
 // Device-resident packing indices (shared by every precision copy of a handle).
 struct DevIndex {
-    int32_t n = 0, nleaves = 0, nlr = 0;
+    int32_t n = 0, nleaves = 0, nlr = 0, nctr = 0;
     const int32_t *perm = nullptr;  // [n]
     const P1Desc *p1 = nullptr;     // [nleaves]
-    const RdDesc *rd = nullptr;     // [nlr] blocks spanning several leaf clusters
-    const Run *p1_runs = nullptr;
+    const P1Run *p1_runs = nullptr;
+    const XDst *xdst = nullptr;
+    const LrDesc *lr = nullptr;     // [nlr]
+    const int32_t *gdst = nullptr;
     const P2Desc *p2 = nullptr;     // [nleaves]
-    const Run *runs = nullptr;
-    int32_t max_runs = 0, max_runs1 = 0;
     int32_t kc = 0;                 // phase-2 column chunk staged in shared memory
     int32_t max_leaf = 0;           // rows of the widest leaf cluster
 };
@@ -28,8 +28,9 @@ struct DevPanels {
     const void *q1 = nullptr;  // phase-1 panels
     const void *p2 = nullptr;  // phase-2 panels
     void *xs = nullptr;        // source-vector operand, cluster order (n entries of the operand type)
-    void *part = nullptr;      // projection partial sums
-    void *ts = nullptr;        // t operand (tlen entries of the operand type)
+    void *part = nullptr;      // projection partial sums of multi-cluster blocks
+    void *g = nullptr;         // phase-2 operand buffers (glen entries of the operand type)
+    int32_t *ctr = nullptr;    // completion counters (zero between products)
 };
 
 // Operand bytes per entry for a store (x and t copies).
@@ -44,8 +45,6 @@ struct SolverScalars;
 // skipS/mode: a solver's product is skipped once its run has stopped (mode 1:
 // flag set; mode 2: flag set or stop at the ||s|| check); mode 0 never skips.
 void launch_phase1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                   cudaStream_t st);
-void launch_reduce(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
                    cudaStream_t st);
 // y[p] (cluster order) or y[out_perm[p]] (original order) = (A~ x)_p
 void launch_phase2(Store s, const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm,

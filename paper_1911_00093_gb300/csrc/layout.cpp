@@ -238,14 +238,14 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
     for (int64_t p = 0; p < n; ++p) L.perm[p] = (int32_t)v.perm[p];
     L.leaf_begin.resize(nleaves + 1);
     for (int64_t l = 0; l <= nleaves; ++l) L.leaf_begin[l] = (int32_t)v.leaf_begin[l];
+    for (int64_t l = 0; l < nleaves; ++l) L.max_leaf = std::max<int32_t>(L.max_leaf, L.leaf_begin[l + 1] - L.leaf_begin[l]);
     auto leaf_index = [&](int64_t x) {
         return (int64_t)(std::lower_bound(v.leaf_begin.begin(), v.leaf_begin.end(), x) - v.leaf_begin.begin());
     };
 
-    // exponents and t offsets
-    std::vector<int32_t> eD(nb, 0), eU(nb, 0), eV(nb, 0), toff(nb, -1);
+    // exponents, low-rank block numbering
+    std::vector<int32_t> eD(nb, 0), eU(nb, 0), eV(nb, 0), lrq(nb, -1);
     std::vector<int64_t> lr_blocks;
-    int64_t tlen = 0;
     for (int64_t b = 0; b < nb; ++b) {
         const int64_t *e = v.blocks + 8 * b;
         int64_t m = e[1] - e[0], w = e[3] - e[2], r = e[5];
@@ -253,42 +253,119 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
         L.stored_entries += e[4] == 0 ? m * w : r * (m + w);
         if (e[4] == 0) {
             eD[b] = exponent_of_max(d, m * w);
-        } else {
+        } else if (r > 0) {
             eU[b] = exponent_of_max(d, m * r);
             eV[b] = exponent_of_max(d + m * r, r * w);
+            lrq[b] = (int32_t)lr_blocks.size();
             lr_blocks.push_back(b);
-            toff[b] = (int32_t)tlen;
-            tlen += r;
             L.rank_sum += r;
         }
-        if (std::abs(eD[b]) > 400 || std::abs(eU[b]) > 400 || std::abs(eV[b]) > 400 || std::abs(eU[b] + eV[b]) > 400) {
+        if (std::abs(eD[b]) > kMaxScaleExp || std::abs(eU[b]) > kMaxScaleExp || std::abs(eV[b]) > kMaxScaleExp ||
+            std::abs(eU[b] + eV[b]) > kMaxScaleExp) {
             if (why) *why = "panel exponent out of range";
             return HMAT_ERR_RANGE;
         }
     }
-    if (tlen > (int64_t(1) << 30)) { if (why) *why = "too many ranks"; return HMAT_ERR_UNSUPPORTED; }
-    L.tlen = tlen;
+    const int64_t nlr = (int64_t)lr_blocks.size();
 
-    // phase 1: low-rank blocks per leaf column cluster, in block order
-    std::vector<std::vector<int64_t>> by_col(nleaves);
-    std::vector<int64_t> kfirst(nb, 0), kcnt(nb, 0), boff(nb, -1);
-    int64_t npart = 0;
-    for (int64_t b : lr_blocks) {
+    // phase 2 first: panel columns and operand buffers g per leaf row cluster
+    std::vector<std::vector<int64_t>> by_row(nleaves);
+    for (int64_t b = 0; b < nb; ++b) {
         const int64_t *e = v.blocks + 8 * b;
-        if (e[5] == 0) continue;
+        if (e[4] == 1 && e[5] == 0) continue;
+        for (int64_t l = leaf_index(e[0]); l < leaf_index(e[1]); ++l) by_row[l].push_back(b);
+    }
+    // column of block b in the panel of leaf rho, in block order per rho
+    std::vector<std::vector<std::pair<int64_t, int32_t>>> col_of(nleaves);
+    L.p2.resize(nleaves);
+    L.p2_slice_ptr.assign(nleaves + 1, 0);
+    int64_t off = 0, goff = 0;
+    for (int64_t k = 0; k < nleaves; ++k) {
+        P2Desc &d = L.p2[k];
+        d.ybeg = (int32_t)v.leaf_begin[k];
+        d.ylen = (int32_t)(v.leaf_begin[k + 1] - v.leaf_begin[k]);
+        int64_t col = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int64_t b : by_row[k]) {
+                const int64_t *e = v.blocks + 8 * b;
+                if (e[4] != pass) continue;
+                const int32_t len = (int32_t)(pass == 0 ? e[3] - e[2] : e[5]);
+                col_of[k].push_back({b, (int32_t)col});
+                L.p2_slices.push_back({b, (int32_t)col, len, (int32_t)(d.ybeg - e[0]), pass, pass == 0 ? eD[b] : eU[b]});
+                col += len;
+            }
+        }
+        d.K = (int32_t)col;
+        d.ld = (int32_t)roundup(std::max<int64_t>(col, 1), kPadElems);
+        d.off = off;
+        d.goff = (int32_t)goff;
+        d.pad = 0;
+        off += (int64_t)d.ld * d.ylen;
+        goff += d.ld;
+        L.phase2_entries += col * d.ylen;
+        L.max_ld2 = std::max(L.max_ld2, d.ld);
+        L.p2_slice_ptr[k + 1] = (int64_t)L.p2_slices.size();
+    }
+    if (goff > (int64_t(1) << 31) - 16) { if (why) *why = "operand buffer too large"; return HMAT_ERR_UNSUPPORTED; }
+    L.p2_elems = off;
+    L.glen = goff;
+    auto column_in = [&](int64_t rho, int64_t b) {
+        const auto &lst = col_of[rho];
+        for (const auto &pr : lst)
+            if (pr.first == b) return pr.second;
+        return -1;
+    };
+
+    // low-rank descriptors: operand destinations in every leaf row cluster of the block
+    std::vector<int64_t> kfirst(nb, 0), kcnt(nb, 0);
+    L.lr.resize(nlr);
+    int64_t npart = 0;
+    int32_t nctr = 0;
+    for (int64_t q = 0; q < nlr; ++q) {
+        const int64_t b = lr_blocks[q];
+        const int64_t *e = v.blocks + 8 * b;
+        LrDesc &d = L.lr[q];
         kfirst[b] = leaf_index(e[2]);
         kcnt[b] = leaf_index(e[3]) - kfirst[b];
+        d.rank = (int32_t)e[5];
+        d.cnt = (int32_t)kcnt[b];
+        d.scale = eU[b] + eV[b];
         if (kcnt[b] > 1) {
-            boff[b] = npart;
+            d.boff = (int32_t)npart;
             npart += kcnt[b] * e[5];
+            d.ctr = nctr++;
+        } else {
+            d.boff = -1;
+            d.ctr = -1;
         }
-        for (int64_t l = kfirst[b]; l < kfirst[b] + kcnt[b]; ++l) by_col[l].push_back(b);
+        d.gbeg = (int32_t)L.gdst.size();
+        for (int64_t rho = leaf_index(e[0]); rho < leaf_index(e[1]); ++rho) {
+            int32_t c = column_in(rho, b);
+            if (c < 0) { if (why) *why = "internal: block missing from a row panel"; return HMAT_ERR_BAD_LAYOUT; }
+            L.gdst.push_back(L.p2[rho].goff + c);
+        }
+        d.gcnt = (int32_t)L.gdst.size() - d.gbeg;
+        d.pad = 0;
     }
     if (npart > (int64_t(1) << 31) - 16) { if (why) *why = "too many partials"; return HMAT_ERR_UNSUPPORTED; }
     L.npart = npart;
+    L.nctr = nctr;
+
+    // phase 1: low-rank blocks per leaf column cluster (block order), and the
+    // dense-block operand slices each leaf column cluster feeds
+    std::vector<std::vector<int64_t>> by_col(nleaves), dense_by_col(nleaves);
+    for (int64_t q = 0; q < nlr; ++q) {
+        const int64_t b = lr_blocks[q];
+        for (int64_t l = kfirst[b]; l < kfirst[b] + kcnt[b]; ++l) by_col[l].push_back(b);
+    }
+    for (int64_t b = 0; b < nb; ++b) {
+        const int64_t *e = v.blocks + 8 * b;
+        if (e[4] != 0) continue;
+        for (int64_t l = leaf_index(e[2]); l < leaf_index(e[3]); ++l) dense_by_col[l].push_back(b);
+    }
     L.p1.resize(nleaves);
     L.p1_slice_ptr.assign(nleaves + 1, 0);
-    int64_t off = 0;
+    off = 0;
     for (int64_t k = 0; k < nleaves; ++k) {
         P1Desc &d = L.p1[k];
         d.xbeg = (int32_t)v.leaf_begin[k];
@@ -298,16 +375,12 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
         for (int64_t b : by_col[k]) {
             const int64_t *e = v.blocks + 8 * b;
             const int64_t r = e[5];
-            Run run;
-            run.dst = (int32_t)col;
+            const LrDesc &ld = L.lr[lrq[b]];
+            P1Run run;
+            run.col0 = (int32_t)col;
             run.len = (int32_t)r;
-            if (kcnt[b] > 1) {
-                run.src = (int32_t)(boff[b] + (k - kfirst[b]) * r);
-                run.info = 1 | (512 << 8);
-            } else {
-                run.src = toff[b];
-                run.info = 0 | ((eU[b] + eV[b] + 512) << 8);
-            }
+            run.q = lrq[b];
+            run.poff = ld.boff >= 0 ? (int32_t)(ld.boff + (k - kfirst[b]) * r) : -1;
             L.p1_runs.push_back(run);
             L.p1_slices.push_back({b, (int32_t)col, (int32_t)r, (int32_t)(d.xbeg - e[2]), 1, eV[b]});
             col += r;
@@ -317,81 +390,54 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
         d.ld = (int32_t)roundup(std::max<int64_t>(col, 1), kPadElems);
         d.off = off;
         off += (int64_t)d.ld * d.xlen;
+        d.xdbeg = (int32_t)L.xdst.size();
+        for (int64_t b : dense_by_col[k]) {
+            const int64_t *e = v.blocks + 8 * b;
+            for (int64_t rho = leaf_index(e[0]); rho < leaf_index(e[1]); ++rho) {
+                int32_t c = column_in(rho, b);
+                if (c < 0) { if (why) *why = "internal: dense block missing from a row panel"; return HMAT_ERR_BAD_LAYOUT; }
+                L.xdst.push_back({(int32_t)(L.p2[rho].goff + c + (d.xbeg - e[2])), eD[b]});
+            }
+        }
+        d.xdcnt = (int32_t)L.xdst.size() - d.xdbeg;
+        d.pad[0] = d.pad[1] = 0;
         L.phase1_entries += col * d.xlen;
         L.max_ld1 = std::max(L.max_ld1, d.ld);
         L.max_runs1 = std::max(L.max_runs1, d.rcnt);
         L.p1_slice_ptr[k + 1] = (int64_t)L.p1_slices.size();
     }
     L.p1_elems = off;
-
-    // reduction descriptors of the blocks that span several leaf clusters
-    for (int64_t b : lr_blocks) {
-        if (kcnt[b] <= 1) continue;
-        RdDesc d;
-        d.boff = (int32_t)boff[b];
-        d.cnt = (int32_t)kcnt[b];
-        d.toff = toff[b];
-        d.rank = (int32_t)v.blocks[8 * b + 5];
-        d.scale = eU[b] + eV[b];
-        d.pad[0] = d.pad[1] = d.pad[2] = 0;
-        L.rd.push_back(d);
-    }
-
-    // phase 2: dense then low-rank blocks per leaf row cluster, each in block order
-    std::vector<std::vector<int64_t>> by_row(nleaves);
-    for (int64_t b = 0; b < nb; ++b) {
-        const int64_t *e = v.blocks + 8 * b;
-        if (e[4] == 1 && e[5] == 0) continue;
-        for (int64_t l = leaf_index(e[0]); l < leaf_index(e[1]); ++l) by_row[l].push_back(b);
-    }
-    L.p2.resize(nleaves);
-    L.p2_slice_ptr.assign(nleaves + 1, 0);
-    off = 0;
-    for (int64_t k = 0; k < nleaves; ++k) {
-        P2Desc &d = L.p2[k];
-        d.ybeg = (int32_t)v.leaf_begin[k];
-        d.ylen = (int32_t)(v.leaf_begin[k + 1] - v.leaf_begin[k]);
-        d.rbeg = (int32_t)L.runs.size();
-        int64_t col = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int64_t b : by_row[k]) {
-                const int64_t *e = v.blocks + 8 * b;
-                if (e[4] != pass) continue;
-                int32_t len = (int32_t)(pass == 0 ? e[3] - e[2] : e[5]);
-                Run run;
-                run.dst = (int32_t)col;
-                run.len = len;
-                if (pass == 0) {
-                    run.src = (int32_t)e[2];
-                    run.info = 0 | ((eD[b] + 512) << 8);
-                    L.p2_slices.push_back({b, (int32_t)col, len, (int32_t)(d.ybeg - e[0]), 0, eD[b]});
-                } else {
-                    run.src = toff[b];
-                    run.info = 1 | (512 << 8);
-                    L.p2_slices.push_back({b, (int32_t)col, len, (int32_t)(d.ybeg - e[0]), 1, eU[b]});
-                }
-                L.runs.push_back(run);
-                col += len;
-            }
-        }
-        d.rcnt = (int32_t)L.runs.size() - d.rbeg;
-        d.K = (int32_t)col;
-        d.ld = (int32_t)roundup(std::max<int64_t>(col, 1), kPadElems);
-        d.off = off;
-        off += (int64_t)d.ld * d.ylen;
-        L.phase2_entries += col * d.ylen;
-        L.max_runs = std::max(L.max_runs, d.rcnt);
-        L.max_ld2 = std::max(L.max_ld2, d.ld);
-        L.p2_slice_ptr[k + 1] = (int64_t)L.p2_slices.size();
-    }
-    L.p2_elems = off;
     return HMAT_OK;
 }
 
 int check_layout(const Layout &L, std::string *why) {
-    // every index the kernels form stays inside its buffer
+    // every index the kernels form stays inside its buffer, and every operand
+    // slot of g is written exactly once per product
     auto bad = [&](const char *m) { if (why) *why = m; return HMAT_ERR_BAD_LAYOUT; };
     if ((int64_t)L.p1.size() != L.nleaves || (int64_t)L.p2.size() != L.nleaves) return bad("work list size");
+    std::vector<uint8_t> gw((size_t)L.glen, 0);
+    for (const P2Desc &d : L.p2) {
+        if (d.ylen < 1 || d.ylen > kMaxLeaf || d.ybeg < 0 || (int64_t)d.ybeg + d.ylen > L.n) return bad("p2 rows");
+        if (d.K < 0 || d.ld < d.K || d.ld % kPadElems || d.off % kPadElems || d.goff % kPadElems) return bad("p2 stride");
+        if (d.off < 0 || d.off + (int64_t)d.ylen * d.ld > L.p2_elems) return bad("p2 extent");
+        if (d.goff < 0 || (int64_t)d.goff + d.ld > L.glen) return bad("p2 operands");
+        for (int c = d.K; c < d.ld; ++c) gw[d.goff + c] = 2;  // zero padding, never written
+    }
+    for (const LrDesc &d : L.lr) {
+        if (d.rank < 1 || d.cnt < 1 || std::abs(d.scale) > kMaxScaleExp) return bad("lr desc");
+        if (d.cnt > 1 ? (d.boff < 0 || (int64_t)d.boff + (int64_t)d.cnt * d.rank > L.npart || d.ctr < 0 || d.ctr >= L.nctr)
+                      : (d.boff != -1 || d.ctr != -1))
+            return bad("lr partials");
+        if (d.gbeg < 0 || d.gcnt < 1 || (int64_t)d.gbeg + d.gcnt > (int64_t)L.gdst.size()) return bad("lr dst");
+        for (int k = 0; k < d.gcnt; ++k) {
+            int32_t g0 = L.gdst[d.gbeg + k];
+            if (g0 < 0 || (int64_t)g0 + d.rank > L.glen) return bad("lr dst range");
+            for (int l = 0; l < d.rank; ++l) {
+                if (gw[g0 + l]) return bad("operand slot written twice");
+                gw[g0 + l] = 1;
+            }
+        }
+    }
     for (const P1Desc &d : L.p1) {
         if (d.xlen < 1 || d.xlen > kMaxLeaf || d.xbeg < 0 || (int64_t)d.xbeg + d.xlen > L.n) return bad("p1 rows");
         if (d.R < 0 || d.ld < d.R || d.ld % kPadElems || d.off % kPadElems) return bad("p1 stride");
@@ -400,36 +446,28 @@ int check_layout(const Layout &L, std::string *why) {
         if (d.R > 0 && d.rcnt < 1) return bad("p1 empty runs");
         int64_t at = 0;
         for (int r = 0; r < d.rcnt; ++r) {
-            const Run &u = L.p1_runs[d.rbeg + r];
-            const int kind = u.info & 0xff;
-            if (u.dst != at || u.len < 1) return bad("p1 runs do not tile the panel");
-            if (kind == 0 ? (u.src < 0 || (int64_t)u.src + u.len > L.tlen) : (kind != 1 || u.src < 0 || (int64_t)u.src + u.len > L.npart))
-                return bad("p1 run output");
+            const P1Run &u = L.p1_runs[d.rbeg + r];
+            if (u.col0 != at || u.len < 1 || u.q < 0 || u.q >= (int32_t)L.lr.size()) return bad("p1 runs do not tile");
+            const LrDesc &ld = L.lr[u.q];
+            if (u.len != ld.rank) return bad("p1 run rank");
+            if (ld.cnt > 1 ? (u.poff < ld.boff || (int64_t)u.poff + u.len > (int64_t)ld.boff + (int64_t)ld.cnt * ld.rank)
+                           : u.poff != -1)
+                return bad("p1 run partial");
             at += u.len;
         }
         if (at != d.R) return bad("p1 runs do not cover R");
-    }
-    for (const RdDesc &d : L.rd) {
-        if (d.boff < 0 || d.cnt < 2 || d.rank < 1 || (int64_t)d.boff + (int64_t)d.cnt * d.rank > L.npart) return bad("rd partials");
-        if (d.toff < 0 || (int64_t)d.toff + d.rank > L.tlen) return bad("rd t");
-    }
-    for (const P2Desc &d : L.p2) {
-        if (d.ylen < 1 || d.ylen > kMaxLeaf || d.ybeg < 0 || (int64_t)d.ybeg + d.ylen > L.n) return bad("p2 rows");
-        if (d.K < 0 || d.ld < d.K || d.ld % kPadElems || d.off % kPadElems) return bad("p2 stride");
-        if (d.off < 0 || d.off + (int64_t)d.ylen * d.ld > L.p2_elems) return bad("p2 extent");
-        if (d.rbeg < 0 || d.rcnt < 0 || (int64_t)d.rbeg + d.rcnt > (int64_t)L.runs.size()) return bad("p2 runs");
-        if (d.K > 0 && d.rcnt < 1) return bad("p2 empty runs");
-        int64_t at = 0;
-        for (int r = 0; r < d.rcnt; ++r) {
-            const Run &u = L.runs[d.rbeg + r];
-            const int kind = u.info & 0xff;
-            if (u.dst != at || u.len < 1) return bad("runs do not tile the panel");
-            if (kind == 0 ? (u.src < 0 || (int64_t)u.src + u.len > L.n) : (kind != 1 || u.src < 0 || (int64_t)u.src + u.len > L.tlen))
-                return bad("run source");
-            at += u.len;
+        if (d.xdbeg < 0 || d.xdcnt < 0 || (int64_t)d.xdbeg + d.xdcnt > (int64_t)L.xdst.size()) return bad("p1 xdst");
+        for (int k = 0; k < d.xdcnt; ++k) {
+            const XDst &x = L.xdst[d.xdbeg + k];
+            if (x.goff < 0 || (int64_t)x.goff + d.xlen > L.glen || std::abs(x.scale) > kMaxScaleExp) return bad("xdst range");
+            for (int j = 0; j < d.xlen; ++j) {
+                if (gw[x.goff + j]) return bad("operand slot written twice");
+                gw[x.goff + j] = 1;
+            }
         }
-        if (at != d.K) return bad("runs do not cover K");
     }
+    for (int64_t k = 0; k < L.glen; ++k)
+        if (!gw[k]) return bad("operand slot never written");
     if ((int64_t)L.perm.size() != L.n) return bad("perm size");
     for (int32_t q : L.perm) if (q < 0 || q >= L.n) return bad("perm entry");
     return HMAT_OK;
