@@ -231,9 +231,9 @@ int hmat_info(hmat_handle h, hmat_handle_info *out);
  * hmat_time_matvec -- enqueue `iters` products of a fixed internal vector on
  * `stream` and time each kernel of the product with CUDA events recorded on
  * that stream; ms_out[0..3] receive the mean milliseconds per launch of the
- * source-vector preparation, the projection (t = W x, with its partial-sum
- * reduction and the operand scatter), 0 (no separate reduction launch) and the
- * expansion (y = D x + V t); ms_out[4] the mean per whole product.  `fp64` = 1 times the FP64 copy.  Synchronises `stream`.
+ * source-vector preparation, the projection (t = W x and the operand scatter),
+ * the reduction of the blocks spanning several leaf clusters and the expansion
+ * (y = D x + V t); ms_out[4] the mean per whole product.  `fp64` = 1 times the FP64 copy.  Synchronises `stream`.
  */
 int hmat_time_matvec(hmat_handle h, int32_t iters, int32_t fp64, void *stream, double *ms_out);
 

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -13,23 +14,11 @@
 #include "hmat.h"
 #include "hmat_internal.h"
 #include "kernels.h"
+#include "handle.h"
 
 using namespace hmat_internal;
 
 namespace {
-
-thread_local std::string g_cuda_error;
-
-bool cuda_ok(cudaError_t e, const char *what) {
-    if (e == cudaSuccess) return true;
-    g_cuda_error = std::string(what) + ": " + cudaGetErrorString(e);
-    return false;
-}
-
-#define CK(call)                                              \
-    do {                                                      \
-        if (!cuda_ok((call), #call)) return HMAT_ERR_CUDA;    \
-    } while (0)
 
 bool is_device_pointer(const void *p) {
     cudaPointerAttributes a;
@@ -52,62 +41,6 @@ Store store_of(int precision) {
 
 }  // namespace
 
-struct hmat_t {
-    int device = 0;
-    int precision = 0;
-    Store store = Store::DF, store64 = Store::DF;
-    bool separate64 = false;
-    DevIndex ix;
-    DevPanels P, P64;
-    std::vector<void *> allocs;
-    // solver state, cluster order
-    double *b = nullptr, *x = nullptr, *r = nullptr, *rt = nullptr, *p = nullptr, *v = nullptr, *s = nullptr,
-           *t = nullptr, *y = nullptr;
-    double *partials = nullptr;
-    SolverScalars *S = nullptr;
-    SolverScalars *S_host = nullptr;  // pinned
-    double *stage_in = nullptr, *stage_out = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    int graph_k = 0, graph_limit = -1;
-    // sizes
-    int64_t panel_bytes = 0, panel_bytes64 = 0, index_bytes = 0;
-    int64_t stored_entries = 0, phase1_entries = 0, phase2_entries = 0, partials_n = 0, rank_sum = 0;
-
-    ~hmat_t() {
-        int cur = 0;
-        cudaGetDevice(&cur);
-        cudaSetDevice(device);
-        if (graph) cudaGraphExecDestroy(graph);
-        if (cap_stream) cudaStreamDestroy(cap_stream);
-        for (void *a : allocs) cudaFree(a);
-        if (S_host) cudaFreeHost(S_host);
-        cudaSetDevice(cur);
-    }
-
-    template <class T>
-    int alloc(T **ptr, size_t bytes) {
-        void *q = nullptr;
-        if (bytes == 0) bytes = 16;
-        cudaError_t e = cudaMalloc(&q, bytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            g_cuda_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
-            return HMAT_ERR_NOMEM;
-        }
-        allocs.push_back(q);
-        *ptr = (T *)q;
-        return HMAT_OK;
-    }
-    template <class T>
-    int upload(T **ptr, const void *host, size_t bytes) {
-        int st = alloc(ptr, bytes);
-        if (st != HMAT_OK) return st;
-        if (bytes) CK(cudaMemcpy(*ptr, host, bytes, cudaMemcpyHostToDevice));
-        return HMAT_OK;
-    }
-};
-
 namespace {
 
 // y = A~ x for one vector, everything on the device.
@@ -117,6 +50,7 @@ void enqueue_product(hmat_t *h, const DevPanels &P, Store s, const double *x_src
                      double *y, const int32_t *out_perm, const SolverScalars *skipS, int mode, cudaStream_t st) {
     if (x_src) launch_prep(s, h->ix, x_src, src_perm, P.xs, st);
     launch_phase1(s, h->ix, P, skipS, mode, st);
+    launch_reduce(s, h->ix, P, skipS, mode, st);
     launch_phase2(s, h->ix, P, y, out_perm, skipS, mode, st);
 }
 
@@ -145,9 +79,6 @@ int alloc_panels(hmat_t *h, const BlobView &v, const Layout &L, Store s, DevPane
     st = h->alloc(&P.g, (size_t)std::max<int64_t>(L.glen, 1) * operand_bytes(s));
     if (st) return st;
     CK(cudaMemset(P.g, 0, (size_t)std::max<int64_t>(L.glen, 1) * operand_bytes(s)));  // zero padding columns
-    st = h->alloc(&P.ctr, (size_t)std::max<int32_t>(L.nctr, 1) * sizeof(int32_t));
-    if (st) return st;
-    CK(cudaMemset(P.ctr, 0, (size_t)std::max<int32_t>(L.nctr, 1) * sizeof(int32_t)));
     *bytes_out = (int64_t)(b1 + b2);
     return HMAT_OK;
 }
@@ -185,9 +116,11 @@ extern "C" int hmat_upload(const void *blob, size_t blob_bytes, int32_t precisio
         ix.n = (int32_t)L.n;
         ix.nleaves = L.nleaves;
         ix.nlr = (int32_t)L.lr.size();
-        ix.nctr = L.nctr;
+        ix.nbig = (int32_t)L.red_big.size();
+        ix.nsmall = (int32_t)L.red_small.size();
         ix.max_leaf = L.max_leaf;
-        int32_t *perm = nullptr, *gdst = nullptr;
+        ix.max_ld2 = L.max_ld2;
+        int32_t *perm = nullptr, *gdst = nullptr, *red_big = nullptr, *red_small = nullptr;
         P1Desc *p1 = nullptr;
         P1Run *p1_runs = nullptr;
         XDst *xdst = nullptr;
@@ -199,18 +132,16 @@ extern "C" int hmat_upload(const void *blob, size_t blob_bytes, int32_t precisio
             (st = h->upload(&xdst, L.xdst.data(), sizeof(XDst) * L.xdst.size())) ||
             (st = h->upload(&lr, L.lr.data(), sizeof(LrDesc) * L.lr.size())) ||
             (st = h->upload(&gdst, L.gdst.data(), 4 * L.gdst.size())) ||
+            (st = h->upload(&red_big, L.red_big.data(), 4 * L.red_big.size())) ||
+            (st = h->upload(&red_small, L.red_small.data(), 4 * L.red_small.size())) ||
             (st = h->upload(&p2, L.p2.data(), sizeof(P2Desc) * L.p2.size()))) {
             return st;
         }
         ix.perm = perm; ix.p1 = p1; ix.p1_runs = p1_runs; ix.xdst = xdst; ix.lr = lr; ix.gdst = gdst; ix.p2 = p2;
+        ix.red_big = red_big; ix.red_small = red_small;
         h->index_bytes = (int64_t)(4 * L.perm.size() + sizeof(P1Desc) * L.p1.size() + sizeof(P1Run) * L.p1_runs.size() +
                                    sizeof(XDst) * L.xdst.size() + sizeof(LrDesc) * L.lr.size() + 4 * L.gdst.size() +
-                                   sizeof(P2Desc) * L.p2.size());
-        // phase-2 column chunk: the widest panel if it fits 32 KB of operands
-        const int64_t kc_cap = (int64_t)(32768 / operand_bytes(Store::DF));
-        ix.kc = (int32_t)std::min<int64_t>(((int64_t)L.max_ld2 + 7) / 8 * 8, kc_cap);
-        size_t smem = std::max(phase2_smem_bytes(Store::DF, ix), phase2_smem_bytes(Store::F32, ix));
-        CK(configure_phase2(smem));
+                                   sizeof(P2Desc) * L.p2.size() + 4 * (L.red_big.size() + L.red_small.size()));
 
         // panels
         if ((st = alloc_panels(h, v, L, h->store, h->P, &h->panel_bytes))) return st;
@@ -225,7 +156,9 @@ extern "C" int hmat_upload(const void *blob, size_t blob_bytes, int32_t precisio
         double **vecs[] = {&h->b, &h->x, &h->r, &h->rt, &h->p, &h->v, &h->s, &h->t, &h->y, &h->stage_in, &h->stage_out};
         for (double **pp : vecs)
             if ((st = h->alloc(pp, nb))) return st;
-        if ((st = h->alloc(&h->partials, 8 * 2 * 4 * 152 * 2)) || (st = h->alloc(&h->S, sizeof(SolverScalars)))) {
+        if ((st = h->alloc(&h->partials, sizeof(double) * 2 * (size_t)vec_blocks(L.n))) ||
+            (st = h->alloc(&h->dpart, sizeof(double) * 2 * (size_t)L.nleaves)) ||
+            (st = h->alloc(&h->S, sizeof(SolverScalars)))) {
             return st;
         }
         CK(cudaMemset(h->S, 0, sizeof(SolverScalars)));
@@ -281,14 +214,17 @@ int matvec_impl(hmat_handle h, const double *x, double *y, int32_t nrhs, void *s
 void enqueue_iteration(hmat_t *h, int iter_limit, cudaStream_t st) {
     const int64_t n = h->ix.n;
     const Store s = h->store;
-    launch_count_iter(h->S, iter_limit, st);
     launch_update_p(s, n, h->r, h->p, h->v, h->P.xs, h->S, st);
-    enqueue_product(h, h->P, s, nullptr, nullptr, h->v, nullptr, h->S, 1, st);        // v = A p
-    launch_alpha(n, h->rt, h->v, h->S, h->partials, st);
+    // v = A p, with alpha = rho / (r~ . v)
+    launch_phase1(s, h->ix, h->P, h->S, 1, st);
+    launch_reduce(s, h->ix, h->P, h->S, 1, st);
+    launch_phase2(s, h->ix, h->P, h->v, nullptr, h->S, 1, st, h->rt, 1, h->S, h->dpart);
     launch_update_s(s, n, h->r, h->v, h->s, h->P.xs, h->x, h->p, h->S, h->partials, st);
-    enqueue_product(h, h->P, s, nullptr, nullptr, h->t, nullptr, h->S, 2, st);        // t = A s
-    launch_omega(n, h->t, h->s, h->S, h->partials, st);
-    launch_update_xr(n, h->x, h->p, h->s, h->t, h->r, h->rt, h->S, h->partials, st);
+    // t = A s, with omega = (t . s) / (t . t)
+    launch_phase1(s, h->ix, h->P, h->S, 2, st);
+    launch_reduce(s, h->ix, h->P, h->S, 2, st);
+    launch_phase2(s, h->ix, h->P, h->t, nullptr, h->S, 2, st, h->s, 2, h->S, h->dpart);
+    launch_update_xr(n, h->x, h->p, h->s, h->t, h->r, h->rt, h->S, h->partials, iter_limit, st);
 }
 
 int read_scalars(hmat_t *h, cudaStream_t st) {
@@ -307,10 +243,10 @@ int ensure_graph(hmat_t *h, int k, int iter_limit) {
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < k; ++i) enqueue_iteration(h, iter_limit, h->cap_stream);
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
-    if (!cuda_ok(e, "cudaStreamEndCapture")) return HMAT_ERR_CUDA;
+    if (!hmat_internal::cuda_ok(e, "cudaStreamEndCapture")) return HMAT_ERR_CUDA;
     e = cudaGraphInstantiate(&h->graph, g, 0);
     cudaGraphDestroy(g);
-    if (!cuda_ok(e, "cudaGraphInstantiate")) return HMAT_ERR_CUDA;
+    if (!hmat_internal::cuda_ok(e, "cudaGraphInstantiate")) return HMAT_ERR_CUDA;
     h->graph_k = k;
     h->graph_limit = iter_limit;
     return HMAT_OK;
@@ -350,10 +286,12 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = h->ix.n;
     const bool db = is_device_pointer(b), dx = is_device_pointer(x);
-    // kernels per product (source operand, projection, expansion) and per iteration (count, p update, two products
-    // without operand preparation, alpha, s update, omega, x/r update)
-    const int kProductLaunches = 3;
-    const int kIterationLaunches = 6 + 2 * (kProductLaunches - 1);
+    // kernels per product (source operand, projection, reduction when some block
+    // spans several leaf clusters, expansion) and per iteration (p update, two
+    // products without operand preparation whose expansions also give alpha and
+    // omega, s update, x/r update with the count of the next iteration)
+    const int kProductLaunches = (h->ix.nbig + h->ix.nsmall) ? 4 : 3;
+    const int kIterationLaunches = 3 + 2 * (kProductLaunches - 1);
     const double *bsrc = b;
     if (!db) {
         CK(cudaMemcpyAsync(h->stage_in, b, 8 * n, cudaMemcpyHostToDevice, st));
@@ -369,7 +307,7 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
     launch_gather(n, h->ix.perm, xsrc, h->x, st);
     CK(cudaMemsetAsync(h->S, 0, sizeof(SolverScalars), st));
     // ||b||
-    launch_residual(n, h->b, nullptr, h->r, h->rt, h->S, h->partials, st);
+    launch_residual(n, h->b, nullptr, h->r, h->rt, h->S, h->partials, -1, st);
     launches += 2;
     int rc = read_scalars(h, st);
     if (rc) return rc;
@@ -384,35 +322,35 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
     } else {
         // first run: r_0 = b - A~ x_0 with the iterated operator (Algorithm 1)
         enqueue_product(h, h->P, h->store, h->x, nullptr, h->y, nullptr, nullptr, 0, st);
-        launch_residual(n, h->b, h->y, h->r, h->rt, h->S, h->partials, st);
+        launch_residual(n, h->b, h->y, h->r, h->rt, h->S, h->partials, o.maxit, st);  // run 1 starts
         launches += kProductLaunches + 1;
         CK(cudaGetLastError());
         for (;;) {
-            // stop threshold of this run
+            // a run: its stop threshold, then batches of iterations until its flag is set
+            // (a run whose start already failed -- budget, non-finite -- goes straight on)
             if ((rc = read_scalars(h, st))) return rc;
-            if (h->S_host->flag != 0) { status = h->S_host->flag; break; }
-            double stop2 = std::max(o.tol * o.tol * bnorm2, o.inner_tol * o.inner_tol * h->S_host->rnorm2);
-            CK(cudaMemcpyAsync(&h->S->stop2, &stop2, sizeof(double), cudaMemcpyHostToDevice, st));
-            CK(cudaStreamSynchronize(st));
-            // iterations
-            for (;;) {
-                launches += o.check_every * kIterationLaunches;
-                if (o.use_graph) {
-                    if ((rc = ensure_graph(h, o.check_every, o.maxit))) return rc;
-                    CK(cudaGraphLaunch(h->graph, st));
-                } else {
-                    for (int i = 0; i < o.check_every; ++i) enqueue_iteration(h, o.maxit, st);
-                    CK(cudaGetLastError());
+            if (h->S_host->flag == 0) {
+                double stop2 = std::max(o.tol * o.tol * bnorm2, o.inner_tol * o.inner_tol * h->S_host->rnorm2);
+                CK(cudaMemcpyAsync(&h->S->stop2, &stop2, sizeof(double), cudaMemcpyHostToDevice, st));
+                for (;;) {
+                    launches += o.check_every * kIterationLaunches;
+                    if (o.use_graph) {
+                        if ((rc = ensure_graph(h, o.check_every, o.maxit))) return rc;
+                        CK(cudaGraphLaunch(h->graph, st));
+                    } else {
+                        for (int i = 0; i < o.check_every; ++i) enqueue_iteration(h, o.maxit, st);
+                        CK(cudaGetLastError());
+                    }
+                    if ((rc = read_scalars(h, st))) return rc;
+                    if (h->S_host->flag != 0) break;
                 }
-                if ((rc = read_scalars(h, st))) return rc;
-                if (h->S_host->flag != 0) break;
             }
             const int flag = h->S_host->flag;
             inf.relres_inner = std::sqrt(h->S_host->rnorm2 / bnorm2);
             inf.iters = h->S_host->iters;
             // true residual with the FP64 H-matrix (Section 4.1.3); r~ = r for a restart
             enqueue_product(h, h->P64, h->store64, h->x, nullptr, h->y, nullptr, nullptr, 0, st);
-            launch_residual(n, h->b, h->y, h->r, h->rt, h->S, h->partials, st);
+            launch_residual(n, h->b, h->y, h->r, h->rt, h->S, h->partials, -1, st);
             launches += kProductLaunches + 1;
             inf.matvecs_fp64 += 1;
             if ((rc = read_scalars(h, st))) return rc;
@@ -423,6 +361,8 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
             if (rel <= o.tol) { status = HMAT_OK; break; }
             if (inf.restarts >= o.max_restarts) { status = HMAT_ERR_MAXIT; break; }
             inf.restarts += 1;
+            launch_count_iter(h->S, o.maxit, st);  // the restarted run starts
+            launches += 1;
         }
     }
     // products with the iterated operator: r_0, then two per iteration except a stop at ||s||
@@ -483,6 +423,7 @@ extern "C" int hmat_time_matvec(hmat_handle h, int32_t iters, int32_t fp64, void
         CK(cudaEventRecord(ev[1], st));
         launch_phase1(s, h->ix, P, nullptr, 0, st);
         CK(cudaEventRecord(ev[2], st));
+        launch_reduce(s, h->ix, P, nullptr, 0, st);
         CK(cudaEventRecord(ev[3], st));
         launch_phase2(s, h->ix, P, h->stage_out, nullptr, nullptr, 0, st);
         CK(cudaEventRecord(ev[4], st));
@@ -518,4 +459,9 @@ extern "C" const char *hmat_strerror(int status) {
     }
 }
 
-extern "C" const char *hmat_last_cuda_error(void) { return g_cuda_error.c_str(); }
+std::string &hmat_internal::last_cuda_error() {
+    static thread_local std::string s;
+    return s;
+}
+
+extern "C" const char *hmat_last_cuda_error(void) { return hmat_internal::last_cuda_error().c_str(); }

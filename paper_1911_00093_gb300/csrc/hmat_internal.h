@@ -43,9 +43,9 @@ int parse_blob(const void *blob, size_t bytes, BlobView &view, std::string *why 
 // Phase 1, one work item per leaf column cluster kappa: a row-major |kappa| x R
 // panel whose columns are the rank vectors of every W_m (eq. 9/22) whose column
 // cluster contains kappa, restricted to kappa.  Its R dot products with x_kappa
-// are either final (the block's column cluster is kappa) or partial sums that
-// the last phase-1 work item to finish the block adds up in a fixed order.
-// Phase 1 also writes every operand phase 2 needs into per-row-cluster operand
+// are either final (the block's column cluster is kappa) or block-major partial
+// sums that a reduction launch adds up in a fixed order.  Phase 1 and the
+// reduction write every operand phase 2 needs into per-row-cluster operand
 // buffers g: the slices 2^e x_kappa of the dense blocks over kappa, and each
 // block's 2^e t = 2^e W_m x_m for every leaf row cluster of the block.
 //
@@ -77,8 +77,7 @@ struct LrDesc {
     int32_t scale;  // exponent e of 2^e t
     int32_t gbeg;   // first entry of gdst (one per leaf row cluster of the block)
     int32_t gcnt;
-    int32_t ctr;    // completion counter index (multi-cluster blocks), -1 otherwise
-    int32_t pad;
+    int32_t pad[2];
 };
 struct XDst {
     int32_t goff;   // operand index of x_kappa[0] in g
@@ -95,6 +94,7 @@ struct P2Desc {
 };
 
 constexpr int kMaxScaleExp = 120;  // |e| of every stored power-of-two scale
+constexpr int kRedBigCnt = 32;     // blocks over this many leaf clusters are reduced by a whole CTA
 
 struct Layout {
     int64_t n = 0;
@@ -109,7 +109,7 @@ struct Layout {
     std::vector<P2Desc> p2;
     int64_t p1_elems = 0, p2_elems = 0;
     int64_t npart = 0, glen = 0;
-    int32_t nctr = 0;
+    std::vector<int32_t> red_big, red_small;  // multi-cluster blocks: >= kRedBigCnt clusters / fewer
     int32_t max_ld2 = 0, max_ld1 = 0, max_runs1 = 0, max_leaf = 0;
     int64_t stored_entries = 0, phase1_entries = 0, phase2_entries = 0, rank_sum = 0;
     // source of each packed entry, used to fill typed panels without

@@ -242,56 +242,43 @@ template <Store S> __device__ __forceinline__ void red_add_part(typename RedT<S>
 template <Store S> __device__ __forceinline__ void red_add(typename RedT<S>::T &a, typename RedT<S>::T b) {
     if constexpr (S == Store::F64) a += b; else a = df_add(a, b);
 }
+template <Store S>
+__device__ __forceinline__ typename RedT<S>::T red_xor(typename RedT<S>::T a, int m, bool upper) {
+    typename RedT<S>::T b;
+    if constexpr (S == Store::F64) b = __shfl_xor_sync(0xffffffffu, a, m);
+    else { b.s = __shfl_xor_sync(0xffffffffu, a.s, m); b.c = __shfl_xor_sync(0xffffffffu, a.c, m); }
+    if (upper) { red_add<S>(b, a); return b; }
+    red_add<S>(a, b);
+    return a;
+}
+
 template <Store S> __device__ __forceinline__ typename Tr<S>::Part red_to_part(typename RedT<S>::T a) {
     if constexpr (S == Store::F64) return a;
     else if constexpr (S == Store::DF) { renorm(a); return make_float2(a.s, a.c); }
     else return __fadd_rn(a.s, a.c);
 }
 
-template <Store S>
-__device__ __forceinline__ typename Tr<S>::Part load_part(const typename Tr<S>::Part *p) {
-    if constexpr (S == Store::DF) return __ldcg(p);
-    else return __ldcg(p);
-}
-
 // ------------------------------------------------------------------------
 // phase 1: per leaf column cluster kappa
 // ------------------------------------------------------------------------
 constexpr int kP1Threads = 256;
-constexpr int kP1RunsSmem = 512;
 
 template <Store S>
-__global__ void __launch_bounds__(kP1Threads) k_phase1(const P1Desc *__restrict__ desc, const P1Run *__restrict__ runs_g,
+__global__ void __launch_bounds__(kP1Threads) k_phase1(const P1Desc *__restrict__ desc, const P1Run *__restrict__ runs,
                                                         const XDst *__restrict__ xdst, const LrDesc *__restrict__ lr,
                                                         const int32_t *__restrict__ gdst, const void *__restrict__ q1,
                                                         const typename Tr<S>::Op *__restrict__ xs,
-                                                        typename Tr<S>::Part *part, typename Tr<S>::Op *__restrict__ g,
-                                                        int32_t *ctr, const SolverScalars *S_, int mode) {
+                                                        typename Tr<S>::Part *__restrict__ part,
+                                                        typename Tr<S>::Op *__restrict__ g, const SolverScalars *S_,
+                                                        int mode) {
     using Op = typename Tr<S>::Op;
     using Part = typename Tr<S>::Part;
-    using RT = typename RedT<S>::T;
     constexpr int VW = Tr<S>::VW;
-    __shared__ Op xk[kMaxLeaf];
-    __shared__ P1Run runs_s[kP1RunsSmem];
-    __shared__ int32_t done_q[kP1RunsSmem];
-    __shared__ int32_t ndone;
-    __shared__ RT red[kP1Threads];
+    __shared__ Op xk[kMaxLeaf];  // x_kappa, broadcast to every thread
     if (skip_product(S_, mode)) return;
     const P1Desc d = desc[blockIdx.x];
     for (int j = threadIdx.x; j < d.xlen; j += blockDim.x) xk[j] = xs[d.xbeg + j];
-    const bool runs_in_smem = d.rcnt <= kP1RunsSmem;
-    if (runs_in_smem)
-        for (int r = threadIdx.x; r < d.rcnt; r += blockDim.x) runs_s[r] = runs_g[d.rbeg + r];
-    const P1Run *runs = runs_in_smem ? runs_s : runs_g + d.rbeg;
-    if (threadIdx.x == 0) ndone = 0;
     __syncthreads();
-
-    // the dense-block operands fed by x_kappa (eq. 21 inputs), scaled by 2^e
-    for (int t = threadIdx.x; t < d.xdcnt * d.xlen; t += blockDim.x) {
-        const int k = t / d.xlen, j = t - k * d.xlen;
-        const XDst x = xdst[d.xdbeg + k];
-        g[x.goff + j] = scale_op<S>(xk[j], x.scale);
-    }
 
     // projections (eq. 9/22): thread = one 16-byte column vector, walk the rows
     const int nvec = d.ld / VW;
@@ -318,18 +305,19 @@ __global__ void __launch_bounds__(kP1Threads) k_phase1(const P1Desc *__restrict_
         }
         const int c0 = vc * VW;
         if (c0 >= d.R) continue;
+        const P1Run *rk = runs + d.rbeg;
         int lo = 0, hi = d.rcnt - 1;  // run holding column c0
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
-            if (runs[mid].col0 <= c0) lo = mid;
+            if (__ldg(&rk[mid].col0) <= c0) lo = mid;
             else hi = mid - 1;
         }
+        P1Run rn = rk[lo];
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
             const int c = c0 + e;
             if (c < d.R) {
-                while (c >= runs[lo].col0 + runs[lo].len) ++lo;
-                const P1Run rn = runs[lo];
+                while (c >= rn.col0 + rn.len) rn = rk[++lo];
                 const int l = c - rn.col0;
                 const Part pv = to_part<S>(acc[e]);
                 if (rn.poff >= 0) {
@@ -343,55 +331,88 @@ __global__ void __launch_bounds__(kP1Threads) k_phase1(const P1Desc *__restrict_
         }
     }
 
-    // blocks spanning several leaf clusters: the work item that completes one
-    // sums its partials in a fixed order (integer ticket; no waiting)
-    __threadfence();
-    for (int r0 = 0; r0 < d.rcnt; r0 += kP1RunsSmem) {
-        __syncthreads();
-        if (threadIdx.x == 0) ndone = 0;
-        __syncthreads();
-        const int r1 = min(d.rcnt, r0 + kP1RunsSmem);
-        for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-            const P1Run rn = runs[r];
-            if (rn.poff >= 0) {
-                const LrDesc ld = lr[rn.q];
-                if (atomicAdd(&ctr[ld.ctr], 1) == ld.cnt - 1) done_q[atomicAdd(&ndone, 1)] = rn.q;
+    // the dense-block operands fed by x_kappa (eq. 21 inputs), scaled by 2^e
+    for (int t = threadIdx.x; t < d.xdcnt * d.xlen; t += blockDim.x) {
+        const int k = t / d.xlen, j = t - k * d.xlen;
+        const XDst x = xdst[d.xdbeg + k];
+        g[x.goff + j] = scale_op<S>(xk[j], x.scale);
+    }
+}
+
+// ------------------------------------------------------------------------
+// reduce: t of the blocks spanning several leaf clusters, in a fixed order,
+// scattered to the operand buffers.  Blocks over >= kRedBigCnt clusters get a
+// whole CTA (kernel blocks [0, nbig)), the others one warp each.
+// ------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+
+template <Store S>
+__global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int nsmall, const int32_t *__restrict__ big,
+                                                         const int32_t *__restrict__ small,
+                                                         const LrDesc *__restrict__ lr, const int32_t *__restrict__ gdst,
+                                                         const typename Tr<S>::Part *__restrict__ part,
+                                                         typename Tr<S>::Op *__restrict__ g, const SolverScalars *S_,
+                                                         int mode) {
+    using Op = typename Tr<S>::Op;
+    using RT = typename RedT<S>::T;
+    __shared__ RT red[kRedThreads];
+    if (skip_product(S_, mode)) return;
+    if ((int)blockIdx.x < nbig) {
+        const LrDesc ld = lr[big[blockIdx.x]];
+        for (int l0 = 0; l0 < ld.rank; l0 += 32) {
+            const int rr = min(32, ld.rank - l0);
+            int rp = 1;
+            while (rp < rr) rp <<= 1;
+            const int G = kRedThreads / rp, gi = threadIdx.x / rp, l = threadIdx.x % rp;
+            RT a;
+            red_zero<S>(a);
+            if (l < rr) {
+                const typename Tr<S>::Part *src = part + ld.boff + l0 + l;
+#pragma unroll 4
+                for (int k = gi; k < ld.cnt; k += G) red_add_part<S>(a, src[(size_t)k * ld.rank]);
             }
+            red[threadIdx.x] = a;
+            __syncthreads();
+            for (int half = G >> 1; half >= 1; half >>= 1) {
+                if (gi < half) {
+                    RT c = red[threadIdx.x];
+                    red_add<S>(c, red[threadIdx.x + half * rp]);
+                    red[threadIdx.x] = c;
+                }
+                __syncthreads();
+            }
+            // every thread scatters: destination k, rank l
+            for (int idx = threadIdx.x; idx < ld.gcnt * rr; idx += kRedThreads) {
+                const int k = idx / rr, ll = idx - k * rr;
+                g[gdst[ld.gbeg + k] + l0 + ll] = part_to_op<S>(red_to_part<S>(red[ll]), ld.scale);
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        const int nd = ndone;  // <= r1 - r0 <= kP1RunsSmem
-        if (nd == 0) continue;
-        __threadfence();
-        for (int i = 0; i < nd; ++i) {
-            const LrDesc ld = lr[done_q[i]];
-            for (int l0 = 0; l0 < ld.rank; l0 += 32) {
-                const int rr = min(32, ld.rank - l0);
-                int rp = 1;
-                while (rp < rr) rp <<= 1;
-                const int G = kP1Threads / rp, gi = threadIdx.x / rp, l = threadIdx.x % rp;
-                RT a;
-                red_zero<S>(a);
-                if (l < rr)
-                    for (int k = gi; k < ld.cnt; k += G)
-                        red_add_part<S>(a, load_part<S>(part + ld.boff + (size_t)k * ld.rank + l0 + l));
-                red[threadIdx.x] = a;
-                __syncthreads();
-                for (int half = G >> 1; half >= 1; half >>= 1) {
-                    if (gi < half) {
-                        RT b = red[threadIdx.x + half * rp];
-                        RT c = red[threadIdx.x];
-                        red_add<S>(c, b);
-                        red[threadIdx.x] = c;
-                    }
-                    __syncthreads();
-                }
-                if (gi == 0 && l < rr) {
-                    const Op o = part_to_op<S>(red_to_part<S>(red[l]), ld.scale);
-                    for (int k = 0; k < ld.gcnt; ++k) g[gdst[ld.gbeg + k] + l0 + l] = o;
-                }
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) ctr[ld.ctr] = 0;
+        return;
+    }
+    // smaller blocks: one warp each; lane groups split the leaf clusters, a fixed
+    // butterfly adds the groups
+    const int wq = ((int)blockIdx.x - nbig) * (kRedThreads / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (wq >= nsmall) return;
+    const LrDesc ld = lr[small[wq]];
+    for (int l0 = 0; l0 < ld.rank; l0 += 32) {
+        const int rr = min(32, ld.rank - l0);
+        int rp = 1;
+        while (rp < rr) rp <<= 1;
+        const int G = 32 / rp, gi = lane / rp, l = lane % rp;
+        RT a;
+        red_zero<S>(a);
+        if (l < rr) {
+            const typename Tr<S>::Part *src = part + ld.boff + l0 + l;
+#pragma unroll 4
+            for (int k = gi; k < ld.cnt; k += G) red_add_part<S>(a, src[(size_t)k * ld.rank]);
+        }
+        for (int m = rp; m < 32; m <<= 1) a = red_xor<S>(a, m, (gi & (m / rp)) != 0);
+        // the butterfly leaves the same total in every lane group: groups share the destinations
+        if (l < rr) {
+            const Op o = part_to_op<S>(red_to_part<S>(a), ld.scale);
+            for (int k = gi; k < ld.gcnt; k += G) g[gdst[ld.gbeg + k] + l0 + l] = o;
         }
     }
 }
@@ -402,28 +423,52 @@ __global__ void __launch_bounds__(kP1Threads) k_phase1(const P1Desc *__restrict_
 constexpr int kP2Threads = 256;
 constexpr int kP2Warps = kP2Threads / 32;
 
-// Multiply one 16-byte panel vector by VW consecutive operands (one row).
+// The VW operands matching one 16-byte panel vector, loaded as vectors through
+// L1 (operand buffers are 16-byte aligned per row cluster).
+template <Store S> struct GV;
+template <> struct GV<Store::DF> {
+    float4 v;  // (hi, lo) of two operands
+    __device__ static GV load(const float2 *p) { GV r; r.v = __ldg(reinterpret_cast<const float4 *>(p)); return r; }
+};
+template <> struct GV<Store::F64> {
+    double2 v;
+    __device__ static GV load(const double *p) { GV r; r.v = __ldg(reinterpret_cast<const double2 *>(p)); return r; }
+};
+template <> struct GV<Store::F32> {
+    float4 v;
+    __device__ static GV load(const float *p) { GV r; r.v = __ldg(reinterpret_cast<const float4 *>(p)); return r; }
+};
+template <> struct GV<Store::BF16> {
+    float4 a, b;
+    __device__ static GV load(const float *p) {
+        GV r;
+        r.a = __ldg(reinterpret_cast<const float4 *>(p));
+        r.b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+        return r;
+    }
+};
+
+// Multiply one 16-byte panel vector by its VW operands (one row).
 template <Store S>
-__device__ __forceinline__ void row_mac(Acc<S> &acc, int4 raw, const typename Tr<S>::Op *g);
+__device__ __forceinline__ void row_mac(Acc<S> &acc, int4 raw, const GV<S> &gv);
 template <>
-__device__ __forceinline__ void row_mac<Store::DF>(Acc<Store::DF> &acc, int4 raw, const float2 *g) {
+__device__ __forceinline__ void row_mac<Store::DF>(Acc<Store::DF> &acc, int4 raw, const GV<Store::DF> &gv) {
     float4 v = *reinterpret_cast<float4 *>(&raw);
-    float4 x = *reinterpret_cast<const float4 *>(g);
+    const float4 x = gv.v;
     df_fma(acc.a, v.x, v.y, x.x, x.y);
     df_fma(acc.a, v.z, v.w, x.z, x.w);
     if (++acc.n == 4) { renorm(acc.a); acc.n = 0; }
 }
 template <>
-__device__ __forceinline__ void row_mac<Store::F64>(Acc<Store::F64> &acc, int4 raw, const double *g) {
+__device__ __forceinline__ void row_mac<Store::F64>(Acc<Store::F64> &acc, int4 raw, const GV<Store::F64> &gv) {
     double2 v = *reinterpret_cast<double2 *>(&raw);
-    double2 x = *reinterpret_cast<const double2 *>(g);
-    acc.a = fma(v.x, x.x, acc.a);
-    acc.a = fma(v.y, x.y, acc.a);
+    acc.a = fma(v.x, gv.v.x, acc.a);
+    acc.a = fma(v.y, gv.v.y, acc.a);
 }
 template <>
-__device__ __forceinline__ void row_mac<Store::F32>(Acc<Store::F32> &acc, int4 raw, const float *g) {
+__device__ __forceinline__ void row_mac<Store::F32>(Acc<Store::F32> &acc, int4 raw, const GV<Store::F32> &gv) {
     float4 v = *reinterpret_cast<float4 *>(&raw);
-    float4 x = *reinterpret_cast<const float4 *>(g);
+    const float4 x = gv.v;
     float c = 0.f;
     c = fmaf(v.x, x.x, c);
     c = fmaf(v.y, x.y, c);
@@ -432,9 +477,8 @@ __device__ __forceinline__ void row_mac<Store::F32>(Acc<Store::F32> &acc, int4 r
     two_sum_acc(acc.a, c);  // one chunk of 4 products
 }
 template <>
-__device__ __forceinline__ void row_mac<Store::BF16>(Acc<Store::BF16> &acc, int4 raw, const float *g) {
-    float4 x0 = *reinterpret_cast<const float4 *>(g);
-    float4 x1 = *reinterpret_cast<const float4 *>(g + 4);
+__device__ __forceinline__ void row_mac<Store::BF16>(Acc<Store::BF16> &acc, int4 raw, const GV<Store::BF16> &gv) {
+    const float4 x0 = gv.a, x1 = gv.b;
     float c = acc.ch;
     c = fmaf(bf_lo((uint32_t)raw.x), x0.x, c);
     c = fmaf(bf_hi((uint32_t)raw.x), x0.y, c);
@@ -459,92 +503,146 @@ __device__ __forceinline__ typename RedT<S>::T row_partial(Acc<S> &a) {
     }
 }
 
+// BiCG-STAB scalars fused into the expansion of a solver product (Algorithm 1):
+//   dotmode 1: alpha = rho / (r~ . v)          (w = r~, y = v)
+//   dotmode 2: omega = (t . s) / (t . t)       (w = s,  y = t)
+// Each work item adds its rows in a fixed order; the last one to finish (integer
+// ticket, no waiting) adds the per-item sums in work-item order.
+__device__ void fused_dots(const P2Desc &d, double out, const double *__restrict__ w, int dotmode, SolverScalars *Sd,
+                           double *dpart) {
+    __shared__ double dsm[2][kMaxLeaf];
+    __shared__ double tot[2][kP2Threads];
+    __shared__ bool am_last;
+    const int t = threadIdx.x;
+    if (t < kMaxLeaf) {
+        const bool live = t < d.ylen;
+        const double wv = live ? w[d.ybeg + t] : 0.0;
+        dsm[0][t] = live ? wv * out : 0.0;
+        dsm[1][t] = live ? out * out : 0.0;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < d.ylen; ++i) { a += dsm[0][i]; b += dsm[1][i]; }
+        dpart[blockIdx.x] = a;
+        dpart[gridDim.x + blockIdx.x] = b;
+        __threadfence();
+        am_last = atomicAdd(&Sd->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int k = t; k < (int)gridDim.x; k += blockDim.x) {
+        a += __ldcg(&dpart[k]);
+        b += __ldcg(&dpart[gridDim.x + k]);
+    }
+    tot[0][t] = a;
+    tot[1][t] = b;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (t < s) { tot[0][t] += tot[0][t + s]; tot[1][t] += tot[1][t + s]; }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double wy = tot[0][0], yy = tot[1][0];
+        if (dotmode == 1) {
+            Sd->rtv = wy;
+            Sd->alpha = Sd->rho / wy;
+            if (!isfinite(Sd->alpha)) Sd->flag = HMAT_ERR_NONFINITE;
+        } else {
+            Sd->ts = wy;
+            Sd->tt = yy;
+            Sd->omega = yy == 0.0 ? 0.0 : wy / yy;
+            if (!isfinite(Sd->omega)) Sd->flag = HMAT_ERR_NONFINITE;
+        }
+        Sd->ticket = 0u;
+    }
+}
+
+
+// Row totals of a phase-2 work item: each warp adds its rows' lane partials with
+// a fixed butterfly; lane 0 writes y.  Returns this thread's row value (rows in
+// thread order: thread t holds row t) through shared memory for the fused dots.
 template <Store S, int MR>
-__global__ void __launch_bounds__(kP2Threads, MR == 4 ? 4 : 2) k_phase2(const P2Desc *__restrict__ desc,
+__device__ __forceinline__ double phase2_epilogue(const P2Desc &d, Acc<S> (&acc)[MR], double *__restrict__ y,
+                                                  const int32_t *__restrict__ out_perm, double *rowval) {
+    using RT = typename RedT<S>::T;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int rr = 0; rr < MR; ++rr) {
+        const int i = warp + rr * kP2Warps;
+        if (i < d.ylen) {
+            RT a = row_partial<S>(acc[rr]);
+            for (int m = 1; m < 32; m <<= 1) a = red_xor<S>(a, m, (lane & m) != 0);
+            double out;
+            if constexpr (S == Store::F64) out = a;
+            else out = df_to_double(a);
+            if (lane == 0) {
+                const int p = d.ybeg + i;
+                y[out_perm ? out_perm[p] : p] = out;
+                rowval[i] = out;
+            }
+        }
+    }
+    __syncthreads();
+    return threadIdx.x < d.ylen ? rowval[threadIdx.x] : 0.0;
+}
+
+template <Store S, int MR>
+__global__ void __launch_bounds__(kP2Threads, MR == 4 ? 3 : 2) k_phase2(const P2Desc *__restrict__ desc,
                                                                        const void *__restrict__ p2,
-                                                                       const typename Tr<S>::Op *__restrict__ g, int kc,
+                                                                       const typename Tr<S>::Op *__restrict__ g,
                                                                        double *__restrict__ y,
                                                                        const int32_t *__restrict__ out_perm,
-                                                                       const SolverScalars *S_, int mode) {
+                                                                       const SolverScalars *S_, int mode,
+                                                                       const double *__restrict__ w, int dotmode,
+                                                                       SolverScalars *Sd, double *dpart) {
     using Op = typename Tr<S>::Op;
-    using RT = typename RedT<S>::T;
     constexpr int VW = Tr<S>::VW;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Op *gs = reinterpret_cast<Op *>(smem_raw);
-    RT *red = reinterpret_cast<RT *>(smem_raw);  // reused after the last chunk
+    __shared__ double rowval[kMaxLeaf];
     if (skip_product(S_, mode)) return;
     const P2Desc d = desc[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const size_t esz = 16 / VW;
     const char *base = (const char *)p2 + (size_t)d.off * esz;
     const size_t row_bytes = (size_t)d.ld * esz;
+    const Op *gr = g + d.goff;  // operands of this row cluster, read through L1 by every warp
 
-    // the first vector of each of this warp's rows, in flight while g is staged
-    int4 pre[MR];
-    {
-        const int nv0 = min(kc, d.ld) / VW;
-#pragma unroll
-        for (int rr = 0; rr < MR; ++rr) {
-            const int i = warp + rr * kP2Warps;
-            pre[rr] = (i < d.ylen && lane < nv0) ? ld_stream(base + (size_t)i * row_bytes + (size_t)lane * 16)
-                                                 : make_int4(0, 0, 0, 0);
-        }
-    }
     Acc<S> acc[MR];
 #pragma unroll
     for (int r = 0; r < MR; ++r) acc[r].init();
-
-    for (int c0 = 0; c0 < d.ld; c0 += kc) {
-        const int cw = min(kc, d.ld - c0);
-        if (c0 > 0) __syncthreads();  // previous chunk consumed
-        {
-            const int4 *src = reinterpret_cast<const int4 *>(g + d.goff + c0);
-            int4 *dst = reinterpret_cast<int4 *>(gs);
-            const int nq = cw * (int)sizeof(Op) / 16;
-            for (int k = threadIdx.x; k < nq; k += blockDim.x) dst[k] = __ldcg(src + k);
+    const int nv = d.ld / VW;
+    int v = lane;
+    // two vectors per row in flight per iteration
+    for (; v + 32 < nv; v += 64) {
+        int4 ra[MR], rb[MR];
+#pragma unroll
+        for (int rr = 0; rr < MR; ++rr) {
+            const int i = warp + rr * kP2Warps;
+            const char *p = base + (size_t)i * row_bytes + (size_t)v * 16;
+            ra[rr] = i < d.ylen ? ld_stream(p) : make_int4(0, 0, 0, 0);
+            rb[rr] = i < d.ylen ? ld_stream(p + 32 * 16) : make_int4(0, 0, 0, 0);
         }
-        __syncthreads();
-        const int nv = cw / VW;
-        const char *chunk = base + (size_t)c0 * esz;
-        int v = lane;
-        if (c0 == 0) {
-            if (v < nv) {
+        const GV<S> ga = GV<S>::load(gr + v * VW), gb = GV<S>::load(gr + (v + 32) * VW);
 #pragma unroll
-                for (int rr = 0; rr < MR; ++rr)
-                    if (warp + rr * kP2Warps < d.ylen) row_mac<S>(acc[rr], pre[rr], gs + v * VW);
-            }
-            v += 32;
+        for (int rr = 0; rr < MR; ++rr)
+            if (warp + rr * kP2Warps < d.ylen) { row_mac<S>(acc[rr], ra[rr], ga); row_mac<S>(acc[rr], rb[rr], gb); }
+    }
+    if (v < nv) {
+        int4 ra[MR];
+#pragma unroll
+        for (int rr = 0; rr < MR; ++rr) {
+            const int i = warp + rr * kP2Warps;
+            ra[rr] = i < d.ylen ? ld_stream(base + (size_t)i * row_bytes + (size_t)v * 16) : make_int4(0, 0, 0, 0);
         }
-        for (; v < nv; v += 32) {
-            int4 raw[MR];
+        const GV<S> ga = GV<S>::load(gr + v * VW);
 #pragma unroll
-            for (int rr = 0; rr < MR; ++rr) {
-                const int i = warp + rr * kP2Warps;
-                raw[rr] = i < d.ylen ? ld_stream(chunk + (size_t)i * row_bytes + (size_t)v * 16) : make_int4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (int rr = 0; rr < MR; ++rr)
-                if (warp + rr * kP2Warps < d.ylen) row_mac<S>(acc[rr], raw[rr], gs + v * VW);
-        }
+        for (int rr = 0; rr < MR; ++rr)
+            if (warp + rr * kP2Warps < d.ylen) row_mac<S>(acc[rr], ra[rr], ga);
     }
-    // row totals: lane partials through shared memory, summed in lane order
-    __syncthreads();
-#pragma unroll
-    for (int rr = 0; rr < MR; ++rr) {
-        const int i = warp + rr * kP2Warps;
-        if (i < d.ylen) red[i * 32 + lane] = row_partial<S>(acc[rr]);
-    }
-    __syncthreads();
-    if (threadIdx.x < d.ylen) {
-        const int i = threadIdx.x;
-        RT a = red[i * 32];
-        for (int k = 1; k < 32; ++k) red_add<S>(a, red[i * 32 + k]);
-        double out;
-        if constexpr (S == Store::F64) out = a;
-        else out = df_to_double(a);
-        const int p = d.ybeg + i;
-        y[out_perm ? out_perm[p] : p] = out;
-    }
+    const double out = phase2_epilogue<S, MR>(d, acc, y, out_perm, rowval);
+    if (dotmode != 0) fused_dots(d, out, w, dotmode, Sd, dpart);
 }
 
 int grid_for(int64_t n, int threads, int cap) {
@@ -576,44 +674,33 @@ void launch_phase1(Store s, const DevIndex &ix, const DevPanels &P, const Solver
                    cudaStream_t st) {
     HMAT_DISPATCH(s, (k_phase1<SS><<<ix.nleaves, kP1Threads, 0, st>>>(
                          ix.p1, ix.p1_runs, ix.xdst, ix.lr, ix.gdst, P.q1, (const typename Tr<SS>::Op *)P.xs,
-                         (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g, P.ctr, skipS, mode)));
+                         (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g, skipS, mode)));
 }
 
-size_t phase2_smem_bytes(Store s, const DevIndex &ix) {
-    const size_t stage = (size_t)ix.kc * operand_bytes(s);
-    const size_t red = (size_t)ix.max_leaf * 32 * 8;  // row partials of the epilogue (8-byte accumulators)
-    return stage > red ? stage : red;
+void launch_reduce(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
+                   cudaStream_t st) {
+    const int blocks = ix.nbig + (ix.nsmall + kRedThreads / 32 - 1) / (kRedThreads / 32);
+    if (blocks == 0) return;
+    HMAT_DISPATCH(s, (k_reduce<SS><<<blocks, kRedThreads, 0, st>>>(
+                         ix.nbig, ix.nsmall, ix.red_big, ix.red_small, ix.lr, ix.gdst,
+                         (const typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g, skipS, mode)));
 }
+
 
 void launch_phase2(Store s, const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm,
-                   const SolverScalars *skipS, int mode, cudaStream_t st) {
-    size_t smem = phase2_smem_bytes(s, ix);
+                   const SolverScalars *skipS, int mode, cudaStream_t st, const double *w, int dotmode,
+                   SolverScalars *Sd, double *dpart) {
     if (ix.max_leaf <= 4 * kP2Warps) {
-        HMAT_DISPATCH(s, (k_phase2<SS, 4><<<ix.nleaves, kP2Threads, smem, st>>>(
-                             ix.p2, P.p2, (const typename Tr<SS>::Op *)P.g, ix.kc, y, out_perm, skipS, mode)));
+        HMAT_DISPATCH(s, (k_phase2<SS, 4><<<ix.nleaves, kP2Threads, 0, st>>>(
+                             ix.p2, P.p2, (const typename Tr<SS>::Op *)P.g, y, out_perm, skipS, mode, w, dotmode, Sd,
+                             dpart)));
     } else {
-        HMAT_DISPATCH(s, (k_phase2<SS, kMaxLeaf / kP2Warps><<<ix.nleaves, kP2Threads, smem, st>>>(
-                             ix.p2, P.p2, (const typename Tr<SS>::Op *)P.g, ix.kc, y, out_perm, skipS, mode)));
+        HMAT_DISPATCH(s, (k_phase2<SS, kMaxLeaf / kP2Warps><<<ix.nleaves, kP2Threads, 0, st>>>(
+                             ix.p2, P.p2, (const typename Tr<SS>::Op *)P.g, y, out_perm, skipS, mode, w, dotmode, Sd,
+                             dpart)));
     }
 }
 
-template <int MR>
-static cudaError_t configure_phase2_mr(size_t max_smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_phase2<Store::DF, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_phase2<Store::F64, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_phase2<Store::F32, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_phase2<Store::BF16, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
-}
-
-// Opt in to large dynamic shared memory for every phase-2 instantiation.
-cudaError_t configure_phase2(size_t max_smem) {
-    cudaError_t e = configure_phase2_mr<4>(max_smem);
-    if (e != cudaSuccess) return e;
-    return configure_phase2_mr<kMaxLeaf / kP2Warps>(max_smem);
-}
 
 // ------------------------------------------------------------------------
 // BiCG-STAB vector kernels: FP64 arithmetic, deterministic two-stage
@@ -701,19 +788,6 @@ __global__ void __launch_bounds__(kVecThreads) k_update_p(int n, const double *_
     }
 }
 
-__global__ void __launch_bounds__(kVecThreads) k_alpha(int n, const double *__restrict__ rt, const double *__restrict__ v,
-                                                       SolverScalars *S, double *partials) {
-    __shared__ double sh[kVecThreads];
-    if (run_stopped(S)) return;
-    double a[1] = {0.0};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[0] += rt[i] * v[i];
-    if (grid_reduce<1>(a, partials, S, sh) && threadIdx.x == 0) {
-        S->rtv = a[0];
-        S->alpha = S->rho / a[0];
-        if (!isfinite(S->alpha)) S->flag = HMAT_ERR_NONFINITE;
-    }
-}
-
 template <Store ST>
 __global__ void __launch_bounds__(kVecThreads) k_update_s(int n, const double *__restrict__ r, const double *__restrict__ v,
                                                           double *__restrict__ s, typename Tr<ST>::Op *__restrict__ ss,
@@ -738,27 +812,10 @@ __global__ void __launch_bounds__(kVecThreads) k_update_s(int n, const double *_
     }
 }
 
-__global__ void __launch_bounds__(kVecThreads) k_omega(int n, const double *__restrict__ t, const double *__restrict__ s,
-                                                       SolverScalars *S, double *partials) {
-    __shared__ double sh[2 * kVecThreads];
-    if (run_stopped(S) || S->stop_on_s) return;
-    double a[2] = {0.0, 0.0};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        a[0] += t[i] * s[i];
-        a[1] += t[i] * t[i];
-    }
-    if (grid_reduce<2>(a, partials, S, sh) && threadIdx.x == 0) {
-        S->ts = a[0];
-        S->tt = a[1];
-        S->omega = a[1] == 0.0 ? 0.0 : a[0] / a[1];
-        if (!isfinite(S->omega)) S->flag = HMAT_ERR_NONFINITE;
-    }
-}
-
 __global__ void __launch_bounds__(kVecThreads) k_update_xr(int n, double *__restrict__ x, const double *__restrict__ p,
                                                            const double *__restrict__ s, const double *__restrict__ t,
                                                            double *__restrict__ r, const double *__restrict__ rt,
-                                                           SolverScalars *S, double *partials) {
+                                                           SolverScalars *S, double *partials, int iter_limit) {
     __shared__ double sh[2 * kVecThreads];
     if (run_stopped(S)) return;
     const bool at_s = S->stop_on_s != 0;
@@ -786,13 +843,17 @@ __global__ void __launch_bounds__(kVecThreads) k_update_xr(int n, double *__rest
             S->flag = 1;
         } else if (omega == 0.0) {
             S->flag = HMAT_ERR_BREAKDOWN_OMEGA;
+        } else if (S->iters >= iter_limit) {  // the next iteration is over budget
+            S->flag = HMAT_ERR_MAXIT;
+        } else {
+            S->iters += 1;
         }
     }
 }
 
 __global__ void __launch_bounds__(kVecThreads) k_residual(int n, const double *__restrict__ b, const double *__restrict__ y,
                                                           double *__restrict__ r, double *__restrict__ rt,
-                                                          SolverScalars *S, double *partials) {
+                                                          SolverScalars *S, double *partials, int iter_limit) {
     __shared__ double sh[kVecThreads];
     double a[1] = {0.0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -807,6 +868,10 @@ __global__ void __launch_bounds__(kVecThreads) k_residual(int n, const double *_
         S->iter_in_run = 0;
         S->stop_on_s = 0;
         S->flag = isfinite(a[0]) ? 0 : HMAT_ERR_NONFINITE;
+        if (iter_limit >= 0 && S->flag == 0) {  // a run starts: count its first iteration
+            if (S->iters >= iter_limit) S->flag = HMAT_ERR_MAXIT;
+            else S->iters += 1;
+        }
     }
 }
 
@@ -829,28 +894,20 @@ void launch_update_p(Store s, int64_t n, const double *r, double *p, const doubl
                                                                            (typename Tr<SS>::Op *)ps, S)));
 }
 
-void launch_alpha(int64_t n, const double *rt, const double *v, SolverScalars *S, double *partials, cudaStream_t st) {
-    k_alpha<<<vec_blocks(n), kVecThreads, 0, st>>>((int)n, rt, v, S, partials);
-}
-
 void launch_update_s(Store s, int64_t n, const double *r, const double *v, double *svec, void *ss, double *,
                      const double *, SolverScalars *S, double *partials, cudaStream_t st) {
     HMAT_DISPATCH(s, (k_update_s<SS><<<vec_blocks(n), kVecThreads, 0, st>>>((int)n, r, v, svec,
                                                                            (typename Tr<SS>::Op *)ss, S, partials)));
 }
 
-void launch_omega(int64_t n, const double *t, const double *svec, SolverScalars *S, double *partials, cudaStream_t st) {
-    k_omega<<<vec_blocks(n), kVecThreads, 0, st>>>((int)n, t, svec, S, partials);
-}
-
 void launch_update_xr(int64_t n, double *x, const double *p, const double *svec, const double *t, double *r,
-                      const double *rt, SolverScalars *S, double *partials, cudaStream_t st) {
-    k_update_xr<<<vec_blocks(n), kVecThreads, 0, st>>>((int)n, x, p, svec, t, r, rt, S, partials);
+                      const double *rt, SolverScalars *S, double *partials, int iter_limit, cudaStream_t st) {
+    k_update_xr<<<vec_blocks(n), kVecThreads, 0, st>>>((int)n, x, p, svec, t, r, rt, S, partials, iter_limit);
 }
 
 void launch_residual(int64_t n, const double *b, const double *y, double *r, double *rt, SolverScalars *S,
-                     double *partials, cudaStream_t st) {
-    k_residual<<<vec_blocks(n), kVecThreads, 0, st>>>((int)n, b, y, r, rt, S, partials);
+                     double *partials, int iter_limit, cudaStream_t st) {
+    k_residual<<<vec_blocks(n), kVecThreads, 0, st>>>((int)n, b, y, r, rt, S, partials, iter_limit);
 }
 
 void launch_gather(int64_t n, const int32_t *perm, const double *src, double *dst_perm, cudaStream_t st) {

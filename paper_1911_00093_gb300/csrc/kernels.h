@@ -10,16 +10,17 @@ namespace hmat_internal {
 
 // Device-resident packing indices (shared by every precision copy of a handle).
 struct DevIndex {
-    int32_t n = 0, nleaves = 0, nlr = 0, nctr = 0;
+    int32_t n = 0, nleaves = 0, nlr = 0, nbig = 0, nsmall = 0;
     const int32_t *perm = nullptr;  // [n]
     const P1Desc *p1 = nullptr;     // [nleaves]
     const P1Run *p1_runs = nullptr;
     const XDst *xdst = nullptr;
     const LrDesc *lr = nullptr;     // [nlr]
     const int32_t *gdst = nullptr;
+    const int32_t *red_big = nullptr, *red_small = nullptr;
     const P2Desc *p2 = nullptr;     // [nleaves]
-    int32_t kc = 0;                 // phase-2 column chunk staged in shared memory
     int32_t max_leaf = 0;           // rows of the widest leaf cluster
+    int32_t max_ld2 = 0;            // widest phase-2 panel (entries)
 };
 
 // One precision copy of the panels plus its work buffers.
@@ -30,7 +31,6 @@ struct DevPanels {
     void *xs = nullptr;        // source-vector operand, cluster order (n entries of the operand type)
     void *part = nullptr;      // projection partial sums of multi-cluster blocks
     void *g = nullptr;         // phase-2 operand buffers (glen entries of the operand type)
-    int32_t *ctr = nullptr;    // completion counters (zero between products)
 };
 
 // Operand bytes per entry for a store (x and t copies).
@@ -46,11 +46,14 @@ struct SolverScalars;
 // flag set; mode 2: flag set or stop at the ||s|| check); mode 0 never skips.
 void launch_phase1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
                    cudaStream_t st);
-// y[p] (cluster order) or y[out_perm[p]] (original order) = (A~ x)_p
+// t of the blocks spanning several leaf clusters, scattered into g (no launch when there is none)
+void launch_reduce(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
+                   cudaStream_t st);
+// y[p] (cluster order) or y[out_perm[p]] (original order) = (A~ x)_p; dotmode 1/2
+// also computes alpha (w = r~) or omega (w = s) of Algorithm 1 into Sd
 void launch_phase2(Store s, const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm,
-                   const SolverScalars *skipS, int mode, cudaStream_t st);
-size_t phase2_smem_bytes(Store s, const DevIndex &ix);
-cudaError_t configure_phase2(size_t max_smem);
+                   const SolverScalars *skipS, int mode, cudaStream_t st, const double *w = nullptr,
+                   int dotmode = 0, SolverScalars *Sd = nullptr, double *dpart = nullptr);
 
 // ---- BiCG-STAB vector kernels (FP64) ----
 struct SolverScalars {
@@ -72,21 +75,17 @@ int vec_blocks(int64_t n);
 void launch_count_iter(SolverScalars *S, int iter_limit, cudaStream_t st);
 void launch_update_p(Store s, int64_t n, const double *r, double *p, const double *v, void *ps,
                      SolverScalars *S, cudaStream_t st);
-// alpha = rho / (r~ . v)
-void launch_alpha(int64_t n, const double *rt, const double *v, SolverScalars *S, double *partials,
-                  cudaStream_t st);
 // s = r - alpha v, operand copy of s, ||s||^2 and the stop check (x += alpha p on a stop)
 void launch_update_s(Store s, int64_t n, const double *r, const double *v, double *svec, void *ss,
                      double *x, const double *p, SolverScalars *S, double *partials, cudaStream_t st);
-// omega = (t . s) / (t . t)
-void launch_omega(int64_t n, const double *t, const double *svec, SolverScalars *S, double *partials,
-                  cudaStream_t st);
-// x += alpha p + omega s; r = s - omega t; rho = r~ . r, ||r||^2, stop check
+// x += alpha p + omega s; r = s - omega t; rho = r~ . r, ||r||^2, stop check;
+// counts the next iteration when the run goes on
 void launch_update_xr(int64_t n, double *x, const double *p, const double *svec, const double *t, double *r,
-                      const double *rt, SolverScalars *S, double *partials, cudaStream_t st);
-// r = b - y; r~ = r; ||r||^2 into S->rnorm2 and rho = r~ . r; resets the run state
+                      const double *rt, SolverScalars *S, double *partials, int iter_limit, cudaStream_t st);
+// r = b - y; r~ = r; ||r||^2 into S->rnorm2 and rho = r~ . r; resets the run state;
+// iter_limit >= 0 starts a run (counts its first iteration)
 void launch_residual(int64_t n, const double *b, const double *y, double *r, double *rt, SolverScalars *S,
-                     double *partials, cudaStream_t st);
+                     double *partials, int iter_limit, cudaStream_t st);
 // gather / scatter between original and cluster order
 void launch_gather(int64_t n, const int32_t *perm, const double *src, double *dst_perm, cudaStream_t st);
 void launch_scatter(int64_t n, const int32_t *perm, const double *src_perm, double *dst, cudaStream_t st);

@@ -320,7 +320,6 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
     std::vector<int64_t> kfirst(nb, 0), kcnt(nb, 0);
     L.lr.resize(nlr);
     int64_t npart = 0;
-    int32_t nctr = 0;
     for (int64_t q = 0; q < nlr; ++q) {
         const int64_t b = lr_blocks[q];
         const int64_t *e = v.blocks + 8 * b;
@@ -333,10 +332,9 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
         if (kcnt[b] > 1) {
             d.boff = (int32_t)npart;
             npart += kcnt[b] * e[5];
-            d.ctr = nctr++;
+            (kcnt[b] >= kRedBigCnt ? L.red_big : L.red_small).push_back((int32_t)q);
         } else {
             d.boff = -1;
-            d.ctr = -1;
         }
         d.gbeg = (int32_t)L.gdst.size();
         for (int64_t rho = leaf_index(e[0]); rho < leaf_index(e[1]); ++rho) {
@@ -345,11 +343,10 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
             L.gdst.push_back(L.p2[rho].goff + c);
         }
         d.gcnt = (int32_t)L.gdst.size() - d.gbeg;
-        d.pad = 0;
+        d.pad[0] = d.pad[1] = 0;
     }
     if (npart > (int64_t(1) << 31) - 16) { if (why) *why = "too many partials"; return HMAT_ERR_UNSUPPORTED; }
     L.npart = npart;
-    L.nctr = nctr;
 
     // phase 1: low-rank blocks per leaf column cluster (block order), and the
     // dense-block operand slices each leaf column cluster feeds
@@ -425,8 +422,7 @@ int check_layout(const Layout &L, std::string *why) {
     }
     for (const LrDesc &d : L.lr) {
         if (d.rank < 1 || d.cnt < 1 || std::abs(d.scale) > kMaxScaleExp) return bad("lr desc");
-        if (d.cnt > 1 ? (d.boff < 0 || (int64_t)d.boff + (int64_t)d.cnt * d.rank > L.npart || d.ctr < 0 || d.ctr >= L.nctr)
-                      : (d.boff != -1 || d.ctr != -1))
+        if (d.cnt > 1 ? (d.boff < 0 || (int64_t)d.boff + (int64_t)d.cnt * d.rank > L.npart) : d.boff != -1)
             return bad("lr partials");
         if (d.gbeg < 0 || d.gcnt < 1 || (int64_t)d.gbeg + d.gcnt > (int64_t)L.gdst.size()) return bad("lr dst");
         for (int k = 0; k < d.gcnt; ++k) {
@@ -468,6 +464,11 @@ int check_layout(const Layout &L, std::string *why) {
     }
     for (int64_t k = 0; k < L.glen; ++k)
         if (!gw[k]) return bad("operand slot never written");
+    size_t multi = 0;
+    for (const LrDesc &d : L.lr) multi += d.cnt > 1;
+    if (multi != L.red_big.size() + L.red_small.size()) return bad("reduction lists");
+    for (int32_t q : L.red_big) if (q < 0 || q >= (int32_t)L.lr.size() || L.lr[q].cnt < kRedBigCnt) return bad("red big");
+    for (int32_t q : L.red_small) if (q < 0 || q >= (int32_t)L.lr.size() || L.lr[q].cnt < 2 || L.lr[q].cnt >= kRedBigCnt) return bad("red small");
     if ((int64_t)L.perm.size() != L.n) return bad("perm size");
     for (int32_t q : L.perm) if (q < 0 || q >= L.n) return bad("perm entry");
     return HMAT_OK;

@@ -137,3 +137,4 @@ def test_upload_rejects_bad_blob():
     with pytest.raises(P.HmatError) as e:
         P.hmat_upload(bad, "fp64")
     assert e.value.status == 2
+
