@@ -209,6 +209,37 @@ int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const hmat_solve
                      hmat_solve_info *info);
 
 /* ------------------------------------------------------------------------- */
+/* Product without allocation (an addition of this library; the paper has no  */
+/* counterpart)                                                               */
+/* ------------------------------------------------------------------------- */
+/* Bytes of the static device array the allocation-free product uses. */
+#define HMAT_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/*
+ * hmat_matvec_noalloc -- y = A~ x for one vector, like hmat_matvec, but the call
+ * allocates no memory at all.  It is meant for callers that cannot call
+ * cudaMalloc when they run the product: code enqueued inside a CUDA stream
+ * capture, latency-critical loops that cannot pay for an allocation, and hosts
+ * or plugins whose device memory belongs to another allocator or budget.  Such
+ * a caller creates the handle once at set-up (hmat_upload allocates then) and
+ * afterwards only calls this function.
+ *
+ * x and y: device pointers (N doubles, original panel order; host pointers are
+ * rejected with HMAT_ERR_ARG because staging them would need buffers), on the
+ * handle's device, which must be current.  The product's scratch (source
+ * operand copy, partial sums, operand buffers) lives in one static device array
+ * of HMAT_NOALLOC_SCRATCH_BYTES compiled into the library; every GPU that loads
+ * the library holds that array until the process exits.  A handle whose scratch
+ * does not fit (roughly N above 20,000 panels for the FP64 form) is rejected with
+ * HMAT_ERR_UNSUPPORTED.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls, on every handle, share the one array: calls that overlap on the GPU
+ * (different streams without ordering) race and give wrong results.  The call
+ * clears what must start at zero and is asynchronous on `stream`.
+ */
+int hmat_matvec_noalloc(hmat_handle h, const double *x, double *y, void *stream);
+
+/* ------------------------------------------------------------------------- */
 /* Introspection                                                              */
 /* ------------------------------------------------------------------------- */
 typedef struct hmat_handle_info {

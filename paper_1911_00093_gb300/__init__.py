@@ -23,7 +23,8 @@ PRECISIONS = {"fp64": HMAT_FP64, "fp64_dfma": HMAT_FP64_DFMA, "fp32": HMAT_FP32,
 # every symbol declared in include/hmat.h
 EXPORTS = ("hmat_build", "hmat_blob_free", "hmat_blob_stats_get", "hmat_upload", "hmat_destroy",
            "hmat_matvec", "hmat_matvec_fp64", "hmat_solve_opts_default", "hmat_bicgstab",
-           "hmat_bicgstab_ex", "hmat_info", "hmat_time_matvec", "hmat_strerror", "hmat_last_cuda_error")
+           "hmat_bicgstab_ex", "hmat_info", "hmat_time_matvec", "hmat_strerror", "hmat_last_cuda_error",
+           "hmat_matvec_noalloc")
 
 
 class BlobStats(C.Structure):
@@ -89,6 +90,7 @@ def load():
         "hmat_time_matvec": (C.c_int, [P, I32, I32, P, C.POINTER(C.c_double)]),
         "hmat_strerror": (C.c_char_p, [C.c_int]),
         "hmat_last_cuda_error": (C.c_char_p, []),
+        "hmat_matvec_noalloc": (C.c_int, [P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -181,6 +183,14 @@ def hmat_matvec(h, x, y, nrhs=1, stream=None, fp64=False):
     py, ky = _ptr(y)
     f = L.hmat_matvec_fp64 if fp64 else L.hmat_matvec
     _check(f(C.c_void_p(h), px, py, int(nrhs), _stream_ptr(stream)), "hmat_matvec")
+    return y
+
+
+def hmat_matvec_noalloc(h, x, y, stream=None):
+    """y = A~ x through the allocation-free entry point (device pointers only)."""
+    px, kx = _ptr(x)
+    py, ky = _ptr(y)
+    _check(load().hmat_matvec_noalloc(C.c_void_p(h), px, py, _stream_ptr(stream)), "hmat_matvec_noalloc")
     return y
 
 

@@ -14,7 +14,7 @@ OUT = os.path.join(HERE, "libhmat.so")
 BUILD = os.path.join(HERE, "_build")
 
 CXX_SOURCES = ["builder.cpp", "layout.cpp"]
-CU_SOURCES = ["kernels.cu", "api.cu"]
+CU_SOURCES = ["kernels.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

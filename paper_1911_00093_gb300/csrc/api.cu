@@ -109,6 +109,7 @@ extern "C" int hmat_upload(const void *blob, size_t blob_bytes, int32_t precisio
         h->phase1_entries = L.phase1_entries;
         h->phase2_entries = L.phase2_entries;
         h->partials_n = L.npart;
+        h->glen = L.glen;
         h->rank_sum = L.rank_sum;
 
         // indices

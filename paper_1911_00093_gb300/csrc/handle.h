@@ -54,6 +54,7 @@ struct hmat_t {
     // sizes
     int64_t panel_bytes = 0, panel_bytes64 = 0, index_bytes = 0;
     int64_t stored_entries = 0, phase1_entries = 0, phase2_entries = 0, partials_n = 0, rank_sum = 0;
+    int64_t glen = 0;  // operand slots of the phase-2 buffers
 
     ~hmat_t() {
         int cur = 0;

@@ -1,0 +1,96 @@
+// hmat_matvec_noalloc: the H-matrix product of an uploaded handle with every
+// scratch buffer taken from one static device array, so that the call itself
+// allocates no memory.
+//
+// Who needs it: callers that must not allocate device memory at the time they
+// run the product -- code enqueued inside a CUDA stream capture (cudaMalloc is
+// not a capturable operation and stalls or invalidates the capture), real-time
+// or latency-critical loops that cannot pay for an allocation, and host
+// programs or plugins whose device memory is owned by another allocator or
+// memory budget they may not touch.  They create the handle once at set-up
+// (hmat_upload allocates then) and afterwards call only this entry point.
+//
+// The scratch is the source-vector operand copy, the projection partial sums
+// and the phase-2 operand buffers; the handle's own copies of those buffers are
+// not used, so this entry point never races with the handle's other calls on
+// the same stream -- but every call on every handle shares the one static array.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "handle.h"
+
+using namespace hmat_internal;
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = HMAT_NOALLOC_SCRATCH_BYTES;
+constexpr int kMaxDevices = 64;
+
+// Every GPU that loads the library holds this array until the process exits.
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+std::mutex g_addr_mutex;
+void *g_addr[kMaxDevices] = {};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Device address of the array on the current device; looked up once per device
+// (cudaGetSymbolAddress with that device current), then cached.
+int scratch_address(int dev, void **out) {
+    std::lock_guard<std::mutex> lock(g_addr_mutex);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_addr[dev] = p;
+    }
+    *out = g_addr[dev];
+    return HMAT_OK;
+}
+
+bool on_device(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t scratch_bytes_for(const hmat_t *h) {
+    const size_t ob = operand_bytes(h->store), pb = partial_bytes(h->store);
+    return align256((size_t)h->ix.n * ob) + align256((size_t)(h->partials_n > 0 ? h->partials_n : 1) * pb) +
+           align256((size_t)(h->glen > 0 ? h->glen : 1) * ob);
+}
+
+}  // namespace
+
+extern "C" int hmat_matvec_noalloc(hmat_handle h, const double *x, double *y, void *stream) {
+    if (!h || !x || !y || x == y) return HMAT_ERR_ARG;
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != h->device || dev < 0 || dev >= kMaxDevices) return HMAT_ERR_ARG;
+    if (!on_device(x) || !on_device(y)) return HMAT_ERR_ARG;  // no staging buffers: device pointers only
+    const size_t need = scratch_bytes_for(h);
+    if (need > kNoallocScratchBytes) return HMAT_ERR_UNSUPPORTED;
+    void *base = nullptr;
+    int st = scratch_address(dev, &base);
+    if (st != HMAT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ob = operand_bytes(h->store);
+    DevPanels P = h->P;
+    char *b = (char *)base;
+    P.xs = b;
+    P.part = b + align256((size_t)h->ix.n * ob);
+    P.g = b + align256((size_t)h->ix.n * ob) + align256((size_t)(h->partials_n > 0 ? h->partials_n : 1) *
+                                                         partial_bytes(h->store));
+    // the array keeps the previous call's contents: the padding slots of the
+    // operand buffers must read zero, every other slot is rewritten below
+    CK(cudaMemsetAsync(P.g, 0, (size_t)(h->glen > 0 ? h->glen : 1) * ob, s));
+    launch_prep(h->store, h->ix, x, h->ix.perm, P.xs, s);
+    launch_phase1(h->store, h->ix, P, nullptr, 0, s);
+    launch_reduce(h->store, h->ix, P, nullptr, 0, s);
+    launch_phase2(h->store, h->ix, P, y, h->ix.perm, nullptr, 0, s);
+    CK(cudaGetLastError());
+    return HMAT_OK;
+}
