@@ -118,10 +118,10 @@ extern "C" int hmat_upload(const void *blob, size_t blob_bytes, int32_t precisio
         ix.nleaves = L.nleaves;
         ix.nlr = (int32_t)L.lr.size();
         ix.nbig = (int32_t)L.red_big.size();
-        ix.nsmall = (int32_t)L.red_small.size();
+        ix.ntasks = (int32_t)L.red_tasks.size();
         ix.max_leaf = L.max_leaf;
         ix.max_ld2 = L.max_ld2;
-        int32_t *perm = nullptr, *gdst = nullptr, *red_big = nullptr, *red_small = nullptr;
+        int32_t *perm = nullptr, *gdst = nullptr, *red_big = nullptr, *red_tasks = nullptr;
         P1Desc *p1 = nullptr;
         P1Run *p1_runs = nullptr;
         XDst *xdst = nullptr;
@@ -134,15 +134,15 @@ extern "C" int hmat_upload(const void *blob, size_t blob_bytes, int32_t precisio
             (st = h->upload(&lr, L.lr.data(), sizeof(LrDesc) * L.lr.size())) ||
             (st = h->upload(&gdst, L.gdst.data(), 4 * L.gdst.size())) ||
             (st = h->upload(&red_big, L.red_big.data(), 4 * L.red_big.size())) ||
-            (st = h->upload(&red_small, L.red_small.data(), 4 * L.red_small.size())) ||
+            (st = h->upload(&red_tasks, L.red_tasks.data(), 4 * L.red_tasks.size())) ||
             (st = h->upload(&p2, L.p2.data(), sizeof(P2Desc) * L.p2.size()))) {
             return st;
         }
         ix.perm = perm; ix.p1 = p1; ix.p1_runs = p1_runs; ix.xdst = xdst; ix.lr = lr; ix.gdst = gdst; ix.p2 = p2;
-        ix.red_big = red_big; ix.red_small = red_small;
+        ix.red_big = red_big; ix.red_tasks = red_tasks;
         h->index_bytes = (int64_t)(4 * L.perm.size() + sizeof(P1Desc) * L.p1.size() + sizeof(P1Run) * L.p1_runs.size() +
                                    sizeof(XDst) * L.xdst.size() + sizeof(LrDesc) * L.lr.size() + 4 * L.gdst.size() +
-                                   sizeof(P2Desc) * L.p2.size() + 4 * (L.red_big.size() + L.red_small.size()));
+                                   sizeof(P2Desc) * L.p2.size() + 4 * (L.red_big.size() + L.red_tasks.size()));
 
         // panels
         if ((st = alloc_panels(h, v, L, h->store, h->P, &h->panel_bytes))) return st;
@@ -291,7 +291,7 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
     // spans several leaf clusters, expansion) and per iteration (p update, two
     // products without operand preparation whose expansions also give alpha and
     // omega, s update, x/r update with the count of the next iteration)
-    const int kProductLaunches = (h->ix.nbig + h->ix.nsmall) ? 4 : 3;
+    const int kProductLaunches = (h->ix.nbig + h->ix.ntasks) ? 4 : 3;
     const int kIterationLaunches = 3 + 2 * (kProductLaunches - 1);
     const double *bsrc = b;
     if (!db) {

@@ -109,7 +109,8 @@ struct Layout {
     std::vector<P2Desc> p2;
     int64_t p1_elems = 0, p2_elems = 0;
     int64_t npart = 0, glen = 0;
-    std::vector<int32_t> red_big, red_small;  // multi-cluster blocks: >= kRedBigCnt clusters / fewer
+    std::vector<int32_t> red_big;    // multi-cluster blocks over >= kRedBigCnt clusters (a CTA each)
+    std::vector<int32_t> red_tasks;  // (block << 6) | rank of the other multi-cluster blocks (a lane each)
     int32_t max_ld2 = 0, max_ld1 = 0, max_runs1 = 0, max_leaf = 0;
     int64_t stored_entries = 0, phase1_entries = 0, phase2_entries = 0, rank_sum = 0;
     // source of each packed entry, used to fill typed panels without

@@ -342,13 +342,14 @@ __global__ void __launch_bounds__(kP1Threads) k_phase1(const P1Desc *__restrict_
 // ------------------------------------------------------------------------
 // reduce: t of the blocks spanning several leaf clusters, in a fixed order,
 // scattered to the operand buffers.  Blocks over >= kRedBigCnt clusters get a
-// whole CTA (kernel blocks [0, nbig)), the others one warp each.
+// whole CTA (kernel blocks [0, nbig)); the others are split into one task per
+// rank, one lane each.
 // ------------------------------------------------------------------------
 constexpr int kRedThreads = 256;
 
 template <Store S>
-__global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int nsmall, const int32_t *__restrict__ big,
-                                                         const int32_t *__restrict__ small,
+__global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int ntasks, const int32_t *__restrict__ big,
+                                                         const int32_t *__restrict__ tasks,
                                                          const LrDesc *__restrict__ lr, const int32_t *__restrict__ gdst,
                                                          const typename Tr<S>::Part *__restrict__ part,
                                                          typename Tr<S>::Op *__restrict__ g, const SolverScalars *S_,
@@ -390,31 +391,20 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int nsmall, co
         }
         return;
     }
-    // smaller blocks: one warp each; lane groups split the leaf clusters, a fixed
-    // butterfly adds the groups
-    const int wq = ((int)blockIdx.x - nbig) * (kRedThreads / 32) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (wq >= nsmall) return;
-    const LrDesc ld = lr[small[wq]];
-    for (int l0 = 0; l0 < ld.rank; l0 += 32) {
-        const int rr = min(32, ld.rank - l0);
-        int rp = 1;
-        while (rp < rr) rp <<= 1;
-        const int G = 32 / rp, gi = lane / rp, l = lane % rp;
-        RT a;
-        red_zero<S>(a);
-        if (l < rr) {
-            const typename Tr<S>::Part *src = part + ld.boff + l0 + l;
+    // the other blocks: one lane per (block, rank), a sequential sum over the
+    // block's leaf clusters (independent loads) and the scatter of that rank
+    const int task = ((int)blockIdx.x - nbig) * kRedThreads + threadIdx.x;
+    if (task >= ntasks) return;
+    const int tq = __ldg(tasks + task);
+    const LrDesc ld = lr[tq >> 6];
+    const int l = tq & 63;
+    const typename Tr<S>::Part *src = part + ld.boff + l;
+    RT a;
+    red_zero<S>(a);
 #pragma unroll 4
-            for (int k = gi; k < ld.cnt; k += G) red_add_part<S>(a, src[(size_t)k * ld.rank]);
-        }
-        for (int m = rp; m < 32; m <<= 1) a = red_xor<S>(a, m, (gi & (m / rp)) != 0);
-        // the butterfly leaves the same total in every lane group: groups share the destinations
-        if (l < rr) {
-            const Op o = part_to_op<S>(red_to_part<S>(a), ld.scale);
-            for (int k = gi; k < ld.gcnt; k += G) g[gdst[ld.gbeg + k] + l0 + l] = o;
-        }
-    }
+    for (int k = 0; k < ld.cnt; ++k) red_add_part<S>(a, src[(size_t)k * ld.rank]);
+    const Op o = part_to_op<S>(red_to_part<S>(a), ld.scale);
+    for (int k = 0; k < ld.gcnt; ++k) g[gdst[ld.gbeg + k] + l] = o;
 }
 
 // ------------------------------------------------------------------------
@@ -679,10 +669,10 @@ void launch_phase1(Store s, const DevIndex &ix, const DevPanels &P, const Solver
 
 void launch_reduce(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
                    cudaStream_t st) {
-    const int blocks = ix.nbig + (ix.nsmall + kRedThreads / 32 - 1) / (kRedThreads / 32);
+    const int blocks = ix.nbig + (ix.ntasks + kRedThreads - 1) / kRedThreads;
     if (blocks == 0) return;
     HMAT_DISPATCH(s, (k_reduce<SS><<<blocks, kRedThreads, 0, st>>>(
-                         ix.nbig, ix.nsmall, ix.red_big, ix.red_small, ix.lr, ix.gdst,
+                         ix.nbig, ix.ntasks, ix.red_big, ix.red_tasks, ix.lr, ix.gdst,
                          (const typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g, skipS, mode)));
 }
 

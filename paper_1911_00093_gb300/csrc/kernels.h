@@ -10,14 +10,14 @@ namespace hmat_internal {
 
 // Device-resident packing indices (shared by every precision copy of a handle).
 struct DevIndex {
-    int32_t n = 0, nleaves = 0, nlr = 0, nbig = 0, nsmall = 0;
+    int32_t n = 0, nleaves = 0, nlr = 0, nbig = 0, ntasks = 0;
     const int32_t *perm = nullptr;  // [n]
     const P1Desc *p1 = nullptr;     // [nleaves]
     const P1Run *p1_runs = nullptr;
     const XDst *xdst = nullptr;
     const LrDesc *lr = nullptr;     // [nlr]
     const int32_t *gdst = nullptr;
-    const int32_t *red_big = nullptr, *red_small = nullptr;
+    const int32_t *red_big = nullptr, *red_tasks = nullptr;
     const P2Desc *p2 = nullptr;     // [nleaves]
     int32_t max_leaf = 0;           // rows of the widest leaf cluster
     int32_t max_ld2 = 0;            // widest phase-2 panel (entries)

@@ -332,7 +332,12 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
         if (kcnt[b] > 1) {
             d.boff = (int32_t)npart;
             npart += kcnt[b] * e[5];
-            (kcnt[b] >= kRedBigCnt ? L.red_big : L.red_small).push_back((int32_t)q);
+            if (kcnt[b] >= kRedBigCnt) {
+                L.red_big.push_back((int32_t)q);
+            } else {
+                if (q >= (int64_t(1) << 25) || e[5] > 63) { if (why) *why = "reduction task out of range"; return HMAT_ERR_UNSUPPORTED; }
+                for (int64_t l = 0; l < e[5]; ++l) L.red_tasks.push_back((int32_t)((q << 6) | l));
+            }
         } else {
             d.boff = -1;
         }
@@ -464,11 +469,17 @@ int check_layout(const Layout &L, std::string *why) {
     }
     for (int64_t k = 0; k < L.glen; ++k)
         if (!gw[k]) return bad("operand slot never written");
-    size_t multi = 0;
-    for (const LrDesc &d : L.lr) multi += d.cnt > 1;
-    if (multi != L.red_big.size() + L.red_small.size()) return bad("reduction lists");
+    size_t multi = 0, multi_ranks = 0;
+    for (const LrDesc &d : L.lr)
+        if (d.cnt > 1 && d.cnt < kRedBigCnt) multi_ranks += d.rank;
+        else if (d.cnt >= kRedBigCnt) ++multi;
+    if (multi != L.red_big.size() || multi_ranks != L.red_tasks.size()) return bad("reduction lists");
     for (int32_t q : L.red_big) if (q < 0 || q >= (int32_t)L.lr.size() || L.lr[q].cnt < kRedBigCnt) return bad("red big");
-    for (int32_t q : L.red_small) if (q < 0 || q >= (int32_t)L.lr.size() || L.lr[q].cnt < 2 || L.lr[q].cnt >= kRedBigCnt) return bad("red small");
+    for (int32_t t : L.red_tasks) {
+        const int32_t q = t >> 6, l = t & 63;
+        if (q < 0 || q >= (int32_t)L.lr.size() || L.lr[q].cnt < 2 || L.lr[q].cnt >= kRedBigCnt || l >= L.lr[q].rank)
+            return bad("red task");
+    }
     if ((int64_t)L.perm.size() != L.n) return bad("perm size");
     for (int32_t q : L.perm) if (q < 0 || q >= L.n) return bad("perm entry");
     return HMAT_OK;
