@@ -27,10 +27,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "BiCG-STAB time to rel. residual 1e-8 & H-matvec HBM GB/s: mixed vs FP64"
 UNIT = "solves/s"
-FORM_OPTS = {"fp64": {}, "fp64_dfma": {}, "fp32": {"inner_tol": 1e-4}, "bf16": {"inner_tol": 1e-2}}
+# form -> (upload precision, Method 3's c, solver options); the m* forms are the
+# paper's own variants (Section 3, Table 1), fp64_dfma is its Method 1-Double
+FORMS = {"fp64": ("fp64", None, {}), "fp64_dfma": ("fp64_dfma", None, {}),
+         "fp32": ("fp32", None, {"inner_tol": 1e-4}), "bf16": ("bf16", None, {"inner_tol": 1e-2}),
+         "m1_single": ("m1_single", None, {"inner_tol": 1e-4}), "m1_mixed": ("m1_mixed", None, {"inner_tol": 1e-4}),
+         "m2_double": ("m2_double", None, {}), "m2_single": ("m2_single", None, {"inner_tol": 1e-4}),
+         "m2_mixed": ("m2_mixed", None, {"inner_tol": 1e-4}), "m3_c-1": ("m3", -1, {"inner_tol": 1e-4}),
+         "m3_c2": ("m3", 2, {"inner_tol": 1e-4})}
+FORM_OPTS = {k: v[2] for k, v in FORMS.items()}
+DEFAULT_FORMS = "fp64,fp64_dfma,fp32,bf16,m1_single,m1_mixed,m2_double,m2_single,m2_mixed,m3_c-1,m3_c2"
 CHECK_EVERY = 4  # iterations per graph replay between host reads of the stop flag
-STORE_BYTES = {"fp64": 8, "fp64_dfma": 8, "fp32": 4, "bf16": 2}
-PART_BYTES = {"fp64": 8, "fp64_dfma": 8, "fp32": 4, "bf16": 4}
+PART_BYTES = {"fp64": 8, "fp64_dfma": 8, "fp32": 4, "bf16": 4}  # partial sums (8 for the paper's variants)
 
 
 def _peaks():
@@ -116,6 +124,36 @@ def _dist_setup(args):
     return world, rank, local
 
 
+def _profiled_traffic(kernel, level):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when
+    there is none for this workload or the kernel source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"traffic_bf16_icosphere_L{level}.json")
+    try:
+        rec = json.load(open(path))
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+    except (OSError, ValueError, KeyError):
+        return None
+    if hashlib.sha256(src).hexdigest() != rec.get("source_sha256"):
+        return None
+    return rec.get("dram_bytes_per_launch", {}).get(kernel)
+
+
+def max_over_ranks(value, dist, device="cuda"):
+    """The largest of every rank's value (the job's time is its slowest replica's)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps, seconds):
+    """Whole-job throughput: every replica solves `steps` systems in at most `seconds`."""
+    return world * steps / seconds
+
+
 def _workload(level):
     import synth
     mesh = synth.icosphere(level)
@@ -186,7 +224,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--level", type=int, default=6)
     ap.add_argument("--form", default="bf16", choices=list(FORM_OPTS))
-    ap.add_argument("--forms", default="fp64,fp64_dfma,fp32,bf16", help="forms measured beside the headline")
+    ap.add_argument("--forms", default=DEFAULT_FORMS, help="forms measured beside the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--matvec-iters", type=int, default=50)
     args = ap.parse_args()
@@ -213,7 +251,7 @@ def main():
         forms.append(args.form)
     handles = {}
     for f in forms:
-        handles[f] = P.hmat_upload(blob, f)
+        handles[f] = P.hmat_upload(blob, FORMS[f][0], FORMS[f][1])
     stream = torch.cuda.current_stream()
     b = torch.from_numpy(b_np).cuda()
     x = torch.zeros_like(b)
@@ -239,11 +277,7 @@ def main():
         torch.cuda.synchronize()
         if clk is not None:
             clk.mark(w0, time.time())
-        ms = ev0.elapsed_time(ev1)
-        if dist:
-            tt = torch.tensor([ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), dist)
         return ms, infos
 
     # ---- headline: the mixed-form solve, clocks sampled during the timed region ----
@@ -253,7 +287,7 @@ def main():
     if any(i["status"] != 0 or i["relres_true"] > 1e-8 for i in infos):
         raise RuntimeError(f"headline solve did not reach the tolerance: {infos[-1]}")
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value = job_rate(world, args.steps, ms / 1e3)
     launches = int(sum(i["launches"] for i in infos))
 
     # ---- every form: solve time and product throughput ----
@@ -263,20 +297,24 @@ def main():
         fms, finf = timed(f, max(3, args.steps // 2), 2)
         info = P.hmat_info(handles[f])
         kt = P.hmat_time_matvec(handles[f], args.matvec_iters, False, stream)
-        s = STORE_BYTES[f]
-        p1_bytes = info["phase1_entries"] * s + info["partials"] * PART_BYTES[f]
-        p2_bytes = info["phase2_entries"] * s + 8 * info["n"]
+        # algorithmic bytes: stored entries at their element size, plus the partial
+        # sums written (projection) and y written once per segment (expansion)
+        p1_bytes = info["phase1_bytes"] + info["partials"] * PART_BYTES.get(f, 8)
+        p2_bytes = info["phase2_bytes"] + 8 * info["n"] * info["segments"]
         table[f] = {"solve_ms": fms / max(3, args.steps // 2), "iters": finf[-1]["iters"],
                     "restarts": finf[-1]["restarts"], "relres_true": finf[-1]["relres_true"],
                     "matvec_ms": kt[4], "kernel_ms": {"prep": kt[0], "phase1": kt[1], "reduce": kt[2], "phase2": kt[3]},
-                    "matvec_gbs": (info["stored_entries"] * s) / (kt[4] * 1e-3) / 1e9,
+                    "matvec_gbs": info["stored_bytes"] / (kt[4] * 1e-3) / 1e9,
                     "phase1_gbs": p1_bytes / (kt[1] * 1e-3) / 1e9, "phase2_gbs": p2_bytes / (kt[3] * 1e-3) / 1e9,
-                    "panel_bytes": info["panel_bytes"]}
+                    "stored_bytes": info["stored_bytes"], "panel_bytes": info["panel_bytes"],
+                    "segments": info["segments"]}
     head = table[args.form]
     dom = "phase2" if head["kernel_ms"]["phase2"] >= head["kernel_ms"]["phase1"] else "phase1"
     achieved = head[dom + "_gbs"]
-    roofline = {"bound": "hbm", "kernel": f"k_{dom}<{args.form}>", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": None}
+    kname = f"k_{dom}<{args.form}>"
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                "traffic": _profiled_traffic(kname, args.level)}
 
     # ---- end to end through the C ABI with pinned host buffers ----
     bh = torch.from_numpy(b_np.copy()).pin_memory()
@@ -289,12 +327,8 @@ def main():
     for _ in range(e2e_steps):
         xh.zero_()
         P.hmat_bicgstab(handles[args.form], bh, xh, tol=1e-8, maxit=2000, check_every=CHECK_EVERY, **FORM_OPTS[args.form])
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * mesh.n,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    e2e = {"value": job_rate(world, e2e_steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 16 * mesh.n,
            "d2h_bytes_per_step": 8 * mesh.n}
 
     cpu = None
@@ -305,7 +339,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": {"bf16": "bf16+f64", "fp32": "f32+f64", "fp64": "f64", "fp64_dfma": "f64"}[args.form],
+                "dtype": {"bf16": "bf16+f64", "fp64": "f64", "fp64_dfma": "f64", "m2_double": "f64"}.get(args.form, "f32+f64"),
                 "data": "synthetic",
                 "config": _config(mesh, args, {"blob_stats": stats, "host_build_s": round(build_s, 3)}),
                 "fp64_solve_ms": table.get("fp64", {}).get("solve_ms"),

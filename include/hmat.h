@@ -68,14 +68,41 @@ typedef enum hmat_status {
  *                  relative; meant to be wrapped in FP64 iterative refinement
  *                  (hmat_solve_opts.inner_tol).
  *
- * Every form stores each array (dense block, V_m, W_m) divided by a power of two
- * (2^floor(log2 max|array|)), which is exact and undone on the fly.
+ * The four forms above store each array (dense block, V_m, W_m) divided by a
+ * power of two (2^floor(log2 max|array|)), which is exact and undone on the fly.
+ *
+ * The paper's own variants (Section 3, Table 1), reproduced literally as
+ * baselines: every operation Table 1 puts in FP64 runs in IEEE FP64 (multiply,
+ * then add), every product of two FP32 operands is rounded to FP32, and the
+ * source vector is rounded to FP32 where Table 1 says FP32 (Section 3.5).
+ * Method 1-Double is HMAT_FP64_DFMA.
+ *  HMAT_M1_SINGLE  FP32 A|^m, V_m, W_m; FP32 x; z_m accumulated in FP32;
+ *                  y^_m in FP64 (Method 1-Single).
+ *  HMAT_M1_MIXED   FP32 A|^m, V_m, W_m; FP64 x; z_m = fl32(z_m + W_m x) with the
+ *                  right side in FP64; y^_m in FP64 (Method 1-Mixed).
+ *  HMAT_M2_DOUBLE  V'_m D_m W'_m (eq. 11-16) in FP64 (Method 2-Double).
+ *  HMAT_M2_SINGLE  FP32 A|^m, V'_m, W'_m, FP64 D_m; FP32 x; z_m in FP64
+ *                  (Method 2-Single).
+ *  HMAT_M2_MIXED   FP32 A|^m, V'_m, W'_m, FP64 D_m; FP64 x; z_m in FP64
+ *                  (Method 2-Mixed).
+ *  HMAT_M3         FP64 A|^m; rank i of a low-rank block in FP64 when
+ *                  d_i >= d_max 10^-c, else in FP32 (eq. 17-20); the FP64 ranks
+ *                  follow Method 2-Double, the FP32 ranks Method 2-Mixed, the two
+ *                  parts are added (Section 3.4).  Upload with hmat_upload_ex.
+ * These variants carry FP64 arithmetic per entry and are bound by the FP64 pipe
+ * of GB300, not by HBM.
  */
 typedef enum hmat_precision {
     HMAT_FP64 = 0,
     HMAT_FP64_DFMA = 1,
     HMAT_FP32 = 2,
-    HMAT_BF16 = 3
+    HMAT_BF16 = 3,
+    HMAT_M1_SINGLE = 4,
+    HMAT_M1_MIXED = 5,
+    HMAT_M2_DOUBLE = 6,
+    HMAT_M2_SINGLE = 7,
+    HMAT_M2_MIXED = 8,
+    HMAT_M3 = 9
 } hmat_precision;
 
 typedef struct hmat_t *hmat_handle;
@@ -152,14 +179,20 @@ int hmat_blob_stats_get(const void *blob, size_t blob_bytes, hmat_blob_stats *ou
  */
 int hmat_upload(const void *blob, size_t blob_bytes, int32_t precision, hmat_handle *out);
 
+/* hmat_upload with Method 3's c (eq. 19-20; ignored by the other forms). */
+int hmat_upload_ex(const void *blob, size_t blob_bytes, int32_t precision, int32_t method3_c, hmat_handle *out);
+
 /* Free every device and host resource of the handle (NULL is accepted). */
 int hmat_destroy(hmat_handle h);
 
 /*
  * hmat_matvec -- y = A~ x (overwrite) for nrhs vectors, column-major N x nrhs,
  * original panel order, in the handle's precision form.  x and y must not
- * overlap.  Asynchronous on `stream` for device pointers.
- * Errors: HMAT_ERR_ARG, HMAT_ERR_CUDA.
+ * overlap.  Asynchronous on `stream` for device pointers.  For a HMAT_BF16
+ * handle and nrhs >= 2 the columns go through the tensor-core product, 64 per
+ * pass (BF16 panels times x and t split into two BF16 parts, FP32
+ * accumulation); it allocates its buffers on first use.
+ * Errors: HMAT_ERR_ARG, HMAT_ERR_NOMEM, HMAT_ERR_CUDA.
  */
 int hmat_matvec(hmat_handle h, const double *x, double *y, int32_t nrhs, void *stream);
 
@@ -209,6 +242,40 @@ int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const hmat_solve
                      hmat_solve_info *info);
 
 /* ------------------------------------------------------------------------- */
+/* Many systems at once                                                       */
+/* ------------------------------------------------------------------------- */
+/*
+ * hmat_upload_batch -- one handle over `count` independent problems (blobs as for
+ * hmat_upload, each validated alone), held as one block-diagonal operator: the
+ * problems' index spaces are concatenated in the given order, so x and y of
+ * every call on the handle are the concatenation of the problems' vectors (each
+ * in its own original panel order), and one product is one launch sequence over
+ * all problems.  `method3_c` as for hmat_upload_ex.  Errors as hmat_upload.
+ */
+int hmat_upload_batch(const void *const *blobs, const size_t *blob_bytes, int32_t count, int32_t precision,
+                      int32_t method3_c, hmat_handle *out);
+
+/* Problems of a handle (1 unless made by hmat_upload_batch); `offsets`
+ * (count + 1 entries, may be NULL) receives their first rows and the total. */
+int hmat_problems(hmat_handle h, int32_t *count, int64_t *offsets);
+
+/*
+ * hmat_bicgstab_multi -- solve every (problem, right-hand side) system of a
+ * handle with its own BiCG-STAB recurrence (Algorithm 1), all advanced together:
+ * one product launch sequence per right-hand side and iteration serves every
+ * problem, the vector kernels run over all systems at once with per-system
+ * inner products, and every decision (stop, breakdown, true residual with the
+ * FP64 H-matrix, restart from it) is taken per system on the device.
+ * b, x: N_total x nrhs column-major (N_total = the handle's N), host or device;
+ * x holds the initial guess and receives the solution.  `opts` as for
+ * hmat_bicgstab_ex (NULL: defaults).  infos (may be NULL): count x nrhs entries,
+ * system (p, k) at index k * count + p; `launches` is the whole call's.
+ * Returns HMAT_OK when every system converged, else the first system's error.
+ */
+int hmat_bicgstab_multi(hmat_handle h, const double *b, double *x, int32_t nrhs, const hmat_solve_opts *opts,
+                        void *stream, hmat_solve_info *infos);
+
+/* ------------------------------------------------------------------------- */
 /* Product without allocation (an addition of this library; the paper has no  */
 /* counterpart)                                                               */
 /* ------------------------------------------------------------------------- */
@@ -230,8 +297,9 @@ int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const hmat_solve
  * operand copy, partial sums, operand buffers) lives in one static device array
  * of HMAT_NOALLOC_SCRATCH_BYTES compiled into the library; every GPU that loads
  * the library holds that array until the process exits.  A handle whose scratch
- * does not fit (roughly N above 20,000 panels for the FP64 form) is rejected with
- * HMAT_ERR_UNSUPPORTED.  The first call on a device looks up the array's device
+ * does not fit (roughly N above 20,000 panels for the FP64 form), and a handle of
+ * one of the paper's two-segment variants (HMAT_M1_MIXED, HMAT_M2_SINGLE,
+ * HMAT_M3), is rejected with HMAT_ERR_UNSUPPORTED.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls, on every handle, share the one array: calls that overlap on the GPU
  * (different streams without ordering) race and give wrong results.  The call
@@ -247,13 +315,19 @@ typedef struct hmat_handle_info {
     int32_t precision;
     int32_t nleaves;
     int64_t panel_bytes;         /* device bytes of the form's panels (algorithmic bytes read per product) */
-    int64_t panel_bytes_fp64;    /* device bytes of the FP64 copy                                           */
+    int64_t panel_bytes_fp64;    /* device bytes of the FP64 H-matrix of the true residual                  */
     int64_t index_bytes;         /* device bytes of the packing indices                                     */
     int64_t stored_entries;      /* dense_entries + lr_entries of the blob                                  */
     int64_t phase1_entries;      /* entries streamed by the projection t = W x                              */
     int64_t phase2_entries;      /* entries streamed by the expansion y = D x + V t                         */
     int64_t partials;            /* partial sums of blocks spanning several leaf clusters                   */
     int64_t rank_sum;
+    int64_t stored_bytes;        /* stored entries times their element bytes (no padding): the bytes one   */
+                                 /* product must read at least                                              */
+    int64_t phase1_bytes;        /* the projection's share of stored_bytes                                  */
+    int64_t phase2_bytes;        /* the expansion's share                                                   */
+    int32_t segments;            /* 1, or 2 for a paper variant whose product adds two expansions           */
+    int32_t method3_c;           /* c of eq. (19)-(20) for HMAT_M3, else 0                                  */
 } hmat_handle_info;
 
 int hmat_info(hmat_handle h, hmat_handle_info *out);
@@ -264,7 +338,12 @@ int hmat_info(hmat_handle h, hmat_handle_info *out);
  * that stream; ms_out[0..3] receive the mean milliseconds per launch of the
  * source-vector preparation, the projection (t = W x and the operand scatter),
  * the reduction of the blocks spanning several leaf clusters and the expansion
- * (y = D x + V t); ms_out[4] the mean per whole product.  `fp64` = 1 times the FP64 copy.  Synchronises `stream`.
+ * (y = D x + V t); ms_out[4] the mean per whole product.  The expansion runs as
+ * in a solver product, with the fused inner products of Algorithm 1, so it
+ * writes the handle's solver scalars: do not overlap it with a solve on the same
+ * handle.  For a paper variant of two segments each entry sums both segments'
+ * launches.  `fp64` = 1 times the FP64 H-matrix of the true residual.
+ * Synchronises `stream`.
  */
 int hmat_time_matvec(hmat_handle h, int32_t iters, int32_t fp64, void *stream, double *ms_out);
 

@@ -18,13 +18,17 @@ HMAT_OK = 0
 STATUS = {0: "ok", 1: "arg", 2: "bad_layout", 3: "nomem", 4: "cuda", 5: "breakdown_rho",
           6: "breakdown_omega", 7: "maxit", 8: "nonfinite", 9: "range", 10: "unsupported"}
 HMAT_FP64, HMAT_FP64_DFMA, HMAT_FP32, HMAT_BF16 = 0, 1, 2, 3
-PRECISIONS = {"fp64": HMAT_FP64, "fp64_dfma": HMAT_FP64_DFMA, "fp32": HMAT_FP32, "bf16": HMAT_BF16}
+HMAT_M1_SINGLE, HMAT_M1_MIXED, HMAT_M2_DOUBLE, HMAT_M2_SINGLE, HMAT_M2_MIXED, HMAT_M3 = 4, 5, 6, 7, 8, 9
+PRECISIONS = {"fp64": HMAT_FP64, "fp64_dfma": HMAT_FP64_DFMA, "fp32": HMAT_FP32, "bf16": HMAT_BF16,
+              # the paper's variants (Section 3, Table 1); Method 1-Double is "fp64_dfma"
+              "m1_single": HMAT_M1_SINGLE, "m1_mixed": HMAT_M1_MIXED, "m2_double": HMAT_M2_DOUBLE,
+              "m2_single": HMAT_M2_SINGLE, "m2_mixed": HMAT_M2_MIXED, "m3": HMAT_M3}
 
 # every symbol declared in include/hmat.h
 EXPORTS = ("hmat_build", "hmat_blob_free", "hmat_blob_stats_get", "hmat_upload", "hmat_destroy",
            "hmat_matvec", "hmat_matvec_fp64", "hmat_solve_opts_default", "hmat_bicgstab",
            "hmat_bicgstab_ex", "hmat_info", "hmat_time_matvec", "hmat_strerror", "hmat_last_cuda_error",
-           "hmat_matvec_noalloc")
+           "hmat_matvec_noalloc", "hmat_upload_ex", "hmat_upload_batch", "hmat_problems", "hmat_bicgstab_multi")
 
 
 class BlobStats(C.Structure):
@@ -47,7 +51,8 @@ class HandleInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("precision", C.c_int32), ("nleaves", C.c_int32), ("panel_bytes", C.c_int64),
                 ("panel_bytes_fp64", C.c_int64), ("index_bytes", C.c_int64), ("stored_entries", C.c_int64),
                 ("phase1_entries", C.c_int64), ("phase2_entries", C.c_int64), ("partials", C.c_int64),
-                ("rank_sum", C.c_int64)]
+                ("rank_sum", C.c_int64), ("stored_bytes", C.c_int64), ("phase1_bytes", C.c_int64),
+                ("phase2_bytes", C.c_int64), ("segments", C.c_int32), ("method3_c", C.c_int32)]
 
 
 class HmatError(RuntimeError):
@@ -91,6 +96,10 @@ def load():
         "hmat_strerror": (C.c_char_p, [C.c_int]),
         "hmat_last_cuda_error": (C.c_char_p, []),
         "hmat_matvec_noalloc": (C.c_int, [P, P, P, P]),
+        "hmat_upload_ex": (C.c_int, [P, SZ, I32, I32, C.POINTER(C.c_void_p)]),
+        "hmat_upload_batch": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(SZ), I32, I32, I32, C.POINTER(C.c_void_p)]),
+        "hmat_problems": (C.c_int, [P, C.POINTER(I32), P]),
+        "hmat_bicgstab_multi": (C.c_int, [P, P, P, I32, C.POINTER(SolveOpts), P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -148,7 +157,8 @@ def hmat_build(centroids, areas, leaf=32, eta=2.0, aca_eps=1e-4) -> bytes:
     _check(L.hmat_build(n, c.ctypes.data, a.ctypes.data, int(leaf), float(eta), float(aca_eps),
                         C.byref(buf), C.byref(size)), "hmat_build")
     try:
-        out = np.frombuffer(C.string_at(buf, size.value), dtype=np.uint8).copy()
+        out = np.empty(size.value, dtype=np.uint8)  # blobs may exceed 2 GiB: copy with memmove
+        C.memmove(out.ctypes.data, buf, size.value)
     finally:
         L.hmat_blob_free(buf)
     return out
@@ -162,14 +172,70 @@ def hmat_blob_stats(blob) -> dict:
     return {k: int(getattr(s, k)) for k, _ in BlobStats._fields_}
 
 
-def hmat_upload(blob, precision="fp64"):
-    """Device handle (int) of a blob in one precision form ("fp64", "fp64_dfma", "fp32", "bf16")."""
+def hmat_upload(blob, precision="fp64", c=None):
+    """Device handle (int) of a blob in one precision form (a key of PRECISIONS);
+    `c` is Method 3's split parameter (eq. 19-20), passed through hmat_upload_ex."""
     L = load()
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     b = np.ascontiguousarray(blob, dtype=np.uint8)
     h = C.c_void_p()
-    _check(L.hmat_upload(b.ctypes.data, b.nbytes, prec, C.byref(h)), "hmat_upload")
+    if c is None:
+        _check(L.hmat_upload(b.ctypes.data, b.nbytes, prec, C.byref(h)), "hmat_upload")
+    else:
+        _check(L.hmat_upload_ex(b.ctypes.data, b.nbytes, prec, int(c), C.byref(h)), "hmat_upload_ex")
     return h.value
+
+
+def hmat_upload_batch(blobs, precision="fp64", c=None):
+    """One handle over several problems (a block-diagonal operator; vectors are the
+    concatenation of the problems' vectors)."""
+    L = load()
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    arrs = [np.ascontiguousarray(b, dtype=np.uint8) for b in blobs]
+    ptrs = (C.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+    sizes = (C.c_size_t * len(arrs))(*[a.nbytes for a in arrs])
+    h = C.c_void_p()
+    _check(L.hmat_upload_batch(ptrs, sizes, len(arrs), prec, 0 if c is None else int(c), C.byref(h)),
+           "hmat_upload_batch")
+    return h.value
+
+
+def hmat_problems(h):
+    """First rows of the handle's problems plus the total (length count + 1)."""
+    L = load()
+    cnt = C.c_int32()
+    _check(L.hmat_problems(C.c_void_p(h), C.byref(cnt), None), "hmat_problems")
+    off = np.empty(cnt.value + 1, dtype=np.int64)
+    _check(L.hmat_problems(C.c_void_p(h), C.byref(cnt), C.c_void_p(off.ctypes.data)), "hmat_problems")
+    return off
+
+
+def hmat_bicgstab_multi(h, b, x, nrhs=1, tol=1e-8, maxit=1000, stream=None, **opts):
+    """Every (problem, right-hand side) system with its own recurrence; b and x are
+    N x nrhs column-major (torch: a contiguous (nrhs, N) tensor).  Returns the list
+    of per-system info dicts, system (p, k) at k * count + p."""
+    L = load()
+
+    def colmajor(a):  # numpy (N, nrhs) -> flat column-major FP64
+        return a if hasattr(a, "data_ptr") else np.asarray(a, dtype=np.float64).ravel(order="F").copy()
+
+    bb, xx = colmajor(b), colmajor(x)
+    pb, kb = _ptr(bb)
+    px, kx = _ptr(xx)
+    cnt = len(hmat_problems(h)) - 1
+    infos = (SolveInfo * (cnt * nrhs))()
+    o = hmat_solve_opts(tol=float(tol), maxit=int(maxit), **opts)
+    st = L.hmat_bicgstab_multi(C.c_void_p(h), pb, px, int(nrhs), C.byref(o), _stream_ptr(stream), infos)
+    if st in (1, 3, 4):
+        raise HmatError(st, "hmat_bicgstab_multi")
+    if not hasattr(x, "data_ptr"):
+        x[...] = kx.reshape(np.shape(x), order="F")
+    out = []
+    for inf in infos:
+        d = {k: getattr(inf, k) for k, _ in SolveInfo._fields_}
+        d["status_name"] = STATUS.get(d["status"], d["status"])
+        out.append(d)
+    return out
 
 
 def hmat_destroy(h):
@@ -240,10 +306,10 @@ def hmat_strerror(status) -> str:
 class HMatrix:
     """Owning wrapper of one uploaded handle."""
 
-    def __init__(self, blob, precision="fp64"):
+    def __init__(self, blob, precision="fp64", c=None):
         self.blob = np.ascontiguousarray(blob, dtype=np.uint8)
         self.precision = precision
-        self.h = hmat_upload(self.blob, precision)
+        self.h = hmat_upload(self.blob, precision, c)
         self.info = hmat_info(self.h)
         self.n = self.info["n"]
 

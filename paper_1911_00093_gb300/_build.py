@@ -13,8 +13,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libhmat.so")
 BUILD = os.path.join(HERE, "_build")
 
-CXX_SOURCES = ["builder.cpp", "layout.cpp"]
-CU_SOURCES = ["kernels.cu", "api.cu", "noalloc.cu"]
+CXX_SOURCES = ["builder.cpp", "layout.cpp", "paper_forms.cpp"]
+CU_SOURCES = ["kernels.cu", "kernels_table1.cu", "multi.cu", "mrhs.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,7 +34,7 @@ def _run(cmd):
 
 def build(force: bool = False, verbose: bool = False) -> str:
     srcs = [os.path.join(CSRC, s) for s in CXX_SOURCES + CU_SOURCES]
-    hdrs = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")] + [os.path.join(INCLUDE, "hmat.h")]
+    hdrs = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))] + [os.path.join(INCLUDE, "hmat.h")]
     if not force and os.path.exists(OUT):
         newest = max(os.path.getmtime(f) for f in srcs + hdrs + [__file__])
         if os.path.getmtime(OUT) >= newest:

@@ -39,22 +39,94 @@ Store store_of(int precision) {
     }
 }
 
+bool is_table1_precision(int precision) { return precision >= HMAT_M1_SINGLE && precision <= HMAT_M3; }
+
 }  // namespace
 
 namespace {
 
-// y = A~ x for one vector, everything on the device.
-//   x_orig != nullptr: source in original order (gathered); else the operand copy P.xs is ready
+// y = A~ x for one vector with the segments of an operator, everything on the device.
+//   x_src != nullptr: source gathered through src_perm (or copied) into the operand copy; else it is ready
 //   out_perm != nullptr: y written in original order
-void enqueue_product(hmat_t *h, const DevPanels &P, Store s, const double *x_src, const int32_t *src_perm,
-                     double *y, const int32_t *out_perm, const SolverScalars *skipS, int mode, cudaStream_t st) {
-    if (x_src) launch_prep(s, h->ix, x_src, src_perm, P.xs, st);
-    launch_phase1(s, h->ix, P, skipS, mode, st);
-    launch_reduce(s, h->ix, P, skipS, mode, st);
-    launch_phase2(s, h->ix, P, y, out_perm, skipS, mode, st);
+// The segments' expansions add up in y; the last one also leaves the shares of
+// Algorithm 1's inner products in dpart (dotmode 1: r~ . v, v . v; 2: s . t, t . t).
+void enqueue_segments(const HmatSegment *seg, int nseg, const double *x_src, const int32_t *src_perm, double *y,
+                      const int32_t *out_perm, const SolverScalars *skipS, int mode, cudaStream_t st,
+                      const double *w = nullptr, int dotmode = 0, double *dpart = nullptr) {
+    if (x_src) launch_prep(seg[0].store, seg[0].ix, x_src, src_perm, seg[0].P.xs, st);
+    for (int k = 0; k < nseg; ++k) {
+        launch_phase1(seg[k].store, seg[k].ix, seg[k].P, skipS, mode, st);
+        launch_reduce(seg[k].store, seg[k].ix, seg[k].P, skipS, mode, st);
+    }
+    for (int k = 0; k < nseg; ++k) {
+        const bool last = k == nseg - 1;
+        launch_phase2(seg[k].store, seg[k].ix, seg[k].P, y, out_perm, k > 0, skipS, mode, st, last ? w : nullptr,
+                      last ? dotmode : 0, dpart);
+    }
 }
 
-int alloc_panels(hmat_t *h, const BlobView &v, const Layout &L, Store s, DevPanels &P, int64_t *bytes_out) {
+int product_launches(const HmatSegment *seg, int nseg) {
+    int n = 1;  // operand copy
+    for (int k = 0; k < nseg; ++k) n += (seg[k].ix.nbig + seg[k].ix.ntasks) ? 3 : 2;
+    return n;
+}
+
+// Device copies of a layout's indices (perm is the handle's).
+int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
+    DevIndex &ix = g.ix;
+    ix.n = (int32_t)L.n;
+    ix.nleaves = L.nleaves;
+    ix.nlr = (int32_t)L.lr.size();
+    ix.nbig = (int32_t)L.red_big.size();
+    ix.ntasks = (int32_t)L.red_tasks.size();
+    ix.max_leaf = L.max_leaf;
+    ix.max_ld2 = L.max_ld2;
+    ix.perm = h->perm;
+    int32_t *gdst = nullptr, *red_big = nullptr, *red_tasks = nullptr;
+    P1Desc *p1 = nullptr;
+    P1Run *p1_runs = nullptr;
+    XDst *xdst = nullptr;
+    LrDesc *lr = nullptr;
+    P2Desc *p2 = nullptr;
+    double *tscale = nullptr;
+    int32_t *row_leaf = nullptr;
+    int st;
+    if ((st = h->upload(&p1, L.p1.data(), sizeof(P1Desc) * L.p1.size())) ||
+        (st = h->upload(&p1_runs, L.p1_runs.data(), sizeof(P1Run) * L.p1_runs.size())) ||
+        (st = h->upload(&xdst, L.xdst.data(), sizeof(XDst) * L.xdst.size())) ||
+        (st = h->upload(&lr, L.lr.data(), sizeof(LrDesc) * L.lr.size())) ||
+        (st = h->upload(&gdst, L.gdst.data(), 4 * L.gdst.size())) ||
+        (st = h->upload(&red_big, L.red_big.data(), 4 * L.red_big.size())) ||
+        (st = h->upload(&red_tasks, L.red_tasks.data(), 4 * L.red_tasks.size())) ||
+        (st = h->upload(&p2, L.p2.data(), sizeof(P2Desc) * L.p2.size())) ||
+        (st = h->upload(&tscale, L.tscale.data(), 8 * L.tscale.size())) ||
+        (st = h->upload(&row_leaf, L.row_leaf.data(), 4 * L.row_leaf.size()))) {
+        return st;
+    }
+    ix.p1 = p1; ix.p1_runs = p1_runs; ix.xdst = xdst; ix.lr = lr; ix.gdst = gdst; ix.p2 = p2;
+    ix.red_big = red_big; ix.red_tasks = red_tasks;
+    ix.tscale = L.tscale.empty() ? nullptr : tscale;
+    // phase-2 launch shape (phase2_rows): HMAT_PHASE2=cluster selects one CTA per
+    // leaf row cluster for every store (a tuning override; both are exact)
+    ix.row_leaf = row_leaf;
+    const char *p2env = std::getenv("HMAT_PHASE2");
+    ix.p2_rows = (p2env && std::strcmp(p2env, "cluster") == 0) ? 0 : 1;
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    ix.p2_grid = ix.p2_rows ? std::max(1, nsm) * kP2RowBlocksPerSM : L.nleaves;
+    g.partials_n = L.npart;
+    g.glen = L.glen;
+    h->index_bytes += (int64_t)(sizeof(P1Desc) * L.p1.size() + sizeof(P1Run) * L.p1_runs.size() +
+                                sizeof(XDst) * L.xdst.size() + sizeof(LrDesc) * L.lr.size() + 4 * L.gdst.size() +
+                                sizeof(P2Desc) * L.p2.size() + 4 * (L.red_big.size() + L.red_tasks.size()) +
+                                8 * L.tscale.size() + 4 * L.row_leaf.size());
+    return HMAT_OK;
+}
+
+// Typed panels of one store plus its work buffers; shared_xs != nullptr reuses
+// another segment's operand copy of x (same cluster order, FP64).
+int alloc_panels(hmat_t *h, const BlobView &v, const Layout &L, Store s, DevPanels &P, int64_t *bytes_out,
+                 void *shared_xs = nullptr) {
     P.store = s;
     const size_t es = store_bytes(s);
     const size_t b1 = (size_t)L.p1_elems * es, b2 = (size_t)L.p2_elems * es;
@@ -72,85 +144,148 @@ int alloc_panels(hmat_t *h, const BlobView &v, const Layout &L, Store s, DevPane
     if (st) return st;
     P.q1 = q1;
     P.p2 = p2;
-    st = h->alloc(&P.xs, (size_t)L.n * operand_bytes(s));
-    if (st) return st;
+    if (shared_xs) {
+        P.xs = shared_xs;
+    } else {
+        st = h->alloc(&P.xs, (size_t)L.n * operand_bytes(s));
+        if (st) return st;
+    }
     st = h->alloc(&P.part, (size_t)std::max<int64_t>(L.npart, 1) * partial_bytes(s));
     if (st) return st;
     st = h->alloc(&P.g, (size_t)std::max<int64_t>(L.glen, 1) * operand_bytes(s));
     if (st) return st;
     CK(cudaMemset(P.g, 0, (size_t)std::max<int64_t>(L.glen, 1) * operand_bytes(s)));  // zero padding columns
-    *bytes_out = (int64_t)(b1 + b2);
+    *bytes_out += (int64_t)(b1 + b2);
     return HMAT_OK;
 }
 
-}  // namespace
+// Indices of the tensor-core product for many right-hand sides (BF16 handles):
+// the U row and power of two feeding every operand slot, the t rows of the
+// low-rank blocks, the reduction tasks of every multi-cluster block.
+int upload_mrhs_index(hmat_t *h, const Layout &L) {
+    MrhsIndex &mx = h->mx;
+    std::vector<int32_t> tbase(L.lr.size());
+    int64_t trows = 0;
+    for (size_t q = 0; q < L.lr.size(); ++q) {
+        tbase[q] = (int32_t)trows;
+        trows += L.lr[q].rank;
+    }
+    const int64_t zero_row = L.n + trows;
+    if (zero_row + 1 > (int64_t(1) << 31) - 16) return HMAT_ERR_UNSUPPORTED;
+    std::vector<MrhsSrc> src((size_t)L.glen, MrhsSrc{(int32_t)zero_row, 0});
+    for (size_t k = 0; k < L.p1.size(); ++k) {
+        const P1Desc &d = L.p1[k];
+        for (int e = 0; e < d.xdcnt; ++e) {
+            const XDst &x = L.xdst[d.xdbeg + e];
+            for (int j = 0; j < d.xlen; ++j) src[x.goff + j] = MrhsSrc{d.xbeg + j, x.scale};
+        }
+    }
+    std::vector<int32_t> tasks;
+    for (size_t q = 0; q < L.lr.size(); ++q) {
+        const LrDesc &d = L.lr[q];
+        for (int k = 0; k < d.gcnt; ++k)
+            for (int l = 0; l < d.rank; ++l)
+                src[L.gdst[d.gbeg + k] + l] = MrhsSrc{(int32_t)(L.n + tbase[q] + l), d.scale};
+        if (d.cnt > 1)
+            for (int l = 0; l < d.rank; ++l) tasks.push_back((int32_t)((q << 6) | l));
+    }
+    MrhsSrc *dsrc = nullptr;
+    int32_t *dtb = nullptr, *dtasks = nullptr;
+    int st;
+    if ((st = h->upload(&dsrc, src.data(), sizeof(MrhsSrc) * src.size())) ||
+        (st = h->upload(&dtb, tbase.data(), 4 * tbase.size())) ||
+        (st = h->upload(&dtasks, tasks.data(), 4 * tasks.size())))
+        return st;
+    mx.src = dsrc;
+    mx.tbase = dtb;
+    mx.tasks = dtasks;
+    mx.ntasks = (int32_t)tasks.size();
+    mx.urows = zero_row + 1;
+    mx.npart = L.npart;
+    h->index_bytes += (int64_t)(sizeof(MrhsSrc) * src.size() + 4 * (tbase.size() + tasks.size()));
+    h->mrhs = true;
+    return HMAT_OK;
+}
 
-extern "C" int hmat_upload(const void *blob, size_t blob_bytes, int32_t precision, hmat_handle *out) {
-    if (!blob || !out) return HMAT_ERR_ARG;
-    if (precision < HMAT_FP64 || precision > HMAT_BF16) return HMAT_ERR_ARG;
-    *out = nullptr;
-    BlobView v;
-    int st = parse_blob(blob, blob_bytes, v);
-    if (st != HMAT_OK) return st;
+void add_stats(hmat_t *h, const Layout &L, Store s) {
+    h->stored_entries += L.stored_entries;
+    h->phase1_entries += L.phase1_entries;
+    h->phase2_entries += L.phase2_entries;
+    h->phase1_bytes += L.phase1_entries * (int64_t)store_bytes(s);
+    h->phase2_bytes += L.phase2_entries * (int64_t)store_bytes(s);
+    h->partials_n += L.npart;
+    h->rank_sum += L.rank_sum;
+}
+
+// A handle over a validated view; `offsets` delimits its problems (one problem:
+// {0, n}; a block-diagonal batch: one range per problem).
+int upload_view(const BlobView &v, int32_t precision, int32_t method3_c, const std::vector<int64_t> &offsets,
+                hmat_handle *out) {
+    int st = HMAT_OK;
     std::unique_ptr<hmat_t> hp;
     try {
         hp.reset(new hmat_t());
         hmat_t *h = hp.get();
+        h->prob_off = offsets;
         Layout L;
         st = build_layout(v, L);
         if (st == HMAT_OK) st = check_layout(L);
         if (st != HMAT_OK) return st;
         CK(cudaGetDevice(&h->device));
         h->precision = precision;
-        h->store = store_of(precision);
-        h->store64 = precision == HMAT_FP64_DFMA ? Store::F64 : Store::DF;
-        h->separate64 = !(precision == HMAT_FP64 || precision == HMAT_FP64_DFMA);
-        h->stored_entries = L.stored_entries;
-        h->phase1_entries = L.phase1_entries;
-        h->phase2_entries = L.phase2_entries;
-        h->partials_n = L.npart;
-        h->glen = L.glen;
-        h->rank_sum = L.rank_sum;
+        h->method3_c = precision == HMAT_M3 ? method3_c : 0;
+        h->n = L.n;
+        int32_t *perm = nullptr;
+        if ((st = h->upload(&perm, L.perm.data(), 4 * L.perm.size()))) return st;
+        h->perm = perm;
+        h->index_bytes = 4 * (int64_t)L.perm.size();
 
-        // indices
-        DevIndex &ix = h->ix;
-        ix.n = (int32_t)L.n;
-        ix.nleaves = L.nleaves;
-        ix.nlr = (int32_t)L.lr.size();
-        ix.nbig = (int32_t)L.red_big.size();
-        ix.ntasks = (int32_t)L.red_tasks.size();
-        ix.max_leaf = L.max_leaf;
-        ix.max_ld2 = L.max_ld2;
-        int32_t *perm = nullptr, *gdst = nullptr, *red_big = nullptr, *red_tasks = nullptr;
-        P1Desc *p1 = nullptr;
-        P1Run *p1_runs = nullptr;
-        XDst *xdst = nullptr;
-        LrDesc *lr = nullptr;
-        P2Desc *p2 = nullptr;
-        if ((st = h->upload(&perm, L.perm.data(), 4 * L.perm.size())) ||
-            (st = h->upload(&p1, L.p1.data(), sizeof(P1Desc) * L.p1.size())) ||
-            (st = h->upload(&p1_runs, L.p1_runs.data(), sizeof(P1Run) * L.p1_runs.size())) ||
-            (st = h->upload(&xdst, L.xdst.data(), sizeof(XDst) * L.xdst.size())) ||
-            (st = h->upload(&lr, L.lr.data(), sizeof(LrDesc) * L.lr.size())) ||
-            (st = h->upload(&gdst, L.gdst.data(), 4 * L.gdst.size())) ||
-            (st = h->upload(&red_big, L.red_big.data(), 4 * L.red_big.size())) ||
-            (st = h->upload(&red_tasks, L.red_tasks.data(), 4 * L.red_tasks.size())) ||
-            (st = h->upload(&p2, L.p2.data(), sizeof(P2Desc) * L.p2.size()))) {
-            return st;
-        }
-        ix.perm = perm; ix.p1 = p1; ix.p1_runs = p1_runs; ix.xdst = xdst; ix.lr = lr; ix.gdst = gdst; ix.p2 = p2;
-        ix.red_big = red_big; ix.red_tasks = red_tasks;
-        h->index_bytes = (int64_t)(4 * L.perm.size() + sizeof(P1Desc) * L.p1.size() + sizeof(P1Run) * L.p1_runs.size() +
-                                   sizeof(XDst) * L.xdst.size() + sizeof(LrDesc) * L.lr.size() + 4 * L.gdst.size() +
-                                   sizeof(P2Desc) * L.p2.size() + 4 * (L.red_big.size() + L.red_tasks.size()));
-
-        // panels
-        if ((st = alloc_panels(h, v, L, h->store, h->P, &h->panel_bytes))) return st;
-        if (h->separate64) {
-            if ((st = alloc_panels(h, v, L, h->store64, h->P64, &h->panel_bytes64))) return st;
+        if (!is_table1_precision(precision)) {
+            // one layout; the FP64 operator shares its indices (DF panels, or the
+            // F64 panels themselves for the FP64 FMA form)
+            HmatSegment &g = h->seg[0];
+            h->nseg = 1;
+            g.store = store_of(precision);
+            if ((st = upload_index(h, L, g))) return st;
+            add_stats(h, L, g.store);
+            if ((st = alloc_panels(h, v, L, g.store, g.P, &h->panel_bytes))) return st;
+            h->seg64.ix = g.ix;
+            h->seg64.partials_n = g.partials_n;
+            h->seg64.glen = g.glen;
+            if (precision == HMAT_BF16 && (st = upload_mrhs_index(h, L))) return st;
+            if (precision == HMAT_FP64 || precision == HMAT_FP64_DFMA) {
+                h->seg64.store = g.store;
+                h->seg64.P = g.P;
+                h->panel_bytes64 = h->panel_bytes;
+            } else {
+                h->seg64.store = Store::DF;
+                if ((st = alloc_panels(h, v, L, Store::DF, h->seg64.P, &h->panel_bytes64))) return st;
+            }
         } else {
-            h->P64 = h->P;
-            h->panel_bytes64 = h->panel_bytes;
+            // the paper's variant: derived segments, plus the FP64 H-matrix
+            // (Method 1-Double) for the true residual
+            DerivedSegment dseg[2];
+            Store dstore[2];
+            int nseg = 0;
+            if ((st = derive_table1(v, precision, method3_c, dseg, dstore, &nseg))) return st;
+            h->nseg = nseg;
+            for (int k = 0; k < nseg; ++k) {
+                Layout Lk;
+                st = build_layout(dseg[k].view, Lk);
+                if (st == HMAT_OK) st = check_layout(Lk);
+                if (st != HMAT_OK) return st;
+                HmatSegment &g = h->seg[k];
+                g.store = dstore[k];
+                if ((st = upload_index(h, Lk, g))) return st;
+                add_stats(h, Lk, g.store);
+                if ((st = alloc_panels(h, dseg[k].view, Lk, g.store, g.P, &h->panel_bytes,
+                                       k > 0 ? h->seg[0].P.xs : nullptr)))
+                    return st;
+            }
+            HmatSegment &g = h->seg64;
+            g.store = Store::F64;
+            if ((st = upload_index(h, L, g))) return st;
+            if ((st = alloc_panels(h, v, L, g.store, g.P, &h->panel_bytes64))) return st;
         }
         // solver vectors and scratch
         const size_t nb = 8 * (size_t)L.n;
@@ -158,7 +293,7 @@ extern "C" int hmat_upload(const void *blob, size_t blob_bytes, int32_t precisio
         for (double **pp : vecs)
             if ((st = h->alloc(pp, nb))) return st;
         if ((st = h->alloc(&h->partials, sizeof(double) * 2 * (size_t)vec_blocks(L.n))) ||
-            (st = h->alloc(&h->dpart, sizeof(double) * 2 * (size_t)L.nleaves)) ||
+            (st = h->alloc(&h->dpart, sizeof(double) * 2 * (size_t)std::max(L.nleaves, h->seg[0].ix.p2_grid))) ||
             (st = h->alloc(&h->S, sizeof(SolverScalars)))) {
             return st;
         }
@@ -175,6 +310,56 @@ extern "C" int hmat_upload(const void *blob, size_t blob_bytes, int32_t precisio
     return HMAT_OK;
 }
 
+int upload_impl(const void *blob, size_t blob_bytes, int32_t precision, int32_t method3_c, hmat_handle *out) {
+    if (!blob || !out) return HMAT_ERR_ARG;
+    if (precision < HMAT_FP64 || precision > HMAT_M3) return HMAT_ERR_ARG;
+    *out = nullptr;
+    BlobView v;
+    int st = parse_blob(blob, blob_bytes, v);
+    if (st != HMAT_OK) return st;
+    return upload_view(v, precision, method3_c, {0, v.h->n}, out);
+}
+
+}  // namespace
+
+extern "C" int hmat_upload(const void *blob, size_t blob_bytes, int32_t precision, hmat_handle *out) {
+    return upload_impl(blob, blob_bytes, precision, 0, out);
+}
+
+extern "C" int hmat_upload_batch(const void *const *blobs, const size_t *blob_bytes, int32_t count, int32_t precision,
+                                 int32_t method3_c, hmat_handle *out) {
+    if (!blobs || !blob_bytes || !out || count < 1) return HMAT_ERR_ARG;
+    if (precision < HMAT_FP64 || precision > HMAT_M3) return HMAT_ERR_ARG;
+    *out = nullptr;
+    try {
+        std::vector<BlobView> views(count);
+        for (int32_t p = 0; p < count; ++p) {
+            if (!blobs[p]) return HMAT_ERR_ARG;
+            int st = parse_blob(blobs[p], blob_bytes[p], views[p]);
+            if (st != HMAT_OK) return st;
+        }
+        CombinedBlob cb;
+        int st = combine_blobs(views.data(), count, cb);
+        if (st != HMAT_OK) return st;
+        return upload_view(cb.view, precision, method3_c, cb.offsets, out);
+    } catch (const std::bad_alloc &) {
+        return HMAT_ERR_NOMEM;
+    }
+}
+
+extern "C" int hmat_problems(hmat_handle h, int32_t *count, int64_t *offsets) {
+    if (!h || !count) return HMAT_ERR_ARG;
+    *count = (int32_t)h->prob_off.size() - 1;
+    if (offsets)
+        for (size_t k = 0; k < h->prob_off.size(); ++k) offsets[k] = h->prob_off[k];
+    return HMAT_OK;
+}
+
+extern "C" int hmat_upload_ex(const void *blob, size_t blob_bytes, int32_t precision, int32_t method3_c,
+                              hmat_handle *out) {
+    return upload_impl(blob, blob_bytes, precision, method3_c, out);
+}
+
 extern "C" int hmat_destroy(hmat_handle h) {
     delete h;
     return HMAT_OK;
@@ -182,12 +367,15 @@ extern "C" int hmat_destroy(hmat_handle h) {
 
 namespace {
 
+int mrhs_matvec(hmat_t *h, const double *x, double *y, int32_t nrhs, cudaStream_t st);
+
 int matvec_impl(hmat_handle h, const double *x, double *y, int32_t nrhs, void *stream, bool fp64) {
     if (!h || !x || !y || nrhs < 1) return HMAT_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    const DevPanels &P = fp64 ? h->P64 : h->P;
-    const Store s = fp64 ? h->store64 : h->store;
-    const int64_t n = h->ix.n;
+    if (!fp64 && h->mrhs && nrhs >= 2) return mrhs_matvec(h, x, y, nrhs, st);
+    const HmatSegment *seg = fp64 ? &h->seg64 : h->seg;
+    const int nseg = fp64 ? 1 : h->nseg;
+    const int64_t n = h->n;
     const bool dx = is_device_pointer(x), dy = is_device_pointer(y);
     for (int32_t k = 0; k < nrhs; ++k) {
         const double *xk = x + (size_t)k * n;
@@ -198,7 +386,7 @@ int matvec_impl(hmat_handle h, const double *x, double *y, int32_t nrhs, void *s
             src = h->stage_in;
         }
         double *dst = dy ? yk : h->stage_out;
-        enqueue_product(h, P, s, src, h->ix.perm, dst, h->ix.perm, nullptr, 0, st);
+        enqueue_segments(seg, nseg, src, h->perm, dst, h->perm, nullptr, 0, st);
         CK(cudaGetLastError());
         if (!dy) {
             CK(cudaMemcpyAsync(yk, h->stage_out, 8 * n, cudaMemcpyDeviceToHost, st));
@@ -213,19 +401,18 @@ int matvec_impl(hmat_handle h, const double *x, double *y, int32_t nrhs, void *s
 // One iteration of Algorithm 1 on the device (every kernel returns at once
 // after the run has stopped).
 void enqueue_iteration(hmat_t *h, int iter_limit, cudaStream_t st) {
-    const int64_t n = h->ix.n;
-    const Store s = h->store;
-    launch_update_p(s, n, h->r, h->p, h->v, h->P.xs, h->S, st);
+    const int64_t n = h->n;
+    const Store s = h->seg[0].store;
+    void *xs = h->seg[0].P.xs;  // operand copy shared by the segments
+    launch_update_p(s, n, h->r, h->p, h->v, xs, h->S, st);
     // v = A p, with alpha = rho / (r~ . v)
-    launch_phase1(s, h->ix, h->P, h->S, 1, st);
-    launch_reduce(s, h->ix, h->P, h->S, 1, st);
-    launch_phase2(s, h->ix, h->P, h->v, nullptr, h->S, 1, st, h->rt, 1, h->S, h->dpart);
-    launch_update_s(s, n, h->r, h->v, h->s, h->P.xs, h->x, h->p, h->S, h->partials, st);
+    enqueue_segments(h->seg, h->nseg, nullptr, nullptr, h->v, nullptr, h->S, 1, st, h->rt, 1, h->dpart);
+    const HmatSegment &last = h->seg[h->nseg - 1];
+    const int ndp = phase2_items(last.store, last.ix);  // work items of the expansion that leaves the shares
+    launch_update_s(s, n, h->r, h->v, h->s, xs, h->S, h->partials, h->dpart, ndp, st);
     // t = A s, with omega = (t . s) / (t . t)
-    launch_phase1(s, h->ix, h->P, h->S, 2, st);
-    launch_reduce(s, h->ix, h->P, h->S, 2, st);
-    launch_phase2(s, h->ix, h->P, h->t, nullptr, h->S, 2, st, h->s, 2, h->S, h->dpart);
-    launch_update_xr(n, h->x, h->p, h->s, h->t, h->r, h->rt, h->S, h->partials, iter_limit, st);
+    enqueue_segments(h->seg, h->nseg, nullptr, nullptr, h->t, nullptr, h->S, 2, st, h->s, 2, h->dpart);
+    launch_update_xr(n, h->x, h->p, h->s, h->t, h->r, h->rt, h->S, h->partials, h->dpart, ndp, iter_limit, st);
 }
 
 int read_scalars(hmat_t *h, cudaStream_t st) {
@@ -285,27 +472,28 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
     hmat_solve_info &inf = info ? *info : loc;
     std::memset(&inf, 0, sizeof(inf));
     cudaStream_t st = (cudaStream_t)stream;
-    const int64_t n = h->ix.n;
+    const int64_t n = h->n;
     const bool db = is_device_pointer(b), dx = is_device_pointer(x);
     // kernels per product (source operand, projection, reduction when some block
     // spans several leaf clusters, expansion) and per iteration (p update, two
     // products without operand preparation whose expansions also give alpha and
     // omega, s update, x/r update with the count of the next iteration)
-    const int kProductLaunches = (h->ix.nbig + h->ix.ntasks) ? 4 : 3;
+    const int kProductLaunches = product_launches(h->seg, h->nseg);
+    const int kProduct64Launches = product_launches(&h->seg64, 1);
     const int kIterationLaunches = 3 + 2 * (kProductLaunches - 1);
     const double *bsrc = b;
     if (!db) {
         CK(cudaMemcpyAsync(h->stage_in, b, 8 * n, cudaMemcpyHostToDevice, st));
         bsrc = h->stage_in;
     }
-    launch_gather(n, h->ix.perm, bsrc, h->b, st);
+    launch_gather(n, h->perm, bsrc, h->b, st);
     int launches = 1;
     const double *xsrc = x;
     if (!dx) {
         CK(cudaMemcpyAsync(h->stage_out, x, 8 * n, cudaMemcpyHostToDevice, st));
         xsrc = h->stage_out;
     }
-    launch_gather(n, h->ix.perm, xsrc, h->x, st);
+    launch_gather(n, h->perm, xsrc, h->x, st);
     CK(cudaMemsetAsync(h->S, 0, sizeof(SolverScalars), st));
     // ||b||
     launch_residual(n, h->b, nullptr, h->r, h->rt, h->S, h->partials, -1, st);
@@ -322,7 +510,7 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
         inf.relres_true = 0.0;
     } else {
         // first run: r_0 = b - A~ x_0 with the iterated operator (Algorithm 1)
-        enqueue_product(h, h->P, h->store, h->x, nullptr, h->y, nullptr, nullptr, 0, st);
+        enqueue_segments(h->seg, h->nseg, h->x, nullptr, h->y, nullptr, nullptr, 0, st);
         launch_residual(n, h->b, h->y, h->r, h->rt, h->S, h->partials, o.maxit, st);  // run 1 starts
         launches += kProductLaunches + 1;
         CK(cudaGetLastError());
@@ -350,9 +538,9 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
             inf.relres_inner = std::sqrt(h->S_host->rnorm2 / bnorm2);
             inf.iters = h->S_host->iters;
             // true residual with the FP64 H-matrix (Section 4.1.3); r~ = r for a restart
-            enqueue_product(h, h->P64, h->store64, h->x, nullptr, h->y, nullptr, nullptr, 0, st);
+            enqueue_segments(&h->seg64, 1, h->x, nullptr, h->y, nullptr, nullptr, 0, st);
             launch_residual(n, h->b, h->y, h->r, h->rt, h->S, h->partials, -1, st);
-            launches += kProductLaunches + 1;
+            launches += kProduct64Launches + 1;
             inf.matvecs_fp64 += 1;
             if ((rc = read_scalars(h, st))) return rc;
             const double rel = std::sqrt(h->S_host->rnorm2 / bnorm2);
@@ -368,7 +556,7 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
     }
     // products with the iterated operator: r_0, then two per iteration except a stop at ||s||
     double *xo = dx ? x : h->stage_out;
-    launch_scatter(n, h->ix.perm, h->x, xo, st);
+    launch_scatter(n, h->perm, h->x, xo, st);
     launches += 1;
     inf.launches = launches;
     if (!dx) CK(cudaMemcpyAsync(x, h->stage_out, 8 * n, cudaMemcpyDeviceToHost, st));
@@ -389,12 +577,258 @@ extern "C" int hmat_bicgstab(hmat_handle h, const double *b, double *x, double t
     return hmat_bicgstab_ex(h, b, x, &o, stream, info);
 }
 
+namespace {
+
+// Buffers of the many-system solver for nrhs right-hand sides (kept while they fit).
+int multi_ensure(hmat_t *h, int nrhs) {
+    auto &m = h->multi;
+    if (m.cap >= nrhs) return HMAT_OK;
+    for (void *q : m.mine) h->release(q);
+    m.mine.clear();
+    if (m.graph) {
+        cudaGraphExecDestroy(m.graph);
+        m.graph = nullptr;
+    }
+    if (m.S_host) {
+        cudaFreeHost(m.S_host);
+        m.S_host = nullptr;
+    }
+    m.cap = 0;
+    const int nprob = (int)h->prob_off.size() - 1;
+    const int nsys = nprob * nrhs;
+    const size_t vb = 8 * (size_t)h->n * nrhs;
+    int64_t maxn = 0;
+    for (int p = 0; p < nprob; ++p) maxn = std::max(maxn, h->prob_off[p + 1] - h->prob_off[p]);
+    const int bx = multi_blocks_x(maxn, nsys);
+    double **vecs[] = {&m.b, &m.x, &m.r, &m.rt, &m.p, &m.v, &m.s, &m.t, &m.y, &m.stage};
+    int st;
+    for (double **pp : vecs) {
+        if ((st = h->alloc(pp, vb))) return st;
+        m.mine.push_back(*pp);
+    }
+    if ((st = h->alloc(&m.partials, sizeof(double) * 2 * (size_t)bx * nsys))) return st;
+    m.mine.push_back(m.partials);
+    if ((st = h->alloc(&m.S, sizeof(SysScalars) * (size_t)nsys))) return st;
+    m.mine.push_back(m.S);
+    std::vector<SysDesc> sys(nsys);
+    for (int k = 0; k < nrhs; ++k)
+        for (int p = 0; p < nprob; ++p) {
+            SysDesc &d = sys[(size_t)k * nprob + p];
+            d.off = (int64_t)k * h->n + h->prob_off[p];
+            d.n = (int32_t)(h->prob_off[p + 1] - h->prob_off[p]);
+            d.pad = 0;
+        }
+    if ((st = h->upload(&m.sys, sys.data(), sizeof(SysDesc) * sys.size()))) return st;
+    m.mine.push_back(m.sys);
+    CK(cudaMemset(m.S, 0, sizeof(SysScalars) * (size_t)nsys));
+    CK(cudaMemset(m.p, 0, vb));
+    CK(cudaMemset(m.v, 0, vb));
+    CK(cudaHostAlloc((void **)&m.S_host, sizeof(SysScalars) * (size_t)nsys, cudaHostAllocDefault));
+    m.cap = nrhs;
+    return HMAT_OK;
+}
+
+MultiGrid multi_grid(hmat_t *h, int nrhs) {
+    MultiGrid g;
+    const int nprob = (int)h->prob_off.size() - 1;
+    int64_t maxn = 0;
+    for (int p = 0; p < nprob; ++p) maxn = std::max(maxn, h->prob_off[p + 1] - h->prob_off[p]);
+    g.nsys = nprob * nrhs;
+    g.bx = multi_blocks_x(maxn, g.nsys);
+    g.sys = h->multi.sys;
+    g.S = h->multi.S;
+    g.partials = h->multi.partials;
+    return g;
+}
+
+// y(:, k) = A x(:, k) for every column, cluster order (a block-diagonal batch is one operator)
+void multi_products(hmat_t *h, const HmatSegment *seg, int nseg, const double *x, double *y, int nrhs,
+                    cudaStream_t st) {
+    if (seg == h->seg && h->mrhs && h->mx.U && nrhs >= 2) {  // tensor cores, 64 columns per pass
+        for (int k0 = 0; k0 < nrhs; k0 += kMrhsCols)
+            launch_mrhs_product(h->seg[0].ix, h->mx, h->seg[0].P, x + (size_t)k0 * h->n, h->n, y + (size_t)k0 * h->n,
+                                h->n, std::min(kMrhsCols, nrhs - k0), st);
+        return;
+    }
+    for (int k = 0; k < nrhs; ++k)
+        enqueue_segments(seg, nseg, x + (size_t)k * h->n, nullptr, y + (size_t)k * h->n, nullptr, nullptr, 0, st);
+}
+
+int multi_product_launches(hmat_t *h, const HmatSegment *seg, int nseg, int nrhs) {
+    if (seg == h->seg && h->mrhs && h->mx.U && nrhs >= 2)
+        return ((nrhs + kMrhsCols - 1) / kMrhsCols) * (h->mx.ntasks > 0 ? 4 : 3);
+    return nrhs * product_launches(seg, nseg);
+}
+
+// buffers of the tensor-core product (first many-right-hand-side solve)
+int mrhs_buffers(hmat_t *h) {
+    if (!h->mrhs || h->mx.U) return HMAT_OK;
+    float *U = nullptr, *part = nullptr;
+    int st;
+    if ((st = h->alloc(&U, sizeof(float) * kMrhsCols * (size_t)h->mx.urows)) ||
+        (st = h->alloc(&part, sizeof(float) * kMrhsCols * (size_t)std::max<int64_t>(h->mx.npart, 1))))
+        return st;
+    CK(cudaMemset(U, 0, sizeof(float) * kMrhsCols * (size_t)h->mx.urows));  // the zero row stays zero
+    h->mx.U = U;
+    h->mx.part = part;
+    return HMAT_OK;
+}
+
+void multi_iteration(hmat_t *h, const MultiGrid &g, int nrhs, int iter_limit, cudaStream_t st) {
+    auto &m = h->multi;
+    const MultiVecs v{m.x, m.r, m.rt, m.p, m.v, m.s, m.t};
+    launch_miteration_vec(g, 0, v, iter_limit, st);  // p
+    multi_products(h, h->seg, h->nseg, m.p, m.v, nrhs, st);
+    launch_miteration_vec(g, 1, v, iter_limit, st);  // alpha
+    launch_miteration_vec(g, 2, v, iter_limit, st);  // s
+    multi_products(h, h->seg, h->nseg, m.s, m.t, nrhs, st);
+    launch_miteration_vec(g, 3, v, iter_limit, st);  // omega
+    launch_miteration_vec(g, 4, v, iter_limit, st);  // x, r
+}
+
+int multi_read(hmat_t *h, int nsys, cudaStream_t st, bool *running) {
+    CK(cudaMemcpyAsync(h->multi.S_host, h->multi.S, sizeof(SysScalars) * (size_t)nsys, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *running = false;
+    for (int k = 0; k < nsys; ++k)
+        if (h->multi.S_host[k].state == 0 && h->multi.S_host[k].flag == 0) *running = true;
+    return HMAT_OK;
+}
+
+// Several columns through the tensor-core product: original order in and out,
+// host or device pointers.
+int mrhs_matvec(hmat_t *h, const double *x, double *y, int32_t nrhs, cudaStream_t st) {
+    int rc;
+    if ((rc = multi_ensure(h, nrhs)) || (rc = mrhs_buffers(h))) return rc;
+    auto &m = h->multi;
+    const int64_t n = h->n;
+    const size_t vb = 8 * (size_t)n * nrhs;
+    const bool dx = is_device_pointer(x), dy = is_device_pointer(y);
+    const double *src = x;
+    if (!dx) {
+        CK(cudaMemcpyAsync(m.stage, x, vb, cudaMemcpyHostToDevice, st));
+        src = m.stage;
+    }
+    launch_mgather(n, nrhs, h->perm, src, m.x, st);
+    multi_products(h, h->seg, h->nseg, m.x, m.y, nrhs, st);
+    double *dst = dy ? y : m.stage;
+    launch_mscatter(n, nrhs, h->perm, m.y, dst, st);
+    if (!dy) CK(cudaMemcpyAsync(y, m.stage, vb, cudaMemcpyDeviceToHost, st));
+    CK(cudaGetLastError());
+    if (!dx || !dy) CK(cudaStreamSynchronize(st));
+    return HMAT_OK;
+}
+
+}  // namespace
+
+extern "C" int hmat_bicgstab_multi(hmat_handle h, const double *b, double *x, int32_t nrhs,
+                                   const hmat_solve_opts *opts_in, void *stream, hmat_solve_info *infos) {
+    if (!h || !b || !x || nrhs < 1) return HMAT_ERR_ARG;
+    hmat_solve_opts o;
+    hmat_solve_opts_default(&o);
+    if (opts_in) o = *opts_in;
+    if (!(o.tol > 0.0) || !(o.inner_tol >= 0.0) || o.maxit < 0 || o.max_restarts < 0 || o.check_every < 1)
+        return HMAT_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = multi_ensure(h, nrhs);
+    if (rc) return rc;
+    if (nrhs >= 2 && (rc = mrhs_buffers(h))) return rc;
+    auto &m = h->multi;
+    const MultiGrid g = multi_grid(h, nrhs);
+    const int64_t n = h->n;
+    const size_t vb = 8 * (size_t)n * nrhs;
+    const bool db = is_device_pointer(b), dx = is_device_pointer(x);
+    // products per iteration: two per column; every launch of a product is counted
+    const int per_pass = multi_product_launches(h, h->seg, h->nseg, nrhs);
+    const int per_pass64 = multi_product_launches(h, &h->seg64, 1, nrhs);
+    int launches = 0;
+    const double *bsrc = b;
+    if (!db) {
+        CK(cudaMemcpyAsync(m.stage, b, vb, cudaMemcpyHostToDevice, st));
+        bsrc = m.stage;
+    }
+    launch_mgather(n, nrhs, h->perm, bsrc, m.b, st);
+    const double *xsrc = x;
+    if (!dx) {  // stream order: the gather of b has read the stage buffer by then
+        CK(cudaMemcpyAsync(m.stage, x, vb, cudaMemcpyHostToDevice, st));
+        xsrc = m.stage;
+    }
+    launch_mgather(n, nrhs, h->perm, xsrc, m.x, st);
+    launch_mresidual(g, 0, m.b, nullptr, m.x, m.r, m.rt, o.tol, o.inner_tol, o.maxit, o.max_restarts, st);
+    multi_products(h, h->seg, h->nseg, m.x, m.y, nrhs, st);
+    launch_mresidual(g, 1, m.b, m.y, m.x, m.r, m.rt, o.tol, o.inner_tol, o.maxit, o.max_restarts, st);
+    launches += 4 + per_pass;
+    CK(cudaGetLastError());
+    bool running = false;
+    for (;;) {
+        if ((rc = multi_read(h, g.nsys, st, &running))) return rc;
+        while (running) {
+            if (o.use_graph) {
+                if (!(m.graph && m.graph_k == o.check_every && m.graph_limit == o.maxit && m.graph_nrhs == nrhs)) {
+                    if (m.graph) {
+                        cudaGraphExecDestroy(m.graph);
+                        m.graph = nullptr;
+                    }
+                    cudaGraph_t gr = nullptr;
+                    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+                    for (int i = 0; i < o.check_every; ++i) multi_iteration(h, g, nrhs, o.maxit, h->cap_stream);
+                    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &gr);
+                    if (!hmat_internal::cuda_ok(e, "cudaStreamEndCapture")) return HMAT_ERR_CUDA;
+                    e = cudaGraphInstantiate(&m.graph, gr, 0);
+                    cudaGraphDestroy(gr);
+                    if (!hmat_internal::cuda_ok(e, "cudaGraphInstantiate")) return HMAT_ERR_CUDA;
+                    m.graph_k = o.check_every;
+                    m.graph_limit = o.maxit;
+                    m.graph_nrhs = nrhs;
+                }
+                CK(cudaGraphLaunch(m.graph, st));
+            } else {
+                for (int i = 0; i < o.check_every; ++i) multi_iteration(h, g, nrhs, o.maxit, st);
+                CK(cudaGetLastError());
+            }
+            launches += o.check_every * (5 + 2 * per_pass);
+            if ((rc = multi_read(h, g.nsys, st, &running))) return rc;
+        }
+        // every system has stopped: true residuals with the FP64 H-matrix decide
+        multi_products(h, &h->seg64, 1, m.x, m.y, nrhs, st);
+        launch_mresidual(g, 2, m.b, m.y, m.x, m.r, m.rt, o.tol, o.inner_tol, o.maxit, o.max_restarts, st);
+        launches += per_pass64 + 1;
+        if ((rc = multi_read(h, g.nsys, st, &running))) return rc;
+        if (!running) break;  // no system restarted
+    }
+    double *xo = dx ? x : m.stage;
+    launch_mscatter(n, nrhs, h->perm, m.x, xo, st);
+    launches += 1;
+    if (!dx) CK(cudaMemcpyAsync(x, m.stage, vb, cudaMemcpyDeviceToHost, st));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    int worst = HMAT_OK;
+    for (int k = 0; k < g.nsys; ++k) {
+        const SysScalars &S = m.S_host[k];
+        const int status = S.state == 1 ? HMAT_OK : (S.flag > 1 ? S.flag : HMAT_ERR_MAXIT);
+        if (status != HMAT_OK && worst == HMAT_OK) worst = status;
+        if (infos) {
+            hmat_solve_info &inf = infos[k];
+            std::memset(&inf, 0, sizeof(inf));
+            inf.status = status;
+            inf.iters = S.iters;
+            inf.restarts = S.restarts;
+            inf.matvecs = S.bnorm2 > 0.0 && std::isfinite(S.bnorm2) ? 1 + S.nmv : 0;
+            inf.matvecs_fp64 = S.nmv64;
+            inf.launches = launches;
+            inf.relres_true = S.relres_true;
+            inf.relres_inner = S.relres_inner;
+        }
+    }
+    return worst;
+}
+
 extern "C" int hmat_info(hmat_handle h, hmat_handle_info *out) {
     if (!h || !out) return HMAT_ERR_ARG;
     std::memset(out, 0, sizeof(*out));
-    out->n = h->ix.n;
+    out->n = h->n;
     out->precision = h->precision;
-    out->nleaves = h->ix.nleaves;
+    out->nleaves = h->seg64.ix.nleaves;
     out->panel_bytes = h->panel_bytes;
     out->panel_bytes_fp64 = h->panel_bytes64;
     out->index_bytes = h->index_bytes;
@@ -403,30 +837,41 @@ extern "C" int hmat_info(hmat_handle h, hmat_handle_info *out) {
     out->phase2_entries = h->phase2_entries;
     out->partials = h->partials_n;
     out->rank_sum = h->rank_sum;
+    out->phase1_bytes = h->phase1_bytes;
+    out->phase2_bytes = h->phase2_bytes;
+    out->stored_bytes = h->phase1_bytes + h->phase2_bytes;
+    out->segments = h->nseg;
+    out->method3_c = h->method3_c;
     return HMAT_OK;
 }
 
 extern "C" int hmat_time_matvec(hmat_handle h, int32_t iters, int32_t fp64, void *stream, double *ms_out) {
     if (!h || !ms_out || iters < 1) return HMAT_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    const DevPanels &P = fp64 ? h->P64 : h->P;
-    const Store s = fp64 ? h->store64 : h->store;
-    const int64_t n = h->ix.n;
+    const HmatSegment *seg = fp64 ? &h->seg64 : h->seg;
+    const int nseg = fp64 ? 1 : h->nseg;
+    const int64_t n = h->n;
     // a fixed source vector: x = 1 in cluster order
     std::vector<double> ones(n, 1.0);
     CK(cudaMemcpyAsync(h->stage_in, ones.data(), 8 * n, cudaMemcpyHostToDevice, st));
+    // the launches of a solver product: the expansion also leaves the shares of
+    // Algorithm 1's inner products (in the handle's solver scratch)
     cudaEvent_t ev[5];
     for (auto &e : ev) CK(cudaEventCreate(&e));
     double tot[5] = {0, 0, 0, 0, 0};
     for (int it = 0; it < iters; ++it) {
         CK(cudaEventRecord(ev[0], st));
-        launch_prep(s, h->ix, h->stage_in, nullptr, P.xs, st);
+        launch_prep(seg[0].store, seg[0].ix, h->stage_in, nullptr, seg[0].P.xs, st);
         CK(cudaEventRecord(ev[1], st));
-        launch_phase1(s, h->ix, P, nullptr, 0, st);
+        for (int k = 0; k < nseg; ++k) launch_phase1(seg[k].store, seg[k].ix, seg[k].P, nullptr, 0, st);
         CK(cudaEventRecord(ev[2], st));
-        launch_reduce(s, h->ix, P, nullptr, 0, st);
+        for (int k = 0; k < nseg; ++k) launch_reduce(seg[k].store, seg[k].ix, seg[k].P, nullptr, 0, st);
         CK(cudaEventRecord(ev[3], st));
-        launch_phase2(s, h->ix, P, h->stage_out, nullptr, nullptr, 0, st);
+        for (int k = 0; k < nseg; ++k) {
+            const bool last = k == nseg - 1;
+            launch_phase2(seg[k].store, seg[k].ix, seg[k].P, h->stage_out, nullptr, k > 0, nullptr, 0, st,
+                          last ? h->stage_in : nullptr, last ? 1 : 0, h->dpart);
+        }
         CK(cudaEventRecord(ev[4], st));
         CK(cudaEventSynchronize(ev[4]));
         for (int k = 0; k < 4; ++k) {

@@ -28,6 +28,16 @@ inline bool cuda_ok(cudaError_t e, const char *what) {
         if (!hmat_internal::cuda_ok((call), #call)) return HMAT_ERR_CUDA;    \
     } while (0)
 
+// One packed operator piece: indices, typed panels and work buffers.  The
+// library's own forms are one segment; a paper variant is one or two segments
+// whose products add up (paper_forms.cpp).
+struct HmatSegment {
+    hmat_internal::DevIndex ix;
+    hmat_internal::DevPanels P;
+    hmat_internal::Store store = hmat_internal::Store::DF;
+    int64_t partials_n = 0, glen = 0;
+};
+
 struct hmat_t {
     using DevIndex = hmat_internal::DevIndex;
     using DevPanels = hmat_internal::DevPanels;
@@ -35,11 +45,27 @@ struct hmat_t {
     using SolverScalars = hmat_internal::SolverScalars;
     int device = 0;
     int precision = 0;
-    Store store = Store::DF, store64 = Store::DF;
-    bool separate64 = false;
-    DevIndex ix;
-    DevPanels P, P64;
+    int method3_c = 0;
+    int64_t n = 0;
+    const int32_t *perm = nullptr;  // [n] cluster order -> original index (device)
+    HmatSegment seg[2];             // the iterated operator A~ (seg[1] adds into seg[0]'s y)
+    int nseg = 1;
+    HmatSegment seg64;              // the FP64 H-matrix of the true residual (Section 4.1.3)
     std::vector<void *> allocs;
+    std::vector<int64_t> prob_off;  // problem p owns [prob_off[p], prob_off[p+1]) (batch handles)
+    bool mrhs = false;              // BF16 handle with the many-right-hand-side tensor-core product
+    hmat_internal::MrhsIndex mx;    // its indices (upload) and buffers (first use)
+    // buffers of the many-system solver, sized for `cap` right-hand sides
+    struct Multi {
+        int cap = 0;
+        double *b = nullptr, *x = nullptr, *r = nullptr, *rt = nullptr, *p = nullptr, *v = nullptr, *s = nullptr,
+               *t = nullptr, *y = nullptr, *stage = nullptr, *partials = nullptr;
+        hmat_internal::SysDesc *sys = nullptr;
+        hmat_internal::SysScalars *S = nullptr, *S_host = nullptr;
+        cudaGraphExec_t graph = nullptr;
+        int graph_k = 0, graph_limit = -1, graph_nrhs = 0;
+        std::vector<void *> mine;
+    } multi;
     // solver state, cluster order
     double *b = nullptr, *x = nullptr, *r = nullptr, *rt = nullptr, *p = nullptr, *v = nullptr, *s = nullptr,
            *t = nullptr, *y = nullptr;
@@ -54,13 +80,15 @@ struct hmat_t {
     // sizes
     int64_t panel_bytes = 0, panel_bytes64 = 0, index_bytes = 0;
     int64_t stored_entries = 0, phase1_entries = 0, phase2_entries = 0, partials_n = 0, rank_sum = 0;
-    int64_t glen = 0;  // operand slots of the phase-2 buffers
+    int64_t phase1_bytes = 0, phase2_bytes = 0;
 
     ~hmat_t() {
         int cur = 0;
         cudaGetDevice(&cur);
         cudaSetDevice(device);
         if (graph) cudaGraphExecDestroy(graph);
+        if (multi.graph) cudaGraphExecDestroy(multi.graph);
+        if (multi.S_host) cudaFreeHost(multi.S_host);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (void *a : allocs) cudaFree(a);
         if (S_host) cudaFreeHost(S_host);
@@ -80,6 +108,16 @@ struct hmat_t {
         allocs.push_back(q);
         *ptr = (T *)q;
         return HMAT_OK;
+    }
+    // release one allocation made by alloc()
+    void release(void *q) {
+        if (!q) return;
+        for (size_t k = 0; k < allocs.size(); ++k)
+            if (allocs[k] == q) {
+                cudaFree(q);
+                allocs.erase(allocs.begin() + k);
+                return;
+            }
     }
     template <class T>
     int upload(T **ptr, const void *host, size_t bytes) {

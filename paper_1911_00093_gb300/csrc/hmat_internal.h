@@ -32,6 +32,10 @@ struct BlobView {
     const int64_t *blocks = nullptr;    // [nb][8]
     const double *data = nullptr;
     std::vector<int64_t> leaf_begin;    // nleaves + 1 boundaries of the leaf clusters
+    // derived block lists of the paper's variants (not set for a parsed blob):
+    bool pow2 = true;                   // false: arrays stored unscaled
+    const int64_t *toff = nullptr;      // per block: first tval of its ranks, or -1
+    const double *tval = nullptr;       // d_l of eq. (14)-(16) multiplied into t (eq. 23)
 };
 
 // Validate a blob; on success fill `view`.  Returns an hmat_status.
@@ -77,7 +81,8 @@ struct LrDesc {
     int32_t scale;  // exponent e of 2^e t
     int32_t gbeg;   // first entry of gdst (one per leaf row cluster of the block)
     int32_t gcnt;
-    int32_t pad[2];
+    int32_t toff;   // first per-rank factor d_l of t = d_l z_l (eq. 23), or -1
+    int32_t pad;
 };
 struct XDst {
     int32_t goff;   // operand index of x_kappa[0] in g
@@ -101,6 +106,7 @@ struct Layout {
     int32_t nleaves = 0;
     std::vector<int32_t> perm;        // perm[p] = original index
     std::vector<int32_t> leaf_begin;  // nleaves + 1
+    std::vector<int32_t> row_leaf;    // [n] leaf cluster of each row (cluster order)
     std::vector<P1Desc> p1;
     std::vector<P1Run> p1_runs;
     std::vector<XDst> xdst;
@@ -109,6 +115,7 @@ struct Layout {
     std::vector<P2Desc> p2;
     int64_t p1_elems = 0, p2_elems = 0;
     int64_t npart = 0, glen = 0;
+    std::vector<double> tscale;      // per-rank factors referenced by LrDesc::toff
     std::vector<int32_t> red_big;    // multi-cluster blocks over >= kRedBigCnt clusters (a CTA each)
     std::vector<int32_t> red_tasks;  // (block << 6) | rank of the other multi-cluster blocks (a lane each)
     int32_t max_ld2 = 0, max_ld1 = 0, max_runs1 = 0, max_leaf = 0;
@@ -132,8 +139,48 @@ int build_layout(const BlobView &v, Layout &L, std::string *why = nullptr);
 int check_layout(const Layout &L, std::string *why = nullptr);
 
 // Fill typed panels from the blob according to the layout.
-enum class Store { F64, DF, F32, BF16 };
+//   F64, DF, F32, BF16  the library's own forms
+//   PM, PS, PM1, PS2    FP32 panels of the paper's variants (classes M, S, M1
+//                       and S2 of paper_forms.cpp)
+enum class Store { F64, DF, F32, BF16, PM, PS, PM1, PS2 };
 size_t store_bytes(Store s);
 void fill_panels(const BlobView &v, const Layout &L, Store s, void *q1, void *p2);
+
+// One segment of a paper variant: a derived block list over the cluster tree
+// of the source blob, with its own arrays (`view` points into this object).
+struct DerivedSegment {
+    BlobHeader hdr{};
+    std::vector<int64_t> blocks;  // [nb][8] like the blob
+    std::vector<double> data;
+    std::vector<int64_t> toff;    // per block
+    std::vector<double> tval;
+    BlobView view;
+    DerivedSegment() = default;
+    DerivedSegment(const DerivedSegment &) = delete;
+    DerivedSegment &operator=(const DerivedSegment &) = delete;
+    DerivedSegment(DerivedSegment &&) = default;
+    DerivedSegment &operator=(DerivedSegment &&) = default;
+};
+
+// Independent problems as one block-diagonal operator (`view` points into this
+// object; offsets[p] = first row of problem p, offsets[count] = n).
+struct CombinedBlob {
+    BlobHeader hdr{};
+    std::vector<int64_t> perm, blocks, offsets;
+    std::vector<double> data;
+    BlobView view;
+    CombinedBlob() = default;
+    CombinedBlob(const CombinedBlob &) = delete;
+    CombinedBlob &operator=(const CombinedBlob &) = delete;
+    CombinedBlob(CombinedBlob &&) = default;
+    CombinedBlob &operator=(CombinedBlob &&) = default;
+};
+int combine_blobs(const BlobView *views, int count, CombinedBlob &out, std::string *why = nullptr);
+
+// Split a validated blob into the segments of a paper variant (precision
+// HMAT_M1_SINGLE .. HMAT_M3, `c` of eq. 19-20 for Method 3).  Sets nseg (1 or 2)
+// and the store of each segment.  Returns an hmat_status.
+int derive_table1(const BlobView &v, int precision, int c, DerivedSegment (&seg)[2], Store (&store)[2], int *nseg,
+                  std::string *why = nullptr);
 
 }  // namespace hmat_internal

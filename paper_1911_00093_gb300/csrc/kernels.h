@@ -19,6 +19,10 @@ struct DevIndex {
     const int32_t *gdst = nullptr;
     const int32_t *red_big = nullptr, *red_tasks = nullptr;
     const P2Desc *p2 = nullptr;     // [nleaves]
+    const double *tscale = nullptr; // per-rank factors of LrDesc::toff (paper's Methods 2 and 3)
+    const int32_t *row_leaf = nullptr;  // [n] leaf row cluster of each row (cluster order)
+    int32_t p2_rows = 1;            // 0: every store's phase 2 runs one CTA per leaf row cluster
+    int32_t p2_grid = 0;            // CTAs of the row-persistent phase-2 launch
     int32_t max_leaf = 0;           // rows of the widest leaf cluster
     int32_t max_ld2 = 0;            // widest phase-2 panel (entries)
 };
@@ -33,9 +37,22 @@ struct DevPanels {
     void *g = nullptr;         // phase-2 operand buffers (glen entries of the operand type)
 };
 
+// CTAs per SM of the row-persistent phase-2 launch (its launch bound).
+constexpr int kP2RowBlocksPerSM = 4;
+
+// Phase-2 launch shape of a store: the row-persistent grid for the stores of
+// 2- and 4-byte entries (short rows, where per-CTA latency dominates), one CTA
+// per leaf row cluster for the 8-byte ones (measured faster on GB300).
+inline bool phase2_rows(Store s, const DevIndex &ix) {
+    return ix.p2_rows && s != Store::DF && s != Store::F64;
+}
+// Work items whose inner-product shares a solver expansion leaves in dpart.
+inline int phase2_items(Store s, const DevIndex &ix) { return phase2_rows(s, ix) ? ix.p2_grid : ix.nleaves; }
+
 // Operand bytes per entry for a store (x and t copies).
 inline size_t operand_bytes(Store s) { return s == Store::F32 || s == Store::BF16 ? 4 : 8; }
 inline size_t partial_bytes(Store s) { return s == Store::F32 || s == Store::BF16 ? 4 : 8; }
+inline bool table1_store(Store s) { return s == Store::PM || s == Store::PS || s == Store::PM1 || s == Store::PS2; }
 
 // Source-vector operand from an FP64 vector: src_perm != nullptr gathers
 // x[src_perm[p]] (original order in), otherwise x is already in cluster order.
@@ -49,11 +66,21 @@ void launch_phase1(Store s, const DevIndex &ix, const DevPanels &P, const Solver
 // t of the blocks spanning several leaf clusters, scattered into g (no launch when there is none)
 void launch_reduce(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
                    cudaStream_t st);
-// y[p] (cluster order) or y[out_perm[p]] (original order) = (A~ x)_p; dotmode 1/2
-// also computes alpha (w = r~) or omega (w = s) of Algorithm 1 into Sd
-void launch_phase2(Store s, const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm,
+// y[p] (cluster order) or y[out_perm[p]] (original order) = (A~ x)_p, or
+// y[.] += (A~ x)_p when accum is set (the second segment of a paper variant);
+// dotmode 1/2 also leaves, per work item k, w . y in dpart[k] and y . y in
+// dpart[nleaves + k] (w = r~ for alpha, w = s for omega of Algorithm 1)
+void launch_phase2(Store s, const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm, int accum,
                    const SolverScalars *skipS, int mode, cudaStream_t st, const double *w = nullptr,
-                   int dotmode = 0, SolverScalars *Sd = nullptr, double *dpart = nullptr);
+                   int dotmode = 0, double *dpart = nullptr);
+// the same for the paper's stores (kernels_table1.cu)
+void launch_phase1_table1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
+                          cudaStream_t st);
+void launch_reduce_table1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
+                          cudaStream_t st);
+void launch_phase2_table1(Store s, const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm,
+                          int accum, const SolverScalars *skipS, int mode, cudaStream_t st, const double *w,
+                          int dotmode, double *dpart);
 
 // ---- BiCG-STAB vector kernels (FP64) ----
 struct SolverScalars {
@@ -70,18 +97,74 @@ struct SolverScalars {
 constexpr int kVecThreads = 256;
 int vec_blocks(int64_t n);
 
+// ---- product for many right-hand sides on the tensor cores (mrhs.cu, BF16 panels) ----
+constexpr int kMrhsCols = 64;  // right-hand sides per pass
+struct MrhsSrc {
+    int32_t row;  // row of U feeding this operand slot (x row, t row, or the zero row)
+    int32_t exp;  // power of two of the stored array the slot multiplies
+};
+struct MrhsIndex {
+    const MrhsSrc *src = nullptr;    // [glen]
+    const int32_t *tbase = nullptr;  // [nlr] first t row of each low-rank block (within T)
+    const int32_t *tasks = nullptr;  // (block << 6) | rank of every multi-cluster block
+    int32_t ntasks = 0;
+    int64_t urows = 0, npart = 0;    // rows of U (n + ranks + 1) and of the partials
+    float *U = nullptr;              // [urows][64]: x rows, then t rows, then a zero row
+    float *part = nullptr;           // [npart][64]
+};
+// y(:, k) = A~ x(:, k), k < nrhs <= 64, cluster order, columns ldx / ldy apart
+void launch_mrhs_product(const DevIndex &ix, const MrhsIndex &mx, const DevPanels &P, const double *x, int64_t ldx,
+                         double *y, int64_t ldy, int nrhs, cudaStream_t st);
+
+// ---- many systems at once (multi.cu) ----
+struct SysDesc {
+    int64_t off;  // first entry of the system in the stacked vectors (cluster order)
+    int32_t n;    // its length
+    int32_t pad;
+};
+struct SysScalars {
+    double rho, rho_prev, alpha, omega, snorm2, rnorm2, bnorm2, stop2, relres_true, relres_inner;
+    int32_t flag;        // run: 0 running, 1 stopped (converged), >1 an hmat_status error
+    int32_t state;       // 0 active, 1 accepted, 2 finished with the error in flag
+    int32_t iters, iter_in_run, stop_on_s, restarts, nmv, nmv64;
+    unsigned int ticket;
+    int32_t pad;
+};
+struct MultiGrid {
+    const SysDesc *sys = nullptr;
+    SysScalars *S = nullptr;
+    double *partials = nullptr;  // nsys x 2 x bx
+    int bx = 1, nsys = 0;
+};
+struct MultiVecs {
+    double *x, *r, *rt, *p, *v, *s, *t;
+};
+int multi_blocks_x(int64_t max_n, int nsys);
+// mode 0: ||b||^2 and a state reset; 1: r = b - y and a run starts; 2: true
+// residual r = b - y, acceptance at tol, error or restart (Section 4.1.3)
+void launch_mresidual(const MultiGrid &g, int mode, const double *b, const double *y, double *x, double *r, double *rt,
+                      double tol, double inner_tol, int iter_limit, int max_restarts, cudaStream_t st);
+// the vector steps of one iteration: 0 p update, 1 alpha, 2 s update, 3 omega, 4 x/r update
+void launch_miteration_vec(const MultiGrid &g, int step, const MultiVecs &v, int iter_limit, cudaStream_t st);
+// column-wise permutation of an n x nrhs block: dst[k n + p] = src[k n + perm[p]] and back
+void launch_mgather(int64_t n, int nrhs, const int32_t *perm, const double *src, double *dst, cudaStream_t st);
+void launch_mscatter(int64_t n, int nrhs, const int32_t *perm, const double *src, double *dst, cudaStream_t st);
+
 // iteration budget test and count; then p = r (first iteration of a run) or
 // p = r + beta (p - omega v), with the operand copy of p
 void launch_count_iter(SolverScalars *S, int iter_limit, cudaStream_t st);
 void launch_update_p(Store s, int64_t n, const double *r, double *p, const double *v, void *ps,
                      SolverScalars *S, cudaStream_t st);
-// s = r - alpha v, operand copy of s, ||s||^2 and the stop check (x += alpha p on a stop)
+// alpha = rho / (r~ . v) from the expansion's shares (ndp work items); s = r -
+// alpha v, operand copy of s, ||s||^2 and the stop check
 void launch_update_s(Store s, int64_t n, const double *r, const double *v, double *svec, void *ss,
-                     double *x, const double *p, SolverScalars *S, double *partials, cudaStream_t st);
-// x += alpha p + omega s; r = s - omega t; rho = r~ . r, ||r||^2, stop check;
-// counts the next iteration when the run goes on
+                     SolverScalars *S, double *partials, const double *dpart, int ndp, cudaStream_t st);
+// omega = (t . s) / (t . t) from the expansion's shares; x += alpha p + omega s;
+// r = s - omega t; rho = r~ . r, ||r||^2, stop check; counts the next iteration
+// when the run goes on
 void launch_update_xr(int64_t n, double *x, const double *p, const double *svec, const double *t, double *r,
-                      const double *rt, SolverScalars *S, double *partials, int iter_limit, cudaStream_t st);
+                      const double *rt, SolverScalars *S, double *partials, const double *dpart, int ndp,
+                      int iter_limit, cudaStream_t st);
 // r = b - y; r~ = r; ||r||^2 into S->rnorm2 and rho = r~ . r; resets the run state;
 // iter_limit >= 0 starts a run (counts its first iteration)
 void launch_residual(int64_t n, const double *b, const double *y, double *r, double *rt, SolverScalars *S,

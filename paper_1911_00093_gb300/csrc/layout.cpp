@@ -239,6 +239,9 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
     L.leaf_begin.resize(nleaves + 1);
     for (int64_t l = 0; l <= nleaves; ++l) L.leaf_begin[l] = (int32_t)v.leaf_begin[l];
     for (int64_t l = 0; l < nleaves; ++l) L.max_leaf = std::max<int32_t>(L.max_leaf, L.leaf_begin[l + 1] - L.leaf_begin[l]);
+    L.row_leaf.resize(n);
+    for (int64_t l = 0; l < nleaves; ++l)
+        for (int64_t p = L.leaf_begin[l]; p < L.leaf_begin[l + 1]; ++p) L.row_leaf[p] = (int32_t)l;
     auto leaf_index = [&](int64_t x) {
         return (int64_t)(std::lower_bound(v.leaf_begin.begin(), v.leaf_begin.end(), x) - v.leaf_begin.begin());
     };
@@ -252,10 +255,12 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
         const double *d = v.data + e[6];
         L.stored_entries += e[4] == 0 ? m * w : r * (m + w);
         if (e[4] == 0) {
-            eD[b] = exponent_of_max(d, m * w);
+            if (v.pow2) eD[b] = exponent_of_max(d, m * w);
         } else if (r > 0) {
-            eU[b] = exponent_of_max(d, m * r);
-            eV[b] = exponent_of_max(d + m * r, r * w);
+            if (v.pow2) {
+                eU[b] = exponent_of_max(d, m * r);
+                eV[b] = exponent_of_max(d + m * r, r * w);
+            }
             lrq[b] = (int32_t)lr_blocks.size();
             lr_blocks.push_back(b);
             L.rank_sum += r;
@@ -348,7 +353,13 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
             L.gdst.push_back(L.p2[rho].goff + c);
         }
         d.gcnt = (int32_t)L.gdst.size() - d.gbeg;
-        d.pad[0] = d.pad[1] = 0;
+        d.toff = -1;
+        d.pad = 0;
+        if (v.toff && v.toff[b] >= 0) {
+            if (L.tscale.size() + e[5] > (size_t(1) << 31) - 16) { if (why) *why = "too many rank factors"; return HMAT_ERR_UNSUPPORTED; }
+            d.toff = (int32_t)L.tscale.size();
+            L.tscale.insert(L.tscale.end(), v.tval + v.toff[b], v.tval + v.toff[b] + e[5]);
+        }
     }
     if (npart > (int64_t(1) << 31) - 16) { if (why) *why = "too many partials"; return HMAT_ERR_UNSUPPORTED; }
     L.npart = npart;
@@ -430,6 +441,7 @@ int check_layout(const Layout &L, std::string *why) {
         if (d.cnt > 1 ? (d.boff < 0 || (int64_t)d.boff + (int64_t)d.cnt * d.rank > L.npart) : d.boff != -1)
             return bad("lr partials");
         if (d.gbeg < 0 || d.gcnt < 1 || (int64_t)d.gbeg + d.gcnt > (int64_t)L.gdst.size()) return bad("lr dst");
+        if (d.toff < -1 || (d.toff >= 0 && (int64_t)d.toff + d.rank > (int64_t)L.tscale.size())) return bad("lr factors");
         for (int k = 0; k < d.gcnt; ++k) {
             int32_t g0 = L.gdst[d.gbeg + k];
             if (g0 < 0 || (int64_t)g0 + d.rank > L.glen) return bad("lr dst range");
@@ -480,6 +492,12 @@ int check_layout(const Layout &L, std::string *why) {
         if (q < 0 || q >= (int32_t)L.lr.size() || L.lr[q].cnt < 2 || L.lr[q].cnt >= kRedBigCnt || l >= L.lr[q].rank)
             return bad("red task");
     }
+    if ((int64_t)L.row_leaf.size() != L.n) return bad("row_leaf size");
+    for (int64_t p = 0; p < L.n; ++p) {
+        const int32_t l = L.row_leaf[p];
+        if (l < 0 || l >= L.nleaves || p < L.p2[l].ybeg || p >= (int64_t)L.p2[l].ybeg + L.p2[l].ylen)
+            return bad("row_leaf entry");
+    }
     if ((int64_t)L.perm.size() != L.n) return bad("perm size");
     for (int32_t q : L.perm) if (q < 0 || q >= L.n) return bad("perm entry");
     return HMAT_OK;
@@ -491,6 +509,7 @@ size_t store_bytes(Store s) {
     case Store::DF: return 8;
     case Store::F32: return 4;
     case Store::BF16: return 2;
+    case Store::PM: case Store::PS: case Store::PM1: case Store::PS2: return 4;
     }
     return 0;
 }
@@ -501,6 +520,9 @@ void fill_panels(const BlobView &v, const Layout &L, Store s, void *q1, void *p2
     case Store::DF: fill_typed<DFPair>(v, L, (DFPair *)q1, (DFPair *)p2); break;
     case Store::F32: fill_typed<float>(v, L, (float *)q1, (float *)p2); break;
     case Store::BF16: fill_typed<uint16_t>(v, L, (uint16_t *)q1, (uint16_t *)p2); break;
+    case Store::PM: case Store::PS: case Store::PM1: case Store::PS2:
+        fill_typed<float>(v, L, (float *)q1, (float *)p2);
+        break;
     }
 }
 

@@ -58,9 +58,10 @@ bool on_device(const void *p) {
 }
 
 size_t scratch_bytes_for(const hmat_t *h) {
-    const size_t ob = operand_bytes(h->store), pb = partial_bytes(h->store);
-    return align256((size_t)h->ix.n * ob) + align256((size_t)(h->partials_n > 0 ? h->partials_n : 1) * pb) +
-           align256((size_t)(h->glen > 0 ? h->glen : 1) * ob);
+    const HmatSegment &g = h->seg[0];
+    const size_t ob = operand_bytes(g.store), pb = partial_bytes(g.store);
+    return align256((size_t)h->n * ob) + align256((size_t)(g.partials_n > 0 ? g.partials_n : 1) * pb) +
+           align256((size_t)(g.glen > 0 ? g.glen : 1) * ob);
 }
 
 }  // namespace
@@ -71,26 +72,28 @@ extern "C" int hmat_matvec_noalloc(hmat_handle h, const double *x, double *y, vo
     CK(cudaGetDevice(&dev));
     if (dev != h->device || dev < 0 || dev >= kMaxDevices) return HMAT_ERR_ARG;
     if (!on_device(x) || !on_device(y)) return HMAT_ERR_ARG;  // no staging buffers: device pointers only
+    if (h->nseg != 1) return HMAT_ERR_UNSUPPORTED;            // the paper's two-segment variants
     const size_t need = scratch_bytes_for(h);
     if (need > kNoallocScratchBytes) return HMAT_ERR_UNSUPPORTED;
     void *base = nullptr;
     int st = scratch_address(dev, &base);
     if (st != HMAT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t ob = operand_bytes(h->store);
-    DevPanels P = h->P;
+    const HmatSegment &g = h->seg[0];
+    const size_t ob = operand_bytes(g.store);
+    DevPanels P = g.P;
     char *b = (char *)base;
     P.xs = b;
-    P.part = b + align256((size_t)h->ix.n * ob);
-    P.g = b + align256((size_t)h->ix.n * ob) + align256((size_t)(h->partials_n > 0 ? h->partials_n : 1) *
-                                                         partial_bytes(h->store));
+    P.part = b + align256((size_t)h->n * ob);
+    P.g = b + align256((size_t)h->n * ob) + align256((size_t)(g.partials_n > 0 ? g.partials_n : 1) *
+                                                      partial_bytes(g.store));
     // the array keeps the previous call's contents: the padding slots of the
     // operand buffers must read zero, every other slot is rewritten below
-    CK(cudaMemsetAsync(P.g, 0, (size_t)(h->glen > 0 ? h->glen : 1) * ob, s));
-    launch_prep(h->store, h->ix, x, h->ix.perm, P.xs, s);
-    launch_phase1(h->store, h->ix, P, nullptr, 0, s);
-    launch_reduce(h->store, h->ix, P, nullptr, 0, s);
-    launch_phase2(h->store, h->ix, P, y, h->ix.perm, nullptr, 0, s);
+    CK(cudaMemsetAsync(P.g, 0, (size_t)(g.glen > 0 ? g.glen : 1) * ob, s));
+    launch_prep(g.store, g.ix, x, h->perm, P.xs, s);
+    launch_phase1(g.store, g.ix, P, nullptr, 0, s);
+    launch_reduce(g.store, g.ix, P, nullptr, 0, s);
+    launch_phase2(g.store, g.ix, P, y, h->perm, 0, nullptr, 0, s);
     CK(cudaGetLastError());
     return HMAT_OK;
 }

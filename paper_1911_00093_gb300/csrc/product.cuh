@@ -1,0 +1,860 @@
+// Device code of the H-matrix vector product (sm_103a), shared by the
+// translation units that instantiate it for each store (kernels.cu: the
+// library's own forms; kernels_table1.cu: the paper's variants).
+//
+// Product (Section 2.1, eq. 5-10 and 21-25), in three launches:
+//   phase 1  one CTA per leaf column cluster kappa: t-partials = Q_kappa^T x_kappa,
+//            Q_kappa the rows of every W_m^T (eq. 9/22) whose column cluster
+//            contains kappa, row-major; each thread owns one 16-byte column vector
+//            and walks the |kappa| rows (coalesced 128-bit loads, x from shared
+//            memory, no cross-thread reduction);
+//   reduce   one warp per low-rank block: t = 2^e sum_kappa partials, in a fixed
+//            order (deterministic, no atomics on values);
+//   phase 2  one CTA per leaf row cluster rho: y_rho = P_rho g_rho with P_rho the
+//            rows of the dense blocks (eq. 21) and of the V_m (eq. 10/24) over rho,
+//            g_rho the matching pieces of x and t staged in shared memory; one warp
+//            per row; each row of y is written once by its owner (eq. 25 without
+//            atomics).
+// Arithmetic per store:
+//   DF    panels are pairs (hi, lo); products and sums in double-float on the
+//         FP32 pipe (the FP64 pipe of GB300 is ~1/60 of FP32);
+//   F64   IEEE FP64 FMA;
+//   F32, BF16  FP32 FMA over chunks of 8 products, chunks summed in double-float;
+//   PM, PS, PM1, PS2  FP32 panels with the arithmetic of Table 1 (Section 3):
+//         FP64 operands and FP64 sums, products of two FP32 values rounded to
+//         FP32 where Table 1 puts both in FP32 (classes of paper_forms.cpp).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "hmat.h"
+#include "kernels.h"
+
+namespace hmat_internal {
+
+namespace {
+
+// ------------------------------------------------------------------------
+// double-float helpers (error-free transformations; intrinsics keep the
+// compiler from contracting or reassociating them)
+// ------------------------------------------------------------------------
+struct DF {
+    float s, c;  // value s + c
+};
+
+__device__ __forceinline__ void two_sum_acc(DF &a, float p) {
+    float t = __fadd_rn(a.s, p);
+    float bb = __fsub_rn(t, a.s);
+    float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    a.s = t;
+    a.c = __fadd_rn(a.c, err);
+}
+
+__device__ __forceinline__ void renorm(DF &a) {
+    float t = __fadd_rn(a.s, a.c);
+    a.c = __fsub_rn(a.c, __fsub_rn(t, a.s));
+    a.s = t;
+}
+
+// a += (ah + al) * (xh + xl), the lo*lo term (~2^-48) dropped
+__device__ __forceinline__ void df_fma(DF &a, float ah, float al, float xh, float xl) {
+    float p = __fmul_rn(ah, xh);
+    float e = __fmaf_rn(ah, xh, -p);  // exact error of the product
+    e = __fmaf_rn(ah, xl, e);
+    e = __fmaf_rn(al, xh, e);
+    float t = __fadd_rn(a.s, p);
+    float bb = __fsub_rn(t, a.s);
+    float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    a.s = t;
+    a.c = __fadd_rn(a.c, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    float t = __fadd_rn(a.s, b.s);
+    float bb = __fsub_rn(t, a.s);
+    float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bb)), __fsub_rn(b.s, bb));
+    float c = __fadd_rn(__fadd_rn(a.c, b.c), err);
+    DF r;
+    r.s = __fadd_rn(t, c);
+    r.c = __fsub_rn(c, __fsub_rn(r.s, t));
+    return r;
+}
+
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.s + (double)a.c; }
+
+__device__ __forceinline__ int4 ld_stream(const void *p) { return __ldcs((const int4 *)p); }
+
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+__device__ __forceinline__ float2 split_double(double v) {
+    float hi = __double2float_rn(v);
+    float lo = __double2float_rn(v - (double)hi);
+    return make_float2(hi, lo);
+}
+
+// ------------------------------------------------------------------------
+// store traits
+// ------------------------------------------------------------------------
+// VW = entries per 16-byte vector; Op = operand type of x and t entries.
+// The primary templates describe the paper's variants (FP32 panels, FP64
+// operands, partial sums and accumulators).
+constexpr bool is_table1(Store s) { return s == Store::PM || s == Store::PS || s == Store::PM1 || s == Store::PS2; }
+// class S products (FP32 x FP32 rounded to FP32) in phase 2
+constexpr bool s_class_expansion(Store s) { return s == Store::PS || s == Store::PM1; }
+// FP32 operand x in phase 1 (Method 1-Single and Method 2-Single)
+constexpr bool fp32_source(Store s) { return s == Store::PS || s == Store::PS2; }
+template <Store S> struct Tr { static constexpr int VW = 4; using Op = double; using Part = double; };
+template <> struct Tr<Store::DF> { static constexpr int VW = 2; using Op = float2; using Part = float2; };
+template <> struct Tr<Store::F64> { static constexpr int VW = 2; using Op = double; using Part = double; };
+template <> struct Tr<Store::F32> { static constexpr int VW = 4; using Op = float; using Part = float; };
+template <> struct Tr<Store::BF16> { static constexpr int VW = 8; using Op = float; using Part = float; };
+
+// per-column / per-row accumulator
+template <Store S> struct Acc {
+    double a;  // FP64 sums
+    float f;   // FP32 projection z_m of Method 1
+    __device__ void init() { a = 0.0; f = 0.f; }
+};
+template <> struct Acc<Store::DF> {
+    DF a;
+    int n;
+    __device__ void init() { a.s = 0.f; a.c = 0.f; n = 0; }
+};
+template <> struct Acc<Store::F64> {
+    double a;
+    __device__ void init() { a = 0.0; }
+};
+template <> struct Acc<Store::F32> {
+    DF a;
+    float ch;
+    __device__ void init() { a.s = 0.f; a.c = 0.f; ch = 0.f; }
+};
+template <> struct Acc<Store::BF16> {
+    DF a;
+    float ch;
+    int cnt;
+    __device__ void init() { a.s = 0.f; a.c = 0.f; ch = 0.f; cnt = 0; }
+};
+
+// Multiply one 16-byte panel vector by VW operands and accumulate into VW
+// separate accumulators (phase 1: one per column).
+template <Store S> struct Cols {
+    __device__ static void mac(Acc<S> *acc, int4 raw, double x) {
+        const float4 v = *reinterpret_cast<float4 *>(&raw);
+        const float w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if constexpr (S == Store::PM) {           // FP32 W promoted, FP64 x and z
+                acc[e].a = fma((double)w[e], x, acc[e].a);
+            } else if constexpr (S == Store::PS) {    // FP32 W, x and z (Method 1-Single)
+                acc[e].f = __fadd_rn(acc[e].f, __fmul_rn(w[e], (float)x));
+            } else if constexpr (S == Store::PM1) {   // z = fl32(z + W x), right side FP64 (Method 1-Mixed)
+                acc[e].f = __double2float_rn(__dadd_rn((double)acc[e].f, __dmul_rn((double)w[e], x)));
+            } else {                                  // PS2: FP32 product into FP64 z (Method 2-Single)
+                acc[e].a = __dadd_rn(acc[e].a, (double)__fmul_rn(w[e], (float)x));
+            }
+        }
+    }
+};
+template <> struct Cols<Store::DF> {
+    __device__ static void mac(Acc<Store::DF> *acc, int4 raw, float2 x) {
+        float4 v = *reinterpret_cast<float4 *>(&raw);
+        df_fma(acc[0].a, v.x, v.y, x.x, x.y);
+        df_fma(acc[1].a, v.z, v.w, x.x, x.y);
+    }
+};
+template <> struct Cols<Store::F64> {
+    __device__ static void mac(Acc<Store::F64> *acc, int4 raw, double x) {
+        double2 v = *reinterpret_cast<double2 *>(&raw);
+        acc[0].a = fma(v.x, x, acc[0].a);
+        acc[1].a = fma(v.y, x, acc[1].a);
+    }
+};
+template <> struct Cols<Store::F32> {
+    __device__ static void mac(Acc<Store::F32> *acc, int4 raw, float x) {
+        float4 v = *reinterpret_cast<float4 *>(&raw);
+        acc[0].ch = fmaf(v.x, x, acc[0].ch);
+        acc[1].ch = fmaf(v.y, x, acc[1].ch);
+        acc[2].ch = fmaf(v.z, x, acc[2].ch);
+        acc[3].ch = fmaf(v.w, x, acc[3].ch);
+    }
+};
+template <> struct Cols<Store::BF16> {
+    __device__ static void mac(Acc<Store::BF16> *acc, int4 raw, float x) {
+        uint32_t w[4] = {(uint32_t)raw.x, (uint32_t)raw.y, (uint32_t)raw.z, (uint32_t)raw.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            acc[2 * k].ch = fmaf(bf_lo(w[k]), x, acc[2 * k].ch);
+            acc[2 * k + 1].ch = fmaf(bf_hi(w[k]), x, acc[2 * k + 1].ch);
+        }
+    }
+};
+
+// fold a chunk (F32/BF16) or renormalise (DF) -- called every 8 rows / products
+template <Store S> __device__ __forceinline__ void fold(Acc<S> &) {}
+template <> __device__ __forceinline__ void fold<Store::DF>(Acc<Store::DF> &a) { renorm(a.a); }
+template <> __device__ __forceinline__ void fold<Store::F64>(Acc<Store::F64> &) {}
+template <> __device__ __forceinline__ void fold<Store::F32>(Acc<Store::F32> &a) { two_sum_acc(a.a, a.ch); a.ch = 0.f; }
+template <> __device__ __forceinline__ void fold<Store::BF16>(Acc<Store::BF16> &a) { two_sum_acc(a.a, a.ch); a.ch = 0.f; }
+
+// partial-sum output of a finished accumulator
+template <Store S> __device__ __forceinline__ typename Tr<S>::Part to_part(Acc<S> &a) {
+    if constexpr (S == Store::PS || S == Store::PM1) return (double)a.f;
+    else return a.a;
+}
+template <> __device__ __forceinline__ float2 to_part<Store::DF>(Acc<Store::DF> &a) {
+    renorm(a.a);
+    return make_float2(a.a.s, a.a.c);
+}
+template <> __device__ __forceinline__ double to_part<Store::F64>(Acc<Store::F64> &a) { return a.a; }
+template <> __device__ __forceinline__ float to_part<Store::F32>(Acc<Store::F32> &a) {
+    fold<Store::F32>(a);
+    return __fadd_rn(a.a.s, a.a.c);
+}
+template <> __device__ __forceinline__ float to_part<Store::BF16>(Acc<Store::BF16> &a) {
+    fold<Store::BF16>(a);
+    return __fadd_rn(a.a.s, a.a.c);
+}
+
+// skip test of the solver's products: mode 0 never, 1 on a set flag,
+// 2 on a set flag or a stop at the ||s|| check
+__device__ __forceinline__ bool skip_product(const SolverScalars *S, int mode) {
+    if (mode == 0 || S == nullptr) return false;
+    int f = *(volatile const int32_t *)&S->flag;
+    if (f != 0) return true;
+    return mode == 2 && *(volatile const int32_t *)&S->stop_on_s != 0;
+}
+
+// ------------------------------------------------------------------------
+// source-vector operand
+// ------------------------------------------------------------------------
+template <Store S>
+__global__ void k_prep(int n, const double *__restrict__ x, const int32_t *__restrict__ src_perm,
+                       typename Tr<S>::Op *__restrict__ xs) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        double v = x[src_perm ? src_perm[p] : p];
+        if constexpr (S == Store::DF) xs[p] = split_double(v);
+        else if constexpr (S == Store::F64 || is_table1(S)) xs[p] = v;
+        else xs[p] = __double2float_rn(v);
+    }
+}
+
+// ------------------------------------------------------------------------
+// exact power-of-two factors (|e| <= 120 is enforced at upload)
+// ------------------------------------------------------------------------
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
+template <Store S>
+__device__ __forceinline__ typename Tr<S>::Op scale_op(typename Tr<S>::Op v, int e) {
+    if constexpr (S == Store::DF) { const float f = pow2f(e); return make_float2(v.x * f, v.y * f); }
+    else if constexpr (S == Store::F64 || is_table1(S)) return v * pow2d(e);
+    else return v * pow2f(e);
+}
+
+// operand from a finished projection (scaled by 2^e, exact)
+template <Store S>
+__device__ __forceinline__ typename Tr<S>::Op part_to_op(typename Tr<S>::Part p, int e) {
+    if constexpr (S == Store::DF) { const float f = pow2f(e); return make_float2(p.x * f, p.y * f); }
+    else if constexpr (S == Store::F64 || is_table1(S)) return p * pow2d(e);
+    else return p * pow2f(e);
+}
+
+// t = d_l z_l of the Method 2/3 structure V' D W' (eq. 23), when the block has factors
+template <Store S>
+__device__ __forceinline__ typename Tr<S>::Op apply_d(typename Tr<S>::Op o, const LrDesc &ld, int l,
+                                                      const double *__restrict__ tscale) {
+    if constexpr (S == Store::F64 || is_table1(S)) {
+        if (ld.toff >= 0) return o * __ldg(tscale + ld.toff + l);
+    }
+    return o;
+}
+
+// accumulator of the completing work item's fixed-order reduction
+template <Store S> struct RedT { using T = DF; };
+template <> struct RedT<Store::F64> { using T = double; };
+template <> struct RedT<Store::PM> { using T = double; };
+template <> struct RedT<Store::PS> { using T = double; };
+template <> struct RedT<Store::PM1> { using T = double; };
+template <> struct RedT<Store::PS2> { using T = double; };
+constexpr bool red_double(Store s) { return s == Store::F64 || is_table1(s); }
+
+// Method 1's z_m stays FP32 across the partial sums of its leaf clusters:
+// FP32 additions (Single), FP64 additions rounded to FP32 (Mixed)
+__device__ __forceinline__ double red_m1(Store s, double a, double b) {
+    return s == Store::PS ? (double)__fadd_rn((float)a, (float)b) : (double)__double2float_rn(a + b);
+}
+
+template <Store S> __device__ __forceinline__ void red_zero(typename RedT<S>::T &a) {
+    if constexpr (red_double(S)) a = 0.0; else { a.s = 0.f; a.c = 0.f; }
+}
+template <Store S> __device__ __forceinline__ void red_add_part(typename RedT<S>::T &a, typename Tr<S>::Part p) {
+    if constexpr (S == Store::PS || S == Store::PM1) a = red_m1(S, a, p);
+    else if constexpr (red_double(S)) a += p;
+    else if constexpr (S == Store::DF) a = df_add(a, DF{p.x, p.y});
+    else two_sum_acc(a, p);
+}
+template <Store S> __device__ __forceinline__ void red_add(typename RedT<S>::T &a, typename RedT<S>::T b) {
+    if constexpr (S == Store::PS || S == Store::PM1) a = red_m1(S, a, b);
+    else if constexpr (red_double(S)) a += b;
+    else a = df_add(a, b);
+}
+template <Store S>
+__device__ __forceinline__ typename RedT<S>::T red_xor(typename RedT<S>::T a, int m, bool upper) {
+    typename RedT<S>::T b;
+    if constexpr (red_double(S)) b = __shfl_xor_sync(0xffffffffu, a, m);
+    else { b.s = __shfl_xor_sync(0xffffffffu, a.s, m); b.c = __shfl_xor_sync(0xffffffffu, a.c, m); }
+    // row sums of phase 2 are FP64 additions for every FP64-accumulated store
+    // (Table 1 puts y^_m in FP64, also for Method 1)
+    if constexpr (red_double(S)) return upper ? b + a : a + b;
+    else {
+        if (upper) { red_add<S>(b, a); return b; }
+        red_add<S>(a, b);
+        return a;
+    }
+}
+
+template <Store S> __device__ __forceinline__ typename Tr<S>::Part red_to_part(typename RedT<S>::T a) {
+    if constexpr (red_double(S)) return a;
+    else if constexpr (S == Store::DF) { renorm(a); return make_float2(a.s, a.c); }
+    else return __fadd_rn(a.s, a.c);
+}
+
+// ------------------------------------------------------------------------
+// phase 1: per leaf column cluster kappa
+// ------------------------------------------------------------------------
+constexpr int kP1Threads = 256;
+
+template <Store S>
+__global__ void __launch_bounds__(kP1Threads) k_phase1(const P1Desc *__restrict__ desc, const P1Run *__restrict__ runs,
+                                                        const XDst *__restrict__ xdst, const LrDesc *__restrict__ lr,
+                                                        const int32_t *__restrict__ gdst, const void *__restrict__ q1,
+                                                        const typename Tr<S>::Op *__restrict__ xs,
+                                                        typename Tr<S>::Part *__restrict__ part,
+                                                        typename Tr<S>::Op *__restrict__ g,
+                                                        const double *__restrict__ tscale, const SolverScalars *S_,
+                                                        int mode) {
+    using Op = typename Tr<S>::Op;
+    using Part = typename Tr<S>::Part;
+    constexpr int VW = Tr<S>::VW;
+    __shared__ Op xk[kMaxLeaf];  // x_kappa, broadcast to every thread
+    if (skip_product(S_, mode)) return;
+    const P1Desc d = desc[blockIdx.x];
+    for (int j = threadIdx.x; j < d.xlen; j += blockDim.x) {
+        if constexpr (fp32_source(S)) xk[j] = (double)__double2float_rn(xs[d.xbeg + j]);  // Section 3.5
+        else xk[j] = xs[d.xbeg + j];
+    }
+    __syncthreads();
+
+    // projections (eq. 9/22): thread = one 16-byte column vector, walk the rows
+    const int nvec = d.ld / VW;
+    const char *base = (const char *)q1 + (size_t)d.off * (16 / VW);
+    const size_t row_bytes = (size_t)d.ld * (16 / VW);
+    for (int vc = threadIdx.x; vc < nvec; vc += blockDim.x) {
+        Acc<S> acc[VW];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) acc[e].init();
+        const char *col = base + (size_t)vc * 16;
+        int j = 0;
+        for (; j + 8 <= d.xlen; j += 8) {
+            int4 raw[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) raw[u] = ld_stream(col + (size_t)(j + u) * row_bytes);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) Cols<S>::mac(acc, raw[u], xk[j + u]);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) fold<S>(acc[e]);
+        }
+        for (; j < d.xlen; ++j) {
+            int4 raw = ld_stream(col + (size_t)j * row_bytes);
+            Cols<S>::mac(acc, raw, xk[j]);
+        }
+        const int c0 = vc * VW;
+        if (c0 >= d.R) continue;
+        const P1Run *rk = runs + d.rbeg;
+        int lo = 0, hi = d.rcnt - 1;  // run holding column c0
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&rk[mid].col0) <= c0) lo = mid;
+            else hi = mid - 1;
+        }
+        P1Run rn = rk[lo];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            const int c = c0 + e;
+            if (c < d.R) {
+                while (c >= rn.col0 + rn.len) rn = rk[++lo];
+                const int l = c - rn.col0;
+                const Part pv = to_part<S>(acc[e]);
+                if (rn.poff >= 0) {
+                    part[rn.poff + l] = pv;
+                } else {  // final: 2^e t to every leaf row cluster of the block
+                    const LrDesc ld = lr[rn.q];
+                    const Op o = apply_d<S>(part_to_op<S>(pv, ld.scale), ld, l, tscale);
+                    for (int k = 0; k < ld.gcnt; ++k) g[gdst[ld.gbeg + k] + l] = o;
+                }
+            }
+        }
+    }
+
+    // the dense-block operands fed by x_kappa (eq. 21 inputs), scaled by 2^e
+    for (int t = threadIdx.x; t < d.xdcnt * d.xlen; t += blockDim.x) {
+        const int k = t / d.xlen, j = t - k * d.xlen;
+        const XDst x = xdst[d.xdbeg + k];
+        g[x.goff + j] = scale_op<S>(xk[j], x.scale);
+    }
+}
+
+
+// ------------------------------------------------------------------------
+// reduce: t of the blocks spanning several leaf clusters, in a fixed order,
+// scattered to the operand buffers.  Blocks over >= kRedBigCnt clusters get a
+// whole CTA (kernel blocks [0, nbig)); the others are split into one task per
+// rank, one lane each.
+// ------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+
+template <Store S>
+__global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int ntasks, const int32_t *__restrict__ big,
+                                                         const int32_t *__restrict__ tasks,
+                                                         const LrDesc *__restrict__ lr, const int32_t *__restrict__ gdst,
+                                                         const typename Tr<S>::Part *__restrict__ part,
+                                                         typename Tr<S>::Op *__restrict__ g,
+                                                         const double *__restrict__ tscale, const SolverScalars *S_,
+                                                         int mode) {
+    using Op = typename Tr<S>::Op;
+    using RT = typename RedT<S>::T;
+    __shared__ RT red[kRedThreads];
+    if (skip_product(S_, mode)) return;
+    if ((int)blockIdx.x < nbig) {
+        const LrDesc ld = lr[big[blockIdx.x]];
+        for (int l0 = 0; l0 < ld.rank; l0 += 32) {
+            const int rr = min(32, ld.rank - l0);
+            int rp = 1;
+            while (rp < rr) rp <<= 1;
+            const int G = kRedThreads / rp, gi = threadIdx.x / rp, l = threadIdx.x % rp;
+            RT a;
+            red_zero<S>(a);
+            if (l < rr) {
+                const typename Tr<S>::Part *src = part + ld.boff + l0 + l;
+#pragma unroll 4
+                for (int k = gi; k < ld.cnt; k += G) red_add_part<S>(a, src[(size_t)k * ld.rank]);
+            }
+            red[threadIdx.x] = a;
+            __syncthreads();
+            for (int half = G >> 1; half >= 1; half >>= 1) {
+                if (gi < half) {
+                    RT c = red[threadIdx.x];
+                    red_add<S>(c, red[threadIdx.x + half * rp]);
+                    red[threadIdx.x] = c;
+                }
+                __syncthreads();
+            }
+            // every thread scatters: destination k, rank l
+            for (int idx = threadIdx.x; idx < ld.gcnt * rr; idx += kRedThreads) {
+                const int k = idx / rr, ll = idx - k * rr;
+                g[gdst[ld.gbeg + k] + l0 + ll] =
+                    apply_d<S>(part_to_op<S>(red_to_part<S>(red[ll]), ld.scale), ld, l0 + ll, tscale);
+            }
+            __syncthreads();
+        }
+        return;
+    }
+    // the other blocks: one lane per (block, rank), a sequential sum over the
+    // block's leaf clusters (independent loads) and the scatter of that rank
+    const int task = ((int)blockIdx.x - nbig) * kRedThreads + threadIdx.x;
+    if (task >= ntasks) return;
+    const int tq = __ldg(tasks + task);
+    const LrDesc ld = lr[tq >> 6];
+    const int l = tq & 63;
+    const typename Tr<S>::Part *src = part + ld.boff + l;
+    RT a;
+    red_zero<S>(a);
+#pragma unroll 4
+    for (int k = 0; k < ld.cnt; ++k) red_add_part<S>(a, src[(size_t)k * ld.rank]);
+    const Op o = apply_d<S>(part_to_op<S>(red_to_part<S>(a), ld.scale), ld, l, tscale);
+    for (int k = 0; k < ld.gcnt; ++k) g[gdst[ld.gbeg + k] + l] = o;
+}
+
+// ------------------------------------------------------------------------
+// phase 2: per leaf row cluster, y_rho = P_rho g_rho
+// ------------------------------------------------------------------------
+constexpr int kP2Threads = 256;
+constexpr int kP2Warps = kP2Threads / 32;
+
+// The VW operands matching one 16-byte panel vector, loaded as vectors through
+// L1 (operand buffers are 16-byte aligned per row cluster).
+template <Store S> struct GV {  // paper's variants: four FP64 operands
+    double2 a, b;
+    __device__ static GV load(const double *p) {
+        GV r;
+        r.a = __ldg(reinterpret_cast<const double2 *>(p));
+        r.b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+        return r;
+    }
+};
+template <> struct GV<Store::DF> {
+    float4 v;  // (hi, lo) of two operands
+    __device__ static GV load(const float2 *p) { GV r; r.v = __ldg(reinterpret_cast<const float4 *>(p)); return r; }
+};
+template <> struct GV<Store::F64> {
+    double2 v;
+    __device__ static GV load(const double *p) { GV r; r.v = __ldg(reinterpret_cast<const double2 *>(p)); return r; }
+};
+template <> struct GV<Store::F32> {
+    float4 v;
+    __device__ static GV load(const float *p) { GV r; r.v = __ldg(reinterpret_cast<const float4 *>(p)); return r; }
+};
+template <> struct GV<Store::BF16> {
+    float4 a, b;
+    __device__ static GV load(const float *p) {
+        GV r;
+        r.a = __ldg(reinterpret_cast<const float4 *>(p));
+        r.b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+        return r;
+    }
+};
+
+// Multiply one 16-byte panel vector by its VW operands (one row).
+template <Store S>
+__device__ __forceinline__ void row_mac(Acc<S> &acc, int4 raw, const GV<S> &gv) {
+    const float4 v = *reinterpret_cast<float4 *>(&raw);
+    const double x[4] = {gv.a.x, gv.a.y, gv.b.x, gv.b.y};
+    const float w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if constexpr (s_class_expansion(S))  // FP32 x FP32 rounded to FP32, added in FP64
+            acc.a = __dadd_rn(acc.a, (double)__fmul_rn(w[e], (float)x[e]));
+        else                                 // FP32 promoted, FP64 operand and sum
+            acc.a = fma((double)w[e], x[e], acc.a);
+    }
+}
+template <>
+__device__ __forceinline__ void row_mac<Store::DF>(Acc<Store::DF> &acc, int4 raw, const GV<Store::DF> &gv) {
+    float4 v = *reinterpret_cast<float4 *>(&raw);
+    const float4 x = gv.v;
+    df_fma(acc.a, v.x, v.y, x.x, x.y);
+    df_fma(acc.a, v.z, v.w, x.z, x.w);
+    if (++acc.n == 4) { renorm(acc.a); acc.n = 0; }
+}
+template <>
+__device__ __forceinline__ void row_mac<Store::F64>(Acc<Store::F64> &acc, int4 raw, const GV<Store::F64> &gv) {
+    double2 v = *reinterpret_cast<double2 *>(&raw);
+    acc.a = fma(v.x, gv.v.x, acc.a);
+    acc.a = fma(v.y, gv.v.y, acc.a);
+}
+template <>
+__device__ __forceinline__ void row_mac<Store::F32>(Acc<Store::F32> &acc, int4 raw, const GV<Store::F32> &gv) {
+    float4 v = *reinterpret_cast<float4 *>(&raw);
+    const float4 x = gv.v;
+    float c = 0.f;
+    c = fmaf(v.x, x.x, c);
+    c = fmaf(v.y, x.y, c);
+    c = fmaf(v.z, x.z, c);
+    c = fmaf(v.w, x.w, c);
+    two_sum_acc(acc.a, c);  // one chunk of 4 products
+}
+template <>
+__device__ __forceinline__ void row_mac<Store::BF16>(Acc<Store::BF16> &acc, int4 raw, const GV<Store::BF16> &gv) {
+    const float4 x0 = gv.a, x1 = gv.b;
+    float c = acc.ch;
+    c = fmaf(bf_lo((uint32_t)raw.x), x0.x, c);
+    c = fmaf(bf_hi((uint32_t)raw.x), x0.y, c);
+    c = fmaf(bf_lo((uint32_t)raw.y), x0.z, c);
+    c = fmaf(bf_hi((uint32_t)raw.y), x0.w, c);
+    c = fmaf(bf_lo((uint32_t)raw.z), x1.x, c);
+    c = fmaf(bf_hi((uint32_t)raw.z), x1.y, c);
+    c = fmaf(bf_lo((uint32_t)raw.w), x1.z, c);
+    c = fmaf(bf_hi((uint32_t)raw.w), x1.w, c);
+    acc.ch = c;
+    if (++acc.cnt == 4) { two_sum_acc(acc.a, acc.ch); acc.ch = 0.f; acc.cnt = 0; }  // chunk of 32
+}
+
+// the lane partial of one row as a reduction accumulator
+template <Store S>
+__device__ __forceinline__ typename RedT<S>::T row_partial(Acc<S> &a) {
+    if constexpr (red_double(S)) return a.a;
+    else {
+        if constexpr (S == Store::BF16) { two_sum_acc(a.a, a.ch); a.ch = 0.f; }
+        renorm(a.a);
+        return a.a;
+    }
+}
+
+// Row totals of a phase-2 work item: each warp adds its rows' lane partials with
+// a fixed butterfly; lane 0 writes y (or adds to it, accum).  In a solver product
+// (dotmode != 0, Algorithm 1) the work item also leaves its share of two inner
+// products in dpart -- w . y in dpart[item], y . y in dpart[items + item] (rows
+// in warp-major order, warps in order) -- for the next vector kernel, which adds
+// the shares up in item order (alpha = rho / (r~ . v), omega = (t . s) / (t . t)).
+template <Store S, int MR>
+__device__ __forceinline__ void phase2_epilogue(const P2Desc &d, Acc<S> (&acc)[MR], double *__restrict__ y,
+                                                const int32_t *__restrict__ out_perm, int accum,
+                                                const double (&wv)[MR], int dotmode, double *dpart) {
+    using RT = typename RedT<S>::T;
+    __shared__ double wsum[2][kP2Warps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double dw = 0.0, dy = 0.0;
+#pragma unroll
+    for (int rr = 0; rr < MR; ++rr) {
+        const int i = warp + rr * kP2Warps;
+        if (i < d.ylen) {
+            RT a = row_partial<S>(acc[rr]);
+            for (int m = 1; m < 32; m <<= 1) a = red_xor<S>(a, m, (lane & m) != 0);
+            double out;
+            if constexpr (red_double(S)) out = a;
+            else out = df_to_double(a);
+            if (lane == 0) {
+                const int p = d.ybeg + i;
+                const int q = out_perm ? out_perm[p] : p;
+                if (accum) out = y[q] + out;  // a later segment adds to the earlier ones' rows
+                y[q] = out;
+                if (dotmode != 0) {
+                    dw += wv[rr] * out;
+                    dy += out * out;
+                }
+            }
+        }
+    }
+    if (dotmode == 0) return;
+    if (lane == 0) {
+        wsum[0][warp] = dw;
+        wsum[1][warp] = dy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < kP2Warps; ++k) { a += wsum[0][k]; b += wsum[1][k]; }
+        dpart[blockIdx.x] = a;
+        dpart[gridDim.x + blockIdx.x] = b;
+    }
+}
+
+template <Store S, int MR>
+__global__ void __launch_bounds__(kP2Threads, MR == 4 ? 3 : 2) k_phase2(const P2Desc *__restrict__ desc,
+                                                                       const void *__restrict__ p2,
+                                                                       const typename Tr<S>::Op *__restrict__ g,
+                                                                       double *__restrict__ y,
+                                                                       const int32_t *__restrict__ out_perm,
+                                                                       int accum, const SolverScalars *S_, int mode,
+                                                                       const double *__restrict__ w, int dotmode,
+                                                                       double *dpart) {
+    using Op = typename Tr<S>::Op;
+    constexpr int VW = Tr<S>::VW;
+    if (skip_product(S_, mode)) return;
+    const P2Desc d = desc[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t esz = 16 / VW;
+    const char *base = (const char *)p2 + (size_t)d.off * esz;
+    const size_t row_bytes = (size_t)d.ld * esz;
+    const Op *gr = g + d.goff;  // operands of this row cluster, read through L1 by every warp
+
+    Acc<S> acc[MR];
+#pragma unroll
+    for (int r = 0; r < MR; ++r) acc[r].init();
+    double wv[MR];  // w of the fused inner products, loaded ahead of the stream
+#pragma unroll
+    for (int r = 0; r < MR; ++r) {
+        const int i = warp + r * kP2Warps;
+        wv[r] = (dotmode != 0 && lane == 0 && i < d.ylen) ? __ldg(w + d.ybeg + i) : 0.0;
+    }
+    const int nv = d.ld / VW;
+    int v = lane;
+    // two vectors per row in flight per iteration
+    for (; v + 32 < nv; v += 64) {
+        int4 ra[MR], rb[MR];
+#pragma unroll
+        for (int rr = 0; rr < MR; ++rr) {
+            const int i = warp + rr * kP2Warps;
+            const char *p = base + (size_t)i * row_bytes + (size_t)v * 16;
+            ra[rr] = i < d.ylen ? ld_stream(p) : make_int4(0, 0, 0, 0);
+            rb[rr] = i < d.ylen ? ld_stream(p + 32 * 16) : make_int4(0, 0, 0, 0);
+        }
+        const GV<S> ga = GV<S>::load(gr + v * VW), gb = GV<S>::load(gr + (v + 32) * VW);
+#pragma unroll
+        for (int rr = 0; rr < MR; ++rr)
+            if (warp + rr * kP2Warps < d.ylen) { row_mac<S>(acc[rr], ra[rr], ga); row_mac<S>(acc[rr], rb[rr], gb); }
+    }
+    if (v < nv) {
+        int4 ra[MR];
+#pragma unroll
+        for (int rr = 0; rr < MR; ++rr) {
+            const int i = warp + rr * kP2Warps;
+            ra[rr] = i < d.ylen ? ld_stream(base + (size_t)i * row_bytes + (size_t)v * 16) : make_int4(0, 0, 0, 0);
+        }
+        const GV<S> ga = GV<S>::load(gr + v * VW);
+#pragma unroll
+        for (int rr = 0; rr < MR; ++rr)
+            if (warp + rr * kP2Warps < d.ylen) row_mac<S>(acc[rr], ra[rr], ga);
+    }
+    phase2_epilogue<S, MR>(d, acc, y, out_perm, accum, wv, dotmode, dpart);
+}
+
+// Row-persistent phase 2: a fixed grid (kP2wBlocksPerSM CTAs per SM) whose
+// warps each own the rows p = gw, gw + W, gw + 2W, ... (W warps in all), two rows
+// at a time with up to p2w_vec 16-byte vectors per lane and row in flight; no
+// barrier until the CTA's last row.  Each row's lane partials are added by the
+// fixed butterfly and lane 0 writes y (or adds to it, accum); with dotmode set
+// the warp adds its rows' w . y and y . y in row order, and the CTA leaves the
+// sum over its warps, in warp order, in dpart[block] and dpart[grid + block].
+constexpr int kP2wBlocksPerSM = kP2RowBlocksPerSM;
+// vectors per lane and row in flight: four for the 8-byte stores, whose rows
+// are twice as many vectors; fewer for the others to stay within 64 registers
+template <Store S> constexpr int p2w_vec() { return Tr<S>::VW == 2 ? 4 : 2; }
+
+template <Store S>
+struct RowCtx {
+    const char *row;                // this row's panel entries
+    const typename Tr<S>::Op *g;    // its leaf row cluster's operands
+    int nv;                         // 16-byte vectors (ld / VW), 0 for no row
+    int p;                          // row (cluster order)
+};
+
+template <Store S>
+__device__ __forceinline__ RowCtx<S> row_ctx(int p, int n, const int32_t *__restrict__ row_leaf,
+                                             const P2Desc *__restrict__ desc, const void *__restrict__ p2,
+                                             const typename Tr<S>::Op *__restrict__ g) {
+    RowCtx<S> r;
+    r.p = p;
+    if (p >= n) {
+        r.row = nullptr; r.g = nullptr; r.nv = 0;
+        return r;
+    }
+    constexpr size_t esz = 16 / Tr<S>::VW;
+    const P2Desc d = desc[__ldg(row_leaf + p)];
+    r.row = (const char *)p2 + ((size_t)d.off + (size_t)(p - d.ybeg) * d.ld) * esz;
+    r.g = g + d.goff;
+    r.nv = d.ld / Tr<S>::VW;
+    return r;
+}
+
+template <Store S>
+__device__ __forceinline__ double row_total(Acc<S> &acc) {
+    using RT = typename RedT<S>::T;
+    const int lane = threadIdx.x & 31;
+    RT a = row_partial<S>(acc);
+    for (int m = 1; m < 32; m <<= 1) a = red_xor<S>(a, m, (lane & m) != 0);
+    if constexpr (red_double(S)) return a;
+    else return df_to_double(a);
+}
+
+template <Store S>
+__global__ void __launch_bounds__(kP2Threads, kP2wBlocksPerSM) k_phase2w(
+    int n, const int32_t *__restrict__ row_leaf, const P2Desc *__restrict__ desc, const void *__restrict__ p2,
+    const typename Tr<S>::Op *__restrict__ g, double *__restrict__ y, const int32_t *__restrict__ out_perm, int accum,
+    const SolverScalars *S_, int mode, const double *__restrict__ w, int dotmode, double *dpart) {
+    constexpr int VW = Tr<S>::VW;
+    __shared__ double wsum[2][kP2Warps];
+    if (skip_product(S_, mode)) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int W = gridDim.x * kP2Warps;
+    double dw = 0.0, dy = 0.0;
+    for (int p0 = blockIdx.x * kP2Warps + warp; p0 < n; p0 += 2 * W) {
+        const RowCtx<S> r0 = row_ctx<S>(p0, n, row_leaf, desc, p2, g);
+        const RowCtx<S> r1 = row_ctx<S>(p0 + W, n, row_leaf, desc, p2, g);
+        // w of the inner products, loaded ahead of the stream
+        const double w0 = (dotmode != 0 && lane == 0) ? __ldg(w + p0) : 0.0;
+        const double w1 = (dotmode != 0 && lane == 0 && r1.nv) ? __ldg(w + p0 + W) : 0.0;
+        Acc<S> a0, a1;
+        a0.init();
+        a1.init();
+        const int nvmax = max(r0.nv, r1.nv);
+        constexpr int NVEC = p2w_vec<S>();
+        for (int c = 0; c < nvmax; c += 32 * NVEC) {
+            int4 ra[NVEC], rb[NVEC];
+#pragma unroll
+            for (int u = 0; u < NVEC; ++u) {
+                const int v = c + lane + 32 * u;
+                ra[u] = v < r0.nv ? ld_stream(r0.row + (size_t)v * 16) : make_int4(0, 0, 0, 0);
+                rb[u] = v < r1.nv ? ld_stream(r1.row + (size_t)v * 16) : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < NVEC; ++u) {
+                const int v = c + lane + 32 * u;
+                if (v < r0.nv) row_mac<S>(a0, ra[u], GV<S>::load(r0.g + v * VW));
+                if (v < r1.nv) row_mac<S>(a1, rb[u], GV<S>::load(r1.g + v * VW));
+            }
+        }
+        const double o0 = row_total<S>(a0);
+        const double o1 = r1.nv ? row_total<S>(a1) : 0.0;  // warp-uniform condition
+        if (lane == 0) {
+            const RowCtx<S> *rs[2] = {&r0, &r1};
+            const double os[2] = {o0, o1}, ws[2] = {w0, w1};
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (rs[k]->nv == 0) continue;
+                const int p = rs[k]->p;
+                const int q = out_perm ? out_perm[p] : p;
+                double out = os[k];
+                if (accum) out = y[q] + out;  // a later segment adds to the earlier ones' rows
+                y[q] = out;
+                if (dotmode != 0) {
+                    dw += ws[k] * out;
+                    dy += out * out;
+                }
+            }
+        }
+    }
+    if (dotmode == 0) return;
+    if (lane == 0) {
+        wsum[0][warp] = dw;
+        wsum[1][warp] = dy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < kP2Warps; ++k) { a += wsum[0][k]; b += wsum[1][k]; }
+        dpart[blockIdx.x] = a;
+        dpart[gridDim.x + blockIdx.x] = b;
+    }
+}
+
+int grid_for(int64_t n, int threads, int cap) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+// launches of one store's product kernels (the dispatchers pick the store)
+template <Store SS>
+void phase1_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st) {
+    k_phase1<SS><<<ix.nleaves, kP1Threads, 0, st>>>(ix.p1, ix.p1_runs, ix.xdst, ix.lr, ix.gdst, P.q1,
+                                                    (const typename Tr<SS>::Op *)P.xs, (typename Tr<SS>::Part *)P.part,
+                                                    (typename Tr<SS>::Op *)P.g, ix.tscale, skipS, mode);
+}
+
+template <Store SS>
+void reduce_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st) {
+    const int blocks = ix.nbig + (ix.ntasks + kRedThreads - 1) / kRedThreads;
+    if (blocks == 0) return;
+    k_reduce<SS><<<blocks, kRedThreads, 0, st>>>(ix.nbig, ix.ntasks, ix.red_big, ix.red_tasks, ix.lr, ix.gdst,
+                                                 (const typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g,
+                                                 ix.tscale, skipS, mode);
+}
+
+template <Store SS>
+void phase2_launch(const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm, int accum,
+                   const SolverScalars *skipS, int mode, cudaStream_t st, const double *w, int dotmode,
+                   double *dpart) {
+    if (phase2_rows(SS, ix)) {
+        k_phase2w<SS><<<ix.p2_grid, kP2Threads, 0, st>>>(ix.n, ix.row_leaf, ix.p2, P.p2,
+                                                         (const typename Tr<SS>::Op *)P.g, y, out_perm, accum, skipS,
+                                                         mode, w, dotmode, dpart);
+        return;
+    }
+    if (ix.max_leaf <= 4 * kP2Warps)
+        k_phase2<SS, 4><<<ix.nleaves, kP2Threads, 0, st>>>(ix.p2, P.p2, (const typename Tr<SS>::Op *)P.g, y, out_perm,
+                                                           accum, skipS, mode, w, dotmode, dpart);
+    else
+        k_phase2<SS, kMaxLeaf / kP2Warps><<<ix.nleaves, kP2Threads, 0, st>>>(
+            ix.p2, P.p2, (const typename Tr<SS>::Op *)P.g, y, out_perm, accum, skipS, mode, w, dotmode, dpart);
+}
+
+}  // namespace
+
+}  // namespace hmat_internal

@@ -1,0 +1,159 @@
+"""Many BiCG-STAB recurrences at once (hmat_bicgstab_multi): the 64 right-hand
+sides of one H-matrix, and a batch of 48 independent problems of uneven size in
+one block-diagonal handle.  Every system must reach a true relative residual of
+1e-8 (checked with the oracle's own FP64 H-matrix) and agree with the oracle's
+single-system FP64 solve to the accuracy the tolerance allows."""
+import numpy as np
+import pytest
+
+import synth
+from blob_util import oracle_blob
+from gpu_util import lib, need_gpu, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _true_rel(H, b, x):
+    return float(np.linalg.norm(b - H.matvec(x)) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("form,opts", [("fp64", {}), ("bf16", {"inner_tol": 1e-2}), ("m2_mixed", {"inner_tol": 1e-4})])
+def test_multi_rhs_small(hcache, oracle_mod, form, opts):
+    torch = need_gpu()
+    P = lib()
+    mesh = synth.icosphere(3)
+    H = hcache(mesh)
+    nrhs = 8
+    B = synth.rhs_normal_columns(mesh.n, nrhs)  # (N, nrhs), column-major
+    h = P.hmat_upload(oracle_blob(H), form)
+    try:
+        X = np.zeros((mesh.n, nrhs), order="F")
+        infos = P.hmat_bicgstab_multi(h, B, X, nrhs, tol=1e-8, maxit=500, check_every=2, **opts)
+        assert len(infos) == nrhs
+        for k in range(nrhs):
+            assert infos[k]["status"] == 0 and infos[k]["relres_true"] <= 1e-8, (k, infos[k])
+            assert _true_rel(H, B[:, k], X[:, k]) <= 1.05e-8
+            xk, _ = H.bicgstab(B[:, k], tol=1e-10)
+            assert rel(X[:, k], xk) <= 1e-6, (k, rel(X[:, k], xk))
+        # device tensors give the same bits; one system alone matches the single solver's accuracy
+        Bd = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+        Xd = torch.zeros_like(Bd)
+        infos_d = P.hmat_bicgstab_multi(h, Bd, Xd, nrhs, tol=1e-8, maxit=500, check_every=2, **opts)
+        torch.cuda.synchronize()
+        assert np.array_equal(Xd.cpu().numpy().T, X)
+        assert [i["iters"] for i in infos_d] == [i["iters"] for i in infos]
+    finally:
+        P.hmat_destroy(h)
+
+
+def test_multi_rhs_statuses(hcache):
+    """A zero right-hand side is solved by x = 0 without iterating; an iteration
+    budget of 2 ends the other systems with HMAT_ERR_MAXIT, each on its own."""
+    need_gpu()
+    P = lib()
+    mesh = synth.icosphere(3)
+    H = hcache(mesh)
+    B = synth.rhs_normal_columns(mesh.n, 3)
+    B[:, 1] = 0.0
+    h = P.hmat_upload(oracle_blob(H), "fp64")
+    try:
+        X = np.ones((mesh.n, 3), order="F")
+        infos = P.hmat_bicgstab_multi(h, B, X, 3, tol=1e-8, maxit=2, max_restarts=0)
+        assert infos[1]["status"] == 0 and infos[1]["iters"] == 0 and np.all(X[:, 1] == 0.0)
+        for k in (0, 2):
+            assert infos[k]["status"] == 7 and infos[k]["iters"] == 2, infos[k]
+    finally:
+        P.hmat_destroy(h)
+
+
+def test_multi_rhs_full_size_64(oracle_mod):
+    """Icosphere level 6 (N = 81,920), 64 right-hand sides of N(0,1) panel
+    potentials, BF16 panels inside the FP64 refinement: all 64 recurrences reach
+    1e-8 (oracle FP64 H-matrix); two columns match the oracle's FP64 solve."""
+    torch = need_gpu()
+    P = lib()
+    mesh = synth.icosphere(6)
+    blob = P.hmat_build(mesh.centroid, mesh.area)
+    H = oracle_mod.HMatrix(mesh.centroid, mesh.area)
+    nrhs = 64
+    B = synth.rhs_normal_columns(mesh.n, nrhs)
+    h = P.hmat_upload(blob, "bf16")
+    try:
+        Bd = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+        Xd = torch.zeros_like(Bd)
+        infos = P.hmat_bicgstab_multi(h, Bd, Xd, nrhs, tol=1e-8, maxit=2000, inner_tol=1e-2, check_every=4)
+        torch.cuda.synchronize()
+        X = Xd.cpu().numpy().T
+        assert all(i["status"] == 0 for i in infos), [i for i in infos if i["status"] != 0][:2]
+        for k in range(nrhs):
+            assert _true_rel(H, B[:, k], X[:, k]) <= 1.05e-8, k
+        for k in (0, 37):  # tol x cond of the level-6 single layer (~ 600) bounds the difference
+            xk, _ = H.bicgstab(B[:, k], tol=1e-10)
+            assert rel(X[:, k], xk) <= 1e-5, (k, rel(X[:, k], xk))
+    finally:
+        P.hmat_destroy(h)
+
+
+def test_uneven_batch_48(oracle_mod):
+    """48 independent problems (unit-cube surfaces and cube-spheres, N drawn
+    log-uniformly in [1280, 20480]) in one block-diagonal handle with FP32 panels:
+    every problem converges to 1e-8 against its own oracle H-matrix, and the
+    batch handle's product is every problem's own product."""
+    torch = need_gpu()
+    P = lib()
+    specs = synth.uneven_batch_specs(48)
+    meshes = [synth.mesh_from_spec(s) for s in specs]
+    blobs = [P.hmat_build(m.centroid, m.area) for m in meshes]
+    h = P.hmat_upload_batch(blobs, "fp32")
+    try:
+        off = P.hmat_problems(h)
+        assert len(off) == 49 and off[-1] == sum(m.n for m in meshes)
+        b = np.concatenate([synth.rhs_constant(m) for m in meshes])
+        x = np.zeros(off[-1])
+        infos = P.hmat_bicgstab_multi(h, b, x, 1, tol=1e-8, maxit=2000, inner_tol=1e-4, check_every=4)
+        assert all(i["status"] == 0 for i in infos), [i for i in infos if i["status"] != 0][:2]
+        xs = np.random.default_rng(48).standard_normal(off[-1])
+        ys = np.empty(off[-1])
+        P.hmat_matvec(h, xs, ys, 1, None, True)  # FP64 operator of the whole batch
+        for p, m in enumerate(meshes):
+            sl = slice(off[p], off[p + 1])
+            H = oracle_mod.HMatrix(m.centroid, m.area)
+            assert _true_rel(H, b[sl], x[sl]) <= 1.05e-8, (p, specs[p])
+            assert rel(ys[sl], H.matvec(xs[sl])) <= 1e-13, p
+    finally:
+        P.hmat_destroy(h)
+
+
+@pytest.mark.parametrize("mesh", [synth.icosphere(3), synth.two_spheres(3), synth.icosphere(4)], ids=lambda m: m.name)
+@pytest.mark.parametrize("nrhs", [64, 5, 70])
+def test_tensor_core_product_parity(hcache, oracle_mod, mesh, nrhs):
+    """The BF16 product of many columns on the tensor cores against the oracle's
+    product on the same BF16-rounded panels (FP64 arithmetic) and against the
+    single-column GPU product: the split x / t operands and FP32 accumulation keep
+    it within 2e-5; 5 columns leave most of a pass empty, 70 take two passes."""
+    torch = need_gpu()
+    P = lib()
+    H = hcache(mesh)
+    h = P.hmat_upload(oracle_blob(H), "bf16")
+    try:
+        X = synth.rhs_normal_columns(mesh.n, nrhs, seed=nrhs)
+        Xd = torch.from_numpy(np.ascontiguousarray(X.T)).cuda()
+        Yd = torch.empty_like(Xd)
+        P.hmat_matvec(h, Xd, Yd, nrhs)
+        torch.cuda.synchronize()
+        Y = Yd.cpu().numpy().T
+        for k in sorted({0, 1, nrhs // 2, nrhs - 1}):
+            ybf = H.matvec(X[:, k], oracle_mod.DATA_BF16)
+            assert rel(Y[:, k], ybf) <= 2e-5, (k, rel(Y[:, k], ybf))
+            y1 = torch.empty(mesh.n, dtype=torch.float64, device="cuda")
+            P.hmat_matvec(h, Xd[k].contiguous(), y1, 1)
+            torch.cuda.synchronize()
+            assert rel(Y[:, k], y1.cpu().numpy()) <= 2e-5
+            assert rel(Y[:, k], H.matvec(X[:, k])) <= 1e-2
+        # repeated passes give the same bits (no atomics)
+        Y2 = torch.empty_like(Xd)
+        P.hmat_matvec(h, Xd, Y2, nrhs)
+        torch.cuda.synchronize()
+        assert torch.equal(Y2, Yd)
+    finally:
+        P.hmat_destroy(h)

@@ -69,3 +69,28 @@ def test_noalloc_rejects_host_pointers_and_oversized_handles():
         assert e.value.status == 10
     finally:
         P.hmat_destroy(hb)
+
+
+def test_noalloc_paper_variants():
+    """A one-segment paper variant runs through the static array like any form;
+    a two-segment one (its products add two expansions) is rejected."""
+    torch = need_gpu()
+    P = lib()
+    mesh = synth.icosphere(3)
+    blob = P.hmat_build(mesh.centroid, mesh.area)
+    x = _device(torch, np.random.default_rng(8).standard_normal(mesh.n))
+    h1 = P.hmat_upload(blob, "m2_mixed")
+    h2 = P.hmat_upload(blob, "m3", 1)
+    try:
+        y_ref = torch.empty_like(x)
+        y = torch.full_like(x, np.nan)
+        P.hmat_matvec(h1, x, y_ref)
+        P.hmat_matvec_noalloc(h1, x, y)
+        torch.cuda.synchronize()
+        assert rel(y.cpu().numpy(), y_ref.cpu().numpy()) <= TOL
+        with pytest.raises(P.HmatError) as e:
+            P.hmat_matvec_noalloc(h2, x, y)
+        assert e.value.status == 10
+    finally:
+        P.hmat_destroy(h1)
+        P.hmat_destroy(h2)
