@@ -216,6 +216,106 @@ def cpu_baseline(mesh, b):
                       f"true relres {info['relres']:.2e}, {t:.1f} s single-threaded; the OpenMP build is untimed)"}
 
 
+def _cuda_ms(torch, fn, reps):
+    """Mean milliseconds of fn() over reps calls, CUDA events on the current stream."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    out = [fn() for _ in range(reps)]
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def run_workload(args):
+    """The other configurations of the study, one JSON line each (not the headline):
+    icosphere_L4 (FP64 correctness size), two_spheres_L7 (BF16 + FP64 refinement,
+    N = 655,360), multirhs64 (64 right-hand sides at level 6, tensor-core products),
+    batch48 (48 uneven cube / sphere problems in one block-diagonal handle)."""
+    import torch
+    import synth
+    import paper_1911_00093_gb300 as P
+    P.load()
+    torch.cuda.set_device(0)
+    out = {"metric": METRIC, "unit": "ms per solve", "higher_is_better": False, "data": "synthetic",
+           "config": {"workload": args.workload}}
+    if args.workload in ("icosphere_L4", "two_spheres_L7"):
+        mesh = synth.icosphere(4) if args.workload == "icosphere_L4" else synth.two_spheres(7)
+        b_np = synth.rhs_constant(mesh) if args.workload == "icosphere_L4" else synth.rhs_two_spheres(mesh)
+        blob = P.hmat_build(mesh.centroid, mesh.area)
+        b = torch.from_numpy(b_np).cuda()
+        x = torch.zeros_like(b)
+        forms = {"fp64": {}, "bf16": {"inner_tol": 1e-2}}
+        out["config"]["n"] = mesh.n
+        for f, opts in forms.items():
+            h = P.hmat_upload(blob, f)
+            def solve():
+                x.zero_()
+                return P.hmat_bicgstab(h, b, x, tol=1e-8, maxit=3000, check_every=CHECK_EVERY, **opts)
+            solve()
+            ms, infos = _cuda_ms(torch, solve, 3)
+            kt = P.hmat_time_matvec(h, 10)
+            info = P.hmat_info(h)
+            out[f] = {"solve_ms": ms, "iters": infos[-1]["iters"], "restarts": infos[-1]["restarts"],
+                      "relres_true": infos[-1]["relres_true"], "matvec_ms": kt[4],
+                      "matvec_gbs": info["stored_bytes"] / (kt[4] * 1e-3) / 1e9}
+            P.hmat_destroy(h)
+        out["value"] = out["bf16"]["solve_ms"]
+        out["speedup_bf16_vs_fp64"] = out["fp64"]["solve_ms"] / out["bf16"]["solve_ms"]
+    elif args.workload == "multirhs64":
+        mesh = synth.icosphere(6)
+        nrhs = 64
+        blob = P.hmat_build(mesh.centroid, mesh.area)
+        h = P.hmat_upload(blob, "bf16")
+        B = torch.from_numpy(np.ascontiguousarray(synth.rhs_normal_columns(mesh.n, nrhs).T)).cuda()
+        X = torch.zeros_like(B)
+        def multi():
+            X.zero_()
+            return P.hmat_bicgstab_multi(h, B, X, nrhs, tol=1e-8, maxit=3000, inner_tol=1e-2, check_every=CHECK_EVERY)
+        multi()
+        ms, infos = _cuda_ms(torch, multi, 2)
+        x1 = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+        def single():
+            x1.zero_()
+            return P.hmat_bicgstab(h, B[0].contiguous(), x1, tol=1e-8, maxit=3000, inner_tol=1e-2,
+                                   check_every=CHECK_EVERY)
+        single()
+        ms1, info1 = _cuda_ms(torch, single, 3)
+        Y = torch.empty_like(B)
+        mv_ms, _ = _cuda_ms(torch, lambda: P.hmat_matvec(h, B, Y, nrhs), 10)
+        assert all(i["status"] == 0 for i in infos[-1])
+        out.update({"unit": "ms per 64 solves", "value": ms, "config": {"workload": "icosphere_L6_64rhs_N(0,1)",
+                    "n": mesh.n, "nrhs": nrhs, "form": "bf16 + FP64 refinement"},
+                    "iters_min_max": [min(i["iters"] for i in infos[-1]), max(i["iters"] for i in infos[-1])],
+                    "single_rhs_solve_ms": ms1, "single_rhs_iters": info1[-1]["iters"],
+                    "tensor_core_product_ms_64_columns": mv_ms,
+                    "single_column_product_ms": P.hmat_time_matvec(h, 10)[4]})
+        P.hmat_destroy(h)
+    elif args.workload == "batch48":
+        specs = synth.uneven_batch_specs(48)
+        meshes = [synth.mesh_from_spec(sp) for sp in specs]
+        blobs = [P.hmat_build(m.centroid, m.area) for m in meshes]
+        b = torch.from_numpy(np.concatenate([synth.rhs_constant(m) for m in meshes])).cuda()
+        x = torch.zeros_like(b)
+        out["config"].update({"problems": len(meshes), "n_total": int(b.numel()),
+                              "n_min_max": [min(m.n for m in meshes), max(m.n for m in meshes)]})
+        out["unit"] = "ms per batch solve"
+        for f, opts in (("fp64", {}), ("fp32", {"inner_tol": 1e-4})):
+            h = P.hmat_upload_batch(blobs, f)
+            def solve():
+                x.zero_()
+                return P.hmat_bicgstab_multi(h, b, x, 1, tol=1e-8, maxit=3000, check_every=CHECK_EVERY, **opts)
+            solve()
+            ms, infos = _cuda_ms(torch, solve, 3)
+            assert all(i["status"] == 0 for i in infos[-1])
+            out[f] = {"batch_solve_ms": ms, "iters_max": max(i["iters"] for i in infos[-1]),
+                      "matvec_ms": P.hmat_time_matvec(h, 10)[4]}
+            P.hmat_destroy(h)
+        out["value"] = out["fp32"]["batch_solve_ms"]
+        out["speedup_fp32_vs_fp64"] = out["fp64"]["batch_solve_ms"] / out["fp32"]["batch_solve_ms"]
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -227,9 +327,14 @@ def main():
     ap.add_argument("--forms", default=DEFAULT_FORMS, help="forms measured beside the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--matvec-iters", type=int, default=50)
+    ap.add_argument("--workload", default="icosphere_L6",
+                    choices=["icosphere_L6", "icosphere_L4", "two_spheres_L7", "multirhs64", "batch48"],
+                    help="icosphere_L6 is the benchmark; the others print one informative line each")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "icosphere_L6":
+        return run_workload(args)
 
     import torch
     world, rank, local = _dist_setup(args)

@@ -89,7 +89,7 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
     LrDesc *lr = nullptr;
     P2Desc *p2 = nullptr;
     double *tscale = nullptr;
-    int32_t *row_leaf = nullptr;
+    RowDesc *rows = nullptr;
     int st;
     if ((st = h->upload(&p1, L.p1.data(), sizeof(P1Desc) * L.p1.size())) ||
         (st = h->upload(&p1_runs, L.p1_runs.data(), sizeof(P1Run) * L.p1_runs.size())) ||
@@ -100,26 +100,28 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
         (st = h->upload(&red_tasks, L.red_tasks.data(), 4 * L.red_tasks.size())) ||
         (st = h->upload(&p2, L.p2.data(), sizeof(P2Desc) * L.p2.size())) ||
         (st = h->upload(&tscale, L.tscale.data(), 8 * L.tscale.size())) ||
-        (st = h->upload(&row_leaf, L.row_leaf.data(), 4 * L.row_leaf.size()))) {
+        (st = h->upload(&rows, L.rows.data(), sizeof(RowDesc) * L.rows.size()))) {
         return st;
     }
     ix.p1 = p1; ix.p1_runs = p1_runs; ix.xdst = xdst; ix.lr = lr; ix.gdst = gdst; ix.p2 = p2;
     ix.red_big = red_big; ix.red_tasks = red_tasks;
     ix.tscale = L.tscale.empty() ? nullptr : tscale;
-    // phase-2 launch shape (phase2_rows): HMAT_PHASE2=cluster selects one CTA per
-    // leaf row cluster for every store (a tuning override; both are exact)
-    ix.row_leaf = row_leaf;
+    ix.rows = rows;
+    // phase-2 launch shape (phase2_shape): row-persistent for 2-/4-byte panels;
+    // HMAT_PHASE2=cluster or =staged selects the others (all are exact)
     const char *p2env = std::getenv("HMAT_PHASE2");
-    ix.p2_rows = (p2env && std::strcmp(p2env, "cluster") == 0) ? 0 : 1;
+    ix.p2_shape = 1;
+    if (p2env && std::strcmp(p2env, "cluster") == 0) ix.p2_shape = 0;
+    if (p2env && std::strcmp(p2env, "staged") == 0) ix.p2_shape = 2;
     int nsm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    ix.p2_grid = ix.p2_rows ? std::max(1, nsm) * kP2RowBlocksPerSM : L.nleaves;
+    ix.nsm = std::max(1, nsm);
     g.partials_n = L.npart;
     g.glen = L.glen;
     h->index_bytes += (int64_t)(sizeof(P1Desc) * L.p1.size() + sizeof(P1Run) * L.p1_runs.size() +
                                 sizeof(XDst) * L.xdst.size() + sizeof(LrDesc) * L.lr.size() + 4 * L.gdst.size() +
                                 sizeof(P2Desc) * L.p2.size() + 4 * (L.red_big.size() + L.red_tasks.size()) +
-                                8 * L.tscale.size() + 4 * L.row_leaf.size());
+                                8 * L.tscale.size() + sizeof(RowDesc) * L.rows.size());
     return HMAT_OK;
 }
 
@@ -232,6 +234,7 @@ int upload_view(const BlobView &v, int32_t precision, int32_t method3_c, const s
         if (st == HMAT_OK) st = check_layout(L);
         if (st != HMAT_OK) return st;
         CK(cudaGetDevice(&h->device));
+        CK(prepare_launches());
         h->precision = precision;
         h->method3_c = precision == HMAT_M3 ? method3_c : 0;
         h->n = L.n;
@@ -293,7 +296,7 @@ int upload_view(const BlobView &v, int32_t precision, int32_t method3_c, const s
         for (double **pp : vecs)
             if ((st = h->alloc(pp, nb))) return st;
         if ((st = h->alloc(&h->partials, sizeof(double) * 2 * (size_t)vec_blocks(L.n))) ||
-            (st = h->alloc(&h->dpart, sizeof(double) * 2 * (size_t)std::max(L.nleaves, h->seg[0].ix.p2_grid))) ||
+            (st = h->alloc(&h->dpart, sizeof(double) * 2 * (size_t)std::max(L.nleaves, 4 * h->seg[0].ix.nsm))) ||
             (st = h->alloc(&h->S, sizeof(SolverScalars)))) {
             return st;
         }

@@ -98,6 +98,13 @@ struct P2Desc {
     int32_t pad;
 };
 
+// One row of the phase-2 panels (the row-persistent expansion's work item).
+struct RowDesc {
+    int64_t off;    // element offset of the row
+    int32_t goff;   // first operand of its leaf row cluster
+    int32_t ld;     // entries (the cluster's panel stride; 0 for no row)
+};
+
 constexpr int kMaxScaleExp = 120;  // |e| of every stored power-of-two scale
 constexpr int kRedBigCnt = 32;     // blocks over this many leaf clusters are reduced by a whole CTA
 
@@ -106,7 +113,7 @@ struct Layout {
     int32_t nleaves = 0;
     std::vector<int32_t> perm;        // perm[p] = original index
     std::vector<int32_t> leaf_begin;  // nleaves + 1
-    std::vector<int32_t> row_leaf;    // [n] leaf cluster of each row (cluster order)
+    std::vector<RowDesc> rows;        // [n] every row's place in the phase-2 panels (cluster order)
     std::vector<P1Desc> p1;
     std::vector<P1Run> p1_runs;
     std::vector<XDst> xdst;

@@ -20,6 +20,12 @@ namespace hmat_internal {
 // the paper's variants keep x in FP64 (their FP32 copies are made in phase 1)
 static Store operand_store(Store s) { return is_table1(s) ? Store::F64 : s; }
 
+cudaError_t prepare_launches() {
+    cudaError_t e = staged_prepare<Store::BF16>();
+    if (e == cudaSuccess) e = staged_prepare<Store::F32>();
+    return e;
+}
+
 void launch_prep(Store s, const DevIndex &ix, const double *x, const int32_t *src_perm, void *xs, cudaStream_t st) {
     int blocks = grid_for(ix.n, 256, 4096);
     HMAT_DISPATCH(operand_store(s), (k_prep<SS><<<blocks, 256, 0, st>>>(ix.n, x, src_perm, (typename Tr<SS>::Op *)xs)));

@@ -20,9 +20,9 @@ struct DevIndex {
     const int32_t *red_big = nullptr, *red_tasks = nullptr;
     const P2Desc *p2 = nullptr;     // [nleaves]
     const double *tscale = nullptr; // per-rank factors of LrDesc::toff (paper's Methods 2 and 3)
-    const int32_t *row_leaf = nullptr;  // [n] leaf row cluster of each row (cluster order)
-    int32_t p2_rows = 1;            // 0: every store's phase 2 runs one CTA per leaf row cluster
-    int32_t p2_grid = 0;            // CTAs of the row-persistent phase-2 launch
+    const RowDesc *rows = nullptr;  // [n] phase-2 rows (cluster order)
+    int32_t p2_shape = 1;           // expansion of 2-/4-byte panels: 0 per cluster, 1 row-persistent, 2 staged
+    int32_t nsm = 1;                // SMs of the device (row-persistent grid = nsm x p2w_blocks)
     int32_t max_leaf = 0;           // rows of the widest leaf cluster
     int32_t max_ld2 = 0;            // widest phase-2 panel (entries)
 };
@@ -37,17 +37,35 @@ struct DevPanels {
     void *g = nullptr;         // phase-2 operand buffers (glen entries of the operand type)
 };
 
-// CTAs per SM of the row-persistent phase-2 launch (its launch bound).
-constexpr int kP2RowBlocksPerSM = 4;
+// CTAs per SM of the row-persistent phase-2 launch (its launch bound).  Four,
+// with two 16-byte vectors per lane and row in flight for 2- and 4-byte panels:
+// BF16 at three CTAs and four vectors measured slower (67.9 vs 57.7 us at L6).
+constexpr int p2w_blocks(Store) { return 4; }
 
-// Phase-2 launch shape of a store: the row-persistent grid for the stores of
-// 2- and 4-byte entries (short rows, where per-CTA latency dominates), one CTA
-// per leaf row cluster for the 8-byte ones (measured faster on GB300).
-inline bool phase2_rows(Store s, const DevIndex &ix) {
-    return ix.p2_rows && s != Store::DF && s != Store::F64;
+// Phase-2 launch shape of a store: 0 one CTA per leaf row cluster (the 8-byte
+// stores, and any store with HMAT_PHASE2=cluster), 1 row-persistent warps over a
+// fixed grid (the default for 2- and 4-byte panels), 2 staged (a persistent CTA
+// per SM streaming through shared memory with bulk copies; BF16 and FP32 panels
+// whose rows fit a slot; HMAT_PHASE2=staged; measured slower, kept as an option).
+constexpr int kStagedSlotBytes = 16384;
+constexpr int kStagedSmemMax = 200 * 1024;  // its ring of slots plus two operand slots
+// raise the launch limits the staged expansion needs (once per process and device)
+cudaError_t prepare_launches();
+inline int phase2_shape(Store s, const DevIndex &ix) {
+    if (s == Store::DF || s == Store::F64 || ix.p2_shape == 0) return 0;
+    const int esz = s == Store::BF16 ? 2 : 4;
+    if (ix.p2_shape == 2 && (s == Store::BF16 || s == Store::F32) && ix.max_ld2 * esz <= kStagedSlotBytes) return 2;
+    return 1;
 }
+inline bool phase2_rows(Store s, const DevIndex &ix) { return phase2_shape(s, ix) == 1; }
 // Work items whose inner-product shares a solver expansion leaves in dpart.
-inline int phase2_items(Store s, const DevIndex &ix) { return phase2_rows(s, ix) ? ix.p2_grid : ix.nleaves; }
+inline int phase2_items(Store s, const DevIndex &ix) {
+    switch (phase2_shape(s, ix)) {
+    case 1: return ix.nsm * p2w_blocks(s);
+    case 2: return ix.nsm;
+    default: return ix.nleaves;
+    }
+}
 
 // Operand bytes per entry for a store (x and t copies).
 inline size_t operand_bytes(Store s) { return s == Store::F32 || s == Store::BF16 ? 4 : 8; }

@@ -239,9 +239,7 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
     L.leaf_begin.resize(nleaves + 1);
     for (int64_t l = 0; l <= nleaves; ++l) L.leaf_begin[l] = (int32_t)v.leaf_begin[l];
     for (int64_t l = 0; l < nleaves; ++l) L.max_leaf = std::max<int32_t>(L.max_leaf, L.leaf_begin[l + 1] - L.leaf_begin[l]);
-    L.row_leaf.resize(n);
-    for (int64_t l = 0; l < nleaves; ++l)
-        for (int64_t p = L.leaf_begin[l]; p < L.leaf_begin[l + 1]; ++p) L.row_leaf[p] = (int32_t)l;
+
     auto leaf_index = [&](int64_t x) {
         return (int64_t)(std::lower_bound(v.leaf_begin.begin(), v.leaf_begin.end(), x) - v.leaf_begin.begin());
     };
@@ -312,6 +310,11 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
         L.p2_slice_ptr[k + 1] = (int64_t)L.p2_slices.size();
     }
     if (goff > (int64_t(1) << 31) - 16) { if (why) *why = "operand buffer too large"; return HMAT_ERR_UNSUPPORTED; }
+    L.rows.resize(n);
+    for (int64_t k = 0; k < nleaves; ++k) {
+        const P2Desc &d = L.p2[k];
+        for (int i = 0; i < d.ylen; ++i) L.rows[d.ybeg + i] = RowDesc{d.off + (int64_t)i * d.ld, d.goff, d.ld};
+    }
     L.p2_elems = off;
     L.glen = goff;
     auto column_in = [&](int64_t rho, int64_t b) {
@@ -492,12 +495,12 @@ int check_layout(const Layout &L, std::string *why) {
         if (q < 0 || q >= (int32_t)L.lr.size() || L.lr[q].cnt < 2 || L.lr[q].cnt >= kRedBigCnt || l >= L.lr[q].rank)
             return bad("red task");
     }
-    if ((int64_t)L.row_leaf.size() != L.n) return bad("row_leaf size");
-    for (int64_t p = 0; p < L.n; ++p) {
-        const int32_t l = L.row_leaf[p];
-        if (l < 0 || l >= L.nleaves || p < L.p2[l].ybeg || p >= (int64_t)L.p2[l].ybeg + L.p2[l].ylen)
-            return bad("row_leaf entry");
-    }
+    if ((int64_t)L.rows.size() != L.n) return bad("rows size");
+    for (const P2Desc &d : L.p2)
+        for (int i = 0; i < d.ylen; ++i) {
+            const RowDesc &r = L.rows[d.ybeg + i];
+            if (r.off != d.off + (int64_t)i * d.ld || r.goff != d.goff || r.ld != d.ld) return bad("row desc");
+        }
     if ((int64_t)L.perm.size() != L.n) return bad("perm size");
     for (int32_t q : L.perm) if (q < 0 || q >= L.n) return bad("perm entry");
     return HMAT_OK;

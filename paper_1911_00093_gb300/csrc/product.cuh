@@ -3,18 +3,20 @@
 // library's own forms; kernels_table1.cu: the paper's variants).
 //
 // Product (Section 2.1, eq. 5-10 and 21-25), in three launches:
-//   phase 1  one CTA per leaf column cluster kappa: t-partials = Q_kappa^T x_kappa,
-//            Q_kappa the rows of every W_m^T (eq. 9/22) whose column cluster
-//            contains kappa, row-major; each thread owns one 16-byte column vector
-//            and walks the |kappa| rows (coalesced 128-bit loads, x from shared
-//            memory, no cross-thread reduction);
-//   reduce   one warp per low-rank block: t = 2^e sum_kappa partials, in a fixed
-//            order (deterministic, no atomics on values);
-//   phase 2  one CTA per leaf row cluster rho: y_rho = P_rho g_rho with P_rho the
-//            rows of the dense blocks (eq. 21) and of the V_m (eq. 10/24) over rho,
-//            g_rho the matching pieces of x and t staged in shared memory; one warp
-//            per row; each row of y is written once by its owner (eq. 25 without
-//            atomics).
+//   phase 1  one CTA per leaf column cluster kappa (128 threads for BF16 panels,
+//            else 256): t-partials = Q_kappa^T x_kappa, Q_kappa the rows of every
+//            W_m^T (eq. 9/22) whose column cluster contains kappa, row-major; each
+//            thread owns one 16-byte column vector and walks the |kappa| rows
+//            (coalesced 128-bit loads, x from shared memory, no cross-thread
+//            reduction);
+//   reduce   t = 2^e sum_kappa partials of the blocks over several leaf clusters,
+//            in a fixed order: a lane per (block, rank), a CTA per block over 32 or
+//            more clusters (deterministic, no atomics on values);
+//   phase 2  y_rho = P_rho g_rho with P_rho the rows of the dense blocks (eq. 21)
+//            and of the V_m (eq. 10/24) over rho, g_rho the matching pieces of x
+//            and t; a warp per row, each row of y written once by its owner (eq. 25
+//            without atomics): row-persistent warps over a fixed grid for 2- and
+//            4-byte panels, one CTA per leaf row cluster for 8-byte ones.
 // Arithmetic per store:
 //   DF    panels are pairs (hi, lo); products and sums in double-float on the
 //         FP32 pipe (the FP64 pipe of GB300 is ~1/60 of FP32);
@@ -327,10 +329,12 @@ template <Store S> __device__ __forceinline__ typename Tr<S>::Part red_to_part(t
 // ------------------------------------------------------------------------
 // phase 1: per leaf column cluster kappa
 // ------------------------------------------------------------------------
-constexpr int kP1Threads = 256;
+// 128 threads for BF16 panels (8 columns per thread: most clusters need fewer
+// than 128 threads, and small CTAs let more clusters stream at once), else 256
+template <Store S> constexpr int p1_threads() { return S == Store::BF16 ? 128 : 256; }
 
 template <Store S>
-__global__ void __launch_bounds__(kP1Threads) k_phase1(const P1Desc *__restrict__ desc, const P1Run *__restrict__ runs,
+__global__ void __launch_bounds__(p1_threads<S>()) k_phase1(const P1Desc *__restrict__ desc, const P1Run *__restrict__ runs,
                                                         const XDst *__restrict__ xdst, const LrDesc *__restrict__ lr,
                                                         const int32_t *__restrict__ gdst, const void *__restrict__ q1,
                                                         const typename Tr<S>::Op *__restrict__ xs,
@@ -344,6 +348,9 @@ __global__ void __launch_bounds__(kP1Threads) k_phase1(const P1Desc *__restrict_
     __shared__ Op xk[kMaxLeaf];  // x_kappa, broadcast to every thread
     if (skip_product(S_, mode)) return;
     const P1Desc d = desc[blockIdx.x];
+    const int nvec = d.ld / VW;
+    const char *base = (const char *)q1 + (size_t)d.off * (16 / VW);
+    const size_t row_bytes = (size_t)d.ld * (16 / VW);
     for (int j = threadIdx.x; j < d.xlen; j += blockDim.x) {
         if constexpr (fp32_source(S)) xk[j] = (double)__double2float_rn(xs[d.xbeg + j]);  // Section 3.5
         else xk[j] = xs[d.xbeg + j];
@@ -351,9 +358,6 @@ __global__ void __launch_bounds__(kP1Threads) k_phase1(const P1Desc *__restrict_
     __syncthreads();
 
     // projections (eq. 9/22): thread = one 16-byte column vector, walk the rows
-    const int nvec = d.ld / VW;
-    const char *base = (const char *)q1 + (size_t)d.off * (16 / VW);
-    const size_t row_bytes = (size_t)d.ld * (16 / VW);
     for (int vc = threadIdx.x; vc < nvec; vc += blockDim.x) {
         Acc<S> acc[VW];
 #pragma unroll
@@ -694,43 +698,16 @@ __global__ void __launch_bounds__(kP2Threads, MR == 4 ? 3 : 2) k_phase2(const P2
     phase2_epilogue<S, MR>(d, acc, y, out_perm, accum, wv, dotmode, dpart);
 }
 
-// Row-persistent phase 2: a fixed grid (kP2wBlocksPerSM CTAs per SM) whose
+// Row-persistent phase 2: a fixed grid (p2w_blocks CTAs per SM) whose
 // warps each own the rows p = gw, gw + W, gw + 2W, ... (W warps in all), two rows
 // at a time with up to p2w_vec 16-byte vectors per lane and row in flight; no
 // barrier until the CTA's last row.  Each row's lane partials are added by the
 // fixed butterfly and lane 0 writes y (or adds to it, accum); with dotmode set
 // the warp adds its rows' w . y and y . y in row order, and the CTA leaves the
 // sum over its warps, in warp order, in dpart[block] and dpart[grid + block].
-constexpr int kP2wBlocksPerSM = kP2RowBlocksPerSM;
 // vectors per lane and row in flight: four for the 8-byte stores, whose rows
 // are twice as many vectors; fewer for the others to stay within 64 registers
 template <Store S> constexpr int p2w_vec() { return Tr<S>::VW == 2 ? 4 : 2; }
-
-template <Store S>
-struct RowCtx {
-    const char *row;                // this row's panel entries
-    const typename Tr<S>::Op *g;    // its leaf row cluster's operands
-    int nv;                         // 16-byte vectors (ld / VW), 0 for no row
-    int p;                          // row (cluster order)
-};
-
-template <Store S>
-__device__ __forceinline__ RowCtx<S> row_ctx(int p, int n, const int32_t *__restrict__ row_leaf,
-                                             const P2Desc *__restrict__ desc, const void *__restrict__ p2,
-                                             const typename Tr<S>::Op *__restrict__ g) {
-    RowCtx<S> r;
-    r.p = p;
-    if (p >= n) {
-        r.row = nullptr; r.g = nullptr; r.nv = 0;
-        return r;
-    }
-    constexpr size_t esz = 16 / Tr<S>::VW;
-    const P2Desc d = desc[__ldg(row_leaf + p)];
-    r.row = (const char *)p2 + ((size_t)d.off + (size_t)(p - d.ybeg) * d.ld) * esz;
-    r.g = g + d.goff;
-    r.nv = d.ld / Tr<S>::VW;
-    return r;
-}
 
 template <Store S>
 __device__ __forceinline__ double row_total(Acc<S> &acc) {
@@ -743,51 +720,59 @@ __device__ __forceinline__ double row_total(Acc<S> &acc) {
 }
 
 template <Store S>
-__global__ void __launch_bounds__(kP2Threads, kP2wBlocksPerSM) k_phase2w(
-    int n, const int32_t *__restrict__ row_leaf, const P2Desc *__restrict__ desc, const void *__restrict__ p2,
-    const typename Tr<S>::Op *__restrict__ g, double *__restrict__ y, const int32_t *__restrict__ out_perm, int accum,
-    const SolverScalars *S_, int mode, const double *__restrict__ w, int dotmode, double *dpart) {
+__global__ void __launch_bounds__(kP2Threads, p2w_blocks(S)) k_phase2w(
+    int n, const RowDesc *__restrict__ rows, const void *__restrict__ p2, const typename Tr<S>::Op *__restrict__ g,
+    double *__restrict__ y, const int32_t *__restrict__ out_perm, int accum, const SolverScalars *S_, int mode,
+    const double *__restrict__ w, int dotmode, double *dpart) {
     constexpr int VW = Tr<S>::VW;
+    constexpr size_t esz = 16 / VW;
     __shared__ double wsum[2][kP2Warps];
     if (skip_product(S_, mode)) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int W = gridDim.x * kP2Warps;
+    const RowDesc none{0, 0, 0};
     double dw = 0.0, dy = 0.0;
-    for (int p0 = blockIdx.x * kP2Warps + warp; p0 < n; p0 += 2 * W) {
-        const RowCtx<S> r0 = row_ctx<S>(p0, n, row_leaf, desc, p2, g);
-        const RowCtx<S> r1 = row_ctx<S>(p0 + W, n, row_leaf, desc, p2, g);
+    int p0 = blockIdx.x * kP2Warps + warp;
+    // descriptors of the current row pair; the next pair's are loaded one pair ahead
+    RowDesc c0 = p0 < n ? rows[p0] : none, c1 = p0 + W < n ? rows[p0 + W] : none;
+    for (; p0 < n; p0 += 2 * W) {
+        const RowDesc n0 = p0 + 2 * W < n ? rows[p0 + 2 * W] : none;
+        const RowDesc n1 = p0 + 3 * W < n ? rows[p0 + 3 * W] : none;
+        const char *row0 = (const char *)p2 + (size_t)c0.off * esz, *row1 = (const char *)p2 + (size_t)c1.off * esz;
+        const typename Tr<S>::Op *g0 = g + c0.goff, *g1 = g + c1.goff;
+        const int nv0 = c0.ld / VW, nv1 = c1.ld / VW;
         // w of the inner products, loaded ahead of the stream
         const double w0 = (dotmode != 0 && lane == 0) ? __ldg(w + p0) : 0.0;
-        const double w1 = (dotmode != 0 && lane == 0 && r1.nv) ? __ldg(w + p0 + W) : 0.0;
+        const double w1 = (dotmode != 0 && lane == 0 && nv1) ? __ldg(w + p0 + W) : 0.0;
         Acc<S> a0, a1;
         a0.init();
         a1.init();
-        const int nvmax = max(r0.nv, r1.nv);
+        const int nvmax = max(nv0, nv1);
         constexpr int NVEC = p2w_vec<S>();
         for (int c = 0; c < nvmax; c += 32 * NVEC) {
             int4 ra[NVEC], rb[NVEC];
 #pragma unroll
             for (int u = 0; u < NVEC; ++u) {
                 const int v = c + lane + 32 * u;
-                ra[u] = v < r0.nv ? ld_stream(r0.row + (size_t)v * 16) : make_int4(0, 0, 0, 0);
-                rb[u] = v < r1.nv ? ld_stream(r1.row + (size_t)v * 16) : make_int4(0, 0, 0, 0);
+                ra[u] = v < nv0 ? ld_stream(row0 + (size_t)v * 16) : make_int4(0, 0, 0, 0);
+                rb[u] = v < nv1 ? ld_stream(row1 + (size_t)v * 16) : make_int4(0, 0, 0, 0);
             }
 #pragma unroll
             for (int u = 0; u < NVEC; ++u) {
                 const int v = c + lane + 32 * u;
-                if (v < r0.nv) row_mac<S>(a0, ra[u], GV<S>::load(r0.g + v * VW));
-                if (v < r1.nv) row_mac<S>(a1, rb[u], GV<S>::load(r1.g + v * VW));
+                if (v < nv0) row_mac<S>(a0, ra[u], GV<S>::load(g0 + v * VW));
+                if (v < nv1) row_mac<S>(a1, rb[u], GV<S>::load(g1 + v * VW));
             }
         }
         const double o0 = row_total<S>(a0);
-        const double o1 = r1.nv ? row_total<S>(a1) : 0.0;  // warp-uniform condition
+        const double o1 = nv1 ? row_total<S>(a1) : 0.0;  // warp-uniform condition
         if (lane == 0) {
-            const RowCtx<S> *rs[2] = {&r0, &r1};
+            const int ps[2] = {p0, p0 + W};
             const double os[2] = {o0, o1}, ws[2] = {w0, w1};
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                if (rs[k]->nv == 0) continue;
-                const int p = rs[k]->p;
+                if (k == 1 && nv1 == 0) continue;
+                const int p = ps[k];
                 const int q = out_perm ? out_perm[p] : p;
                 double out = os[k];
                 if (accum) out = y[q] + out;  // a later segment adds to the earlier ones' rows
@@ -798,6 +783,8 @@ __global__ void __launch_bounds__(kP2Threads, kP2wBlocksPerSM) k_phase2w(
                 }
             }
         }
+        c0 = n0;
+        c1 = n1;
     }
     if (dotmode == 0) return;
     if (lane == 0) {
@@ -813,6 +800,213 @@ __global__ void __launch_bounds__(kP2Threads, kP2wBlocksPerSM) k_phase2w(
     }
 }
 
+// ------------------------------------------------------------------------
+// Staged expansion (2- and 4-byte panels): a persistent CTA per SM in which one
+// producer thread streams the row clusters' operands and panel rows into rings
+// of shared-memory slots with bulk copies (cp.async.bulk, completion counted on
+// mbarriers) while eight consumer warps compute rows out of shared memory, so
+// the HBM stream does not wait on the arithmetic or on per-item latencies.
+// Items (leaf row clusters) are dealt round robin; a warp owns rows of a chunk;
+// each row's lane partials are added by the fixed butterfly and lane 0 writes y
+// (deterministic, no atomics).  Every wait is bounded in time: a wait that gives
+// up sets g_stage_abort and the CTA abandons the product (never expected).
+// ------------------------------------------------------------------------
+constexpr int kTsSlots = 8;                    // panel chunk slots
+constexpr int kTsSlot = kStagedSlotBytes;      // bytes per chunk slot (>= one row, checked by phase2_shape)
+constexpr int kTsGSlots = 2;                   // operand slots
+constexpr int kTsConsumers = 8;                // consumer warps
+constexpr int kTsThreads = 32 * (kTsConsumers + 1);
+constexpr long long kTsWaitCycles = 4000000000ll;  // ~2 s at the SM clock
+
+__device__ unsigned int g_stage_abort;
+
+__device__ __forceinline__ uint32_t s_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mb_init(uint64_t *b, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(s_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(s_addr(b)) : "memory");
+}
+__device__ __forceinline__ void mb_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(s_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mb_test(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(s_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for the phase of `parity` to complete; false when this CTA has given up.
+__device__ __forceinline__ bool mb_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag) {
+    const long long t0 = clock64();
+    while (!mb_test(b, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kTsWaitCycles) {
+            *abort_flag = 1;
+            atomicExch(&g_stage_abort, 1u);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     s_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(s_addr(bar))
+                 : "memory");
+}
+
+template <Store S>
+__device__ __forceinline__ GV<S> gv_shared(const typename Tr<S>::Op *p) {
+    GV<S> r;
+    if constexpr (S == Store::BF16) {
+        r.a = reinterpret_cast<const float4 *>(p)[0];
+        r.b = reinterpret_cast<const float4 *>(p)[1];
+    } else {
+        r.v = reinterpret_cast<const float4 *>(p)[0];
+    }
+    return r;
+}
+
+template <Store S>
+__global__ void __launch_bounds__(kTsThreads, 1) k_phase2t(int nitems, const P2Desc *__restrict__ desc,
+                                                          const void *__restrict__ p2,
+                                                          const typename Tr<S>::Op *__restrict__ g,
+                                                          double *__restrict__ y, const int32_t *__restrict__ out_perm,
+                                                          int accum, const SolverScalars *S_, int mode,
+                                                          const double *__restrict__ w, int dotmode, double *dpart,
+                                                          int gslot_bytes) {
+    using Op = typename Tr<S>::Op;
+    constexpr int VW = Tr<S>::VW;
+    constexpr uint32_t esz = 16 / VW;
+    extern __shared__ __align__(128) unsigned char ts_smem[];
+    __shared__ uint64_t full[kTsSlots], empty[kTsSlots], gfull[kTsGSlots], gempty[kTsGSlots];
+    __shared__ int abort_flag;
+    __shared__ uint32_t issued, consumed;
+    __shared__ double wsum[2][kTsConsumers];
+    if (skip_product(S_, mode)) return;
+    unsigned char *data = ts_smem;
+    unsigned char *gbuf = ts_smem + (size_t)kTsSlots * kTsSlot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTsSlots; ++s) {
+            mb_init(&full[s], 1);
+            mb_init(&empty[s], kTsConsumers);
+        }
+        for (int s = 0; s < kTsGSlots; ++s) {
+            mb_init(&gfull[s], 1);
+            mb_init(&gempty[s], kTsConsumers);
+        }
+        abort_flag = 0;
+        issued = 0;
+        consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == kTsConsumers) {
+        // producer: one thread issues every copy of this CTA's items in order
+        if (lane == 0) {
+            uint32_t c = 0, gc = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
+                const P2Desc d = desc[it];
+                const uint32_t row_bytes = (uint32_t)d.ld * esz;
+                const int k = max(1, kTsSlot / (int)row_bytes);
+                const int gs = gc % kTsGSlots;
+                if (gc >= kTsGSlots && !(ok = mb_wait(&gempty[gs], ((gc / kTsGSlots) - 1) & 1, &abort_flag))) break;
+                mb_expect_tx(&gfull[gs], (uint32_t)d.ld * sizeof(Op));
+                bulk_copy(gbuf + (size_t)gs * gslot_bytes, g + d.goff, (uint32_t)d.ld * sizeof(Op), &gfull[gs]);
+                ++gc;
+                for (int r0 = 0; r0 < d.ylen; r0 += k) {
+                    const uint32_t bytes = (uint32_t)min(k, d.ylen - r0) * row_bytes;
+                    const int s = c % kTsSlots;
+                    if (c >= kTsSlots && !(ok = mb_wait(&empty[s], ((c / kTsSlots) - 1) & 1, &abort_flag))) break;
+                    mb_expect_tx(&full[s], bytes);
+                    bulk_copy(data + (size_t)s * kTsSlot,
+                              (const unsigned char *)p2 + ((size_t)d.off + (size_t)r0 * d.ld) * esz, bytes, &full[s]);
+                    ++c;
+                    issued = c;
+                }
+            }
+        }
+    } else {
+        // consumers: a warp per row of each chunk, operands from the item's slot
+        uint32_t c = 0, gc = 0;
+        double dw = 0.0, dy = 0.0;
+        bool ok = true;
+        for (int it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
+            const P2Desc d = desc[it];
+            const uint32_t row_bytes = (uint32_t)d.ld * esz;
+            const int k = max(1, kTsSlot / (int)row_bytes);
+            const int nv = d.ld / VW;
+            const int gs = gc % kTsGSlots;
+            if (!(ok = mb_wait(&gfull[gs], (gc / kTsGSlots) & 1, &abort_flag))) break;
+            const Op *gsm = reinterpret_cast<const Op *>(gbuf + (size_t)gs * gslot_bytes);
+            for (int r0 = 0; r0 < d.ylen; r0 += k) {
+                const int rows = min(k, d.ylen - r0);
+                const int s = c % kTsSlots;
+                if (!(ok = mb_wait(&full[s], (c / kTsSlots) & 1, &abort_flag))) break;
+                const unsigned char *chunk = data + (size_t)s * kTsSlot;
+                for (int i = warp; i < rows; i += kTsConsumers) {
+                    const int4 *rowp = reinterpret_cast<const int4 *>(chunk + (size_t)i * row_bytes);
+                    Acc<S> a;
+                    a.init();
+                    for (int v = lane; v < nv; v += 32) row_mac<S>(a, rowp[v], gv_shared<S>(gsm + v * VW));
+                    const double o = row_total<S>(a);
+                    if (lane == 0) {
+                        const int p = d.ybeg + r0 + i;
+                        const int q = out_perm ? out_perm[p] : p;
+                        double out = o;
+                        if (accum) out = y[q] + out;
+                        y[q] = out;
+                        if (dotmode != 0) {
+                            dw += __ldg(w + p) * out;
+                            dy += out * out;
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mb_arrive(&empty[s]);
+                ++c;
+                if (warp == 0 && lane == 0) consumed = c;
+            }
+            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) mb_arrive(&gempty[gs]);
+            ++gc;
+        }
+        if (lane == 0) {
+            wsum[0][warp] = dw;
+            wsum[1][warp] = dy;
+        }
+    }
+    __syncthreads();
+    if (abort_flag && threadIdx.x == 0) {
+        // a wait gave up: let the copies still in flight land before the CTA exits
+        for (uint32_t q = consumed; q < issued; ++q) {
+            const long long t0 = clock64();
+            while (!mb_test(&full[q % kTsSlots], (q / kTsSlots) & 1) && clock64() - t0 < kTsWaitCycles) {
+            }
+        }
+    }
+    if (dotmode != 0 && threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < kTsConsumers; ++k) { a += wsum[0][k]; b += wsum[1][k]; }
+        dpart[blockIdx.x] = a;
+        dpart[gridDim.x + blockIdx.x] = b;
+    }
+}
+
+// The staged expansion's shared memory beyond the 48 KB default (set once, at
+// upload, outside any stream capture).
+template <Store SS>
+cudaError_t staged_prepare() {
+    return cudaFuncSetAttribute(k_phase2t<SS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
+}
+
 int grid_for(int64_t n, int threads, int cap) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -823,9 +1017,10 @@ int grid_for(int64_t n, int threads, int cap) {
 // launches of one store's product kernels (the dispatchers pick the store)
 template <Store SS>
 void phase1_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st) {
-    k_phase1<SS><<<ix.nleaves, kP1Threads, 0, st>>>(ix.p1, ix.p1_runs, ix.xdst, ix.lr, ix.gdst, P.q1,
-                                                    (const typename Tr<SS>::Op *)P.xs, (typename Tr<SS>::Part *)P.part,
-                                                    (typename Tr<SS>::Op *)P.g, ix.tscale, skipS, mode);
+    k_phase1<SS><<<ix.nleaves, p1_threads<SS>(), 0, st>>>(ix.p1, ix.p1_runs, ix.xdst, ix.lr, ix.gdst, P.q1,
+                                                          (const typename Tr<SS>::Op *)P.xs,
+                                                          (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g,
+                                                          ix.tscale, skipS, mode);
 }
 
 template <Store SS>
@@ -841,10 +1036,19 @@ template <Store SS>
 void phase2_launch(const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm, int accum,
                    const SolverScalars *skipS, int mode, cudaStream_t st, const double *w, int dotmode,
                    double *dpart) {
+    if constexpr (SS == Store::BF16 || SS == Store::F32) {
+        if (phase2_shape(SS, ix) == 2) {
+            const int gslot = (int)((ix.max_ld2 * sizeof(typename Tr<SS>::Op) + 127) / 128 * 128);
+            const size_t smem = (size_t)kTsSlots * kTsSlot + (size_t)kTsGSlots * gslot;
+            k_phase2t<SS><<<ix.nsm, kTsThreads, smem, st>>>(ix.nleaves, ix.p2, P.p2, (const typename Tr<SS>::Op *)P.g, y,
+                                                            out_perm, accum, skipS, mode, w, dotmode, dpart, gslot);
+            return;
+        }
+    }
     if (phase2_rows(SS, ix)) {
-        k_phase2w<SS><<<ix.p2_grid, kP2Threads, 0, st>>>(ix.n, ix.row_leaf, ix.p2, P.p2,
-                                                         (const typename Tr<SS>::Op *)P.g, y, out_perm, accum, skipS,
-                                                         mode, w, dotmode, dpart);
+        k_phase2w<SS><<<ix.nsm * p2w_blocks(SS), kP2Threads, 0, st>>>(ix.n, ix.rows, P.p2,
+                                                                      (const typename Tr<SS>::Op *)P.g, y, out_perm,
+                                                                      accum, skipS, mode, w, dotmode, dpart);
         return;
     }
     if (ix.max_leaf <= 4 * kP2Warps)

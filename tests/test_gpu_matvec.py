@@ -138,3 +138,33 @@ def test_upload_rejects_bad_blob():
         P.hmat_upload(bad, "fp64")
     assert e.value.status == 2
 
+
+
+@pytest.mark.parametrize("shape", ["cluster", "staged"])
+def test_expansion_launch_shapes_agree(hcache, oracle_mod, monkeypatch, shape):
+    """The other launch shapes of the expansion (one CTA per leaf row cluster; the
+    staged bulk-copy pipeline) against the default row-persistent one: the same
+    rows and operands in the same fixed order per row, so the same bits."""
+    torch = need_gpu()
+    P = lib()
+    for mesh in (synth.icosphere(4), synth.two_spheres(3)):
+        blob = oracle_blob(hcache(mesh))
+        x = np.random.default_rng(31).standard_normal(mesh.n)
+        for form in ("bf16", "fp32"):
+            monkeypatch.delenv("HMAT_PHASE2", raising=False)
+            h0 = P.hmat_upload(blob, form)
+            monkeypatch.setenv("HMAT_PHASE2", shape)
+            h1 = P.hmat_upload(blob, form)
+            try:
+                y0 = _gpu_matvec(P, torch, h0, x)
+                y1 = _gpu_matvec(P, torch, h1, x)
+                assert np.array_equal(y0, y1), (form, shape, rel(y1, y0))
+                # and inside a solve (the expansion also leaves the inner-product shares)
+                b = synth.rhs_one_plus_half_z(mesh)
+                opts = {"inner_tol": 1e-2 if form == "bf16" else 1e-4}
+                i0 = P.hmat_bicgstab(h0, b, np.zeros(mesh.n), tol=1e-8, **opts)
+                i1 = P.hmat_bicgstab(h1, b, np.zeros(mesh.n), tol=1e-8, **opts)
+                assert i0["status"] == 0 and i1["status"] == 0 and i1["relres_true"] <= 1e-8
+            finally:
+                P.hmat_destroy(h0)
+                P.hmat_destroy(h1)
