@@ -53,7 +53,8 @@ enum {
     OR_M2_MIXED = 5,  /* V' D W' form, FP32 matrix x FP64 source, z FP64          */
     OR_M3 = 6,        /* per-rank FP64/FP32 split by d_i >= d_max 10^-c           */
     OR_DATA_FP32 = 7, /* panels rounded to FP32, all arithmetic FP64              */
-    OR_DATA_BF16 = 8  /* panels rounded to pow2-scaled BF16, arithmetic FP64      */
+    OR_DATA_BF16 = 8, /* panels rounded to pow2-scaled BF16, arithmetic FP64      */
+    OR_M3_TRUNC = 9   /* Section 4.5: ranks with d_i < d_max 10^-c deleted        */
 };
 
 /* ------------------------------------------------------------------------- */
@@ -713,12 +714,16 @@ static void hmatvec_perm(const or_hmat *h, int variant, int c3, const double *xp
                 for (int64_t l = 0; l < r; l++) if (d[l] > dmax) dmax = d[l];
                 for (int64_t l = 0; l < r; l++) {
                     if (variant == OR_M2_DOUBLE) is64[l] = 1;
-                    else if (variant == OR_M3) is64[l] = (d[l] >= dmax * pow(10.0, -(double)c3));
+                    else if (variant == OR_M3 || variant == OR_M3_TRUNC)
+                        is64[l] = (d[l] >= dmax * pow(10.0, -(double)c3));
                     else is64[l] = 0;
                 }
                 double *yhat64 = (double *)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
                 double *yhat32 = (double *)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
                 for (int64_t l = 0; l < r; l++) {
+                    /* Section 4.5: a rank much smaller than the largest is deleted
+                       with its column of V' and row of W' instead of demoted */
+                    if (variant == OR_M3_TRUNC && !is64[l]) continue;
                     double z = 0.0;                                             /* z_m FP64 (Table 1) */
                     for (int64_t j = 0; j < n; j++) {
                         double w = Wp[l * n + j];

@@ -123,6 +123,45 @@ def test_method3_limits(hcache, oracle_mod):
     assert e[7] <= e[1] <= e[-1] * 1.01   # more ranks in FP64 as c grows
 
 
+def test_rank_truncation(hcache, oracle_mod):
+    """Section 4.5's alternative to Method 3: ranks with d_i < d_max 10^-c are
+    deleted.  Pins: nothing deleted for a large c (= Method 2-Double); every rank
+    deleted for c = -1 (= the dense blocks alone, summed here from the raw block
+    data); in between, what is lost is exactly the deleted ranks' d_l v'_l (w'_l x),
+    and it shrinks as c grows."""
+    mesh = synth.icosphere(3)
+    H = hcache(mesh)
+    x = np.random.default_rng(45).standard_normal(mesh.n)
+    T = oracle_mod.M3_TRUNC
+    assert np.array_equal(H.matvec(x, T, c=30), H.matvec(x, oracle_mod.M2_DOUBLE))
+    perm = H.perm
+    xp = x[perm]
+    blk = H.blocks
+    y_dense = np.zeros(mesh.n)
+    lost = {c: np.zeros(mesh.n) for c in (1, 3)}
+    for b in range(len(blk)):
+        i_s, i_e, j_s, j_e, kind, r, _ = blk[b]
+        if kind == 0:
+            y_dense[i_s:i_e] += H.block_data(b) @ xp[j_s:j_e]
+        elif r > 0:
+            Vp, Wp, d = H.method2_factors(b)
+            for c in lost:
+                for l in np.nonzero(d < d.max() * 10.0 ** (-c))[0]:
+                    lost[c][i_s:i_e] += d[l] * Vp[:, l] * (Wp[l] @ xp[j_s:j_e])
+    yd = np.empty(mesh.n)
+    yd[perm] = y_dense
+    assert np.linalg.norm(H.matvec(x, T, c=-1) - yd) <= 1e-14 * np.linalg.norm(yd)
+    y2d = H.matvec(x, oracle_mod.M2_DOUBLE)
+    errs = []
+    for c in (1, 3):
+        lc = np.empty(mesh.n)
+        lc[perm] = lost[c]
+        yt = H.matvec(x, T, c=c)
+        assert np.linalg.norm((y2d - yt) - lc) <= 1e-13 * np.linalg.norm(y2d)
+        errs.append(np.linalg.norm(y2d - yt))
+    assert errs[1] < errs[0]
+
+
 def test_data_rounding_forms(hcache, oracle_mod):
     mesh = synth.icosphere(3)
     H = hcache(mesh)
