@@ -966,3 +966,138 @@ int or_bicgstab_dense(int64_t n, const double *A, const double *b, double *x, do
     or_dop op = {n, A};
     return or_bicgstab_generic(n, dop_apply, &op, dop_apply, &op, b, x, tol, 0.0, maxit, 0, NULL, 0, info);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Restarted GMRES(m) with the same products (Section 4.5: other solvers)      */
+/* ------------------------------------------------------------------------- */
+/* The textbook method (Saad & Schultz): Arnoldi with classical Gram-Schmidt
+ * applied twice (CGS2), Givens rotations on the Hessenberg matrix, the least-
+ * squares update x += V_j y at the end of each cycle of at most m steps.
+ * A run iterates with the iterated operator until the residual estimate
+ * |g_{j+1}| <= max(tol ||b||, inner_tol ||r_start||) (a new cycle starts from
+ * r = b - A~ x after every m steps); then, as for BiCG-STAB, the true residual
+ * with the FP64 operator accepts x or starts a new run from it.
+ * info: [iterations, true relres, status, restarts, products, FP64 products]. */
+int or_gmres_generic(int64_t n, int64_t m, or_op_fn op, const void *opctx, or_op_fn op64, const void *op64ctx,
+                     const double *b, double *x, double tol, double inner_tol, int64_t maxit, int64_t maxrestart,
+                     double *info)
+{
+    double *V = (double *)malloc(sizeof(double) * n * (m + 1));
+    double *H = (double *)calloc((size_t)((m + 1) * m), sizeof(double));  /* column j: H[j * (m + 1) + i] */
+    double *cs = (double *)malloc(sizeof(double) * m), *sn = (double *)malloc(sizeof(double) * m);
+    double *g = (double *)malloc(sizeof(double) * (m + 1)), *y = (double *)malloc(sizeof(double) * m);
+    double *h = (double *)malloc(sizeof(double) * (m + 1)), *h2 = (double *)malloc(sizeof(double) * (m + 1));
+    double *r = (double *)malloc(sizeof(double) * n), *w = (double *)malloc(sizeof(double) * n);
+    int64_t it = 0, restarts = 0, nmv = 0, nmv64 = 0;
+    int status = OR_MAXIT;
+    double relres = 0.0;
+    double bnorm = sqrt(dot(n, b, b));
+    if (bnorm == 0.0) {
+        for (int64_t i = 0; i < n; i++) x[i] = 0.0;
+        status = OR_OK;
+        goto done;
+    }
+    for (;;) {
+        /* a run */
+        op(opctx, x, w); nmv++;
+        for (int64_t i = 0; i < n; i++) r[i] = b[i] - w[i];
+        double rstart = sqrt(dot(n, r, r));
+        double stop = tol * bnorm;
+        if (inner_tol * rstart > stop) stop = inner_tol * rstart;
+        int run_err = 0;
+        for (;;) {
+            /* a cycle from r */
+            double beta = sqrt(dot(n, r, r));
+            if (!isfinite(beta)) { run_err = OR_NONFINITE; break; }
+            if (beta <= stop) break;
+            if (it >= maxit) { run_err = OR_MAXIT; break; }
+            for (int64_t i = 0; i < n; i++) V[i] = r[i] / beta;
+            for (int64_t i = 0; i <= m; i++) g[i] = 0.0;
+            g[0] = beta;
+            int64_t j = 0;
+            for (; j < m && it < maxit; j++) {
+                it++;
+                op(opctx, V + j * n, w); nmv++;                 /* w = A v_j */
+                /* CGS2: h = V^T w, w -= V h, twice */
+                for (int64_t i = 0; i <= j; i++) h[i] = 0.0;
+                for (int pass = 0; pass < 2; pass++) {
+                    for (int64_t i = 0; i <= j; i++) h2[i] = dot(n, V + i * n, w);
+                    for (int64_t k = 0; k < n; k++) {
+                        double s = w[k];
+                        for (int64_t i = 0; i <= j; i++) s -= h2[i] * V[i * n + k];
+                        w[k] = s;
+                    }
+                    for (int64_t i = 0; i <= j; i++) h[i] += h2[i];
+                }
+                double hn = sqrt(dot(n, w, w));
+                double *col = H + j * (m + 1);
+                for (int64_t i = 0; i <= j; i++) col[i] = h[i];
+                col[j + 1] = hn;
+                /* previous rotations, then the one that zeroes col[j + 1] */
+                for (int64_t i = 0; i < j; i++) {
+                    double a = col[i], c = col[i + 1];
+                    col[i] = cs[i] * a + sn[i] * c;
+                    col[i + 1] = -sn[i] * a + cs[i] * c;
+                }
+                double den = sqrt(col[j] * col[j] + col[j + 1] * col[j + 1]);
+                cs[j] = den == 0.0 ? 1.0 : col[j] / den;
+                sn[j] = den == 0.0 ? 0.0 : col[j + 1] / den;
+                col[j] = den;
+                col[j + 1] = 0.0;
+                g[j + 1] = -sn[j] * g[j];
+                g[j] = cs[j] * g[j];
+                double resid = fabs(g[j + 1]);
+                if (!isfinite(resid)) { run_err = OR_NONFINITE; j++; break; }
+                if (hn == 0.0 || resid <= stop) { j++; break; }        /* invariant subspace / converged */
+                for (int64_t k = 0; k < n; k++) V[(j + 1) * n + k] = w[k] / hn;
+            }
+            /* y = R^-1 g over the j columns built, x += V y */
+            for (int64_t i = j - 1; i >= 0; i--) {
+                double s = g[i];
+                for (int64_t k = i + 1; k < j; k++) s -= H[k * (m + 1) + i] * y[k];
+                y[i] = H[i * (m + 1) + i] == 0.0 ? 0.0 : s / H[i * (m + 1) + i];
+            }
+            for (int64_t k = 0; k < n; k++) {
+                double s = x[k];
+                for (int64_t i = 0; i < j; i++) s += V[i * n + k] * y[i];
+                x[k] = s;
+            }
+            if (run_err) break;
+            op(opctx, x, w); nmv++;                             /* the next cycle's residual */
+            for (int64_t i = 0; i < n; i++) r[i] = b[i] - w[i];
+        }
+        op64(op64ctx, x, w); nmv64++;
+        for (int64_t k = 0; k < n; k++) r[k] = b[k] - w[k];
+        relres = sqrt(dot(n, r, r)) / bnorm;
+        if (relres <= tol) { status = OR_OK; break; }
+        if (run_err) { status = run_err; break; }
+        if (restarts >= maxrestart) { status = OR_MAXIT; break; }
+        restarts++;
+    }
+done:
+    info[0] = (double)it; info[1] = relres; info[2] = (double)status;
+    info[3] = (double)restarts; info[4] = (double)nmv; info[5] = (double)nmv64;
+    free(V); free(H); free(cs); free(sn); free(g); free(y); free(h); free(h2); free(r); free(w);
+    return status;
+}
+
+int or_gmres(const or_hmat *h, int variant, int c3, int64_t m, const double *b, double *x, double tol,
+             double inner_tol, int64_t maxit, int64_t maxrestart, double *info)
+{
+    int64_t N = h->n;
+    double *bp = (double *)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    double *xp = (double *)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    for (int64_t q = 0; q < N; q++) { bp[q] = b[h->perm[q]]; xp[q] = x[h->perm[q]]; }
+    or_hop op = {h, variant, c3}, op64 = {h, OR_M1_DOUBLE, 0};
+    int st = or_gmres_generic(N, m, hop_apply, &op, hop_apply, &op64, bp, xp, tol, inner_tol, maxit, maxrestart, info);
+    for (int64_t q = 0; q < N; q++) x[h->perm[q]] = xp[q];
+    free(bp); free(xp);
+    return st;
+}
+
+int or_gmres_dense(int64_t n, int64_t m, const double *A, const double *b, double *x, double tol, int64_t maxit,
+                   double *info)
+{
+    or_dop op = {n, A};
+    return or_gmres_generic(n, m, dop_apply, &op, dop_apply, &op, b, x, tol, 0.0, maxit, 0, info);
+}

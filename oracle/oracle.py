@@ -56,6 +56,8 @@ def lib():
             "or_hmat_to_dense": (None, [P, P]),
             "or_bicgstab": (I, [P, I, I, P, P, D, D, I64, I64, P, I64, P]),
             "or_bicgstab_dense": (I, [I64, P, P, P, D, I64, P]),
+            "or_gmres": (I, [P, I, I, I64, P, P, D, D, I64, I64, P]),
+            "or_gmres_dense": (I, [I64, I64, P, P, P, D, I64, P]),
             "or_round_bf16_pow2": (None, [P, I64, P]),
         }
         for name, (res, args) in sig.items():
@@ -134,6 +136,16 @@ def dense_bicgstab(A, b, tol=1e-10, maxit=1000):
     info = np.zeros(6)
     st = lib().or_bicgstab_dense(A.shape[0], _p(A), _p(b), _p(x), float(tol), int(maxit), _p(info))
     return x, {"iters": int(info[0]), "relres": info[1], "status": STATUS[st]}
+
+
+def dense_gmres(A, b, m=30, tol=1e-10, maxit=1000):
+    """Restarted GMRES(m) (CGS2 Arnoldi, Givens rotations) on a dense matrix."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    b = _f64(b)
+    x = np.zeros(A.shape[0])
+    info = np.zeros(6)
+    st = lib().or_gmres_dense(A.shape[0], int(m), _p(A), _p(b), _p(x), float(tol), int(maxit), _p(info))
+    return x, {"iters": int(info[0]), "relres": float(info[1]), "status": STATUS[st]}
 
 
 class HMatrix:
@@ -236,6 +248,15 @@ class HMatrix:
         if history:
             out["history"] = hist[:out["iters"]]
         return x, out
+
+    def gmres(self, b, m=30, variant=M1_DOUBLE, c=0, tol=1e-8, inner_tol=0.0, maxit=1000, maxrestart=30, x0=None):
+        b = _f64(b)
+        x = np.zeros(self.n) if x0 is None else _f64(x0).copy()
+        info = np.zeros(6)
+        st = lib().or_gmres(self._h, int(variant), int(c), int(m), _p(b), _p(x), float(tol), float(inner_tol),
+                            int(maxit), int(maxrestart), _p(info))
+        return x, {"iters": int(info[0]), "relres": float(info[1]), "status": STATUS[st],
+                   "restarts": int(info[3]), "matvecs": int(info[4]), "matvecs_fp64": int(info[5])}
 
     # --- sizes ---
     def stats(self):
