@@ -973,10 +973,12 @@ int or_bicgstab_dense(int64_t n, const double *A, const double *b, double *x, do
 /* The textbook method (Saad & Schultz): Arnoldi with classical Gram-Schmidt
  * applied twice (CGS2), Givens rotations on the Hessenberg matrix, the least-
  * squares update x += V_j y at the end of each cycle of at most m steps.
- * A run iterates with the iterated operator until the residual estimate
- * |g_{j+1}| <= max(tol ||b||, inner_tol ||r_start||) (a new cycle starts from
- * r = b - A~ x after every m steps); then, as for BiCG-STAB, the true residual
- * with the FP64 operator accepts x or starts a new run from it.
+ * READING (Section 4.1.3 with the iterated operator of lower precision): every
+ * run starts from the true residual r_0 = b - A64 x_0 and solves the correction
+ * equation A~ d = r_0 with GMRES: a cycle that ends before the run's stop
+ * (|g_{j+1}| <= max(tol ||b||, inner_tol ||r_0||)) is followed by one starting
+ * from r_0 - A~ (x - x_0); when the run stops, the true residual accepts x or
+ * starts the next run from it (iterative refinement when A~ is not A64).
  * info: [iterations, true relres, status, restarts, products, FP64 products]. */
 int or_gmres_generic(int64_t n, int64_t m, or_op_fn op, const void *opctx, or_op_fn op64, const void *op64ctx,
                      const double *b, double *x, double tol, double inner_tol, int64_t maxit, int64_t maxrestart,
@@ -988,6 +990,7 @@ int or_gmres_generic(int64_t n, int64_t m, or_op_fn op, const void *opctx, or_op
     double *g = (double *)malloc(sizeof(double) * (m + 1)), *y = (double *)malloc(sizeof(double) * m);
     double *h = (double *)malloc(sizeof(double) * (m + 1)), *h2 = (double *)malloc(sizeof(double) * (m + 1));
     double *r = (double *)malloc(sizeof(double) * n), *w = (double *)malloc(sizeof(double) * n);
+    double *r0 = (double *)malloc(sizeof(double) * n), *x0 = (double *)malloc(sizeof(double) * n);
     int64_t it = 0, restarts = 0, nmv = 0, nmv64 = 0;
     int status = OR_MAXIT;
     double relres = 0.0;
@@ -997,13 +1000,17 @@ int or_gmres_generic(int64_t n, int64_t m, or_op_fn op, const void *opctx, or_op
         status = OR_OK;
         goto done;
     }
+    op64(op64ctx, x, w); nmv64++;                           /* the first run's r_0 */
+    for (int64_t i = 0; i < n; i++) r0[i] = b[i] - w[i];
     for (;;) {
-        /* a run */
-        op(opctx, x, w); nmv++;
-        for (int64_t i = 0; i < n; i++) r[i] = b[i] - w[i];
-        double rstart = sqrt(dot(n, r, r));
+        relres = sqrt(dot(n, r0, r0)) / bnorm;
+        if (relres <= tol) { status = OR_OK; break; }
+        if (!isfinite(relres)) { status = OR_NONFINITE; break; }
+        /* a run on A~ d = r_0 */
+        memcpy(x0, x, sizeof(double) * n);
+        memcpy(r, r0, sizeof(double) * n);
         double stop = tol * bnorm;
-        if (inner_tol * rstart > stop) stop = inner_tol * rstart;
+        if (inner_tol * relres * bnorm > stop) stop = inner_tol * relres * bnorm;
         int run_err = 0;
         for (;;) {
             /* a cycle from r */
@@ -1017,7 +1024,7 @@ int or_gmres_generic(int64_t n, int64_t m, or_op_fn op, const void *opctx, or_op
             int64_t j = 0;
             for (; j < m && it < maxit; j++) {
                 it++;
-                op(opctx, V + j * n, w); nmv++;                 /* w = A v_j */
+                op(opctx, V + j * n, w); nmv++;                 /* w = A~ v_j */
                 /* CGS2: h = V^T w, w -= V h, twice */
                 for (int64_t i = 0; i <= j; i++) h[i] = 0.0;
                 for (int pass = 0; pass < 2; pass++) {
@@ -1063,12 +1070,14 @@ int or_gmres_generic(int64_t n, int64_t m, or_op_fn op, const void *opctx, or_op
                 x[k] = s;
             }
             if (run_err) break;
-            op(opctx, x, w); nmv++;                             /* the next cycle's residual */
-            for (int64_t i = 0; i < n; i++) r[i] = b[i] - w[i];
+            /* the next cycle's residual of the correction equation */
+            for (int64_t k = 0; k < n; k++) r[k] = x[k] - x0[k];
+            op(opctx, r, w); nmv++;
+            for (int64_t k = 0; k < n; k++) r[k] = r0[k] - w[k];
         }
-        op64(op64ctx, x, w); nmv64++;
-        for (int64_t k = 0; k < n; k++) r[k] = b[k] - w[k];
-        relres = sqrt(dot(n, r, r)) / bnorm;
+        op64(op64ctx, x, w); nmv64++;                       /* true residual: the next run's r_0 */
+        for (int64_t k = 0; k < n; k++) r0[k] = b[k] - w[k];
+        relres = sqrt(dot(n, r0, r0)) / bnorm;
         if (relres <= tol) { status = OR_OK; break; }
         if (run_err) { status = run_err; break; }
         if (restarts >= maxrestart) { status = OR_MAXIT; break; }
@@ -1077,7 +1086,7 @@ int or_gmres_generic(int64_t n, int64_t m, or_op_fn op, const void *opctx, or_op
 done:
     info[0] = (double)it; info[1] = relres; info[2] = (double)status;
     info[3] = (double)restarts; info[4] = (double)nmv; info[5] = (double)nmv64;
-    free(V); free(H); free(cs); free(sn); free(g); free(y); free(h); free(h2); free(r); free(w);
+    free(V); free(H); free(cs); free(sn); free(g); free(y); free(h); free(h2); free(r); free(w); free(r0); free(x0);
     return status;
 }
 
