@@ -34,9 +34,10 @@ FORMS = {"fp64": ("fp64", None, {}), "fp64_dfma": ("fp64_dfma", None, {}),
          "m1_single": ("m1_single", None, {"inner_tol": 1e-4}), "m1_mixed": ("m1_mixed", None, {"inner_tol": 1e-4}),
          "m2_double": ("m2_double", None, {}), "m2_single": ("m2_single", None, {"inner_tol": 1e-4}),
          "m2_mixed": ("m2_mixed", None, {"inner_tol": 1e-4}), "m3_c-1": ("m3", -1, {"inner_tol": 1e-4}),
-         "m3_c2": ("m3", 2, {"inner_tol": 1e-4})}
+         "m3_c2": ("m3", 2, {"inner_tol": 1e-4}), "m3_c3": ("m3", 3, {"inner_tol": 1e-4}),
+         "m3trunc_c3": ("m3_trunc", 3, {"inner_tol": 1e-4})}
 FORM_OPTS = {k: v[2] for k, v in FORMS.items()}
-DEFAULT_FORMS = "fp64,fp64_dfma,fp32,bf16,m1_single,m1_mixed,m2_double,m2_single,m2_mixed,m3_c-1,m3_c2"
+DEFAULT_FORMS = "fp64,fp64_dfma,fp32,bf16,m1_single,m1_mixed,m2_double,m2_single,m2_mixed,m3_c-1,m3_c3,m3trunc_c3"
 CHECK_EVERY = 4  # iterations per graph replay between host reads of the stop flag
 PART_BYTES = {"fp64": 8, "fp64_dfma": 8, "fp32": 4, "bf16": 4}  # partial sums (8 for the paper's variants)
 

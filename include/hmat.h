@@ -89,6 +89,10 @@ typedef enum hmat_status {
  *                  d_i >= d_max 10^-c, else in FP32 (eq. 17-20); the FP64 ranks
  *                  follow Method 2-Double, the FP32 ranks Method 2-Mixed, the two
  *                  parts are added (Section 3.4).  Upload with hmat_upload_ex.
+ *  HMAT_M3_TRUNC   Section 4.5's alternative: the ranks Method 3 would store in
+ *                  FP32 (d_i < d_max 10^-c) are deleted with their column of V'_m
+ *                  and row of W'_m; the rest as Method 2-Double.  Upload with
+ *                  hmat_upload_ex.
  * These variants carry FP64 arithmetic per entry and are bound by the FP64 pipe
  * of GB300, not by HBM.
  */
@@ -102,7 +106,8 @@ typedef enum hmat_precision {
     HMAT_M2_DOUBLE = 6,
     HMAT_M2_SINGLE = 7,
     HMAT_M2_MIXED = 8,
-    HMAT_M3 = 9
+    HMAT_M3 = 9,
+    HMAT_M3_TRUNC = 10
 } hmat_precision;
 
 typedef struct hmat_t *hmat_handle;
@@ -240,6 +245,18 @@ int hmat_bicgstab(hmat_handle h, const double *b, double *x, double tol, int32_t
 /* hmat_bicgstab with every option explicit (opts NULL = defaults). */
 int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const hmat_solve_opts *opts, void *stream,
                      hmat_solve_info *info);
+
+/*
+ * hmat_gmres -- solve A~ x = b with restarted GMRES(m) (1 <= m <= 64) on the same
+ * products (Section 4.5 names other solvers as the next use of the mixed
+ * products): Arnoldi with classical Gram-Schmidt applied twice, Givens
+ * rotations, x += V y after each cycle of at most m steps; a cycle is one graph
+ * launch.  Runs, the FP64 true residual and restarts as hmat_bicgstab_ex
+ * (`check_every` and `use_graph` of opts are not used); `iters` counts Arnoldi
+ * steps.  Allocates its Krylov basis (N x (m + 1) doubles) on first use.
+ */
+int hmat_gmres(hmat_handle h, const double *b, double *x, int32_t m, const hmat_solve_opts *opts, void *stream,
+               hmat_solve_info *info);
 
 /* ------------------------------------------------------------------------- */
 /* Many systems at once                                                       */

@@ -19,16 +19,18 @@ STATUS = {0: "ok", 1: "arg", 2: "bad_layout", 3: "nomem", 4: "cuda", 5: "breakdo
           6: "breakdown_omega", 7: "maxit", 8: "nonfinite", 9: "range", 10: "unsupported"}
 HMAT_FP64, HMAT_FP64_DFMA, HMAT_FP32, HMAT_BF16 = 0, 1, 2, 3
 HMAT_M1_SINGLE, HMAT_M1_MIXED, HMAT_M2_DOUBLE, HMAT_M2_SINGLE, HMAT_M2_MIXED, HMAT_M3 = 4, 5, 6, 7, 8, 9
+HMAT_M3_TRUNC = 10
 PRECISIONS = {"fp64": HMAT_FP64, "fp64_dfma": HMAT_FP64_DFMA, "fp32": HMAT_FP32, "bf16": HMAT_BF16,
               # the paper's variants (Section 3, Table 1); Method 1-Double is "fp64_dfma"
               "m1_single": HMAT_M1_SINGLE, "m1_mixed": HMAT_M1_MIXED, "m2_double": HMAT_M2_DOUBLE,
-              "m2_single": HMAT_M2_SINGLE, "m2_mixed": HMAT_M2_MIXED, "m3": HMAT_M3}
+              "m2_single": HMAT_M2_SINGLE, "m2_mixed": HMAT_M2_MIXED, "m3": HMAT_M3, "m3_trunc": HMAT_M3_TRUNC}
 
 # every symbol declared in include/hmat.h
 EXPORTS = ("hmat_build", "hmat_blob_free", "hmat_blob_stats_get", "hmat_upload", "hmat_destroy",
            "hmat_matvec", "hmat_matvec_fp64", "hmat_solve_opts_default", "hmat_bicgstab",
            "hmat_bicgstab_ex", "hmat_info", "hmat_time_matvec", "hmat_strerror", "hmat_last_cuda_error",
-           "hmat_matvec_noalloc", "hmat_upload_ex", "hmat_upload_batch", "hmat_problems", "hmat_bicgstab_multi")
+           "hmat_matvec_noalloc", "hmat_upload_ex", "hmat_upload_batch", "hmat_problems", "hmat_bicgstab_multi",
+           "hmat_gmres")
 
 
 class BlobStats(C.Structure):
@@ -100,6 +102,7 @@ def load():
         "hmat_upload_batch": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(SZ), I32, I32, I32, C.POINTER(C.c_void_p)]),
         "hmat_problems": (C.c_int, [P, C.POINTER(I32), P]),
         "hmat_bicgstab_multi": (C.c_int, [P, P, P, I32, C.POINTER(SolveOpts), P, P]),
+        "hmat_gmres": (C.c_int, [P, P, P, I32, C.POINTER(SolveOpts), P, C.POINTER(SolveInfo)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -278,6 +281,23 @@ def hmat_bicgstab(h, b, x, tol=1e-8, maxit=1000, stream=None, **opts) -> dict:
     st = L.hmat_bicgstab_ex(C.c_void_p(h), pb, px, C.byref(o), _stream_ptr(stream), C.byref(info))
     if st in (1, 3, 4):
         raise HmatError(st, "hmat_bicgstab")
+    if kx is not x and not hasattr(x, "data_ptr"):
+        np.copyto(x, kx)
+    out = {k: getattr(info, k) for k, _ in SolveInfo._fields_}
+    out["status_name"] = STATUS.get(out["status"], out["status"])
+    return out
+
+
+def hmat_gmres(h, b, x, m=30, tol=1e-8, maxit=1000, stream=None, **opts) -> dict:
+    """Restarted GMRES(m) with the handle's products; x in place; returns the info dict."""
+    L = load()
+    pb, kb = _ptr(b)
+    px, kx = _ptr(x)
+    info = SolveInfo()
+    o = hmat_solve_opts(tol=float(tol), maxit=int(maxit), **opts)
+    st = L.hmat_gmres(C.c_void_p(h), pb, px, int(m), C.byref(o), _stream_ptr(stream), C.byref(info))
+    if st in (1, 3, 4):
+        raise HmatError(st, "hmat_gmres")
     if kx is not x and not hasattr(x, "data_ptr"):
         np.copyto(x, kx)
     out = {k: getattr(info, k) for k, _ in SolveInfo._fields_}

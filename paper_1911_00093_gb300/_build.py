@@ -14,7 +14,7 @@ OUT = os.path.join(HERE, "libhmat.so")
 BUILD = os.path.join(HERE, "_build")
 
 CXX_SOURCES = ["builder.cpp", "layout.cpp", "paper_forms.cpp"]
-CU_SOURCES = ["kernels.cu", "kernels_table1.cu", "multi.cu", "mrhs.cu", "api.cu", "noalloc.cu"]
+CU_SOURCES = ["kernels.cu", "kernels_table1.cu", "multi.cu", "mrhs.cu", "gmres.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -39,7 +40,7 @@ Store store_of(int precision) {
     }
 }
 
-bool is_table1_precision(int precision) { return precision >= HMAT_M1_SINGLE && precision <= HMAT_M3; }
+bool is_table1_precision(int precision) { return precision >= HMAT_M1_SINGLE && precision <= HMAT_M3_TRUNC; }
 
 }  // namespace
 
@@ -90,6 +91,7 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
     P2Desc *p2 = nullptr;
     double *tscale = nullptr;
     RowDesc *rows = nullptr;
+    GroupDesc *groups = nullptr;
     int st;
     if ((st = h->upload(&p1, L.p1.data(), sizeof(P1Desc) * L.p1.size())) ||
         (st = h->upload(&p1_runs, L.p1_runs.data(), sizeof(P1Run) * L.p1_runs.size())) ||
@@ -100,19 +102,27 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
         (st = h->upload(&red_tasks, L.red_tasks.data(), 4 * L.red_tasks.size())) ||
         (st = h->upload(&p2, L.p2.data(), sizeof(P2Desc) * L.p2.size())) ||
         (st = h->upload(&tscale, L.tscale.data(), 8 * L.tscale.size())) ||
-        (st = h->upload(&rows, L.rows.data(), sizeof(RowDesc) * L.rows.size()))) {
+        (st = h->upload(&rows, L.rows.data(), sizeof(RowDesc) * L.rows.size())) ||
+        (st = h->upload(&groups, L.groups.data(), sizeof(GroupDesc) * L.groups.size()))) {
         return st;
     }
     ix.p1 = p1; ix.p1_runs = p1_runs; ix.xdst = xdst; ix.lr = lr; ix.gdst = gdst; ix.p2 = p2;
     ix.red_big = red_big; ix.red_tasks = red_tasks;
     ix.tscale = L.tscale.empty() ? nullptr : tscale;
     ix.rows = rows;
-    // phase-2 launch shape (phase2_shape): row-persistent for 2-/4-byte panels;
-    // HMAT_PHASE2=cluster or =staged selects the others (all are exact)
+    ix.groups = groups;
+    ix.ngroups = (int32_t)L.groups.size();
+    // phase-2 launch shape (phase2_shape): row groups for 2-/4-byte panels;
+    // HMAT_PHASE2=cluster, =rows, =staged select the others (all are exact)
     const char *p2env = std::getenv("HMAT_PHASE2");
-    ix.p2_shape = 1;
+    ix.p2_shape = 3;
     if (p2env && std::strcmp(p2env, "cluster") == 0) ix.p2_shape = 0;
+    if (p2env && std::strcmp(p2env, "rows") == 0) ix.p2_shape = 1;
+    if (p2env && std::strcmp(p2env, "groups8") == 0) ix.p2_groups8 = 1;
     if (p2env && std::strcmp(p2env, "staged") == 0) ix.p2_shape = 2;
+    if (p2env && std::strcmp(p2env, "groups") == 0) ix.p2_shape = 3;
+    const char *p1env = std::getenv("HMAT_P1_THREADS");
+    ix.p1_threads = p1env ? std::atoi(p1env) : 0;
     int nsm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     ix.nsm = std::max(1, nsm);
@@ -121,7 +131,8 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
     h->index_bytes += (int64_t)(sizeof(P1Desc) * L.p1.size() + sizeof(P1Run) * L.p1_runs.size() +
                                 sizeof(XDst) * L.xdst.size() + sizeof(LrDesc) * L.lr.size() + 4 * L.gdst.size() +
                                 sizeof(P2Desc) * L.p2.size() + 4 * (L.red_big.size() + L.red_tasks.size()) +
-                                8 * L.tscale.size() + sizeof(RowDesc) * L.rows.size());
+                                8 * L.tscale.size() + sizeof(RowDesc) * L.rows.size() +
+                                sizeof(GroupDesc) * L.groups.size());
     return HMAT_OK;
 }
 
@@ -236,7 +247,7 @@ int upload_view(const BlobView &v, int32_t precision, int32_t method3_c, const s
         CK(cudaGetDevice(&h->device));
         CK(prepare_launches());
         h->precision = precision;
-        h->method3_c = precision == HMAT_M3 ? method3_c : 0;
+        h->method3_c = (precision == HMAT_M3 || precision == HMAT_M3_TRUNC) ? method3_c : 0;
         h->n = L.n;
         int32_t *perm = nullptr;
         if ((st = h->upload(&perm, L.perm.data(), 4 * L.perm.size()))) return st;
@@ -296,7 +307,7 @@ int upload_view(const BlobView &v, int32_t precision, int32_t method3_c, const s
         for (double **pp : vecs)
             if ((st = h->alloc(pp, nb))) return st;
         if ((st = h->alloc(&h->partials, sizeof(double) * 2 * (size_t)vec_blocks(L.n))) ||
-            (st = h->alloc(&h->dpart, sizeof(double) * 2 * (size_t)std::max(L.nleaves, 4 * h->seg[0].ix.nsm))) ||
+            (st = h->alloc(&h->dpart, sizeof(double) * 2 * (size_t)std::max(L.nleaves, 8 * h->seg[0].ix.nsm))) ||
             (st = h->alloc(&h->S, sizeof(SolverScalars)))) {
             return st;
         }
@@ -315,7 +326,7 @@ int upload_view(const BlobView &v, int32_t precision, int32_t method3_c, const s
 
 int upload_impl(const void *blob, size_t blob_bytes, int32_t precision, int32_t method3_c, hmat_handle *out) {
     if (!blob || !out) return HMAT_ERR_ARG;
-    if (precision < HMAT_FP64 || precision > HMAT_M3) return HMAT_ERR_ARG;
+    if (precision < HMAT_FP64 || precision > HMAT_M3_TRUNC) return HMAT_ERR_ARG;
     *out = nullptr;
     BlobView v;
     int st = parse_blob(blob, blob_bytes, v);
@@ -332,7 +343,7 @@ extern "C" int hmat_upload(const void *blob, size_t blob_bytes, int32_t precisio
 extern "C" int hmat_upload_batch(const void *const *blobs, const size_t *blob_bytes, int32_t count, int32_t precision,
                                  int32_t method3_c, hmat_handle *out) {
     if (!blobs || !blob_bytes || !out || count < 1) return HMAT_ERR_ARG;
-    if (precision < HMAT_FP64 || precision > HMAT_M3) return HMAT_ERR_ARG;
+    if (precision < HMAT_FP64 || precision > HMAT_M3_TRUNC) return HMAT_ERR_ARG;
     *out = nullptr;
     try {
         std::vector<BlobView> views(count);
@@ -824,6 +835,172 @@ extern "C" int hmat_bicgstab_multi(hmat_handle h, const double *b, double *x, in
         }
     }
     return worst;
+}
+
+namespace {
+
+int gmres_ensure(hmat_t *h, int m) {
+    auto &g = h->gm;
+    if (g.m == m) return HMAT_OK;
+    for (void *q : g.mine) h->release(q);
+    g.mine.clear();
+    if (g.graph) {
+        cudaGraphExecDestroy(g.graph);
+        g.graph = nullptr;
+    }
+    if (g.G_host) {
+        cudaFreeHost(g.G_host);
+        g.G_host = nullptr;
+    }
+    g.m = 0;
+    const size_t n = (size_t)h->n;
+    const int nb = vec_blocks(h->n);
+    int st;
+    double **vecs[] = {&g.w, &g.r, &g.b, &g.x, &g.x0, &g.r0, &g.d};
+    if ((st = h->alloc(&g.V, 8 * n * (m + 1)))) return st;
+    g.mine.push_back(g.V);
+    for (double **pp : vecs) {
+        if ((st = h->alloc(pp, 8 * n))) return st;
+        g.mine.push_back(*pp);
+    }
+    if ((st = h->alloc(&g.part, sizeof(double) * (size_t)nb * (m + 1))) ||
+        (st = h->alloc(&g.partials, sizeof(double) * (size_t)nb)) || (st = h->alloc(&g.G, sizeof(GmresState))))
+        return st;
+    g.mine.push_back(g.part);
+    g.mine.push_back(g.partials);
+    g.mine.push_back(g.G);
+    CK(cudaHostAlloc((void **)&g.G_host, sizeof(GmresState), cudaHostAllocDefault));
+    g.m = m;
+    return HMAT_OK;
+}
+
+int gmres_read(hmat_t *h, cudaStream_t st) {
+    CK(cudaMemcpyAsync(h->gm.G_host, h->gm.G, offsetof(GmresState, H), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return HMAT_OK;
+}
+
+}  // namespace
+
+extern "C" int hmat_gmres(hmat_handle h, const double *b, double *x, int32_t m, const hmat_solve_opts *opts_in,
+                          void *stream, hmat_solve_info *info) {
+    if (!h || !b || !x || m < 1 || m > kGmresMaxM) return HMAT_ERR_ARG;
+    hmat_solve_opts o;
+    hmat_solve_opts_default(&o);
+    if (opts_in) o = *opts_in;
+    if (!(o.tol > 0.0) || !(o.inner_tol >= 0.0) || o.maxit < 0 || o.max_restarts < 0) return HMAT_ERR_ARG;
+    hmat_solve_info loc{};
+    hmat_solve_info &inf = info ? *info : loc;
+    std::memset(&inf, 0, sizeof(inf));
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = gmres_ensure(h, m);
+    if (rc) return rc;
+    auto &g = h->gm;
+    const int64_t n = h->n;
+    const bool db = is_device_pointer(b), dx = is_device_pointer(x);
+    const int per_product = product_launches(h->seg, h->nseg), per_product64 = product_launches(&h->seg64, 1);
+    int launches = 0, products = 0;
+    // state: zero, then the scratch pointer
+    CK(cudaMemsetAsync(g.G, 0, sizeof(GmresState), st));
+    CK(cudaMemcpyAsync(&g.G->partials, &g.partials, sizeof(double *), cudaMemcpyHostToDevice, st));
+    const double *bsrc = b;
+    if (!db) {
+        CK(cudaMemcpyAsync(h->stage_in, b, 8 * n, cudaMemcpyHostToDevice, st));
+        bsrc = h->stage_in;
+    }
+    launch_gather(n, h->perm, bsrc, g.b, st);
+    const double *xsrc = x;
+    if (!dx) {
+        CK(cudaMemcpyAsync(h->stage_out, x, 8 * n, cudaMemcpyHostToDevice, st));
+        xsrc = h->stage_out;
+    }
+    launch_gather(n, h->perm, xsrc, g.x, st);
+    launch_g_residual(n, 2, g.b, nullptr, nullptr, g.G, o.tol, o.inner_tol, st);
+    launches += 3;
+    if ((rc = gmres_read(h, st))) return rc;
+    const double bnorm2 = g.G_host->bnorm2;
+    int status = HMAT_OK;
+    if (!std::isfinite(bnorm2)) {
+        status = HMAT_ERR_NONFINITE;
+        inf.relres_true = NAN;
+    } else if (bnorm2 == 0.0) {
+        CK(cudaMemsetAsync(g.x, 0, 8 * n, st));
+    } else {
+        // the first run starts from the true residual r_0 = b - A64 x_0
+        enqueue_segments(&h->seg64, 1, g.x, nullptr, g.w, nullptr, nullptr, 0, st);
+        launch_g_residual(n, 3, g.b, g.w, g.r0, g.G, o.tol, o.inner_tol, st);
+        launches += per_product64 + 1;
+        if ((rc = gmres_read(h, st))) return rc;
+        for (;;) {
+            const double rel = g.G_host->relres_true;
+            inf.relres_true = rel;
+            if (!std::isfinite(rel)) { status = HMAT_ERR_NONFINITE; break; }
+            if (rel <= o.tol) { status = HMAT_OK; break; }
+            // a run on the correction equation A~ d = r_0 from x_0 = x
+            CK(cudaMemcpyAsync(g.x0, g.x, 8 * n, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(g.r, g.r0, 8 * n, cudaMemcpyDeviceToDevice, st));
+            for (;;) {
+                // a cycle of at most m Arnoldi steps, one graph launch
+                launch_g_start_cycle(n, g.r, g.V, g.G, m, o.maxit, st);
+                launches += 2;
+                if (!(g.graph && g.graph_m == m && g.graph_limit == o.maxit)) {
+                    if (g.graph) {
+                        cudaGraphExecDestroy(g.graph);
+                        g.graph = nullptr;
+                    }
+                    cudaGraph_t gr = nullptr;
+                    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+                    for (int jj = 0; jj < m; ++jj) {
+                        enqueue_segments(h->seg, h->nseg, g.V + (size_t)jj * n, nullptr, g.w, nullptr, &g.G->s, 1,
+                                         h->cap_stream);
+                        launch_g_arnoldi(n, g.V, (int)n, g.w, g.G, jj, m, o.maxit, g.part, h->cap_stream);
+                    }
+                    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &gr);
+                    if (!hmat_internal::cuda_ok(e, "cudaStreamEndCapture")) return HMAT_ERR_CUDA;
+                    e = cudaGraphInstantiate(&g.graph, gr, 0);
+                    cudaGraphDestroy(gr);
+                    if (!hmat_internal::cuda_ok(e, "cudaGraphInstantiate")) return HMAT_ERR_CUDA;
+                    g.graph_m = m;
+                    g.graph_limit = o.maxit;
+                }
+                CK(cudaGraphLaunch(g.graph, st));
+                launch_g_finish_cycle(n, g.V, (int)n, g.x, g.G, m, st);
+                launches += m * (per_product + 8) + 2;
+                if ((rc = gmres_read(h, st))) return rc;
+                if (g.G_host->run_over || g.G_host->status != HMAT_OK) break;
+                // the next cycle starts from r_0 - A~ (x - x_0)
+                launch_g_diff(n, g.x, g.x0, g.d, st);
+                enqueue_segments(h->seg, h->nseg, g.d, nullptr, g.w, nullptr, nullptr, 0, st);
+                launch_g_residual(n, 1, g.r0, g.w, g.r, g.G, o.tol, o.inner_tol, st);
+                launches += per_product + 2;
+                products += 1;
+            }
+            // true residual with the FP64 H-matrix (Section 4.1.3): accept, or the next run's r_0
+            enqueue_segments(&h->seg64, 1, g.x, nullptr, g.w, nullptr, nullptr, 0, st);
+            launch_g_residual(n, 3, g.b, g.w, g.r0, g.G, o.tol, o.inner_tol, st);
+            launches += per_product64 + 1;
+            if ((rc = gmres_read(h, st))) return rc;
+            inf.relres_true = g.G_host->relres_true;
+            if (!std::isfinite(g.G_host->relres_true)) { status = HMAT_ERR_NONFINITE; break; }
+            if (g.G_host->relres_true <= o.tol) { status = HMAT_OK; break; }
+            if (g.G_host->status != HMAT_OK) { status = g.G_host->status; break; }
+            if (inf.restarts >= o.max_restarts) { status = HMAT_ERR_MAXIT; break; }
+            inf.restarts += 1;
+        }
+    }
+    double *xo = dx ? x : h->stage_out;
+    launch_scatter(n, h->perm, g.x, xo, st);
+    launches += 1;
+    if (!dx) CK(cudaMemcpyAsync(x, h->stage_out, 8 * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    inf.status = status;
+    inf.iters = g.G_host->it;
+    inf.matvecs = g.G_host->s.nmv + products;
+    inf.matvecs_fp64 = g.G_host->nmv64;
+    inf.launches = launches;
+    inf.relres_inner = bnorm2 > 0.0 ? g.G_host->rnorm / std::sqrt(bnorm2) : 0.0;
+    return status;
 }
 
 extern "C" int hmat_info(hmat_handle h, hmat_handle_info *out) {

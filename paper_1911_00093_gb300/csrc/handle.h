@@ -53,6 +53,16 @@ struct hmat_t {
     HmatSegment seg64;              // the FP64 H-matrix of the true residual (Section 4.1.3)
     std::vector<void *> allocs;
     std::vector<int64_t> prob_off;  // problem p owns [prob_off[p], prob_off[p+1]) (batch handles)
+    // GMRES buffers (first GMRES solve; sized for the restart length m)
+    struct Gmres {
+        int m = 0;
+        double *V = nullptr, *w = nullptr, *r = nullptr, *b = nullptr, *x = nullptr, *part = nullptr, *partials = nullptr;
+        double *x0 = nullptr, *r0 = nullptr, *d = nullptr;  // the run's start and the correction d = x - x0
+        hmat_internal::GmresState *G = nullptr, *G_host = nullptr;
+        cudaGraphExec_t graph = nullptr;
+        int graph_m = 0, graph_limit = -1;
+        std::vector<void *> mine;
+    } gm;
     bool mrhs = false;              // BF16 handle with the many-right-hand-side tensor-core product
     hmat_internal::MrhsIndex mx;    // its indices (upload) and buffers (first use)
     // buffers of the many-system solver, sized for `cap` right-hand sides
@@ -88,6 +98,8 @@ struct hmat_t {
         cudaSetDevice(device);
         if (graph) cudaGraphExecDestroy(graph);
         if (multi.graph) cudaGraphExecDestroy(multi.graph);
+        if (gm.graph) cudaGraphExecDestroy(gm.graph);
+        if (gm.G_host) cudaFreeHost(gm.G_host);
         if (multi.S_host) cudaFreeHost(multi.S_host);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (void *a : allocs) cudaFree(a);

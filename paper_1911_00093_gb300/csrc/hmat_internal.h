@@ -105,6 +105,18 @@ struct RowDesc {
     int32_t ld;     // entries (the cluster's panel stride; 0 for no row)
 };
 
+// Up to kGroupRows consecutive rows of one leaf row cluster (the row-group
+// expansion's work item).
+constexpr int kGroupRows = 4;
+struct GroupDesc {
+    int64_t off;    // element offset of the first row
+    int32_t goff;   // first operand of the leaf row cluster
+    int32_t ld;     // entries per row
+    int32_t p0;     // first row (cluster order)
+    int32_t nr;     // rows (1..kGroupRows)
+    int32_t pad[2];
+};
+
 constexpr int kMaxScaleExp = 120;  // |e| of every stored power-of-two scale
 constexpr int kRedBigCnt = 32;     // blocks over this many leaf clusters are reduced by a whole CTA
 
@@ -114,6 +126,7 @@ struct Layout {
     std::vector<int32_t> perm;        // perm[p] = original index
     std::vector<int32_t> leaf_begin;  // nleaves + 1
     std::vector<RowDesc> rows;        // [n] every row's place in the phase-2 panels (cluster order)
+    std::vector<GroupDesc> groups;    // row groups of the leaf row clusters, in cluster order
     std::vector<P1Desc> p1;
     std::vector<P1Run> p1_runs;
     std::vector<XDst> xdst;

@@ -21,8 +21,12 @@ struct DevIndex {
     const P2Desc *p2 = nullptr;     // [nleaves]
     const double *tscale = nullptr; // per-rank factors of LrDesc::toff (paper's Methods 2 and 3)
     const RowDesc *rows = nullptr;  // [n] phase-2 rows (cluster order)
-    int32_t p2_shape = 1;           // expansion of 2-/4-byte panels: 0 per cluster, 1 row-persistent, 2 staged
+    const GroupDesc *groups = nullptr;  // row groups of the row-group expansion
+    int32_t ngroups = 0;
+    int32_t p2_shape = 3;           // expansion: 0 per cluster, 1 row-persistent, 2 staged, 3 row groups
+    int32_t p2_groups8 = 0;         // 1: the 8-byte stores use the row groups too (tuning override)
     int32_t nsm = 1;                // SMs of the device (row-persistent grid = nsm x p2w_blocks)
+    int32_t p1_threads = 0;         // BF16 projection CTA size override (0: the default)
     int32_t max_leaf = 0;           // rows of the widest leaf cluster
     int32_t max_ld2 = 0;            // widest phase-2 panel (entries)
 };
@@ -43,18 +47,23 @@ struct DevPanels {
 constexpr int p2w_blocks(Store) { return 4; }
 
 // Phase-2 launch shape of a store: 0 one CTA per leaf row cluster (the 8-byte
-// stores, and any store with HMAT_PHASE2=cluster), 1 row-persistent warps over a
-// fixed grid (the default for 2- and 4-byte panels), 2 staged (a persistent CTA
-// per SM streaming through shared memory with bulk copies; BF16 and FP32 panels
-// whose rows fit a slot; HMAT_PHASE2=staged; measured slower, kept as an option).
+// stores, and any store with HMAT_PHASE2=cluster), 3 row groups (persistent
+// warps over groups of four rows of one cluster sharing each operand load; the
+// default for 2- and 4-byte panels), 1 row-persistent warps over single rows
+// (HMAT_PHASE2=rows), 2 staged (a persistent CTA per SM streaming through shared
+// memory with bulk copies; BF16 and FP32 panels whose rows fit a slot;
+// HMAT_PHASE2=staged).  Measured at L6: BF16 expansion 51.0 us (groups), 57.7
+// (rows), 61.7 (cluster), 100.5 (staged).
 constexpr int kStagedSlotBytes = 16384;
 constexpr int kStagedSmemMax = 200 * 1024;  // its ring of slots plus two operand slots
 // raise the launch limits the staged expansion needs (once per process and device)
 cudaError_t prepare_launches();
 inline int phase2_shape(Store s, const DevIndex &ix) {
-    if (s == Store::DF || s == Store::F64 || ix.p2_shape == 0) return 0;
+    if (ix.p2_shape == 0) return 0;
+    if (s == Store::DF || s == Store::F64) return (ix.p2_groups8 && ix.p2_shape == 3) ? 3 : 0;
     const int esz = s == Store::BF16 ? 2 : 4;
     if (ix.p2_shape == 2 && (s == Store::BF16 || s == Store::F32) && ix.max_ld2 * esz <= kStagedSlotBytes) return 2;
+    if (ix.p2_shape == 3) return 3;
     return 1;
 }
 inline bool phase2_rows(Store s, const DevIndex &ix) { return phase2_shape(s, ix) == 1; }
@@ -63,6 +72,7 @@ inline int phase2_items(Store s, const DevIndex &ix) {
     switch (phase2_shape(s, ix)) {
     case 1: return ix.nsm * p2w_blocks(s);
     case 2: return ix.nsm;
+    case 3: return ix.nsm * 4;
     default: return ix.nleaves;
     }
 }
@@ -114,6 +124,31 @@ struct SolverScalars {
 
 constexpr int kVecThreads = 256;
 int vec_blocks(int64_t n);
+
+// ---- restarted GMRES(m) (gmres.cu) ----
+constexpr int kGmresMaxM = 64;
+struct GmresState {
+    SolverScalars s;  // s.flag: the current cycle has ended (its remaining products skip); s.nmv: Arnoldi steps
+    double bnorm2, rnorm, stop, hn, resid, relres_true;
+    int32_t j, jend, it, status, run_over, nmv64;
+    unsigned int ticket;
+    int32_t pad;
+    double *partials;  // grid-reduction scratch (vec_blocks entries)
+    double H[(kGmresMaxM + 1) * kGmresMaxM], cs[kGmresMaxM], sn[kGmresMaxM], g[kGmresMaxM + 1], y[kGmresMaxM];
+    double h[kGmresMaxM + 1], hp[kGmresMaxM + 1];
+};
+// mode 2: ||b||; 3: true residual r = b - y, which starts the next run; 1: r = b - y
+// between cycles (b = the run's r_0, y = A~ (x - x_0))
+void launch_g_diff(int64_t n, const double *x, const double *x0, double *d, cudaStream_t st);
+void launch_g_residual(int64_t n, int mode, const double *b, const double *y, double *r, GmresState *G, double tol,
+                       double inner_tol, cudaStream_t st);
+// a cycle starts from r (or the run ends): v_0 = r / ||r||
+void launch_g_start_cycle(int64_t n, const double *r, double *v0, GmresState *G, int m, int maxit, cudaStream_t st);
+// step jj after w = A v_jj: CGS2 against v_0..v_jj, column jj of H, rotations, v_{jj+1}
+void launch_g_arnoldi(int64_t n, const double *V, int ldv, double *w, GmresState *G, int jj, int m, int maxit,
+                      double *part, cudaStream_t st);
+// y = R^-1 g, x += V y
+void launch_g_finish_cycle(int64_t n, const double *V, int ldv, double *x, GmresState *G, int m, cudaStream_t st);
 
 // ---- product for many right-hand sides on the tensor cores (mrhs.cu, BF16 panels) ----
 constexpr int kMrhsCols = 64;  // right-hand sides per pass

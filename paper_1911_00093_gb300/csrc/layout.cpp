@@ -314,6 +314,9 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
     for (int64_t k = 0; k < nleaves; ++k) {
         const P2Desc &d = L.p2[k];
         for (int i = 0; i < d.ylen; ++i) L.rows[d.ybeg + i] = RowDesc{d.off + (int64_t)i * d.ld, d.goff, d.ld};
+        for (int i = 0; i < d.ylen; i += kGroupRows)
+            L.groups.push_back(GroupDesc{d.off + (int64_t)i * d.ld, d.goff, d.ld, d.ybeg + i,
+                                         std::min(kGroupRows, d.ylen - i), {0, 0}});
     }
     L.p2_elems = off;
     L.glen = goff;
@@ -496,6 +499,19 @@ int check_layout(const Layout &L, std::string *why) {
             return bad("red task");
     }
     if ((int64_t)L.rows.size() != L.n) return bad("rows size");
+    {  // row groups: cover every row once, inside its cluster's panel
+        int64_t covered = 0;
+        for (const GroupDesc &gd : L.groups) {
+            if (gd.nr < 1 || gd.nr > kGroupRows || gd.p0 < 0 || (int64_t)gd.p0 + gd.nr > L.n) return bad("group rows");
+            const RowDesc &r0 = L.rows[gd.p0], &r1 = L.rows[gd.p0 + gd.nr - 1];
+            if (gd.off != r0.off || gd.goff != r0.goff || gd.ld != r0.ld || r1.goff != gd.goff ||
+                r1.off != gd.off + (int64_t)(gd.nr - 1) * gd.ld)
+                return bad("group desc");
+            if (gd.p0 != covered) return bad("groups do not tile the rows");
+            covered += gd.nr;
+        }
+        if (covered != L.n) return bad("groups do not cover the rows");
+    }
     for (const P2Desc &d : L.p2)
         for (int i = 0; i < d.ylen; ++i) {
             const RowDesc &r = L.rows[d.ybeg + i];

@@ -39,7 +39,7 @@ namespace hmat_internal {
 
 namespace {
 
-bool is_table1(int precision) { return precision >= HMAT_M1_SINGLE && precision <= HMAT_M3; }
+bool is_table1(int precision) { return precision >= HMAT_M1_SINGLE && precision <= HMAT_M3_TRUNC; }
 
 // FP32 storage must not overflow; underflow is the precision loss the variant accepts
 bool fits_fp32(const double *a, int64_t cnt) {
@@ -100,7 +100,8 @@ void finish(DerivedSegment &s, const BlobView &v) {
 int derive_table1(const BlobView &v, int precision, int c, DerivedSegment (&seg)[2], Store (&store)[2], int *nseg,
                   std::string *why) {
     if (!is_table1(precision)) return HMAT_ERR_ARG;
-    if (precision == HMAT_M3 && (c < -1 || c > 16)) {
+    const bool m3 = precision == HMAT_M3 || precision == HMAT_M3_TRUNC;
+    if (m3 && (c < -1 || c > 16)) {
         if (why) *why = "Method 3 c outside [-1, 16]";
         return HMAT_ERR_ARG;
     }
@@ -115,6 +116,7 @@ int derive_table1(const BlobView &v, int precision, int c, DerivedSegment (&seg)
     case HMAT_M2_SINGLE: store[0] = Store::PS; store[1] = Store::PS2; lr_seg = 1; break;
     case HMAT_M2_MIXED: store[0] = Store::PM; store[1] = Store::PM; break;
     case HMAT_M3: store[0] = Store::F64; store[1] = Store::PM; break;
+    case HMAT_M3_TRUNC: store[0] = Store::F64; store[1] = Store::F64; break;
     }
     SegBuilder sb[2] = {{&seg[0]}, {&seg[1]}};
     std::vector<double> Vp, Wp, d;
@@ -167,7 +169,7 @@ int derive_table1(const BlobView &v, int precision, int c, DerivedSegment (&seg)
                 return HMAT_ERR_RANGE;
             }
         }
-        if (precision == HMAT_M3) {
+        if (m3) {
             // eq. (19)-(20): rank l in FP64 iff d_l >= d_max 10^-c
             double dmax = 0.0;
             for (int64_t l = 0; l < r; ++l) dmax = std::max(dmax, d[l]);
@@ -179,6 +181,8 @@ int derive_table1(const BlobView &v, int precision, int c, DerivedSegment (&seg)
         if (precision == HMAT_M3) {
             sb[0].add_lr(e, Vp.data(), Wp.data(), r, lsA, d.data());
             sb[1].add_lr(e, Vp.data(), Wp.data(), r, lsB, d.data());
+        } else if (precision == HMAT_M3_TRUNC) {
+            sb[0].add_lr(e, Vp.data(), Wp.data(), r, lsA, d.data());  // Section 4.5: lsB deleted
         } else {
             sb[lr_seg].add_lr(e, Vp.data(), Wp.data(), r, lsA, d.data());
         }

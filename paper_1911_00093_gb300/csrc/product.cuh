@@ -333,8 +333,8 @@ template <Store S> __device__ __forceinline__ typename Tr<S>::Part red_to_part(t
 // than 128 threads, and small CTAs let more clusters stream at once), else 256
 template <Store S> constexpr int p1_threads() { return S == Store::BF16 ? 128 : 256; }
 
-template <Store S>
-__global__ void __launch_bounds__(p1_threads<S>()) k_phase1(const P1Desc *__restrict__ desc, const P1Run *__restrict__ runs,
+template <Store S, int NT = p1_threads<S>()>
+__global__ void __launch_bounds__(NT) k_phase1(const P1Desc *__restrict__ desc, const P1Run *__restrict__ runs,
                                                         const XDst *__restrict__ xdst, const LrDesc *__restrict__ lr,
                                                         const int32_t *__restrict__ gdst, const void *__restrict__ q1,
                                                         const typename Tr<S>::Op *__restrict__ xs,
@@ -800,6 +800,74 @@ __global__ void __launch_bounds__(kP2Threads, p2w_blocks(S)) k_phase2w(
     }
 }
 
+// Row-group expansion: persistent warps over groups of up to four consecutive
+// rows of one leaf row cluster, so each 16-byte operand vector g_rho is loaded
+// once for the group's rows (the row-persistent kernel loads it per row).
+template <Store S> constexpr int p2g_blocks() { return 4; }
+
+template <Store S>
+__global__ void __launch_bounds__(kP2Threads, p2g_blocks<S>()) k_phase2g(
+    int ng, const GroupDesc *__restrict__ groups, const void *__restrict__ p2, const typename Tr<S>::Op *__restrict__ g,
+    double *__restrict__ y, const int32_t *__restrict__ out_perm, int accum, const SolverScalars *S_, int mode,
+    const double *__restrict__ w, int dotmode, double *dpart) {
+    constexpr int VW = Tr<S>::VW;
+    constexpr size_t esz = 16 / VW;
+    constexpr int GR = kGroupRows;
+    __shared__ double wsum[2][kP2Warps];
+    if (skip_product(S_, mode)) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int W = gridDim.x * kP2Warps;
+    double dw = 0.0, dy = 0.0;
+    for (int t = blockIdx.x * kP2Warps + warp; t < ng; t += W) {
+        const GroupDesc gd = groups[t];
+        const char *base = (const char *)p2 + (size_t)gd.off * esz;
+        const size_t row_bytes = (size_t)gd.ld * esz;
+        const typename Tr<S>::Op *gr = g + gd.goff;
+        const int nv = gd.ld / VW, nr = gd.nr;
+        Acc<S> acc[GR];
+#pragma unroll
+        for (int r = 0; r < GR; ++r) acc[r].init();
+        for (int v = lane; v < nv; v += 32) {
+            int4 raw[GR];
+#pragma unroll
+            for (int r = 0; r < GR; ++r)
+                raw[r] = r < nr ? ld_stream(base + (size_t)r * row_bytes + (size_t)v * 16) : make_int4(0, 0, 0, 0);
+            const GV<S> gv = GV<S>::load(gr + v * VW);
+#pragma unroll
+            for (int r = 0; r < GR; ++r)
+                if (r < nr) row_mac<S>(acc[r], raw[r], gv);
+        }
+#pragma unroll
+        for (int r = 0; r < GR; ++r) {
+            if (r >= nr) break;  // warp-uniform
+            const double o = row_total<S>(acc[r]);
+            if (lane == 0) {
+                const int p = gd.p0 + r;
+                const int q = out_perm ? out_perm[p] : p;
+                double out = o;
+                if (accum) out = y[q] + out;  // a later segment adds to the earlier ones' rows
+                y[q] = out;
+                if (dotmode != 0) {
+                    dw += __ldg(w + p) * out;
+                    dy += out * out;
+                }
+            }
+        }
+    }
+    if (dotmode == 0) return;
+    if (lane == 0) {
+        wsum[0][warp] = dw;
+        wsum[1][warp] = dy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < kP2Warps; ++k) { a += wsum[0][k]; b += wsum[1][k]; }
+        dpart[blockIdx.x] = a;
+        dpart[gridDim.x + blockIdx.x] = b;
+    }
+}
+
 // ------------------------------------------------------------------------
 // Staged expansion (2- and 4-byte panels): a persistent CTA per SM in which one
 // producer thread streams the row clusters' operands and panel rows into rings
@@ -1017,6 +1085,15 @@ int grid_for(int64_t n, int threads, int cap) {
 // launches of one store's product kernels (the dispatchers pick the store)
 template <Store SS>
 void phase1_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st) {
+    if constexpr (SS == Store::BF16) {
+        if (ix.p1_threads == 64 || ix.p1_threads == 96) {  // tuning override (HMAT_P1_THREADS)
+            auto k = ix.p1_threads == 64 ? k_phase1<SS, 64> : k_phase1<SS, 96>;
+            k<<<ix.nleaves, ix.p1_threads, 0, st>>>(ix.p1, ix.p1_runs, ix.xdst, ix.lr, ix.gdst, P.q1,
+                                                   (const typename Tr<SS>::Op *)P.xs, (typename Tr<SS>::Part *)P.part,
+                                                   (typename Tr<SS>::Op *)P.g, ix.tscale, skipS, mode);
+            return;
+        }
+    }
     k_phase1<SS><<<ix.nleaves, p1_threads<SS>(), 0, st>>>(ix.p1, ix.p1_runs, ix.xdst, ix.lr, ix.gdst, P.q1,
                                                           (const typename Tr<SS>::Op *)P.xs,
                                                           (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g,
@@ -1044,6 +1121,13 @@ void phase2_launch(const DevIndex &ix, const DevPanels &P, double *y, const int3
                                                             out_perm, accum, skipS, mode, w, dotmode, dpart, gslot);
             return;
         }
+    }
+    if (phase2_shape(SS, ix) == 3) {
+        k_phase2g<SS><<<ix.nsm * p2g_blocks<SS>(), kP2Threads, 0, st>>>(ix.ngroups, ix.groups, P.p2,
+                                                                        (const typename Tr<SS>::Op *)P.g, y,
+                                                                        out_perm, accum, skipS, mode, w, dotmode,
+                                                                        dpart);
+        return;
     }
     if (phase2_rows(SS, ix)) {
         k_phase2w<SS><<<ix.nsm * p2w_blocks(SS), kP2Threads, 0, st>>>(ix.n, ix.rows, P.p2,

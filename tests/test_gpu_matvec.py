@@ -140,11 +140,12 @@ def test_upload_rejects_bad_blob():
 
 
 
-@pytest.mark.parametrize("shape", ["cluster", "staged"])
+@pytest.mark.parametrize("shape", ["cluster", "staged", "rows"])
 def test_expansion_launch_shapes_agree(hcache, oracle_mod, monkeypatch, shape):
     """The other launch shapes of the expansion (one CTA per leaf row cluster; the
-    staged bulk-copy pipeline) against the default row-persistent one: the same
-    rows and operands in the same fixed order per row, so the same bits."""
+    staged bulk-copy pipeline; single-row persistent warps) against the default
+    row groups: the same rows and operands in the same fixed order per row, so
+    the same bits."""
     torch = need_gpu()
     P = lib()
     for mesh in (synth.icosphere(4), synth.two_spheres(3)):

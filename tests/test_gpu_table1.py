@@ -27,8 +27,9 @@ MESHES = [synth.icosphere(3), synth.unit_cube(8), synth.two_spheres(3)]
 VARIANTS = [("m1_single", "M1_SINGLE", None), ("m1_mixed", "M1_MIXED", None),
             ("m2_double", "M2_DOUBLE", None), ("m2_single", "M2_SINGLE", None),
             ("m2_mixed", "M2_MIXED", None),
-            ("m3", "M3", -1), ("m3", "M3", 1), ("m3", "M3", 3), ("m3", "M3", 7)]
-FP64_SUMS = ("M2_DOUBLE", "M2_SINGLE", "M2_MIXED", "M3")
+            ("m3", "M3", -1), ("m3", "M3", 1), ("m3", "M3", 3), ("m3", "M3", 7),
+            ("m3_trunc", "M3_TRUNC", 1), ("m3_trunc", "M3_TRUNC", 3)]
+FP64_SUMS = ("M2_DOUBLE", "M2_SINGLE", "M2_MIXED", "M3", "M3_TRUNC")
 
 
 def _ids(v):
@@ -130,7 +131,8 @@ def test_table1_host_pointers_and_determinism(hcache, oracle_mod):
 
 @pytest.mark.parametrize("form,variant,c", [("m1_single", "M1_SINGLE", None), ("m1_mixed", "M1_MIXED", None),
                                             ("m2_double", "M2_DOUBLE", None), ("m2_single", "M2_SINGLE", None),
-                                            ("m2_mixed", "M2_MIXED", None), ("m3", "M3", -1), ("m3", "M3", 2)],
+                                            ("m2_mixed", "M2_MIXED", None), ("m3", "M3", -1), ("m3", "M3", 2),
+                                            ("m3_trunc", "M3_TRUNC", 3)],
                          ids=lambda v: str(v))
 def test_table1_solve(hcache, oracle_mod, form, variant, c):
     """BiCG-STAB with the variant as the iterated operator and the FP64
