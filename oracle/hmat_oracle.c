@@ -54,7 +54,10 @@ enum {
     OR_M3 = 6,        /* per-rank FP64/FP32 split by d_i >= d_max 10^-c           */
     OR_DATA_FP32 = 7, /* panels rounded to FP32, all arithmetic FP64              */
     OR_DATA_BF16 = 8, /* panels rounded to pow2-scaled BF16, arithmetic FP64      */
-    OR_M3_TRUNC = 9   /* Section 4.5: ranks with d_i < d_max 10^-c deleted        */
+    OR_M3_TRUNC = 9,  /* Section 4.5: ranks with d_i < d_max 10^-c deleted        */
+    OR_M3_DENSE = 10  /* Section 4.5: dense blocks split like Method 3, column j
+                         FP64 iff max_i |a_ij| >= (largest dense entry) 10^-c,
+                         the rest and every low-rank block as Method 2-Mixed     */
 };
 
 /* ------------------------------------------------------------------------- */
@@ -619,6 +622,14 @@ static void hmatvec_perm(const or_hmat *h, int variant, int c3, const double *xp
     /* Section 3.5: the FP32 source vector is a fresh copy of the FP64 one */
     for (int64_t i = 0; i < N; i++) x32[i] = (float)xp[i];
     for (int64_t i = 0; i < N; i++) yp[i] = 0.0;
+    double dense_dmax = 0.0;  /* largest |entry| of the dense blocks (OR_M3_DENSE) */
+    if (variant == OR_M3_DENSE)
+        for (int64_t b = 0; b < h->nb; b++) {
+            if (h->bkind[b] != 0) continue;
+            int64_t cnt = (h->bi_e[b] - h->bi_s[b]) * (h->bj_e[b] - h->bj_s[b]);
+            for (int64_t k = 0; k < cnt; k++)
+                if (fabs(h->bdata[b][k]) > dense_dmax) dense_dmax = fabs(h->bdata[b][k]);
+        }
 
     for (int64_t b = 0; b < h->nb; b++) {
         int64_t is = h->bi_s[b], js = h->bj_s[b];
@@ -652,12 +663,41 @@ static void hmatvec_perm(const or_hmat *h, int variant, int c3, const double *xp
                     case OR_DATA_BF16:
                         yhat[i] = yhat[i] + Ab[i * n + j] * xm[j];
                         break;
+                    case OR_M3_DENSE:                                          /* below, per column */
+                        break;
                     default:                                                   /* M1/M2-Double, M3 */
                         yhat[i] = yhat[i] + a * xm[j];                         /* eq. (21), FP64 */
                     }
                 }
             }
             free(Ab);
+            if (variant == OR_M3_DENSE) {
+                /* READING of Section 4.5's multi-level dense blocks: A^m = sum_j
+                   a_j e_j^T is Method 2's V' D W' form with W' = I, so column j
+                   has the weight d_j = max_i |a_ij| (eq. 16), and Method 3's rule
+                   (eq. 19-20) keeps it FP64 iff d_j >= d_max 10^-c.  d_max is the
+                   largest entry of the whole near field (every dense block), not
+                   of the block: inside one block of the collocation matrix the
+                   column weights span about one decade, so a per-block d_max
+                   splits nothing for c >= 1.  The other columns take Method
+                   2-Mixed's dense arithmetic (FP32 entry promoted, FP64 x); the
+                   two parts are added (Section 3.4). */
+                const double thr = dense_dmax * pow(10.0, -(double)c3);
+                double *yhat64 = (double *)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
+                double *yhat32 = (double *)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
+                for (int64_t j = 0; j < n; j++) {
+                    double dj = 0.0;
+                    for (int64_t i = 0; i < m; i++) if (fabs(A[i * n + j]) > dj) dj = fabs(A[i * n + j]);
+                    const int col64 = dj >= thr;
+                    for (int64_t i = 0; i < m; i++) {
+                        double a = A[i * n + j];
+                        if (col64) yhat64[i] = yhat64[i] + a * xm[j];
+                        else yhat32[i] = yhat32[i] + (double)(float)a * xm[j];
+                    }
+                }
+                for (int64_t i = 0; i < m; i++) yhat[i] = yhat64[i] + yhat32[i];
+                free(yhat64); free(yhat32);
+            }
         } else {
             const double *Vm = h->bdata[b];          /* #I x r */
             const double *Wm = h->bdata[b] + m * r;  /* r x #J */

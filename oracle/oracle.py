@@ -9,10 +9,10 @@ _SRC = os.path.join(_HERE, "hmat_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 # precision variants (Table 1 rows, plus data-rounding references)
-M1_DOUBLE, M1_SINGLE, M1_MIXED, M2_DOUBLE, M2_SINGLE, M2_MIXED, M3, DATA_FP32, DATA_BF16, M3_TRUNC = range(10)
+M1_DOUBLE, M1_SINGLE, M1_MIXED, M2_DOUBLE, M2_SINGLE, M2_MIXED, M3, DATA_FP32, DATA_BF16, M3_TRUNC, M3_DENSE = range(11)
 VARIANTS = {"M1_DOUBLE": M1_DOUBLE, "M1_SINGLE": M1_SINGLE, "M1_MIXED": M1_MIXED,
             "M2_DOUBLE": M2_DOUBLE, "M2_SINGLE": M2_SINGLE, "M2_MIXED": M2_MIXED, "M3": M3,
-            "DATA_FP32": DATA_FP32, "DATA_BF16": DATA_BF16, "M3_TRUNC": M3_TRUNC}
+            "DATA_FP32": DATA_FP32, "DATA_BF16": DATA_BF16, "M3_TRUNC": M3_TRUNC, "M3_DENSE": M3_DENSE}
 STATUS = {0: "ok", 1: "breakdown_rho", 2: "breakdown_omega", 3: "maxit", 4: "nonfinite"}
 
 

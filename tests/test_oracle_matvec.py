@@ -162,6 +162,54 @@ def test_rank_truncation(hcache, oracle_mod):
     assert errs[1] < errs[0]
 
 
+def test_dense_split(hcache, oracle_mod):
+    """Section 4.5's multi-level dense blocks (Method 3's rule applied to the
+    columns of the dense blocks against the largest near-field entry, the
+    low-rank blocks as Method 2-Mixed).  Pins:
+    a large c keeps every dense column FP64, which is Method 3 with c = -1 (dense
+    FP64, low rank FP32) bit for bit; c = -1 demotes every column, which is
+    Method 2-Mixed bit for bit; in between, what changes against c = 16 is exactly
+    sum over the demoted columns of (fl32(a_ij) - a_ij) x_j, computed here from
+    the raw block data; the error shrinks as c grows."""
+    mesh = synth.icosphere(3)
+    H = hcache(mesh)
+    x = np.random.default_rng(46).standard_normal(mesh.n)
+    MD = oracle_mod.M3_DENSE
+    y_hi = H.matvec(x, MD, c=16)
+    assert np.array_equal(y_hi, H.matvec(x, oracle_mod.M3, c=-1))
+    assert np.array_equal(H.matvec(x, MD, c=-1), H.matvec(x, oracle_mod.M2_MIXED))
+    perm = H.perm
+    xp = x[perm]
+    blk = H.blocks
+    dense = [b for b in range(len(blk)) if blk[b][4] == 0]
+    dmax = max(np.abs(H.block_data(b)).max() for b in dense)   # the largest near-field entry
+    delta = {c: np.zeros(mesh.n) for c in (0, 1, 2)}
+    demoted = {c: 0 for c in delta}
+    for b in dense:
+        i_s, i_e, j_s, j_e, kind, r, _ = blk[b]
+        A = H.block_data(b)
+        w = np.abs(A).max(axis=0)
+        for c in delta:
+            lo = w < dmax * 10.0 ** (-c)
+            demoted[c] += int(lo.sum())
+            E = A.astype(np.float32).astype(np.float64) - A
+            delta[c][i_s:i_e] += E[:, lo] @ xp[j_s:j_e][lo]
+    y64 = H.matvec(x, oracle_mod.M1_DOUBLE)
+    # near-field column weights lie within 2e-2..1 of the self term here: c = 2 demotes nothing
+    assert demoted[2] == 0 and np.array_equal(H.matvec(x, MD, c=2), y_hi)
+    del delta[2]
+    errs = []
+    for c in delta:
+        assert demoted[c] > 0
+        dc = np.empty(mesh.n)
+        dc[perm] = delta[c]
+        yc = H.matvec(x, MD, c=c)
+        # the change is reproduced to six digits (y's own rounding is ~1e-16 |y|)
+        assert np.linalg.norm((yc - y_hi) - dc) <= 1e-6 * np.linalg.norm(dc)
+        errs.append(np.linalg.norm(yc - y64))
+    assert demoted[1] < demoted[0] and errs[1] <= errs[0]
+
+
 def test_data_rounding_forms(hcache, oracle_mod):
     mesh = synth.icosphere(3)
     H = hcache(mesh)
