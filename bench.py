@@ -35,9 +35,11 @@ FORMS = {"fp64": ("fp64", None, {}), "fp64_dfma": ("fp64_dfma", None, {}),
          "m2_double": ("m2_double", None, {}), "m2_single": ("m2_single", None, {"inner_tol": 1e-4}),
          "m2_mixed": ("m2_mixed", None, {"inner_tol": 1e-4}), "m3_c-1": ("m3", -1, {"inner_tol": 1e-4}),
          "m3_c2": ("m3", 2, {"inner_tol": 1e-4}), "m3_c3": ("m3", 3, {"inner_tol": 1e-4}),
-         "m3trunc_c3": ("m3_trunc", 3, {"inner_tol": 1e-4})}
+         "m3trunc_c3": ("m3_trunc", 3, {"inner_tol": 1e-4}), "m3dense_c0": ("m3_dense", 0, {"inner_tol": 1e-4}),
+         "m3dense_c1": ("m3_dense", 1, {"inner_tol": 1e-4})}
 FORM_OPTS = {k: v[2] for k, v in FORMS.items()}
-DEFAULT_FORMS = "fp64,fp64_dfma,fp32,bf16,m1_single,m1_mixed,m2_double,m2_single,m2_mixed,m3_c-1,m3_c3,m3trunc_c3"
+DEFAULT_FORMS = ("fp64,fp64_dfma,fp32,bf16,m1_single,m1_mixed,m2_double,m2_single,m2_mixed,m3_c-1,m3_c3,m3trunc_c3,"
+                 "m3dense_c1")
 CHECK_EVERY = 4  # iterations per graph replay between host reads of the stop flag
 PART_BYTES = {"fp64": 8, "fp64_dfma": 8, "fp32": 4, "bf16": 4}  # partial sums (8 for the paper's variants)
 
@@ -232,7 +234,8 @@ def run_workload(args):
     """The other configurations of the study, one JSON line each (not the headline):
     icosphere_L4 (FP64 correctness size), two_spheres_L7 (BF16 + FP64 refinement,
     N = 655,360), multirhs64 (64 right-hand sides at level 6, tensor-core products),
-    batch48 (48 uneven cube / sphere problems in one block-diagonal handle)."""
+    batch48 (48 uneven cube / sphere problems in one block-diagonal handle);
+    build_icosphere_L6 / build_batch48 (H-matrix construction, host vs device)."""
     import torch
     import synth
     import paper_1911_00093_gb300 as P
@@ -314,6 +317,54 @@ def run_workload(args):
             P.hmat_destroy(h)
         out["value"] = out["fp32"]["batch_solve_ms"]
         out["speedup_fp32_vs_fp64"] = out["fp64"]["batch_solve_ms"] / out["fp32"]["batch_solve_ms"]
+    elif args.workload in ("build_icosphere_L6", "build_batch48"):
+        # H-matrix construction: the host builder (OpenMP on the host cores) against
+        # the device ACA builder; both produce the same blob (checked here)
+        import os
+        import time
+        if args.workload == "build_icosphere_L6":
+            meshes = [synth.icosphere(6)]
+        else:
+            meshes = [synth.mesh_from_spec(sp) for sp in synth.uneven_batch_specs(48)]
+        import ctypes as C
+        L = P.load()
+        # the library calls alone (the blob stays in the library's buffer): best of a few
+        def call(fn, m, info=None):
+            buf, size = C.c_void_p(), C.c_size_t()
+            c = np.ascontiguousarray(m.centroid)
+            a = np.ascontiguousarray(m.area)
+            args = [m.n, c.ctypes.data, a.ctypes.data, 32, 2.0, 1e-4, C.byref(buf), C.byref(size)]
+            if info is not None:
+                args.append(C.byref(info))
+            t0 = time.perf_counter()
+            st = fn(*args)
+            dt = (time.perf_counter() - t0) * 1e3
+            assert st == 0, st
+            return dt, buf, size.value
+        def timed(fn, reps, info=None):
+            best = None
+            for _ in range(reps):
+                tot, bufs = 0.0, []
+                for m in meshes:
+                    dt, buf, size = call(fn, m, info)
+                    tot += dt
+                    bufs.append((buf, size))
+                for buf, _ in bufs:
+                    L.hmat_blob_free(buf)
+                best = tot if best is None or tot < best else best
+            return best
+        L.hmat_build_device.restype = C.c_int  # (signature set by load())
+        timed(L.hmat_build_device, 1, P.BuildDeviceInfo())  # context and allocator warm-up
+        dinfo = P.BuildDeviceInfo()
+        dev_ms = timed(L.hmat_build_device, 3, dinfo)
+        host_ms = timed(L.hmat_build, 2)
+        same = all(np.array_equal(P.hmat_build_device(m.centroid, m.area), P.hmat_build(m.centroid, m.area))
+                   for m in meshes[:4])
+        out.update({"metric": "H-matrix construction (cluster tree, partition, ACA, dense blocks)",
+                    "unit": "ms", "value": dev_ms, "host_ms": host_ms, "speedup_device_vs_host": host_ms / dev_ms,
+                    "host_threads": os.cpu_count(), "identical_blobs_checked": same,
+                    "last_device_build": {k: getattr(dinfo, k) for k, _ in P.BuildDeviceInfo._fields_}})
+        out["config"].update({"problems": len(meshes), "n_total": int(sum(m.n for m in meshes))})
     print(json.dumps(out))
 
 
@@ -329,7 +380,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--matvec-iters", type=int, default=50)
     ap.add_argument("--workload", default="icosphere_L6",
-                    choices=["icosphere_L6", "icosphere_L4", "two_spheres_L7", "multirhs64", "batch48"],
+                    choices=["icosphere_L6", "icosphere_L4", "two_spheres_L7", "multirhs64", "batch48",
+                             "build_icosphere_L6", "build_batch48"],
                     help="icosphere_L6 is the benchmark; the others print one informative line each")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -417,7 +469,8 @@ def main():
     head = table[args.form]
     dom = "phase2" if head["kernel_ms"]["phase2"] >= head["kernel_ms"]["phase1"] else "phase1"
     achieved = head[dom + "_gbs"]
-    kname = f"k_{dom}<{args.form}>"
+    # the kernels of the default launch shapes: the row-group expansion and the per-cluster projection
+    kname = f"k_phase2g<{args.form}>" if dom == "phase2" else f"k_phase1<{args.form}>"
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                 "traffic": _profiled_traffic(kname, args.level)}

@@ -93,6 +93,13 @@ typedef enum hmat_status {
  *                  FP32 (d_i < d_max 10^-c) are deleted with their column of V'_m
  *                  and row of W'_m; the rest as Method 2-Double.  Upload with
  *                  hmat_upload_ex.
+ *  HMAT_M3_DENSE   Section 4.5's multi-level dense blocks: column j of a dense
+ *                  block stays FP64 when max_i |a_ij| >= d_max 10^-c, d_max the
+ *                  largest entry of all dense blocks (Method 3's rule, eq. 19-20,
+ *                  on the form A|^m = A|^m I); the other columns and every
+ *                  low-rank block follow Method 2-Mixed; the parts are added.
+ *                  c = -1 is Method 2-Mixed, c >= 2 keeps the collocation near
+ *                  field all FP64.  Upload with hmat_upload_ex.
  * These variants carry FP64 arithmetic per entry and are bound by the FP64 pipe
  * of GB300, not by HBM.
  */
@@ -107,7 +114,8 @@ typedef enum hmat_precision {
     HMAT_M2_SINGLE = 7,
     HMAT_M2_MIXED = 8,
     HMAT_M3 = 9,
-    HMAT_M3_TRUNC = 10
+    HMAT_M3_TRUNC = 10,
+    HMAT_M3_DENSE = 11
 } hmat_precision;
 
 typedef struct hmat_t *hmat_handle;
@@ -140,6 +148,34 @@ int hmat_build(int64_t n, const double *centroids, const double *areas, int32_t 
                double aca_eps, void **blob, size_t *blob_bytes);
 
 void hmat_blob_free(void *blob);
+
+/*
+ * hmat_build_device -- hmat_build with the entries computed on the current CUDA
+ * device: the cluster tree and block partition are planned on the host, then one
+ * CTA per admissible block runs the same ACA with partial pivoting and another
+ * launch writes the dense blocks and the factors, which are copied into the host
+ * blob.  Every floating-point operation is the host builder's in the same order
+ * (no contraction; IEEE division and square root), so the blob equals
+ * hmat_build's byte for byte.  A block whose ACA needs more than 64 ranks
+ * without becoming dense is finished by the host builder's own code.  The
+ * paper takes this step from HACApK on the CPU (Section 4.1.3); it is not on
+ * the product's path.  Arguments, ownership and errors as hmat_build, plus
+ * HMAT_ERR_CUDA; `info` (may be NULL) receives counts and host-clock times.
+ * Synchronous; the device memory it uses is freed before it returns.
+ */
+typedef struct hmat_build_device_info {
+    int64_t aca_blocks;        /* admissible blocks approximated on the device            */
+    int64_t host_blocks;       /* of those, finished on the host (ranks above 64)        */
+    int64_t workspace_bytes;   /* device workspace of the ACA (factors and pivot flags)  */
+    double plan_ms;            /* host: cluster tree and block partition                 */
+    double alloc_ms;           /* device buffers (ACA workspace) and input uploads        */
+    double aca_ms;             /* the ACA launch, up to the ranks on the host             */
+    double pack_ms;            /* block kinds, blob index, dense entries and factor pack  */
+    double copy_ms;            /* the blob's values, device to host                      */
+} hmat_build_device_info;
+
+int hmat_build_device(int64_t n, const double *centroids, const double *areas, int32_t leaf, double eta,
+                      double aca_eps, void **blob, size_t *blob_bytes, hmat_build_device_info *info);
 
 /*
  * Serialized H-matrix, version 1 (all integers little-endian int64, all values
@@ -344,7 +380,7 @@ typedef struct hmat_handle_info {
     int64_t phase1_bytes;        /* the projection's share of stored_bytes                                  */
     int64_t phase2_bytes;        /* the expansion's share                                                   */
     int32_t segments;            /* 1, or 2 for a paper variant whose product adds two expansions           */
-    int32_t method3_c;           /* c of eq. (19)-(20) for HMAT_M3, else 0                                  */
+    int32_t method3_c;           /* c of eq. (19)-(20) for HMAT_M3, _TRUNC and _DENSE, else 0               */
 } hmat_handle_info;
 
 int hmat_info(hmat_handle h, hmat_handle_info *out);

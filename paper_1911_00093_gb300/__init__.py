@@ -20,17 +20,25 @@ STATUS = {0: "ok", 1: "arg", 2: "bad_layout", 3: "nomem", 4: "cuda", 5: "breakdo
 HMAT_FP64, HMAT_FP64_DFMA, HMAT_FP32, HMAT_BF16 = 0, 1, 2, 3
 HMAT_M1_SINGLE, HMAT_M1_MIXED, HMAT_M2_DOUBLE, HMAT_M2_SINGLE, HMAT_M2_MIXED, HMAT_M3 = 4, 5, 6, 7, 8, 9
 HMAT_M3_TRUNC = 10
+HMAT_M3_DENSE = 11
 PRECISIONS = {"fp64": HMAT_FP64, "fp64_dfma": HMAT_FP64_DFMA, "fp32": HMAT_FP32, "bf16": HMAT_BF16,
               # the paper's variants (Section 3, Table 1); Method 1-Double is "fp64_dfma"
               "m1_single": HMAT_M1_SINGLE, "m1_mixed": HMAT_M1_MIXED, "m2_double": HMAT_M2_DOUBLE,
-              "m2_single": HMAT_M2_SINGLE, "m2_mixed": HMAT_M2_MIXED, "m3": HMAT_M3, "m3_trunc": HMAT_M3_TRUNC}
+              "m2_single": HMAT_M2_SINGLE, "m2_mixed": HMAT_M2_MIXED, "m3": HMAT_M3, "m3_trunc": HMAT_M3_TRUNC,
+              "m3_dense": HMAT_M3_DENSE}
 
 # every symbol declared in include/hmat.h
 EXPORTS = ("hmat_build", "hmat_blob_free", "hmat_blob_stats_get", "hmat_upload", "hmat_destroy",
            "hmat_matvec", "hmat_matvec_fp64", "hmat_solve_opts_default", "hmat_bicgstab",
            "hmat_bicgstab_ex", "hmat_info", "hmat_time_matvec", "hmat_strerror", "hmat_last_cuda_error",
            "hmat_matvec_noalloc", "hmat_upload_ex", "hmat_upload_batch", "hmat_problems", "hmat_bicgstab_multi",
-           "hmat_gmres")
+           "hmat_gmres", "hmat_build_device")
+
+
+class BuildDeviceInfo(C.Structure):
+    _fields_ = [("aca_blocks", C.c_int64), ("host_blocks", C.c_int64), ("workspace_bytes", C.c_int64),
+                ("plan_ms", C.c_double), ("alloc_ms", C.c_double), ("aca_ms", C.c_double),
+                ("pack_ms", C.c_double), ("copy_ms", C.c_double)]
 
 
 class BlobStats(C.Structure):
@@ -103,6 +111,8 @@ def load():
         "hmat_problems": (C.c_int, [P, C.POINTER(I32), P]),
         "hmat_bicgstab_multi": (C.c_int, [P, P, P, I32, C.POINTER(SolveOpts), P, P]),
         "hmat_gmres": (C.c_int, [P, P, P, I32, C.POINTER(SolveOpts), P, C.POINTER(SolveInfo)]),
+        "hmat_build_device": (C.c_int, [I64, P, P, I32, D, D, C.POINTER(C.c_void_p), C.POINTER(SZ),
+                                        C.POINTER(BuildDeviceInfo)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -164,6 +174,28 @@ def hmat_build(centroids, areas, leaf=32, eta=2.0, aca_eps=1e-4) -> bytes:
         C.memmove(out.ctypes.data, buf, size.value)
     finally:
         L.hmat_blob_free(buf)
+    return out
+
+
+def hmat_build_device(centroids, areas, leaf=32, eta=2.0, aca_eps=1e-4, info=None):
+    """hmat_build with the ACA and the dense entries on the current CUDA device (the
+    same blob, byte for byte); `info`, if a dict, receives the build's counts and times."""
+    L = load()
+    c = np.ascontiguousarray(centroids, dtype=np.float64)
+    a = np.ascontiguousarray(areas, dtype=np.float64)
+    n = a.shape[0]
+    if c.shape != (n, 3):
+        raise ValueError("centroids must be (n, 3)")
+    buf, size, inf = C.c_void_p(), C.c_size_t(), BuildDeviceInfo()
+    _check(L.hmat_build_device(n, c.ctypes.data, a.ctypes.data, int(leaf), float(eta), float(aca_eps),
+                               C.byref(buf), C.byref(size), C.byref(inf)), "hmat_build_device")
+    try:
+        out = np.empty(size.value, dtype=np.uint8)
+        C.memmove(out.ctypes.data, buf, size.value)
+    finally:
+        L.hmat_blob_free(buf)
+    if isinstance(info, dict):
+        info.update({k: getattr(inf, k) for k, _ in BuildDeviceInfo._fields_})
     return out
 
 

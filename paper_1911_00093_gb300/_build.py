@@ -14,7 +14,10 @@ OUT = os.path.join(HERE, "libhmat.so")
 BUILD = os.path.join(HERE, "_build")
 
 CXX_SOURCES = ["builder.cpp", "layout.cpp", "paper_forms.cpp"]
-CU_SOURCES = ["kernels.cu", "kernels_table1.cu", "multi.cu", "mrhs.cu", "gmres.cu", "api.cu", "noalloc.cu"]
+CU_SOURCES = ["kernels.cu", "kernels_table1.cu", "multi.cu", "mrhs.cu", "gmres.cu", "api.cu", "noalloc.cu",
+              "aca_device.cu"]
+# per-file flags: the device builder reproduces the host builder's rounding (no FMA contraction)
+CU_FLAGS = {"aca_device.cu": ["-fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -51,7 +54,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for s in CU_SOURCES:
         o = os.path.join(BUILD, s + ".o")
         jobs.append(([nvcc] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                                      "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr"] + inc +
+                                      "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr"] +
+                     CU_FLAGS.get(s, []) + inc +
                      ["-c", os.path.join(CSRC, s), "-o", o], o))
     with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         outs = list(ex.map(lambda j: _run(j[0]), jobs))

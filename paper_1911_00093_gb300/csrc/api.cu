@@ -40,7 +40,7 @@ Store store_of(int precision) {
     }
 }
 
-bool is_table1_precision(int precision) { return precision >= HMAT_M1_SINGLE && precision <= HMAT_M3_TRUNC; }
+bool is_table1_precision(int precision) { return precision >= HMAT_M1_SINGLE && precision <= HMAT_M3_DENSE; }
 
 }  // namespace
 
@@ -87,6 +87,7 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
     P1Desc *p1 = nullptr;
     P1Run *p1_runs = nullptr;
     XDst *xdst = nullptr;
+    int32_t *xsel = nullptr;
     LrDesc *lr = nullptr;
     P2Desc *p2 = nullptr;
     double *tscale = nullptr;
@@ -96,6 +97,7 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
     if ((st = h->upload(&p1, L.p1.data(), sizeof(P1Desc) * L.p1.size())) ||
         (st = h->upload(&p1_runs, L.p1_runs.data(), sizeof(P1Run) * L.p1_runs.size())) ||
         (st = h->upload(&xdst, L.xdst.data(), sizeof(XDst) * L.xdst.size())) ||
+        (st = h->upload(&xsel, L.xsel.data(), 4 * L.xsel.size())) ||
         (st = h->upload(&lr, L.lr.data(), sizeof(LrDesc) * L.lr.size())) ||
         (st = h->upload(&gdst, L.gdst.data(), 4 * L.gdst.size())) ||
         (st = h->upload(&red_big, L.red_big.data(), 4 * L.red_big.size())) ||
@@ -106,30 +108,28 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
         (st = h->upload(&groups, L.groups.data(), sizeof(GroupDesc) * L.groups.size()))) {
         return st;
     }
-    ix.p1 = p1; ix.p1_runs = p1_runs; ix.xdst = xdst; ix.lr = lr; ix.gdst = gdst; ix.p2 = p2;
+    ix.p1 = p1; ix.p1_runs = p1_runs; ix.xdst = xdst; ix.xsel = xsel; ix.lr = lr; ix.gdst = gdst; ix.p2 = p2;
     ix.red_big = red_big; ix.red_tasks = red_tasks;
     ix.tscale = L.tscale.empty() ? nullptr : tscale;
     ix.rows = rows;
     ix.groups = groups;
     ix.ngroups = (int32_t)L.groups.size();
-    // phase-2 launch shape (phase2_shape): row groups for 2-/4-byte panels;
+    // phase-2 launch shape (phase2_shape): row groups for every store;
     // HMAT_PHASE2=cluster, =rows, =staged select the others (all are exact)
     const char *p2env = std::getenv("HMAT_PHASE2");
     ix.p2_shape = 3;
     if (p2env && std::strcmp(p2env, "cluster") == 0) ix.p2_shape = 0;
     if (p2env && std::strcmp(p2env, "rows") == 0) ix.p2_shape = 1;
-    if (p2env && std::strcmp(p2env, "groups8") == 0) ix.p2_groups8 = 1;
     if (p2env && std::strcmp(p2env, "staged") == 0) ix.p2_shape = 2;
     if (p2env && std::strcmp(p2env, "groups") == 0) ix.p2_shape = 3;
-    const char *p1env = std::getenv("HMAT_P1_THREADS");
-    ix.p1_threads = p1env ? std::atoi(p1env) : 0;
     int nsm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     ix.nsm = std::max(1, nsm);
     g.partials_n = L.npart;
     g.glen = L.glen;
     h->index_bytes += (int64_t)(sizeof(P1Desc) * L.p1.size() + sizeof(P1Run) * L.p1_runs.size() +
-                                sizeof(XDst) * L.xdst.size() + sizeof(LrDesc) * L.lr.size() + 4 * L.gdst.size() +
+                                sizeof(XDst) * L.xdst.size() + 4 * L.xsel.size() + sizeof(LrDesc) * L.lr.size() +
+                                4 * L.gdst.size() +
                                 sizeof(P2Desc) * L.p2.size() + 4 * (L.red_big.size() + L.red_tasks.size()) +
                                 8 * L.tscale.size() + sizeof(RowDesc) * L.rows.size() +
                                 sizeof(GroupDesc) * L.groups.size());
@@ -190,7 +190,8 @@ int upload_mrhs_index(hmat_t *h, const Layout &L) {
         const P1Desc &d = L.p1[k];
         for (int e = 0; e < d.xdcnt; ++e) {
             const XDst &x = L.xdst[d.xdbeg + e];
-            for (int j = 0; j < d.xlen; ++j) src[x.goff + j] = MrhsSrc{d.xbeg + j, x.scale};
+            for (int j = 0; j < x.cnt; ++j)
+                src[x.goff + j] = MrhsSrc{d.xbeg + (x.sel < 0 ? j : L.xsel[x.sel + j]), x.scale};
         }
     }
     std::vector<int32_t> tasks;
@@ -247,7 +248,8 @@ int upload_view(const BlobView &v, int32_t precision, int32_t method3_c, const s
         CK(cudaGetDevice(&h->device));
         CK(prepare_launches());
         h->precision = precision;
-        h->method3_c = (precision == HMAT_M3 || precision == HMAT_M3_TRUNC) ? method3_c : 0;
+        h->method3_c =
+            (precision == HMAT_M3 || precision == HMAT_M3_TRUNC || precision == HMAT_M3_DENSE) ? method3_c : 0;
         h->n = L.n;
         int32_t *perm = nullptr;
         if ((st = h->upload(&perm, L.perm.data(), 4 * L.perm.size()))) return st;
@@ -326,7 +328,7 @@ int upload_view(const BlobView &v, int32_t precision, int32_t method3_c, const s
 
 int upload_impl(const void *blob, size_t blob_bytes, int32_t precision, int32_t method3_c, hmat_handle *out) {
     if (!blob || !out) return HMAT_ERR_ARG;
-    if (precision < HMAT_FP64 || precision > HMAT_M3_TRUNC) return HMAT_ERR_ARG;
+    if (precision < HMAT_FP64 || precision > HMAT_M3_DENSE) return HMAT_ERR_ARG;
     *out = nullptr;
     BlobView v;
     int st = parse_blob(blob, blob_bytes, v);
@@ -343,7 +345,7 @@ extern "C" int hmat_upload(const void *blob, size_t blob_bytes, int32_t precisio
 extern "C" int hmat_upload_batch(const void *const *blobs, const size_t *blob_bytes, int32_t count, int32_t precision,
                                  int32_t method3_c, hmat_handle *out) {
     if (!blobs || !blob_bytes || !out || count < 1) return HMAT_ERR_ARG;
-    if (precision < HMAT_FP64 || precision > HMAT_M3_TRUNC) return HMAT_ERR_ARG;
+    if (precision < HMAT_FP64 || precision > HMAT_M3_DENSE) return HMAT_ERR_ARG;
     *out = nullptr;
     try {
         std::vector<BlobView> views(count);

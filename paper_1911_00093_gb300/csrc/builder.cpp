@@ -262,10 +262,12 @@ int64_t align64(int64_t x) { return (x + 63) & ~int64_t(63); }
 
 }  // namespace
 
-extern "C" int hmat_build(int64_t n, const double *centroids, const double *areas, int32_t leaf, double eta,
-                          double aca_eps, void **blob, size_t *blob_bytes) {
-    if (!centroids || !areas || !blob || !blob_bytes || n < 1 || leaf < 1 || leaf > hmat_internal::kMaxLeaf ||
-        !(eta >= 0.0) || !(aca_eps > 0.0) || !std::isfinite(eta) || !std::isfinite(aca_eps))
+namespace hmat_internal {
+
+int plan_build(int64_t n, const double *centroids, const double *areas, int32_t leaf, double eta, double aca_eps,
+               BuildPlan &plan) {
+    if (!centroids || !areas || n < 1 || leaf < 1 || leaf > kMaxLeaf || !(eta >= 0.0) || !(aca_eps > 0.0) ||
+        !std::isfinite(eta) || !std::isfinite(aca_eps))
         return HMAT_ERR_ARG;
     for (int64_t i = 0; i < n; ++i) {
         if (!std::isfinite(areas[i]) || areas[i] < 0.0) return HMAT_ERR_ARG;
@@ -273,76 +275,145 @@ extern "C" int hmat_build(int64_t n, const double *centroids, const double *area
             if (!std::isfinite(centroids[3 * i + d])) return HMAT_ERR_ARG;
     }
     try {
-        std::vector<int64_t> perm;
         std::vector<Node> nodes;
-        TreeBuilder(n, centroids, leaf).build(perm, nodes);
+        TreeBuilder(n, centroids, leaf).build(plan.perm, nodes);
         std::vector<BlockRec> blocks;
         partition(nodes, eta, blocks);
-        Kernel K{centroids, areas};
-        const int64_t nb = (int64_t)blocks.size();
-#pragma omp parallel for schedule(dynamic, 8)
-        for (int64_t b = 0; b < nb; ++b) fill(blocks[b], K, perm, aca_eps);
+        plan.clusters.resize(4 * nodes.size());
+        for (size_t k = 0; k < nodes.size(); ++k) {
+            plan.clusters[4 * k + 0] = nodes[k].begin;
+            plan.clusters[4 * k + 1] = nodes[k].end;
+            plan.clusters[4 * k + 2] = nodes[k].child0;
+            plan.clusters[4 * k + 3] = nodes[k].child1;
+        }
+        plan.blocks.resize(4 * blocks.size());
+        plan.lowrank.resize(blocks.size());
+        for (size_t b = 0; b < blocks.size(); ++b) {
+            plan.blocks[4 * b + 0] = blocks[b].is;
+            plan.blocks[4 * b + 1] = blocks[b].ie;
+            plan.blocks[4 * b + 2] = blocks[b].js;
+            plan.blocks[4 * b + 3] = blocks[b].je;
+            plan.lowrank[b] = (uint8_t)blocks[b].kind;
+        }
+        plan.n = n;
+        plan.leaf = leaf;
+        plan.eta = eta;
+        plan.aca_eps = aca_eps;
+    } catch (const std::bad_alloc &) {
+        return HMAT_ERR_NOMEM;
+    }
+    return HMAT_OK;
+}
 
-        int64_t ndata = 0, dense_entries = 0, lr_entries = 0, rank_sum = 0, rank_max = 0;
-        for (auto &b : blocks) {
-            ndata += (int64_t)b.data.size();
-            if (b.kind == 0) dense_entries += (int64_t)b.data.size();
-            else {
-                lr_entries += (int64_t)b.data.size();
-                rank_sum += b.rank;
-                rank_max = std::max(rank_max, b.rank);
-            }
+int serialize_blob(const BuildPlan &plan, const std::vector<int64_t> &kind, const std::vector<int64_t> &rank,
+                   char **out, size_t *out_bytes, std::vector<int64_t> &data_off, int64_t *off_data_bytes) {
+    const int64_t n = plan.n, nb = (int64_t)kind.size(), nc = (int64_t)plan.clusters.size() / 4;
+    int64_t ndata = 0, dense_entries = 0, lr_entries = 0, rank_sum = 0, rank_max = 0;
+    data_off.resize(nb);
+    for (int64_t b = 0; b < nb; ++b) {
+        const int64_t *e = plan.blocks.data() + 4 * b;
+        const int64_t m = e[1] - e[0], w = e[3] - e[2];
+        const int64_t cnt = kind[b] == 0 ? m * w : rank[b] * (m + w);
+        data_off[b] = ndata;
+        ndata += cnt;
+        if (kind[b] == 0) dense_entries += cnt;
+        else {
+            lr_entries += cnt;
+            rank_sum += rank[b];
+            rank_max = std::max(rank_max, rank[b]);
         }
-        const int64_t nc = (int64_t)nodes.size();
-        const int64_t off_perm = hmat_internal::kBlobHeaderBytes;
-        const int64_t off_clusters = align64(off_perm + 8 * n);
-        const int64_t off_blocks = align64(off_clusters + 32 * nc);
-        const int64_t off_data = align64(off_blocks + 64 * nb);
-        const int64_t total = align64(off_data + 8 * ndata);
-        char *buf = (char *)std::calloc((size_t)total, 1);
-        if (!buf) return HMAT_ERR_NOMEM;
-        hmat_internal::BlobHeader hdr{};
-        std::memcpy(hdr.magic, hmat_internal::kBlobMagic, 8);
-        hdr.version = 1;
-        hdr.header_bytes = hmat_internal::kBlobHeaderBytes;
-        hdr.n = n;
-        hdr.nclusters = nc;
-        hdr.nblocks = nb;
-        hdr.ndata = ndata;
-        hdr.leaf = leaf;
-        hdr.eta = eta;
-        hdr.aca_eps = aca_eps;
-        hdr.off_perm = off_perm;
-        hdr.off_clusters = off_clusters;
-        hdr.off_blocks = off_blocks;
-        hdr.off_data = off_data;
-        hdr.total_bytes = total;
-        hdr.dense_entries = dense_entries;
-        hdr.lr_entries = lr_entries;
-        hdr.rank_sum = rank_sum;
-        hdr.rank_max = rank_max;
-        std::memcpy(buf, &hdr, sizeof(hdr));
-        std::memcpy(buf + off_perm, perm.data(), 8 * n);
-        int64_t *cl = (int64_t *)(buf + off_clusters);
-        for (int64_t k = 0; k < nc; ++k) {
-            cl[4 * k + 0] = nodes[k].begin;
-            cl[4 * k + 1] = nodes[k].end;
-            cl[4 * k + 2] = nodes[k].child0;
-            cl[4 * k + 3] = nodes[k].child1;
-        }
-        int64_t *bt = (int64_t *)(buf + off_blocks);
-        double *data = (double *)(buf + off_data);
-        int64_t pos = 0;
+    }
+    const int64_t off_perm = kBlobHeaderBytes;
+    const int64_t off_clusters = align64(off_perm + 8 * n);
+    const int64_t off_blocks = align64(off_clusters + 32 * nc);
+    const int64_t off_data = align64(off_blocks + 64 * nb);
+    const int64_t total = align64(off_data + 8 * ndata);
+    char *buf = (char *)std::calloc((size_t)total, 1);
+    if (!buf) return HMAT_ERR_NOMEM;
+    BlobHeader hdr{};
+    std::memcpy(hdr.magic, kBlobMagic, 8);
+    hdr.version = 1;
+    hdr.header_bytes = kBlobHeaderBytes;
+    hdr.n = n;
+    hdr.nclusters = nc;
+    hdr.nblocks = nb;
+    hdr.ndata = ndata;
+    hdr.leaf = plan.leaf;
+    hdr.eta = plan.eta;
+    hdr.aca_eps = plan.aca_eps;
+    hdr.off_perm = off_perm;
+    hdr.off_clusters = off_clusters;
+    hdr.off_blocks = off_blocks;
+    hdr.off_data = off_data;
+    hdr.total_bytes = total;
+    hdr.dense_entries = dense_entries;
+    hdr.lr_entries = lr_entries;
+    hdr.rank_sum = rank_sum;
+    hdr.rank_max = rank_max;
+    std::memcpy(buf, &hdr, sizeof(hdr));
+    std::memcpy(buf + off_perm, plan.perm.data(), 8 * n);
+    std::memcpy(buf + off_clusters, plan.clusters.data(), 32 * nc);
+    int64_t *bt = (int64_t *)(buf + off_blocks);
+    for (int64_t b = 0; b < nb; ++b) {
+        int64_t *e = bt + 8 * b;
+        const int64_t *pe = plan.blocks.data() + 4 * b;
+        e[0] = pe[0]; e[1] = pe[1]; e[2] = pe[2]; e[3] = pe[3];
+        e[4] = kind[b]; e[5] = kind[b] == 0 ? 0 : rank[b]; e[6] = data_off[b]; e[7] = 0;
+    }
+    *out = buf;
+    *out_bytes = (size_t)total;
+    *off_data_bytes = off_data;
+    return HMAT_OK;
+}
+
+int host_block_data(const BuildPlan &plan, int64_t b, const double *centroids, const double *areas, int64_t *kind,
+                    int64_t *rank, std::vector<double> &data) {
+    try {
+        const int64_t *e = plan.blocks.data() + 4 * b;
+        BlockRec r{e[0], e[1], e[2], e[3], (int)plan.lowrank[b], 0, {}};
+        fill(r, Kernel{centroids, areas}, plan.perm, plan.aca_eps);
+        *kind = r.kind;
+        *rank = r.rank;
+        data = std::move(r.data);
+    } catch (const std::bad_alloc &) {
+        return HMAT_ERR_NOMEM;
+    }
+    return HMAT_OK;
+}
+
+}  // namespace hmat_internal
+
+extern "C" int hmat_build(int64_t n, const double *centroids, const double *areas, int32_t leaf, double eta,
+                          double aca_eps, void **blob, size_t *blob_bytes) {
+    if (!blob || !blob_bytes) return HMAT_ERR_ARG;
+    hmat_internal::BuildPlan plan;
+    int st = hmat_internal::plan_build(n, centroids, areas, leaf, eta, aca_eps, plan);
+    if (st != HMAT_OK) return st;
+    try {
+        const int64_t nb = (int64_t)plan.lowrank.size();
+        std::vector<BlockRec> blocks(nb);
         for (int64_t b = 0; b < nb; ++b) {
-            const BlockRec &r = blocks[b];
-            int64_t *e = bt + 8 * b;
-            e[0] = r.is; e[1] = r.ie; e[2] = r.js; e[3] = r.je;
-            e[4] = r.kind; e[5] = r.rank; e[6] = pos; e[7] = 0;
-            std::memcpy(data + pos, r.data.data(), 8 * r.data.size());
-            pos += (int64_t)r.data.size();
+            const int64_t *e = plan.blocks.data() + 4 * b;
+            blocks[b] = BlockRec{e[0], e[1], e[2], e[3], (int)plan.lowrank[b], 0, {}};
         }
+        Kernel K{centroids, areas};
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int64_t b = 0; b < nb; ++b) fill(blocks[b], K, plan.perm, aca_eps);
+        std::vector<int64_t> kind(nb), rank(nb), off;
+        for (int64_t b = 0; b < nb; ++b) {
+            kind[b] = blocks[b].kind;
+            rank[b] = blocks[b].rank;
+        }
+        char *buf = nullptr;
+        size_t total = 0;
+        int64_t off_data = 0;
+        st = hmat_internal::serialize_blob(plan, kind, rank, &buf, &total, off, &off_data);
+        if (st != HMAT_OK) return st;
+        double *data = (double *)(buf + off_data);
+        for (int64_t b = 0; b < nb; ++b)
+            std::memcpy(data + off[b], blocks[b].data.data(), 8 * blocks[b].data.size());
         *blob = buf;
-        *blob_bytes = (size_t)total;
+        *blob_bytes = total;
         return HMAT_OK;
     } catch (const std::bad_alloc &) {
         return HMAT_ERR_NOMEM;

@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+struct hmat_build_device_info;
+
 namespace hmat_internal {
 
 constexpr int kMaxLeaf = 64;               // rows of a leaf cluster the kernels accept
@@ -24,6 +26,31 @@ struct BlobHeader {
 };
 static_assert(sizeof(BlobHeader) <= kBlobHeaderBytes, "header too large");
 
+// Cluster tree and block partition of the collocation H-matrix (host), the
+// part of the build shared by the host builder and the device ACA builder.
+struct BuildPlan {
+    int64_t n = 0;
+    int32_t leaf = 0;
+    double eta = 0.0, aca_eps = 0.0;
+    std::vector<int64_t> perm;      // cluster order -> original index
+    std::vector<int64_t> clusters;  // [nc][4] begin, end, child0, child1
+    std::vector<int64_t> blocks;    // [nb][4] i_s, i_e, j_s, j_e (partition order)
+    std::vector<uint8_t> lowrank;   // per block: 1 admissible (ACA), 0 dense
+};
+// Validates the arguments as hmat_build does.
+int plan_build(int64_t n, const double *centroids, const double *areas, int32_t leaf, double eta, double aca_eps,
+               BuildPlan &plan);
+// A blob buffer (calloc'ed) with header, perm, clusters and block table written
+// for the given kinds (0 dense, 1 low rank) and ranks; data_off[b] is block b's
+// first value, the data section starts at *off_data_bytes and is left zero.
+int serialize_blob(const BuildPlan &plan, const std::vector<int64_t> &kind, const std::vector<int64_t> &rank,
+                   char **out, size_t *out_bytes, std::vector<int64_t> &data_off, int64_t *off_data_bytes);
+
+// The host builder's ACA and dense fill of block b of the plan (kind 0 dense,
+// 1 low rank; data as in the blob).
+int host_block_data(const BuildPlan &plan, int64_t b, const double *centroids, const double *areas, int64_t *kind,
+                    int64_t *rank, std::vector<double> &data);
+
 // A validated, read-only view of a blob.
 struct BlobView {
     const BlobHeader *h = nullptr;
@@ -36,7 +63,14 @@ struct BlobView {
     bool pow2 = true;                   // false: arrays stored unscaled
     const int64_t *toff = nullptr;      // per block: first tval of its ranks, or -1
     const double *tval = nullptr;       // d_l of eq. (14)-(16) multiplied into t (eq. 23)
+    // kind 2 blocks (a dense block restricted to some of its columns, stored
+    // #I x e[5] row-major): their e[5] columns, ascending, at dcols[e[7] ...]
+    const int32_t *dcols = nullptr;
 };
+
+// dense blocks: kind 0 (every column) or kind 2 (the columns listed in dcols)
+inline bool block_is_dense(const int64_t *e) { return e[4] == 0 || e[4] == 2; }
+inline int64_t dense_width(const int64_t *e) { return e[4] == 2 ? e[5] : e[3] - e[2]; }
 
 // Validate a blob; on success fill `view`.  Returns an hmat_status.
 int parse_blob(const void *blob, size_t bytes, BlobView &view, std::string *why = nullptr);
@@ -85,8 +119,10 @@ struct LrDesc {
     int32_t pad;
 };
 struct XDst {
-    int32_t goff;   // operand index of x_kappa[0] in g
+    int32_t goff;   // operand index of the slice's first entry in g
     int32_t scale;  // exponent e
+    int32_t cnt;    // operands written: |kappa| for a whole slice, fewer for a column subset
+    int32_t sel;    // -1: x_kappa[0..cnt) in order; else first of cnt local indices in Layout::xsel
 };
 struct P2Desc {
     int64_t off;    // element offset of the panel
@@ -130,6 +166,7 @@ struct Layout {
     std::vector<P1Desc> p1;
     std::vector<P1Run> p1_runs;
     std::vector<XDst> xdst;
+    std::vector<int32_t> xsel;       // local indices of the column-subset slices (XDst::sel)
     std::vector<LrDesc> lr;
     std::vector<int32_t> gdst;
     std::vector<P2Desc> p2;
@@ -174,6 +211,7 @@ struct DerivedSegment {
     std::vector<double> data;
     std::vector<int64_t> toff;    // per block
     std::vector<double> tval;
+    std::vector<int32_t> dcols;   // column lists of the kind 2 blocks
     BlobView view;
     DerivedSegment() = default;
     DerivedSegment(const DerivedSegment &) = delete;

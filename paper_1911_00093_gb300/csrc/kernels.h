@@ -15,6 +15,7 @@ struct DevIndex {
     const P1Desc *p1 = nullptr;     // [nleaves]
     const P1Run *p1_runs = nullptr;
     const XDst *xdst = nullptr;
+    const int32_t *xsel = nullptr;  // local indices of the column-subset operand slices
     const LrDesc *lr = nullptr;     // [nlr]
     const int32_t *gdst = nullptr;
     const int32_t *red_big = nullptr, *red_tasks = nullptr;
@@ -24,9 +25,7 @@ struct DevIndex {
     const GroupDesc *groups = nullptr;  // row groups of the row-group expansion
     int32_t ngroups = 0;
     int32_t p2_shape = 3;           // expansion: 0 per cluster, 1 row-persistent, 2 staged, 3 row groups
-    int32_t p2_groups8 = 0;         // 1: the 8-byte stores use the row groups too (tuning override)
     int32_t nsm = 1;                // SMs of the device (row-persistent grid = nsm x p2w_blocks)
-    int32_t p1_threads = 0;         // BF16 projection CTA size override (0: the default)
     int32_t max_leaf = 0;           // rows of the widest leaf cluster
     int32_t max_ld2 = 0;            // widest phase-2 panel (entries)
 };
@@ -46,24 +45,25 @@ struct DevPanels {
 // BF16 at three CTAs and four vectors measured slower (67.9 vs 57.7 us at L6).
 constexpr int p2w_blocks(Store) { return 4; }
 
-// Phase-2 launch shape of a store: 0 one CTA per leaf row cluster (the 8-byte
-// stores, and any store with HMAT_PHASE2=cluster), 3 row groups (persistent
-// warps over groups of four rows of one cluster sharing each operand load; the
-// default for 2- and 4-byte panels), 1 row-persistent warps over single rows
+// Phase-2 launch shape of a store: 3 row groups (persistent warps over groups
+// of four rows of one cluster sharing each operand load; the default for every
+// store), 0 one CTA per leaf row cluster (HMAT_PHASE2=cluster; also the 8-byte
+// stores under the two shapes below), 1 row-persistent warps over single rows
 // (HMAT_PHASE2=rows), 2 staged (a persistent CTA per SM streaming through shared
 // memory with bulk copies; BF16 and FP32 panels whose rows fit a slot;
 // HMAT_PHASE2=staged).  Measured at L6: BF16 expansion 51.0 us (groups), 57.7
-// (rows), 61.7 (cluster), 100.5 (staged).
+// (rows), 61.7 (cluster), 100.5 (staged); double-float 129.1 (groups) vs 133.3
+// (cluster); IEEE FP64 221.6 vs 277.1.
 constexpr int kStagedSlotBytes = 16384;
 constexpr int kStagedSmemMax = 200 * 1024;  // its ring of slots plus two operand slots
 // raise the launch limits the staged expansion needs (once per process and device)
 cudaError_t prepare_launches();
 inline int phase2_shape(Store s, const DevIndex &ix) {
     if (ix.p2_shape == 0) return 0;
-    if (s == Store::DF || s == Store::F64) return (ix.p2_groups8 && ix.p2_shape == 3) ? 3 : 0;
+    if (ix.p2_shape == 3) return 3;
+    if (s == Store::DF || s == Store::F64) return 0;
     const int esz = s == Store::BF16 ? 2 : 4;
     if (ix.p2_shape == 2 && (s == Store::BF16 || s == Store::F32) && ix.max_ld2 * esz <= kStagedSlotBytes) return 2;
-    if (ix.p2_shape == 3) return 3;
     return 1;
 }
 inline bool phase2_rows(Store s, const DevIndex &ix) { return phase2_shape(s, ix) == 1; }

@@ -106,9 +106,9 @@ void fill_typed(const BlobView &v, const Layout &L, T *q1, T *p2) {
         for (int64_t s = L.p2_slice_ptr[w]; s < L.p2_slice_ptr[w + 1]; ++s) {
             const Layout::Slice &sl = L.p2_slices[s];
             const int64_t *e = bt + 8 * sl.block;
-            const int64_t n = e[3] - e[2], r = e[5];
+            const int64_t r = e[5];
             const double *src = data + e[6];
-            const int64_t ld_src = sl.kind == 0 ? n : r;  // dense row-major m x n, V_m row-major m x r
+            const int64_t ld_src = sl.kind == 0 ? dense_width(e) : r;  // dense row-major, V_m row-major m x r
             const double inv = std::ldexp(1.0, -sl.scale);
             for (int64_t i = 0; i < d.ylen; ++i)
                 for (int64_t k = 0; k < sl.ncols; ++k)
@@ -251,9 +251,9 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
         const int64_t *e = v.blocks + 8 * b;
         int64_t m = e[1] - e[0], w = e[3] - e[2], r = e[5];
         const double *d = v.data + e[6];
-        L.stored_entries += e[4] == 0 ? m * w : r * (m + w);
-        if (e[4] == 0) {
-            if (v.pow2) eD[b] = exponent_of_max(d, m * w);
+        L.stored_entries += block_is_dense(e) ? m * dense_width(e) : r * (m + w);
+        if (block_is_dense(e)) {
+            if (v.pow2) eD[b] = exponent_of_max(d, m * dense_width(e));
         } else if (r > 0) {
             if (v.pow2) {
                 eU[b] = exponent_of_max(d, m * r);
@@ -291,8 +291,8 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
         for (int pass = 0; pass < 2; ++pass) {
             for (int64_t b : by_row[k]) {
                 const int64_t *e = v.blocks + 8 * b;
-                if (e[4] != pass) continue;
-                const int32_t len = (int32_t)(pass == 0 ? e[3] - e[2] : e[5]);
+                if ((block_is_dense(e) ? 0 : 1) != pass) continue;
+                const int32_t len = (int32_t)(pass == 0 ? dense_width(e) : e[5]);
                 col_of[k].push_back({b, (int32_t)col});
                 L.p2_slices.push_back({b, (int32_t)col, len, (int32_t)(d.ybeg - e[0]), pass, pass == 0 ? eD[b] : eU[b]});
                 col += len;
@@ -379,7 +379,7 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
     }
     for (int64_t b = 0; b < nb; ++b) {
         const int64_t *e = v.blocks + 8 * b;
-        if (e[4] != 0) continue;
+        if (!block_is_dense(e)) continue;
         for (int64_t l = leaf_index(e[2]); l < leaf_index(e[3]); ++l) dense_by_col[l].push_back(b);
     }
     L.p1.resize(nleaves);
@@ -412,10 +412,22 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
         d.xdbeg = (int32_t)L.xdst.size();
         for (int64_t b : dense_by_col[k]) {
             const int64_t *e = v.blocks + 8 * b;
+            // the block's stored columns inside kappa: all of them (kind 0), or
+            // the listed ones [a, a + cnt) of its column list (kind 2)
+            int32_t a = (int32_t)(d.xbeg - e[2]), cnt = d.xlen, sel = -1;
+            if (e[4] == 2) {
+                const int32_t *cl = v.dcols + e[7], *ce = cl + e[5];
+                const int32_t *lo = std::lower_bound(cl, ce, d.xbeg), *hi = std::lower_bound(cl, ce, d.xbeg + d.xlen);
+                a = (int32_t)(lo - cl);
+                cnt = (int32_t)(hi - lo);
+                if (cnt == 0) continue;
+                sel = (int32_t)L.xsel.size();
+                for (const int32_t *q = lo; q < hi; ++q) L.xsel.push_back(*q - d.xbeg);
+            }
             for (int64_t rho = leaf_index(e[0]); rho < leaf_index(e[1]); ++rho) {
                 int32_t c = column_in(rho, b);
                 if (c < 0) { if (why) *why = "internal: dense block missing from a row panel"; return HMAT_ERR_BAD_LAYOUT; }
-                L.xdst.push_back({(int32_t)(L.p2[rho].goff + c + (d.xbeg - e[2])), eD[b]});
+                L.xdst.push_back({(int32_t)(L.p2[rho].goff + c + a), eD[b], cnt, sel});
             }
         }
         d.xdcnt = (int32_t)L.xdst.size() - d.xdbeg;
@@ -478,8 +490,14 @@ int check_layout(const Layout &L, std::string *why) {
         if (d.xdbeg < 0 || d.xdcnt < 0 || (int64_t)d.xdbeg + d.xdcnt > (int64_t)L.xdst.size()) return bad("p1 xdst");
         for (int k = 0; k < d.xdcnt; ++k) {
             const XDst &x = L.xdst[d.xdbeg + k];
-            if (x.goff < 0 || (int64_t)x.goff + d.xlen > L.glen || std::abs(x.scale) > kMaxScaleExp) return bad("xdst range");
-            for (int j = 0; j < d.xlen; ++j) {
+            if (x.cnt < 1 || x.cnt > d.xlen || (x.sel < 0 && (x.sel != -1 || x.cnt != d.xlen))) return bad("xdst count");
+            if (x.goff < 0 || (int64_t)x.goff + x.cnt > L.glen || std::abs(x.scale) > kMaxScaleExp) return bad("xdst range");
+            if (x.sel >= 0) {
+                if ((int64_t)x.sel + x.cnt > (int64_t)L.xsel.size()) return bad("xdst selection");
+                for (int j = 0; j < x.cnt; ++j)
+                    if (L.xsel[x.sel + j] < 0 || L.xsel[x.sel + j] >= d.xlen) return bad("xdst selection entry");
+            }
+            for (int j = 0; j < x.cnt; ++j) {
                 if (gw[x.goff + j]) return bad("operand slot written twice");
                 gw[x.goff + j] = 1;
             }

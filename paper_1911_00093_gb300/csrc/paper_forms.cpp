@@ -15,6 +15,11 @@
 //   Method 2-Mixed   all blocks (V' D W'), class M   -
 //   Method 3         dense + ranks with d_i >= d_max 10^-c (eq. 20), FP64
 //                                                    ranks with d_i < d_max 10^-c (eq. 19), class M
+//   dense split      dense columns with weight       the other dense columns and every
+//   (Section 4.5)    >= d_max 10^-c, FP64            low-rank V' D W', class M
+//     (a dense column's weight is max_i |a_ij|, d_max the largest near-field
+//     entry; a block whose columns fall on both sides is stored as two column
+//     subsets, kind 2 blocks with their column lists)
 //
 // Classes (what the kernels compute per stored entry p and operand):
 //   FP64  p FP64, x FP64, FP64 products and sums;
@@ -39,7 +44,7 @@ namespace hmat_internal {
 
 namespace {
 
-bool is_table1(int precision) { return precision >= HMAT_M1_SINGLE && precision <= HMAT_M3_TRUNC; }
+bool is_table1(int precision) { return precision >= HMAT_M1_SINGLE && precision <= HMAT_M3_DENSE; }
 
 // FP32 storage must not overflow; underflow is the precision loss the variant accepts
 bool fits_fp32(const double *a, int64_t cnt) {
@@ -55,6 +60,18 @@ struct SegBuilder {
         const int64_t off = (int64_t)seg->data.size();
         seg->data.insert(seg->data.end(), src, src + m * n);
         seg->blocks.insert(seg->blocks.end(), {e[0], e[1], e[2], e[3], 0, 0, off, 0});
+        seg->toff.push_back(-1);
+    }
+    // the columns `js` (ascending, block-local) of a dense block, as a kind 2 block
+    void add_dense_cols(const int64_t *e, const double *src, const std::vector<int64_t> &js) {
+        const int64_t m = e[1] - e[0], n = e[3] - e[2], k = (int64_t)js.size();
+        const int64_t off = (int64_t)seg->data.size();
+        seg->data.resize(off + m * k);
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t c = 0; c < k; ++c) seg->data[off + i * k + c] = src[i * n + js[c]];
+        const int64_t coff = (int64_t)seg->dcols.size();
+        for (int64_t j : js) seg->dcols.push_back((int32_t)(e[2] + j));
+        seg->blocks.insert(seg->blocks.end(), {e[0], e[1], e[2], e[3], 2, k, off, coff});
         seg->toff.push_back(-1);
     }
     // low-rank block with the ranks `ls` of (V, W) (V #I x r row-major, W r x #J
@@ -93,6 +110,7 @@ void finish(DerivedSegment &s, const BlobView &v) {
     s.view.pow2 = false;
     s.view.toff = s.toff.data();
     s.view.tval = s.tval.data();
+    s.view.dcols = s.dcols.data();
 }
 
 }  // namespace
@@ -101,7 +119,8 @@ int derive_table1(const BlobView &v, int precision, int c, DerivedSegment (&seg)
                   std::string *why) {
     if (!is_table1(precision)) return HMAT_ERR_ARG;
     const bool m3 = precision == HMAT_M3 || precision == HMAT_M3_TRUNC;
-    if (m3 && (c < -1 || c > 16)) {
+    const bool split_dense = precision == HMAT_M3_DENSE;
+    if ((m3 || split_dense) && (c < -1 || c > 16)) {
         if (why) *why = "Method 3 c outside [-1, 16]";
         return HMAT_ERR_ARG;
     }
@@ -117,7 +136,22 @@ int derive_table1(const BlobView &v, int precision, int c, DerivedSegment (&seg)
     case HMAT_M2_MIXED: store[0] = Store::PM; store[1] = Store::PM; break;
     case HMAT_M3: store[0] = Store::F64; store[1] = Store::PM; break;
     case HMAT_M3_TRUNC: store[0] = Store::F64; store[1] = Store::F64; break;
+    case HMAT_M3_DENSE: store[0] = Store::F64; store[1] = Store::PM; lr_seg = 1; break;
     }
+    // dense split: the threshold on the column weights, from the largest entry
+    // of the near field (every dense block)
+    double dense_thr = 0.0;
+    if (split_dense) {
+        double dmax = 0.0;
+        for (int64_t b = 0; b < v.h->nblocks; ++b) {
+            const int64_t *e = v.blocks + 8 * b;
+            if (e[4] != 0) continue;
+            const double *a = v.data + e[6];
+            for (int64_t k = 0; k < (e[1] - e[0]) * (e[3] - e[2]); ++k) dmax = std::max(dmax, std::fabs(a[k]));
+        }
+        dense_thr = dmax * std::pow(10.0, -(double)c);
+    }
+    std::vector<int64_t> j64, j32;
     SegBuilder sb[2] = {{&seg[0]}, {&seg[1]}};
     std::vector<double> Vp, Wp, d;
     std::vector<int64_t> lsA, lsB;
@@ -127,6 +161,29 @@ int derive_table1(const BlobView &v, int precision, int c, DerivedSegment (&seg)
         const int64_t m = e[1] - e[0], n = e[3] - e[2], r = e[5];
         const double *src = data + e[6];
         if (e[4] == 0) {
+            if (split_dense) {
+                // a column is FP64 iff max_i |a_ij| >= d_max 10^-c (eq. 19-20 on W' = I)
+                j64.clear();
+                j32.clear();
+                for (int64_t j = 0; j < n; ++j) {
+                    double w = 0.0;
+                    for (int64_t i = 0; i < m; ++i) w = std::max(w, std::fabs(src[i * n + j]));
+                    (w >= dense_thr ? j64 : j32).push_back(j);
+                }
+                for (int64_t j : j32)
+                    for (int64_t i = 0; i < m; ++i)
+                        if (std::fabs(src[i * n + j]) > (double)FLT_MAX) {
+                            if (why) *why = "dense block outside the FP32 range";
+                            return HMAT_ERR_RANGE;
+                        }
+                if (j32.empty()) sb[0].add_dense(e, src);
+                else if (j64.empty()) sb[1].add_dense(e, src);
+                else {
+                    sb[0].add_dense_cols(e, src, j64);
+                    sb[1].add_dense_cols(e, src, j32);
+                }
+                continue;
+            }
             if (store[dense_seg] != Store::F64 && !fits_fp32(src, m * n)) {
                 if (why) *why = "dense block outside the FP32 range";
                 return HMAT_ERR_RANGE;

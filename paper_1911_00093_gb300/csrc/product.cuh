@@ -15,8 +15,8 @@
 //   phase 2  y_rho = P_rho g_rho with P_rho the rows of the dense blocks (eq. 21)
 //            and of the V_m (eq. 10/24) over rho, g_rho the matching pieces of x
 //            and t; a warp per row, each row of y written once by its owner (eq. 25
-//            without atomics): row-persistent warps over a fixed grid for 2- and
-//            4-byte panels, one CTA per leaf row cluster for 8-byte ones.
+//            without atomics): by default persistent warps over groups of four
+//            rows of one cluster sharing each operand load.
 // Arithmetic per store:
 //   DF    panels are pairs (hi, lo); products and sums in double-float on the
 //         FP32 pipe (the FP64 pipe of GB300 is ~1/60 of FP32);
@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 
 #include "hmat.h"
@@ -332,10 +333,18 @@ template <Store S> __device__ __forceinline__ typename Tr<S>::Part red_to_part(t
 // 128 threads for BF16 panels (8 columns per thread: most clusters need fewer
 // than 128 threads, and small CTAs let more clusters stream at once), else 256
 template <Store S> constexpr int p1_threads() { return S == Store::BF16 ? 128 : 256; }
+// resident CTAs per SM the register budget is held to: 64 registers a thread
+// (BF16, FP32), 48 for the others
+template <Store S> constexpr int p1_min_blocks() {
+    return S == Store::BF16 ? 8 : S == Store::F32 ? 4 : 5;
+}
+constexpr int kP1SmemRuns = 256;  // runs of a cluster staged in shared memory (4 KB)
+constexpr int kP1SmemXd = 64;     // dense-operand slices staged in shared memory
 
 template <Store S, int NT = p1_threads<S>()>
-__global__ void __launch_bounds__(NT) k_phase1(const P1Desc *__restrict__ desc, const P1Run *__restrict__ runs,
-                                                        const XDst *__restrict__ xdst, const LrDesc *__restrict__ lr,
+__global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc *__restrict__ desc, const P1Run *__restrict__ runs,
+                                                        const XDst *__restrict__ xdst, const int32_t *__restrict__ xsel,
+                                                        const LrDesc *__restrict__ lr,
                                                         const int32_t *__restrict__ gdst, const void *__restrict__ q1,
                                                         const typename Tr<S>::Op *__restrict__ xs,
                                                         typename Tr<S>::Part *__restrict__ part,
@@ -346,15 +355,24 @@ __global__ void __launch_bounds__(NT) k_phase1(const P1Desc *__restrict__ desc, 
     using Part = typename Tr<S>::Part;
     constexpr int VW = Tr<S>::VW;
     __shared__ Op xk[kMaxLeaf];  // x_kappa, broadcast to every thread
+    // the cluster's run and dense-operand descriptors, loaded with x_kappa so
+    // that the epilogue's lookups stay on chip (global reads past the limits)
+    __shared__ P1Run rs[kP1SmemRuns];
+    __shared__ XDst xds[kP1SmemXd];
     if (skip_product(S_, mode)) return;
     const P1Desc d = desc[blockIdx.x];
     const int nvec = d.ld / VW;
     const char *base = (const char *)q1 + (size_t)d.off * (16 / VW);
     const size_t row_bytes = (size_t)d.ld * (16 / VW);
+    const bool runs_sm = d.rcnt <= kP1SmemRuns, xd_sm = d.xdcnt <= kP1SmemXd;
     for (int j = threadIdx.x; j < d.xlen; j += blockDim.x) {
         if constexpr (fp32_source(S)) xk[j] = (double)__double2float_rn(xs[d.xbeg + j]);  // Section 3.5
         else xk[j] = xs[d.xbeg + j];
     }
+    if (runs_sm)
+        for (int j = threadIdx.x; j < d.rcnt; j += blockDim.x) rs[j] = runs[d.rbeg + j];
+    if (xd_sm)
+        for (int j = threadIdx.x; j < d.xdcnt; j += blockDim.x) xds[j] = xdst[d.xdbeg + j];
     __syncthreads();
 
     // projections (eq. 9/22): thread = one 16-byte column vector, walk the rows
@@ -373,17 +391,27 @@ __global__ void __launch_bounds__(NT) k_phase1(const P1Desc *__restrict__ desc, 
 #pragma unroll
             for (int e = 0; e < VW; ++e) fold<S>(acc[e]);
         }
-        for (; j < d.xlen; ++j) {
-            int4 raw = ld_stream(col + (size_t)j * row_bytes);
-            Cols<S>::mac(acc, raw, xk[j]);
+        if constexpr (is_table1(S)) {  // FP64-pipe bound: the last rows one at a time
+            for (; j < d.xlen; ++j) Cols<S>::mac(acc, ld_stream(col + (size_t)j * row_bytes), xk[j]);
+        } else if (j < d.xlen) {  // the last rows: one batch of loads in flight, the same sums in row order
+            const int rem = d.xlen - j;
+            int4 raw[7];
+#pragma unroll
+            for (int u = 0; u < 7; ++u)
+                raw[u] = u < rem ? ld_stream(col + (size_t)(j + u) * row_bytes) : make_int4(0, 0, 0, 0);
+#pragma unroll
+            for (int u = 0; u < 7; ++u) {
+                if (u >= rem) break;  // CTA-uniform: no multiply-adds on the padding
+                Cols<S>::mac(acc, raw[u], xk[j + u]);
+            }
         }
         const int c0 = vc * VW;
         if (c0 >= d.R) continue;
-        const P1Run *rk = runs + d.rbeg;
+        const P1Run *rk = runs_sm ? rs : runs + d.rbeg;  // generic pointer: shared or global
         int lo = 0, hi = d.rcnt - 1;  // run holding column c0
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
-            if (__ldg(&rk[mid].col0) <= c0) lo = mid;
+            if (rk[mid].col0 <= c0) lo = mid;
             else hi = mid - 1;
         }
         P1Run rn = rk[lo];
@@ -405,11 +433,12 @@ __global__ void __launch_bounds__(NT) k_phase1(const P1Desc *__restrict__ desc, 
         }
     }
 
-    // the dense-block operands fed by x_kappa (eq. 21 inputs), scaled by 2^e
+    // the dense-block operands fed by x_kappa (eq. 21 inputs), scaled by 2^e: a
+    // whole slice, or the listed entries of a column subset
     for (int t = threadIdx.x; t < d.xdcnt * d.xlen; t += blockDim.x) {
         const int k = t / d.xlen, j = t - k * d.xlen;
-        const XDst x = xdst[d.xdbeg + k];
-        g[x.goff + j] = scale_op<S>(xk[j], x.scale);
+        const XDst x = xd_sm ? xds[k] : xdst[d.xdbeg + k];
+        if (j < x.cnt) g[x.goff + j] = scale_op<S>(xk[x.sel < 0 ? j : __ldg(xsel + x.sel + j)], x.scale);
     }
 }
 
@@ -545,6 +574,33 @@ __device__ __forceinline__ void row_mac<Store::DF>(Acc<Store::DF> &acc, int4 raw
     df_fma(acc.a, v.z, v.w, x.z, x.w);
     if (++acc.n == 4) { renorm(acc.a); acc.n = 0; }
 }
+// row_mac without the per-row fold counter: a caller that advances several rows
+// in step folds them itself (fold<S>) after every kFoldVecs vectors, which
+// gives the same bits as the per-row counters
+constexpr int kFoldVecs = 4;
+template <Store S>
+__device__ __forceinline__ void row_mac_nofold(Acc<S> &acc, int4 raw, const GV<S> &gv) {
+    if constexpr (S == Store::DF) {
+        float4 v = *reinterpret_cast<float4 *>(&raw);
+        df_fma(acc.a, v.x, v.y, gv.v.x, gv.v.y);
+        df_fma(acc.a, v.z, v.w, gv.v.z, gv.v.w);
+    } else if constexpr (S == Store::BF16) {
+        const float4 x0 = gv.a, x1 = gv.b;
+        float c = acc.ch;
+        c = fmaf(bf_lo((uint32_t)raw.x), x0.x, c);
+        c = fmaf(bf_hi((uint32_t)raw.x), x0.y, c);
+        c = fmaf(bf_lo((uint32_t)raw.y), x0.z, c);
+        c = fmaf(bf_hi((uint32_t)raw.y), x0.w, c);
+        c = fmaf(bf_lo((uint32_t)raw.z), x1.x, c);
+        c = fmaf(bf_hi((uint32_t)raw.z), x1.y, c);
+        c = fmaf(bf_lo((uint32_t)raw.w), x1.z, c);
+        c = fmaf(bf_hi((uint32_t)raw.w), x1.w, c);
+        acc.ch = c;
+    } else {
+        row_mac<S>(acc, raw, gv);
+    }
+}
+template <Store S> constexpr bool row_folds() { return S == Store::DF || S == Store::BF16; }
 template <>
 __device__ __forceinline__ void row_mac<Store::F64>(Acc<Store::F64> &acc, int4 raw, const GV<Store::F64> &gv) {
     double2 v = *reinterpret_cast<double2 *>(&raw);
@@ -805,6 +861,22 @@ __global__ void __launch_bounds__(kP2Threads, p2w_blocks(S)) k_phase2w(
 // once for the group's rows (the row-persistent kernel loads it per row).
 template <Store S> constexpr int p2g_blocks() { return 4; }
 
+static_assert(sizeof(GroupDesc) == 32 && offsetof(GroupDesc, goff) == 8 && offsetof(GroupDesc, nr) == 20,
+              "GroupDesc is read as eight 32-bit words");
+// a GroupDesc from its words 0..5, held one per lane in lanes 0..5
+__device__ __forceinline__ GroupDesc group_from_words(int32_t word) {
+    GroupDesc d;
+    const uint32_t lo = (uint32_t)__shfl_sync(0xffffffffu, word, 0);
+    const uint32_t hi = (uint32_t)__shfl_sync(0xffffffffu, word, 1);
+    d.off = (int64_t)(((uint64_t)hi << 32) | lo);
+    d.goff = __shfl_sync(0xffffffffu, word, 2);
+    d.ld = __shfl_sync(0xffffffffu, word, 3);
+    d.p0 = __shfl_sync(0xffffffffu, word, 4);
+    d.nr = __shfl_sync(0xffffffffu, word, 5);
+    d.pad[0] = d.pad[1] = 0;
+    return d;
+}
+
 template <Store S>
 __global__ void __launch_bounds__(kP2Threads, p2g_blocks<S>()) k_phase2g(
     int ng, const GroupDesc *__restrict__ groups, const void *__restrict__ p2, const typename Tr<S>::Op *__restrict__ g,
@@ -817,16 +889,34 @@ __global__ void __launch_bounds__(kP2Threads, p2g_blocks<S>()) k_phase2g(
     if (skip_product(S_, mode)) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int W = gridDim.x * kP2Warps;
+    // lane r < nr owns row r of a group: its output index, w and (accum) old y
+    // are loaded at the group's start, so the epilogue waits on no load
     double dw = 0.0, dy = 0.0;
-    for (int t = blockIdx.x * kP2Warps + warp; t < ng; t += W) {
-        const GroupDesc gd = groups[t];
-        const char *base = (const char *)p2 + (size_t)gd.off * esz;
-        const size_t row_bytes = (size_t)gd.ld * esz;
-        const typename Tr<S>::Op *gr = g + gd.goff;
-        const int nv = gd.ld / VW, nr = gd.nr;
+    int t = blockIdx.x * kP2Warps + warp;
+    // the next group's descriptor travels as one word per lane (lanes 0..5)
+    // while this group streams, then is broadcast: one register, not six
+    const int32_t *gwords = reinterpret_cast<const int32_t *>(groups);
+    int32_t word = (lane < 6 && t < ng) ? __ldg(gwords + (size_t)t * 8 + lane) : 0;
+    GroupDesc cur = group_from_words(word);
+    for (; t < ng; t += W) {
+        word = (lane < 6 && t + W < ng) ? __ldg(gwords + (size_t)(t + W) * 8 + lane) : 0;
+        const bool own = lane < cur.nr;
+        const int p = cur.p0 + lane;
+        int q = p;
+        double wl = 0.0, yl = 0.0;
+        if (own) {
+            if (out_perm) q = __ldg(out_perm + p);
+            if (dotmode != 0) wl = __ldg(w + p);
+            if (accum) yl = y[q];  // a later segment adds to the earlier ones' rows
+        }
+        const char *base = (const char *)p2 + (size_t)cur.off * esz;
+        const size_t row_bytes = (size_t)cur.ld * esz;
+        const typename Tr<S>::Op *gr = g + cur.goff;
+        const int nv = cur.ld / VW, nr = cur.nr;
         Acc<S> acc[GR];
 #pragma unroll
         for (int r = 0; r < GR; ++r) acc[r].init();
+        int nf = 0;  // vectors since the rows' last fold (the rows advance in step)
         for (int v = lane; v < nv; v += 32) {
             int4 raw[GR];
 #pragma unroll
@@ -835,36 +925,51 @@ __global__ void __launch_bounds__(kP2Threads, p2g_blocks<S>()) k_phase2g(
             const GV<S> gv = GV<S>::load(gr + v * VW);
 #pragma unroll
             for (int r = 0; r < GR; ++r)
-                if (r < nr) row_mac<S>(acc[r], raw[r], gv);
+                if (r < nr) row_mac_nofold<S>(acc[r], raw[r], gv);
+            if constexpr (row_folds<S>()) {
+                if (++nf == kFoldVecs) {
+#pragma unroll
+                    for (int r = 0; r < GR; ++r) fold<S>(acc[r]);
+                    nf = 0;
+                }
+            }
         }
+        // every lane holds every row total (the butterfly gives all lanes the same bits)
+        double mine = 0.0;
 #pragma unroll
         for (int r = 0; r < GR; ++r) {
             if (r >= nr) break;  // warp-uniform
             const double o = row_total<S>(acc[r]);
-            if (lane == 0) {
-                const int p = gd.p0 + r;
-                const int q = out_perm ? out_perm[p] : p;
-                double out = o;
-                if (accum) out = y[q] + out;  // a later segment adds to the earlier ones' rows
-                y[q] = out;
-                if (dotmode != 0) {
-                    dw += __ldg(w + p) * out;
-                    dy += out * out;
-                }
+            if (lane == r) mine = o;
+        }
+        if (own) {
+            const double out = accum ? yl + mine : mine;
+            y[q] = out;
+            if (dotmode != 0) {
+                dw += wl * out;
+                dy += out * out;
             }
         }
+        cur = group_from_words(word);
     }
     if (dotmode == 0) return;
+    // the warp's share: lanes 0..3 in lane order
+    double a = 0.0, b = 0.0;
+#pragma unroll
+    for (int r = 0; r < GR; ++r) {
+        a += __shfl_sync(0xffffffffu, dw, r);
+        b += __shfl_sync(0xffffffffu, dy, r);
+    }
     if (lane == 0) {
-        wsum[0][warp] = dw;
-        wsum[1][warp] = dy;
+        wsum[0][warp] = a;
+        wsum[1][warp] = b;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int k = 0; k < kP2Warps; ++k) { a += wsum[0][k]; b += wsum[1][k]; }
-        dpart[blockIdx.x] = a;
-        dpart[gridDim.x + blockIdx.x] = b;
+        double sa = 0.0, sb = 0.0;
+        for (int k = 0; k < kP2Warps; ++k) { sa += wsum[0][k]; sb += wsum[1][k]; }
+        dpart[blockIdx.x] = sa;
+        dpart[gridDim.x + blockIdx.x] = sb;
     }
 }
 
@@ -1085,16 +1190,7 @@ int grid_for(int64_t n, int threads, int cap) {
 // launches of one store's product kernels (the dispatchers pick the store)
 template <Store SS>
 void phase1_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st) {
-    if constexpr (SS == Store::BF16) {
-        if (ix.p1_threads == 64 || ix.p1_threads == 96) {  // tuning override (HMAT_P1_THREADS)
-            auto k = ix.p1_threads == 64 ? k_phase1<SS, 64> : k_phase1<SS, 96>;
-            k<<<ix.nleaves, ix.p1_threads, 0, st>>>(ix.p1, ix.p1_runs, ix.xdst, ix.lr, ix.gdst, P.q1,
-                                                   (const typename Tr<SS>::Op *)P.xs, (typename Tr<SS>::Part *)P.part,
-                                                   (typename Tr<SS>::Op *)P.g, ix.tscale, skipS, mode);
-            return;
-        }
-    }
-    k_phase1<SS><<<ix.nleaves, p1_threads<SS>(), 0, st>>>(ix.p1, ix.p1_runs, ix.xdst, ix.lr, ix.gdst, P.q1,
+    k_phase1<SS><<<ix.nleaves, p1_threads<SS>(), 0, st>>>(ix.p1, ix.p1_runs, ix.xdst, ix.xsel, ix.lr, ix.gdst, P.q1,
                                                           (const typename Tr<SS>::Op *)P.xs,
                                                           (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g,
                                                           ix.tscale, skipS, mode);

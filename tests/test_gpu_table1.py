@@ -28,8 +28,9 @@ VARIANTS = [("m1_single", "M1_SINGLE", None), ("m1_mixed", "M1_MIXED", None),
             ("m2_double", "M2_DOUBLE", None), ("m2_single", "M2_SINGLE", None),
             ("m2_mixed", "M2_MIXED", None),
             ("m3", "M3", -1), ("m3", "M3", 1), ("m3", "M3", 3), ("m3", "M3", 7),
-            ("m3_trunc", "M3_TRUNC", 1), ("m3_trunc", "M3_TRUNC", 3)]
-FP64_SUMS = ("M2_DOUBLE", "M2_SINGLE", "M2_MIXED", "M3", "M3_TRUNC")
+            ("m3_trunc", "M3_TRUNC", 1), ("m3_trunc", "M3_TRUNC", 3),
+            ("m3_dense", "M3_DENSE", 0), ("m3_dense", "M3_DENSE", 1)]
+FP64_SUMS = ("M2_DOUBLE", "M2_SINGLE", "M2_MIXED", "M3", "M3_TRUNC", "M3_DENSE")
 
 
 def _ids(v):
@@ -106,6 +107,34 @@ def test_method3_limits(hcache, oracle_mod):
     assert e.value.status == 1
 
 
+def test_dense_split_limits(hcache, oracle_mod):
+    """Section 4.5's dense split at its ends: c = -1 demotes every dense column
+    (Method 2-Mixed), c = 16 none (Method 3 with c = -1); c = 1 stores the near
+    field as two column subsets, between the two in accuracy and in bytes."""
+    torch = need_gpu()
+    P = lib()
+    mesh = synth.icosphere(4)
+    H = hcache(mesh)
+    blob = oracle_blob(H)
+    x = np.random.default_rng(8).standard_normal(mesh.n)
+    y64 = H.matvec(x, oracle_mod.M1_DOUBLE)
+    hs = {c: P.hmat_upload(blob, "m3_dense", c) for c in (-1, 1, 16)}
+    try:
+        y = {c: _gpu_matvec(P, torch, h, x) for c, h in hs.items()}
+        assert rel(y[-1], H.matvec(x, oracle_mod.M2_MIXED)) <= 1e-12
+        assert rel(y[16], H.matvec(x, oracle_mod.M3, -1)) <= 1e-12
+        assert rel(y[1], H.matvec(x, oracle_mod.M3_DENSE, 1)) <= 1e-12
+        assert rel(y[16], y64) < rel(y[1], y64) < rel(y[-1], y64)
+        st = {c: P.hmat_info(h)["stored_bytes"] for c, h in hs.items()}
+        assert st[-1] < st[1] < st[16]
+    finally:
+        for h in hs.values():
+            P.hmat_destroy(h)
+    with pytest.raises(P.HmatError) as e:
+        P.hmat_upload(blob, "m3_dense", 17)
+    assert e.value.status == 1
+
+
 def test_table1_host_pointers_and_determinism(hcache, oracle_mod):
     """A two-segment variant through host pointers gives the device result's bits,
     and repeated products are bitwise identical (no atomics)."""
@@ -132,7 +161,7 @@ def test_table1_host_pointers_and_determinism(hcache, oracle_mod):
 @pytest.mark.parametrize("form,variant,c", [("m1_single", "M1_SINGLE", None), ("m1_mixed", "M1_MIXED", None),
                                             ("m2_double", "M2_DOUBLE", None), ("m2_single", "M2_SINGLE", None),
                                             ("m2_mixed", "M2_MIXED", None), ("m3", "M3", -1), ("m3", "M3", 2),
-                                            ("m3_trunc", "M3_TRUNC", 3)],
+                                            ("m3_trunc", "M3_TRUNC", 3), ("m3_dense", "M3_DENSE", 1)],
                          ids=lambda v: str(v))
 def test_table1_solve(hcache, oracle_mod, form, variant, c):
     """BiCG-STAB with the variant as the iterated operator and the FP64
@@ -173,7 +202,8 @@ def test_table1_full_size(oracle_mod):
     H = oracle_mod.HMatrix(mesh.centroid, mesh.area)
     x = synth.rhs_one_plus_half_z(mesh) + 0.1 * np.random.default_rng(16).standard_normal(mesh.n)
     y64 = H.matvec(x, oracle_mod.M1_DOUBLE)
-    for form, variant, c in (("m2_mixed", "M2_MIXED", None), ("m3", "M3", -1), ("m1_single", "M1_SINGLE", None)):
+    for form, variant, c in (("m2_mixed", "M2_MIXED", None), ("m3", "M3", -1), ("m1_single", "M1_SINGLE", None),
+                             ("m3_dense", "M3_DENSE", 1)):
         h = P.hmat_upload(blob, form, c)
         try:
             y = _gpu_matvec(P, torch, h, x)
