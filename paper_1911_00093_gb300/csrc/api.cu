@@ -122,6 +122,8 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
     if (p2env && std::strcmp(p2env, "rows") == 0) ix.p2_shape = 1;
     if (p2env && std::strcmp(p2env, "staged") == 0) ix.p2_shape = 2;
     if (p2env && std::strcmp(p2env, "groups") == 0) ix.p2_shape = 3;
+    const char *p1env = std::getenv("HMAT_PHASE1");
+    ix.p1_persistent = p1env && std::strcmp(p1env, "persistent") == 0;
     int nsm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     ix.nsm = std::max(1, nsm);

@@ -54,25 +54,31 @@ void launch_phase2(Store s, const DevIndex &ix, const DevPanels &P, double *y, c
 
 // ------------------------------------------------------------------------
 // BiCG-STAB vector kernels: FP64 arithmetic, deterministic two-stage
-// reductions (per-block tree, then the last block sums the block partials in
-// block order)
+// reductions (per block: warp butterflies, then the warps in order; then the
+// last block sums the block partials in block order)
 // ------------------------------------------------------------------------
 namespace {
 
+// Every thread gets the CTA's sums: a butterfly inside each warp (partners add
+// the same two values, so every lane holds the same bits), then the warp sums
+// in warp order.  sh: NV * (kVecThreads / 32) doubles; ends with a barrier.
 template <int NV>
 __device__ __forceinline__ void block_reduce(double (&v)[NV], double *sh) {
-    // sh: NV * kVecThreads doubles
+    constexpr int W = kVecThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < NV; ++q) sh[q * kVecThreads + threadIdx.x] = v[q];
-    __syncthreads();
-    for (int s = kVecThreads / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-#pragma unroll
-            for (int q = 0; q < NV; ++q) sh[q * kVecThreads + threadIdx.x] += sh[q * kVecThreads + threadIdx.x + s];
-        __syncthreads();
+    for (int q = 0; q < NV; ++q) {
+        for (int m = 16; m >= 1; m >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], m);
+        if (lane == 0) sh[q * W + warp] = v[q];
     }
+    __syncthreads();
 #pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] = sh[q * kVecThreads];
+    for (int q = 0; q < NV; ++q) {
+        double t = 0.0;
+        for (int k = 0; k < W; ++k) t += sh[q * W + k];
+        v[q] = t;
+    }
+    __syncthreads();
 }
 
 // Block partials -> last block; returns true in the last block, where tot[] holds the totals.
@@ -112,8 +118,7 @@ __device__ __forceinline__ void share_sum(const double *__restrict__ dpart, int 
         v[q] = 0.0;
         for (int k = threadIdx.x; k < ndp; k += blockDim.x) v[q] += __ldg(dpart + (size_t)q * ndp + k);
     }
-    block_reduce<NV>(v, sh);
-    __syncthreads();  // sh is reused by the caller
+    block_reduce<NV>(v, sh);  // ends with a barrier: sh is free for the caller
 }
 
 __device__ __forceinline__ bool run_stopped(const SolverScalars *S) {

@@ -26,6 +26,7 @@ struct DevIndex {
     int32_t ngroups = 0;
     int32_t p2_shape = 3;           // expansion: 0 per cluster, 1 row-persistent, 2 staged, 3 row groups
     int32_t nsm = 1;                // SMs of the device (row-persistent grid = nsm x p2w_blocks)
+    int32_t p1_persistent = 0;      // projection: 1 persistent CTAs with staged prologues (HMAT_PHASE1)
     int32_t max_leaf = 0;           // rows of the widest leaf cluster
     int32_t max_ld2 = 0;            // widest phase-2 panel (entries)
 };

@@ -341,48 +341,32 @@ template <Store S> constexpr int p1_min_blocks() {
 constexpr int kP1SmemRuns = 256;  // runs of a cluster staged in shared memory (4 KB)
 constexpr int kP1SmemXd = 64;     // dense-operand slices staged in shared memory
 
-template <Store S, int NT = p1_threads<S>()>
-__global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc *__restrict__ desc, const P1Run *__restrict__ runs,
-                                                        const XDst *__restrict__ xdst, const int32_t *__restrict__ xsel,
-                                                        const LrDesc *__restrict__ lr,
-                                                        const int32_t *__restrict__ gdst, const void *__restrict__ q1,
-                                                        const typename Tr<S>::Op *__restrict__ xs,
-                                                        typename Tr<S>::Part *__restrict__ part,
-                                                        typename Tr<S>::Op *__restrict__ g,
-                                                        const double *__restrict__ tscale, const SolverScalars *S_,
-                                                        int mode) {
+// One leaf column cluster of the projection, its x slice, runs and dense
+// slices already staged in shared memory (rs / xds null: read them from global
+// memory): the column vectors' dot products with x_kappa and their
+// destinations, then the dense-block operand slices.
+template <Store S, int NT>
+__device__ __forceinline__ void p1_cluster(const P1Desc &d, const typename Tr<S>::Op *xk, const P1Run *rs,
+                                           const XDst *xds, const P1Run *__restrict__ runs,
+                                           const XDst *__restrict__ xdst, const int32_t *__restrict__ xsel,
+                                           const LrDesc *__restrict__ lr, const int32_t *__restrict__ gdst,
+                                           const void *__restrict__ q1, typename Tr<S>::Part *__restrict__ part,
+                                           typename Tr<S>::Op *__restrict__ g, const double *__restrict__ tscale) {
     using Op = typename Tr<S>::Op;
     using Part = typename Tr<S>::Part;
     constexpr int VW = Tr<S>::VW;
-    __shared__ Op xk[kMaxLeaf];  // x_kappa, broadcast to every thread
-    // the cluster's run and dense-operand descriptors, loaded with x_kappa so
-    // that the epilogue's lookups stay on chip (global reads past the limits)
-    __shared__ P1Run rs[kP1SmemRuns];
-    __shared__ XDst xds[kP1SmemXd];
-    if (skip_product(S_, mode)) return;
-    const P1Desc d = desc[blockIdx.x];
-    const int nvec = d.ld / VW;
+    const int nvec = d.ld / VW, xlen = d.xlen, R = d.R, rcnt = d.rcnt;
     const char *base = (const char *)q1 + (size_t)d.off * (16 / VW);
     const size_t row_bytes = (size_t)d.ld * (16 / VW);
-    const bool runs_sm = d.rcnt <= kP1SmemRuns, xd_sm = d.xdcnt <= kP1SmemXd;
-    for (int j = threadIdx.x; j < d.xlen; j += blockDim.x) {
-        if constexpr (fp32_source(S)) xk[j] = (double)__double2float_rn(xs[d.xbeg + j]);  // Section 3.5
-        else xk[j] = xs[d.xbeg + j];
-    }
-    if (runs_sm)
-        for (int j = threadIdx.x; j < d.rcnt; j += blockDim.x) rs[j] = runs[d.rbeg + j];
-    if (xd_sm)
-        for (int j = threadIdx.x; j < d.xdcnt; j += blockDim.x) xds[j] = xdst[d.xdbeg + j];
-    __syncthreads();
 
     // projections (eq. 9/22): thread = one 16-byte column vector, walk the rows
-    for (int vc = threadIdx.x; vc < nvec; vc += blockDim.x) {
+    for (int vc = threadIdx.x; vc < nvec; vc += NT) {
         Acc<S> acc[VW];
 #pragma unroll
         for (int e = 0; e < VW; ++e) acc[e].init();
         const char *col = base + (size_t)vc * 16;
         int j = 0;
-        for (; j + 8 <= d.xlen; j += 8) {
+        for (; j + 8 <= xlen; j += 8) {
             int4 raw[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) raw[u] = ld_stream(col + (size_t)(j + u) * row_bytes);
@@ -392,9 +376,9 @@ __global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc 
             for (int e = 0; e < VW; ++e) fold<S>(acc[e]);
         }
         if constexpr (is_table1(S)) {  // FP64-pipe bound: the last rows one at a time
-            for (; j < d.xlen; ++j) Cols<S>::mac(acc, ld_stream(col + (size_t)j * row_bytes), xk[j]);
-        } else if (j < d.xlen) {  // the last rows: one batch of loads in flight, the same sums in row order
-            const int rem = d.xlen - j;
+            for (; j < xlen; ++j) Cols<S>::mac(acc, ld_stream(col + (size_t)j * row_bytes), xk[j]);
+        } else if (j < xlen) {  // the last rows: one batch of loads in flight, the same sums in row order
+            const int rem = xlen - j;
             int4 raw[7];
 #pragma unroll
             for (int u = 0; u < 7; ++u)
@@ -406,9 +390,9 @@ __global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc 
             }
         }
         const int c0 = vc * VW;
-        if (c0 >= d.R) continue;
-        const P1Run *rk = runs_sm ? rs : runs + d.rbeg;  // generic pointer: shared or global
-        int lo = 0, hi = d.rcnt - 1;  // run holding column c0
+        if (c0 >= R) continue;
+        const P1Run *rk = rs ? rs : runs + d.rbeg;  // generic pointer: shared or global
+        int lo = 0, hi = rcnt - 1;  // run holding column c0
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
             if (rk[mid].col0 <= c0) lo = mid;
@@ -418,7 +402,7 @@ __global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc 
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
             const int c = c0 + e;
-            if (c < d.R) {
+            if (c < R) {
                 while (c >= rn.col0 + rn.len) rn = rk[++lo];
                 const int l = c - rn.col0;
                 const Part pv = to_part<S>(acc[e]);
@@ -435,11 +419,115 @@ __global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc 
 
     // the dense-block operands fed by x_kappa (eq. 21 inputs), scaled by 2^e: a
     // whole slice, or the listed entries of a column subset
-    for (int t = threadIdx.x; t < d.xdcnt * d.xlen; t += blockDim.x) {
-        const int k = t / d.xlen, j = t - k * d.xlen;
-        const XDst x = xd_sm ? xds[k] : xdst[d.xdbeg + k];
+    const int xdcnt = d.xdcnt;
+    for (int t = threadIdx.x; t < xdcnt * xlen; t += NT) {
+        const int k = t / xlen, j = t - k * xlen;
+        const XDst x = xds ? xds[k] : xdst[d.xdbeg + k];
         if (j < x.cnt) g[x.goff + j] = scale_op<S>(xk[x.sel < 0 ? j : __ldg(xsel + x.sel + j)], x.scale);
     }
+}
+
+template <Store S, int NT = p1_threads<S>()>
+__global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc *__restrict__ desc, const P1Run *__restrict__ runs,
+                                                        const XDst *__restrict__ xdst, const int32_t *__restrict__ xsel,
+                                                        const LrDesc *__restrict__ lr,
+                                                        const int32_t *__restrict__ gdst, const void *__restrict__ q1,
+                                                        const typename Tr<S>::Op *__restrict__ xs,
+                                                        typename Tr<S>::Part *__restrict__ part,
+                                                        typename Tr<S>::Op *__restrict__ g,
+                                                        const double *__restrict__ tscale, const SolverScalars *S_,
+                                                        int mode) {
+    using Op = typename Tr<S>::Op;
+    __shared__ Op xk[kMaxLeaf];  // x_kappa, broadcast to every thread
+    // the cluster's run and dense-operand descriptors, loaded with x_kappa so
+    // that the epilogue's lookups stay on chip (global reads past the limits)
+    __shared__ P1Run rs[kP1SmemRuns];
+    __shared__ XDst xds[kP1SmemXd];
+    if (skip_product(S_, mode)) return;
+    const P1Desc d = desc[blockIdx.x];
+    const bool runs_sm = d.rcnt <= kP1SmemRuns, xd_sm = d.xdcnt <= kP1SmemXd;
+    for (int j = threadIdx.x; j < d.xlen; j += NT) {
+        if constexpr (fp32_source(S)) xk[j] = (double)__double2float_rn(xs[d.xbeg + j]);  // Section 3.5
+        else xk[j] = xs[d.xbeg + j];
+    }
+    if (runs_sm)
+        for (int j = threadIdx.x; j < d.rcnt; j += NT) rs[j] = runs[d.rbeg + j];
+    if (xd_sm)
+        for (int j = threadIdx.x; j < d.xdcnt; j += NT) xds[j] = xdst[d.xdbeg + j];
+    __syncthreads();
+    p1_cluster<S, NT>(d, xk, runs_sm ? rs : nullptr, xd_sm ? xds : nullptr, runs, xdst, xsel, lr, gdst, q1, part, g,
+                      tscale);
+}
+
+// asynchronous global -> shared copies (cp.async; 4, 8 or 16 bytes, both
+// addresses aligned to the size), completed by cp_async_wait_all
+template <int B> __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (B == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(gmem), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Persistent projection: CTA b takes the clusters b, b + G, b + 2G, ... (G
+// CTAs), and while it works on one cluster the next one's x slice, runs and
+// dense slices are already on their way into the other half of a double
+// buffer (cp.async), the descriptor two clusters ahead into a third slot; so a
+// cluster starts streaming without the two dependent loads of its prologue.
+// The same arithmetic per cluster as k_phase1, so the same bits.
+template <Store S, int NT = p1_threads<S>()>
+__global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1p(
+    int ncl, const P1Desc *__restrict__ desc, const P1Run *__restrict__ runs, const XDst *__restrict__ xdst,
+    const int32_t *__restrict__ xsel, const LrDesc *__restrict__ lr, const int32_t *__restrict__ gdst,
+    const void *__restrict__ q1, const typename Tr<S>::Op *__restrict__ xs, typename Tr<S>::Part *__restrict__ part,
+    typename Tr<S>::Op *__restrict__ g, const double *__restrict__ tscale, const SolverScalars *S_, int mode) {
+    using Op = typename Tr<S>::Op;
+    static_assert(sizeof(P1Desc) == 48 && sizeof(P1Run) == 16 && sizeof(XDst) == 16, "cp.async granules");
+    __shared__ __align__(16) Op xk[2][kMaxLeaf];
+    __shared__ __align__(16) P1Run rs[2][kP1SmemRuns];
+    __shared__ __align__(16) XDst xds[2][kP1SmemXd];
+    __shared__ __align__(16) P1Desc dsm[3];
+    if (skip_product(S_, mode)) return;
+    const int G = gridDim.x;
+    int c = blockIdx.x;
+    if (c >= ncl) return;
+    auto stage_desc = [&](int cl, int slot) {
+        if (threadIdx.x < 3) cp_async<16>(reinterpret_cast<int4 *>(&dsm[slot]) + threadIdx.x,
+                                          reinterpret_cast<const int4 *>(desc + cl) + threadIdx.x);
+    };
+    auto stage_body = [&](const P1Desc &d, int b) {
+        for (int j = threadIdx.x; j < d.xlen; j += NT) cp_async<sizeof(Op)>(&xk[b][j], xs + d.xbeg + j);
+        if (d.rcnt <= kP1SmemRuns)
+            for (int j = threadIdx.x; j < d.rcnt; j += NT) cp_async<16>(&rs[b][j], runs + d.rbeg + j);
+        if (d.xdcnt <= kP1SmemXd)
+            for (int j = threadIdx.x; j < d.xdcnt; j += NT) cp_async<16>(&xds[b][j], xdst + d.xdbeg + j);
+    };
+    // the first cluster's descriptor and body, the second's descriptor
+    stage_desc(c, 0);
+    if (c + G < ncl) stage_desc(c + G, 1);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    stage_body(dsm[0], 0);
+    cp_async_commit();
+    int slot = 0, b = 0;
+    for (; c < ncl; c += G) {
+        cp_async_wait_all();  // this cluster's body and the next one's descriptor
+        __syncthreads();      // ... visible to all; the other buffer's last reader is done
+        const P1Desc &d = dsm[slot];
+        if constexpr (fp32_source(S)) {  // Section 3.5: the FP32 copy of x
+            for (int j = threadIdx.x; j < d.xlen; j += NT) xk[b][j] = (double)__double2float_rn(xk[b][j]);
+            __syncthreads();
+        }
+        if (c + G < ncl) stage_body(dsm[(slot + 1) % 3], b ^ 1);
+        if (c + 2 * G < ncl) stage_desc(c + 2 * G, (slot + 2) % 3);
+        cp_async_commit();
+        p1_cluster<S, NT>(d, xk[b], d.rcnt <= kP1SmemRuns ? rs[b] : nullptr, d.xdcnt <= kP1SmemXd ? xds[b] : nullptr,
+                          runs, xdst, xsel, lr, gdst, q1, part, g, tscale);
+        slot = (slot + 1) % 3;
+        b ^= 1;
+    }
+    cp_async_wait_all();
 }
 
 
@@ -664,7 +752,7 @@ __device__ __forceinline__ void phase2_epilogue(const P2Desc &d, Acc<S> (&acc)[M
         const int i = warp + rr * kP2Warps;
         if (i < d.ylen) {
             RT a = row_partial<S>(acc[rr]);
-            for (int m = 1; m < 32; m <<= 1) a = red_xor<S>(a, m, (lane & m) != 0);
+            for (int m = 16; m >= 1; m >>= 1) a = red_xor<S>(a, m, (lane & m) != 0);  // the canonical row order
             double out;
             if constexpr (red_double(S)) out = a;
             else out = df_to_double(a);
@@ -770,7 +858,7 @@ __device__ __forceinline__ double row_total(Acc<S> &acc) {
     using RT = typename RedT<S>::T;
     const int lane = threadIdx.x & 31;
     RT a = row_partial<S>(acc);
-    for (int m = 1; m < 32; m <<= 1) a = red_xor<S>(a, m, (lane & m) != 0);
+    for (int m = 16; m >= 1; m >>= 1) a = red_xor<S>(a, m, (lane & m) != 0);  // the canonical row order
     if constexpr (red_double(S)) return a;
     else return df_to_double(a);
 }
@@ -861,6 +949,43 @@ __global__ void __launch_bounds__(kP2Threads, p2w_blocks(S)) k_phase2w(
 // once for the group's rows (the row-persistent kernel loads it per row).
 template <Store S> constexpr int p2g_blocks() { return 4; }
 
+// Totals of a group's four rows from the lanes' partials with 12 shuffles
+// instead of four butterflies of 5: the xor-16 step keeps rows 0-1 in the lower
+// half-warp and rows 2-3 in the upper, the xor-8 step one row per quarter, and
+// xor 4, 2, 1 finish it.  Every pairing adds the lower lane's value first, in
+// the canonical order (16, 8, 4, 2, 1), so lanes 8r..8r+7 hold exactly row r's
+// canonical total.  Rows past the group's end are zero and unused.
+template <Store S>
+__device__ __forceinline__ double group_totals(Acc<S> (&acc)[kGroupRows], int lane) {
+    static_assert(kGroupRows == 4, "the transposed reduction is written for four rows");
+    using RT = typename RedT<S>::T;
+    RT a[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) a[r] = row_partial<S>(acc[r]);
+    auto shfl = [](RT v, int m) {
+        RT w;
+        if constexpr (red_double(S)) w = __shfl_xor_sync(0xffffffffu, v, m);
+        else { w.s = __shfl_xor_sync(0xffffffffu, v.s, m); w.c = __shfl_xor_sync(0xffffffffu, v.c, m); }
+        return w;
+    };
+    // (lower lane's value) + (upper lane's value), as red_xor adds them
+    auto add = [](RT lo, RT hi) {
+        if constexpr (red_double(S)) return lo + hi;
+        else { red_add<S>(lo, hi); return lo; }
+    };
+    const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0;
+    // xor 16: send the rows the other half keeps
+    const RT r0 = shfl(up16 ? a[0] : a[2], 16), r1 = shfl(up16 ? a[1] : a[3], 16);
+    const RT k0 = up16 ? add(r0, a[2]) : add(a[0], r0);
+    const RT k1 = up16 ? add(r1, a[3]) : add(a[1], r1);
+    // xor 8: one row per quarter-warp
+    const RT rv = shfl(up8 ? k0 : k1, 8);
+    RT k = up8 ? add(rv, k1) : add(k0, rv);
+    for (int m = 4; m >= 1; m >>= 1) k = red_xor<S>(k, m, (lane & m) != 0);
+    if constexpr (red_double(S)) return k;
+    else return df_to_double(k);
+}
+
 static_assert(sizeof(GroupDesc) == 32 && offsetof(GroupDesc, goff) == 8 && offsetof(GroupDesc, nr) == 20,
               "GroupDesc is read as eight 32-bit words");
 // a GroupDesc from its words 0..5, held one per lane in lanes 0..5
@@ -889,8 +1014,8 @@ __global__ void __launch_bounds__(kP2Threads, p2g_blocks<S>()) k_phase2g(
     if (skip_product(S_, mode)) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int W = gridDim.x * kP2Warps;
-    // lane r < nr owns row r of a group: its output index, w and (accum) old y
-    // are loaded at the group's start, so the epilogue waits on no load
+    // lane 8r owns row r of a group (r < nr): its output index, w and (accum)
+    // old y are loaded at the group's start, so the epilogue waits on no load
     double dw = 0.0, dy = 0.0;
     int t = blockIdx.x * kP2Warps + warp;
     // the next group's descriptor travels as one word per lane (lanes 0..5)
@@ -900,8 +1025,8 @@ __global__ void __launch_bounds__(kP2Threads, p2g_blocks<S>()) k_phase2g(
     GroupDesc cur = group_from_words(word);
     for (; t < ng; t += W) {
         word = (lane < 6 && t + W < ng) ? __ldg(gwords + (size_t)(t + W) * 8 + lane) : 0;
-        const bool own = lane < cur.nr;
-        const int p = cur.p0 + lane;
+        const bool own = (lane & 7) == 0 && (lane >> 3) < cur.nr;
+        const int p = cur.p0 + (lane >> 3);
         int q = p;
         double wl = 0.0, yl = 0.0;
         if (own) {
@@ -934,14 +1059,9 @@ __global__ void __launch_bounds__(kP2Threads, p2g_blocks<S>()) k_phase2g(
                 }
             }
         }
-        // every lane holds every row total (the butterfly gives all lanes the same bits)
-        double mine = 0.0;
-#pragma unroll
-        for (int r = 0; r < GR; ++r) {
-            if (r >= nr) break;  // warp-uniform
-            const double o = row_total<S>(acc[r]);
-            if (lane == r) mine = o;
-        }
+        // lanes 8r..8r+7 end with row r's total, the same bits as the
+        // canonical butterfly (group_totals)
+        const double mine = group_totals<S>(acc, lane);
         if (own) {
             const double out = accum ? yl + mine : mine;
             y[q] = out;
@@ -953,12 +1073,12 @@ __global__ void __launch_bounds__(kP2Threads, p2g_blocks<S>()) k_phase2g(
         cur = group_from_words(word);
     }
     if (dotmode == 0) return;
-    // the warp's share: lanes 0..3 in lane order
+    // the warp's share: the owner lanes 0, 8, 16, 24 in lane order
     double a = 0.0, b = 0.0;
 #pragma unroll
     for (int r = 0; r < GR; ++r) {
-        a += __shfl_sync(0xffffffffu, dw, r);
-        b += __shfl_sync(0xffffffffu, dy, r);
+        a += __shfl_sync(0xffffffffu, dw, 8 * r);
+        b += __shfl_sync(0xffffffffu, dy, 8 * r);
     }
     if (lane == 0) {
         wsum[0][warp] = a;
@@ -1190,6 +1310,14 @@ int grid_for(int64_t n, int threads, int cap) {
 // launches of one store's product kernels (the dispatchers pick the store)
 template <Store SS>
 void phase1_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st) {
+    if (ix.p1_persistent) {
+        const int grid = std::min(ix.nleaves, ix.nsm * p1_min_blocks<SS>());
+        k_phase1p<SS><<<grid, p1_threads<SS>(), 0, st>>>(ix.nleaves, ix.p1, ix.p1_runs, ix.xdst, ix.xsel, ix.lr,
+                                                         ix.gdst, P.q1, (const typename Tr<SS>::Op *)P.xs,
+                                                         (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g,
+                                                         ix.tscale, skipS, mode);
+        return;
+    }
     k_phase1<SS><<<ix.nleaves, p1_threads<SS>(), 0, st>>>(ix.p1, ix.p1_runs, ix.xdst, ix.xsel, ix.lr, ix.gdst, P.q1,
                                                           (const typename Tr<SS>::Op *)P.xs,
                                                           (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g,
