@@ -220,7 +220,11 @@ int hmat_blob_stats_get(const void *blob, size_t blob_bytes, hmat_blob_stats *ou
  */
 int hmat_upload(const void *blob, size_t blob_bytes, int32_t precision, hmat_handle *out);
 
-/* hmat_upload with Method 3's c (eq. 19-20; ignored by the other forms). */
+/* hmat_upload with Method 3's c (eq. 19-20) for HMAT_M3, HMAT_M3_TRUNC and
+ * HMAT_M3_DENSE (-1..16, else HMAT_ERR_ARG); ignored by the other forms.
+ * Launch shapes (same results): the environment variable HMAT_PHASE2 =
+ * cluster | rows | staged selects another expansion shape than the row groups,
+ * HMAT_PHASE1 = persistent the persistent projection; read at upload. */
 int hmat_upload_ex(const void *blob, size_t blob_bytes, int32_t precision, int32_t method3_c, hmat_handle *out);
 
 /* Free every device and host resource of the handle (NULL is accepted). */
