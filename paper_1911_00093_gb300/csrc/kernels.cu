@@ -59,25 +59,28 @@ void launch_phase2(Store s, const DevIndex &ix, const DevPanels &P, double *y, c
 // ------------------------------------------------------------------------
 namespace {
 
-// Every thread gets the CTA's sums: a butterfly inside each warp (partners add
-// the same two values, so every lane holds the same bits), then the warp sums
-// in warp order.  sh: NV * (kVecThreads / 32) doubles; ends with a barrier.
+// Every thread gets the CTA's sums: the first warp adds 8 consecutive values
+// per lane, then a butterfly over its lanes (FP64 additions run at about one
+// per clock per SM on GB300, so few warp-wide ones: 13 per sum).
+// sh: NV * kVecThreads doubles; ends with a barrier.
 template <int NV>
 __device__ __forceinline__ void block_reduce(double (&v)[NV], double *sh) {
-    constexpr int W = kVecThreads / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int PER = kVecThreads / 32;
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        for (int m = 16; m >= 1; m >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], m);
-        if (lane == 0) sh[q * W + warp] = v[q];
+    for (int q = 0; q < NV; ++q) sh[q * kVecThreads + threadIdx.x] = v[q];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double t = 0.0;
+            for (int k = 0; k < PER; ++k) t += sh[q * kVecThreads + threadIdx.x * PER + k];
+            for (int m = 16; m >= 1; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
+            if (threadIdx.x == 0) sh[q * kVecThreads] = t;
+        }
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        double t = 0.0;
-        for (int k = 0; k < W; ++k) t += sh[q * W + k];
-        v[q] = t;
-    }
+    for (int q = 0; q < NV; ++q) v[q] = sh[q * kVecThreads];
     __syncthreads();
 }
 
