@@ -513,11 +513,14 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
     }
     launch_gather(n, h->perm, xsrc, h->x, st);
     CK(cudaMemsetAsync(h->S, 0, sizeof(SolverScalars), st));
-    // ||b||
-    launch_residual(n, h->b, nullptr, h->r, h->rt, h->S, h->partials, -1, st);
-    launches += 2;
+    // ||x_0|| (a zero initial guess needs no product for r_0 = b), then ||b||
+    launch_residual(n, h->x, nullptr, h->r, h->rt, h->S, h->partials, -1, st);
     int rc = read_scalars(h, st);
     if (rc) return rc;
+    const bool x0_zero = h->S_host->rnorm2 == 0.0;
+    launch_residual(n, h->b, nullptr, h->r, h->rt, h->S, h->partials, -1, st);
+    launches += 3;
+    if ((rc = read_scalars(h, st))) return rc;
     const double bnorm2 = h->S_host->rnorm2;
     int status = HMAT_OK;
     if (!std::isfinite(bnorm2)) {
@@ -527,10 +530,16 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
         CK(cudaMemsetAsync(h->x, 0, 8 * n, st));
         inf.relres_true = 0.0;
     } else {
-        // first run: r_0 = b - A~ x_0 with the iterated operator (Algorithm 1)
-        enqueue_segments(h->seg, h->nseg, h->x, nullptr, h->y, nullptr, nullptr, 0, st);
-        launch_residual(n, h->b, h->y, h->r, h->rt, h->S, h->partials, o.maxit, st);  // run 1 starts
-        launches += kProductLaunches + 1;
+        // first run: r_0 = b - A~ x_0 with the iterated operator (Algorithm 1); for
+        // x_0 = 0 that is b exactly, without the product
+        if (x0_zero) {
+            launch_residual(n, h->b, nullptr, h->r, h->rt, h->S, h->partials, o.maxit, st);  // run 1 starts
+            launches += 1;
+        } else {
+            enqueue_segments(h->seg, h->nseg, h->x, nullptr, h->y, nullptr, nullptr, 0, st);
+            launch_residual(n, h->b, h->y, h->r, h->rt, h->S, h->partials, o.maxit, st);  // run 1 starts
+            launches += kProductLaunches + 1;
+        }
         CK(cudaGetLastError());
         for (;;) {
             // a run: its stop threshold, then batches of iterations until its flag is set
@@ -581,7 +590,7 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
     inf.iters = h->S_host->iters;
-    inf.matvecs = bnorm2 > 0.0 && std::isfinite(bnorm2) ? 1 + h->S_host->nmv : 0;
+    inf.matvecs = bnorm2 > 0.0 && std::isfinite(bnorm2) ? (x0_zero ? 0 : 1) + h->S_host->nmv : 0;
     inf.status = status;
     return status;
 }
