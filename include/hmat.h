@@ -252,7 +252,10 @@ typedef struct hmat_solve_opts {
     int32_t maxit;         /* total Algorithm 1 iterations over all runs                        */
     int32_t max_restarts;  /* runs after the first one                                          */
     int32_t check_every;   /* iterations enqueued between host reads of the stop flag (>= 1)    */
-    int32_t use_graph;     /* 1: replay the enqueued iterations as one CUDA graph               */
+    int32_t use_graph;     /* 1: replay check_every iterations as one CUDA graph, the host
+                              reading the stop flag between replays; 2: a whole run as one graph
+                              launch (a conditional WHILE node over those batches; the device
+                              decides when the run ends); 0: plain launches                     */
 } hmat_solve_opts;
 
 typedef struct hmat_solve_info {

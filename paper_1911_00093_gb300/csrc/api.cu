@@ -458,6 +458,47 @@ int ensure_graph(hmat_t *h, int k, int iter_limit) {
     return HMAT_OK;
 }
 
+// A run of Algorithm 1 as one graph launch: a conditional WHILE node whose body
+// is k iterations and the loop condition, so the host waits once per run
+// instead of once per batch.  The condition stops after iter_limit / k + 2
+// batches whatever the flag says (the iteration budget ends a run before).
+int ensure_loop_graph(hmat_t *h, int k, int iter_limit) {
+    if (h->loop_graph && h->loop_k == k && h->loop_limit == iter_limit) return HMAT_OK;
+    if (h->loop_graph) {
+        cudaGraphExecDestroy(h->loop_graph);
+        h->loop_graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle cond;
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    }
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int i = 0; i < k; ++i) enqueue_iteration(h, iter_limit, h->cap_stream);
+            launch_loop_condition(h->S, cond, iter_limit / k + 2, h->cap_stream);
+            cudaGraph_t out = nullptr;
+            e = cudaStreamEndCapture(h->cap_stream, &out);
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->loop_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (!hmat_internal::cuda_ok(e, "device loop graph")) return HMAT_ERR_CUDA;
+    h->loop_k = k;
+    h->loop_limit = iter_limit;
+    return HMAT_OK;
+}
+
 }  // namespace
 
 extern "C" int hmat_matvec(hmat_handle h, const double *x, double *y, int32_t nrhs, void *stream) {
@@ -548,7 +589,19 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
             if (h->S_host->flag == 0) {
                 double stop2 = std::max(o.tol * o.tol * bnorm2, o.inner_tol * o.inner_tol * h->S_host->rnorm2);
                 CK(cudaMemcpyAsync(&h->S->stop2, &stop2, sizeof(double), cudaMemcpyHostToDevice, st));
-                for (;;) {
+                if (o.use_graph == 2) {  // the whole run on the device
+                    if ((rc = ensure_loop_graph(h, o.check_every, o.maxit))) return rc;
+                    CK(cudaMemsetAsync(&h->S->loops, 0, sizeof(int32_t), st));
+                    CK(cudaGraphLaunch(h->loop_graph, st));
+                    if ((rc = read_scalars(h, st))) return rc;
+                    launches += h->S_host->loops * (o.check_every * kIterationLaunches + 1);
+                    if (h->S_host->flag == 0) {  // the loop bound ended it: count it as the budget
+                        const int32_t maxit_flag = HMAT_ERR_MAXIT;
+                        CK(cudaMemcpyAsync(&h->S->flag, &maxit_flag, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+                        if ((rc = read_scalars(h, st))) return rc;
+                    }
+                }
+                for (; o.use_graph != 2;) {
                     launches += o.check_every * kIterationLaunches;
                     if (o.use_graph) {
                         if ((rc = ensure_graph(h, o.check_every, o.maxit))) return rc;

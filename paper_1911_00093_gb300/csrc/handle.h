@@ -87,6 +87,9 @@ struct hmat_t {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_k = 0, graph_limit = -1;
+    // a run as one graph: a WHILE node over batches of graph_k iterations
+    cudaGraphExec_t loop_graph = nullptr;
+    int loop_k = 0, loop_limit = -1;
     // sizes
     int64_t panel_bytes = 0, panel_bytes64 = 0, index_bytes = 0;
     int64_t stored_entries = 0, phase1_entries = 0, phase2_entries = 0, partials_n = 0, rank_sum = 0;
@@ -101,6 +104,7 @@ struct hmat_t {
         if (gm.graph) cudaGraphExecDestroy(gm.graph);
         if (gm.G_host) cudaFreeHost(gm.G_host);
         if (multi.S_host) cudaFreeHost(multi.S_host);
+        if (loop_graph) cudaGraphExecDestroy(loop_graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (void *a : allocs) cudaFree(a);
         if (S_host) cudaFreeHost(S_host);

@@ -283,6 +283,17 @@ int vec_blocks(int64_t n) { return grid_for(n, kVecThreads, 4 * 152); }
 
 void launch_count_iter(SolverScalars *S, int iter_limit, cudaStream_t st) { k_count_iter<<<1, 1, 0, st>>>(S, iter_limit); }
 
+namespace {
+__global__ void k_loop_condition(SolverScalars *S, cudaGraphConditionalHandle cond, int max_loops) {
+    const int loops = ++S->loops;
+    cudaGraphSetConditional(cond, (S->flag == 0 && loops < max_loops) ? 1u : 0u);
+}
+}  // namespace
+
+void launch_loop_condition(SolverScalars *S, cudaGraphConditionalHandle cond, int max_loops, cudaStream_t st) {
+    k_loop_condition<<<1, 1, 0, st>>>(S, cond, max_loops);
+}
+
 void launch_update_p(Store s, int64_t n, const double *r, double *p, const double *v, void *ps, SolverScalars *S,
                      cudaStream_t st) {
     HMAT_DISPATCH(operand_store(s), (k_update_p<SS><<<vec_blocks(n), kVecThreads, 0, st>>>((int)n, r, p, v,

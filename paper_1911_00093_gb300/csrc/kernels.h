@@ -121,10 +121,16 @@ struct SolverScalars {
     int32_t stop_on_s;    // 1 if the run stopped at the ||s|| check
     unsigned int ticket;  // last-block counter of the fused reductions
     int32_t nmv;          // products with the iterated operator, excluding r_0
+    int32_t loops;        // batches of iterations the device loop of a run has replayed
+    int32_t pad_;
 };
 
 constexpr int kVecThreads = 256;
 int vec_blocks(int64_t n);
+// The end of one batch of iterations inside a run's device loop (a conditional
+// WHILE graph node): counts the batch and keeps looping while the run goes on
+// and fewer than max_loops batches have run.
+void launch_loop_condition(SolverScalars *S, cudaGraphConditionalHandle cond, int max_loops, cudaStream_t st);
 
 // ---- restarted GMRES(m) (gmres.cu) ----
 constexpr int kGmresMaxM = 64;

@@ -81,8 +81,17 @@ def test_graph_batches_and_host_pointers_agree(hcache):
         x3, i3 = _solve(P, torch, h, b, tol=1e-8, use_graph=1, check_every=5)
         xh = np.zeros(mesh.n)
         i4 = P.hmat_bicgstab(h, b.copy(), xh, tol=1e-8)
-        for x, i in ((x2, i2), (x3, i3), (xh, i4)):
+        # a whole run as one graph launch (a device-side WHILE loop over batches)
+        x5, i5 = _solve(P, torch, h, b, tol=1e-8, use_graph=2, check_every=1)
+        x6, i6 = _solve(P, torch, h, b, tol=1e-8, use_graph=2, check_every=4)
+        for x, i in ((x2, i2), (x3, i3), (xh, i4), (x5, i5), (x6, i6)):
             assert np.array_equal(x, x1) and i["iters"] == i1["iters"]
+        # the device loop also ends on the iteration budget, and with refinement runs
+        _, i7 = _solve(P, torch, h, b, tol=1e-8, use_graph=2, check_every=3, maxit=5, max_restarts=0)
+        assert i7["status"] == 7 and i7["iters"] == 5, i7
+        x8, i8 = _solve(P, torch, h, b, tol=1e-8, use_graph=2, check_every=4, inner_tol=1e-3)
+        x9, i9 = _solve(P, torch, h, b, tol=1e-8, use_graph=1, check_every=4, inner_tol=1e-3)
+        assert i8["status"] == 0 and i8["restarts"] >= 1 and np.array_equal(x8, x9) and i8["iters"] == i9["iters"]
     finally:
         P.hmat_destroy(h)
 
