@@ -53,10 +53,11 @@ namespace {
 // Algorithm 1's inner products in dpart (dotmode 1: r~ . v, v . v; 2: s . t, t . t).
 void enqueue_segments(const HmatSegment *seg, int nseg, const double *x_src, const int32_t *src_perm, double *y,
                       const int32_t *out_perm, const SolverScalars *skipS, int mode, cudaStream_t st,
-                      const double *w = nullptr, int dotmode = 0, double *dpart = nullptr) {
+                      const double *w = nullptr, int dotmode = 0, double *dpart = nullptr,
+                      const PFold &fold = PFold()) {
     if (x_src) launch_prep(seg[0].store, seg[0].ix, x_src, src_perm, seg[0].P.xs, st);
     for (int k = 0; k < nseg; ++k) {
-        launch_phase1(seg[k].store, seg[k].ix, seg[k].P, skipS, mode, st);
+        launch_phase1(seg[k].store, seg[k].ix, seg[k].P, skipS, mode, st, fold);
         launch_reduce(seg[k].store, seg[k].ix, seg[k].P, skipS, mode, st);
     }
     for (int k = 0; k < nseg; ++k) {
@@ -250,6 +251,8 @@ int upload_view(const BlobView &v, int32_t precision, int32_t method3_c, const s
         CK(cudaGetDevice(&h->device));
         CK(prepare_launches());
         h->precision = precision;
+        const char *fold_env = std::getenv("HMAT_FOLD_P");
+        h->fold_p = fold_env && std::strcmp(fold_env, "1") == 0;
         h->method3_c =
             (precision == HMAT_M3 || precision == HMAT_M3_TRUNC || precision == HMAT_M3_DENSE) ? method3_c : 0;
         h->n = L.n;
@@ -416,15 +419,30 @@ int matvec_impl(hmat_handle h, const double *x, double *y, int32_t nrhs, void *s
     return HMAT_OK;
 }
 
+// Whether an iteration folds the p update into the first projection (one
+// segment, HMAT_FOLD_P=1 at upload; measured slower at level 6: the
+// projection's prologue gets one more dependent round).
+bool fold_p_update(const hmat_t *h) { return h->fold_p && h->nseg == 1; }
+
 // One iteration of Algorithm 1 on the device (every kernel returns at once
 // after the run has stopped).
 void enqueue_iteration(hmat_t *h, int iter_limit, cudaStream_t st) {
     const int64_t n = h->n;
     const Store s = h->seg[0].store;
     void *xs = h->seg[0].P.xs;  // operand copy shared by the segments
-    launch_update_p(s, n, h->r, h->p, h->v, xs, h->S, st);
-    // v = A p, with alpha = rho / (r~ . v)
-    enqueue_segments(h->seg, h->nseg, nullptr, nullptr, h->v, nullptr, h->S, 1, st, h->rt, 1, h->dpart);
+    // v = A p, with alpha = rho / (r~ . v); a one-segment operator folds the p
+    // update into its projection (each projection CTA owns its cluster's rows)
+    if (fold_p_update(h)) {
+        PFold fold;
+        fold.r = h->r;
+        fold.p = h->p;
+        fold.v = h->v;
+        fold.S = h->S;
+        enqueue_segments(h->seg, h->nseg, nullptr, nullptr, h->v, nullptr, h->S, 1, st, h->rt, 1, h->dpart, fold);
+    } else {
+        launch_update_p(s, n, h->r, h->p, h->v, xs, h->S, st);
+        enqueue_segments(h->seg, h->nseg, nullptr, nullptr, h->v, nullptr, h->S, 1, st, h->rt, 1, h->dpart);
+    }
     const HmatSegment &last = h->seg[h->nseg - 1];
     const int ndp = phase2_items(last.store, last.ix);  // work items of the expansion that leaves the shares
     launch_update_s(s, n, h->r, h->v, h->s, xs, h->S, h->partials, h->dpart, ndp, st);
@@ -539,7 +557,7 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
     // omega, s update, x/r update with the count of the next iteration)
     const int kProductLaunches = product_launches(h->seg, h->nseg);
     const int kProduct64Launches = product_launches(&h->seg64, 1);
-    const int kIterationLaunches = 3 + 2 * (kProductLaunches - 1);
+    const int kIterationLaunches = (fold_p_update(h) ? 2 : 3) + 2 * (kProductLaunches - 1);
     const double *bsrc = b;
     if (!db) {
         CK(cudaMemcpyAsync(h->stage_in, b, 8 * n, cudaMemcpyHostToDevice, st));

@@ -32,9 +32,9 @@ void launch_prep(Store s, const DevIndex &ix, const double *x, const int32_t *sr
 }
 
 void launch_phase1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                   cudaStream_t st) {
-    if (is_table1(s)) return launch_phase1_table1(s, ix, P, skipS, mode, st);
-    HMAT_DISPATCH(s, phase1_launch<SS>(ix, P, skipS, mode, st));
+                   cudaStream_t st, const PFold &fold) {
+    if (is_table1(s)) return launch_phase1_table1(s, ix, P, skipS, mode, st, fold);
+    HMAT_DISPATCH(s, phase1_launch<SS>(ix, P, skipS, mode, st, fold));
 }
 
 void launch_reduce(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kVecThreads) k_update_p(int n, const double *_
     const double beta = first ? 0.0 : (rho / S->rho_prev) * (S->alpha / S->omega);
     const double omega = S->omega;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double pv = first ? r[i] : r[i] + beta * (p[i] - omega * v[i]);
+        const double pv = p_next(first, r[i], p[i], v[i], beta, omega);
         p[i] = pv;
         if constexpr (ST == Store::DF) ps[i] = split_double(pv);
         else if constexpr (ST == Store::F64) ps[i] = pv;

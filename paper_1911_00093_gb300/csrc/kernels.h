@@ -31,6 +31,17 @@ struct DevIndex {
     int32_t max_ld2 = 0;            // widest phase-2 panel (entries)
 };
 
+// Algorithm 1's p update folded into the next projection: each projection CTA
+// updates the rows of its leaf cluster, p = r + beta (p - omega v) (p = r at a
+// run's first iteration), and projects the new p (null: the operand copy).
+struct SolverScalars;
+struct PFold {
+    const double *r = nullptr;
+    double *p = nullptr;
+    const double *v = nullptr;
+    SolverScalars *S = nullptr;
+};
+
 // One precision copy of the panels plus its work buffers.
 struct DevPanels {
     Store store = Store::DF;
@@ -91,7 +102,7 @@ struct SolverScalars;
 // skipS/mode: a solver's product is skipped once its run has stopped (mode 1:
 // flag set; mode 2: flag set or stop at the ||s|| check); mode 0 never skips.
 void launch_phase1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                   cudaStream_t st);
+                   cudaStream_t st, const PFold &fold = PFold());
 // t of the blocks spanning several leaf clusters, scattered into g (no launch when there is none)
 void launch_reduce(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
                    cudaStream_t st);
@@ -104,7 +115,7 @@ void launch_phase2(Store s, const DevIndex &ix, const DevPanels &P, double *y, c
                    int dotmode = 0, double *dpart = nullptr);
 // the same for the paper's stores (kernels_table1.cu)
 void launch_phase1_table1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                          cudaStream_t st);
+                          cudaStream_t st, const PFold &fold);
 void launch_reduce_table1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
                           cudaStream_t st);
 void launch_phase2_table1(Store s, const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm,

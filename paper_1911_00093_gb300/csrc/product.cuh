@@ -90,6 +90,13 @@ __device__ __forceinline__ double df_to_double(DF a) { return (double)a.s + (dou
 
 __device__ __forceinline__ int4 ld_stream(const void *p) { return __ldcs((const int4 *)p); }
 
+// Algorithm 1's search direction, p = r + beta (p - omega v), or r at a run's
+// first iteration; explicit roundings, so the p-update kernel and the
+// projection that folds it in give the same bits
+__device__ __forceinline__ double p_next(bool first, double r, double p, double v, double beta, double omega) {
+    return first ? r : __fma_rn(beta, __fma_rn(-omega, v, p), r);
+}
+
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
@@ -436,7 +443,7 @@ __global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc 
                                                         typename Tr<S>::Part *__restrict__ part,
                                                         typename Tr<S>::Op *__restrict__ g,
                                                         const double *__restrict__ tscale, const SolverScalars *S_,
-                                                        int mode) {
+                                                        int mode, PFold fold) {
     using Op = typename Tr<S>::Op;
     __shared__ Op xk[kMaxLeaf];  // x_kappa, broadcast to every thread
     // the cluster's run and dense-operand descriptors, loaded with x_kappa so
@@ -446,9 +453,32 @@ __global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc 
     if (skip_product(S_, mode)) return;
     const P1Desc d = desc[blockIdx.x];
     const bool runs_sm = d.rcnt <= kP1SmemRuns, xd_sm = d.xdcnt <= kP1SmemXd;
-    for (int j = threadIdx.x; j < d.xlen; j += NT) {
-        if constexpr (fp32_source(S)) xk[j] = (double)__double2float_rn(xs[d.xbeg + j]);  // Section 3.5
-        else xk[j] = xs[d.xbeg + j];
+    if (fold.S) {  // Algorithm 1's p update of this cluster's rows, then project the new p
+        SolverScalars *FS = fold.S;
+        const double rho = FS->rho;
+        if (!isfinite(rho) || rho == 0.0) {  // rho_{i-1} = 0: the method fails (every CTA returns)
+            if (blockIdx.x == 0 && threadIdx.x == 0)
+                FS->flag = isfinite(rho) ? HMAT_ERR_BREAKDOWN_RHO : HMAT_ERR_NONFINITE;
+            return;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) FS->nmv += 1;  // v = A p
+        const bool first = FS->iter_in_run == 0;
+        const double beta = first ? 0.0 : (rho / FS->rho_prev) * (FS->alpha / FS->omega);
+        const double omega = FS->omega;
+        for (int j = threadIdx.x; j < d.xlen; j += NT) {
+            const int i = d.xbeg + j;
+            const double pv = p_next(first, fold.r[i], fold.p[i], fold.v[i], beta, omega);
+            fold.p[i] = pv;
+            if constexpr (S == Store::DF) xk[j] = split_double(pv);
+            else if constexpr (S == Store::F64) xk[j] = pv;
+            else if constexpr (is_table1(S)) xk[j] = fp32_source(S) ? (double)__double2float_rn(pv) : pv;
+            else xk[j] = __double2float_rn(pv);
+        }
+    } else {
+        for (int j = threadIdx.x; j < d.xlen; j += NT) {
+            if constexpr (fp32_source(S)) xk[j] = (double)__double2float_rn(xs[d.xbeg + j]);  // Section 3.5
+            else xk[j] = xs[d.xbeg + j];
+        }
     }
     if (runs_sm)
         for (int j = threadIdx.x; j < d.rcnt; j += NT) rs[j] = runs[d.rbeg + j];
@@ -1309,8 +1339,9 @@ int grid_for(int64_t n, int threads, int cap) {
 
 // launches of one store's product kernels (the dispatchers pick the store)
 template <Store SS>
-void phase1_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st) {
-    if (ix.p1_persistent) {
+void phase1_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st,
+                   const PFold &fold) {
+    if (ix.p1_persistent && !fold.S) {  // (the folded p update runs in the one-CTA-per-cluster form)
         const int grid = std::min(ix.nleaves, ix.nsm * p1_min_blocks<SS>());
         k_phase1p<SS><<<grid, p1_threads<SS>(), 0, st>>>(ix.nleaves, ix.p1, ix.p1_runs, ix.xdst, ix.xsel, ix.lr,
                                                          ix.gdst, P.q1, (const typename Tr<SS>::Op *)P.xs,
@@ -1321,7 +1352,7 @@ void phase1_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *
     k_phase1<SS><<<ix.nleaves, p1_threads<SS>(), 0, st>>>(ix.p1, ix.p1_runs, ix.xdst, ix.xsel, ix.lr, ix.gdst, P.q1,
                                                           (const typename Tr<SS>::Op *)P.xs,
                                                           (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g,
-                                                          ix.tscale, skipS, mode);
+                                                          ix.tscale, skipS, mode, fold);
 }
 
 template <Store SS>
