@@ -203,6 +203,27 @@ typedef struct hmat_blob_stats {
 /* Validate a blob (the same checks as hmat_upload) and report its sizes. */
 int hmat_blob_stats_get(const void *blob, size_t blob_bytes, hmat_blob_stats *out);
 
+/*
+ * hmat_form_stats_get -- what hmat_upload_ex would store for `precision` (and
+ * Method 3's c), on the host only (no device is touched): the segments of a
+ * paper variant (Table 1 / Section 4.5 derivation) or the one segment of a
+ * GPU-native form, each packed and checked as at upload, with per-segment
+ * counts.  Errors as hmat_upload_ex, without HMAT_ERR_CUDA / HMAT_ERR_NOMEM
+ * from the device.
+ */
+typedef struct hmat_form_stats {
+    int32_t segments;              /* 1 or 2                                                   */
+    int32_t pad;
+    int64_t blocks[2];             /* derived blocks per segment                               */
+    int64_t dense_entries[2];      /* dense-block entries stored per segment                   */
+    int64_t lr_ranks[2];           /* low-rank columns (ranks) stored per segment               */
+    int64_t lr_entries[2];         /* low-rank factor entries stored per segment                */
+    int64_t column_subsets[2];     /* dense blocks stored as column subsets per segment         */
+    int64_t selected_operands[2];  /* entries of the operand selection lists per segment        */
+} hmat_form_stats;
+int hmat_form_stats_get(const void *blob, size_t blob_bytes, int32_t precision, int32_t method3_c,
+                        hmat_form_stats *out);
+
 /* ------------------------------------------------------------------------- */
 /* Device H-matrix                                                            */
 /* ------------------------------------------------------------------------- */

@@ -32,13 +32,19 @@ EXPORTS = ("hmat_build", "hmat_blob_free", "hmat_blob_stats_get", "hmat_upload",
            "hmat_matvec", "hmat_matvec_fp64", "hmat_solve_opts_default", "hmat_bicgstab",
            "hmat_bicgstab_ex", "hmat_info", "hmat_time_matvec", "hmat_strerror", "hmat_last_cuda_error",
            "hmat_matvec_noalloc", "hmat_upload_ex", "hmat_upload_batch", "hmat_problems", "hmat_bicgstab_multi",
-           "hmat_gmres", "hmat_build_device")
+           "hmat_gmres", "hmat_build_device", "hmat_form_stats_get")
 
 
 class BuildDeviceInfo(C.Structure):
     _fields_ = [("aca_blocks", C.c_int64), ("host_blocks", C.c_int64), ("workspace_bytes", C.c_int64),
                 ("plan_ms", C.c_double), ("alloc_ms", C.c_double), ("aca_ms", C.c_double),
                 ("pack_ms", C.c_double), ("copy_ms", C.c_double)]
+
+
+class FormStats(C.Structure):
+    _fields_ = [("segments", C.c_int32), ("pad", C.c_int32)] + [
+        (k, C.c_int64 * 2) for k in ("blocks", "dense_entries", "lr_ranks", "lr_entries", "column_subsets",
+                                     "selected_operands")]
 
 
 class BlobStats(C.Structure):
@@ -113,6 +119,7 @@ def load():
         "hmat_gmres": (C.c_int, [P, P, P, I32, C.POINTER(SolveOpts), P, C.POINTER(SolveInfo)]),
         "hmat_build_device": (C.c_int, [I64, P, P, I32, D, D, C.POINTER(C.c_void_p), C.POINTER(SZ),
                                         C.POINTER(BuildDeviceInfo)]),
+        "hmat_form_stats_get": (C.c_int, [P, SZ, I32, I32, C.POINTER(FormStats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -196,6 +203,19 @@ def hmat_build_device(centroids, areas, leaf=32, eta=2.0, aca_eps=1e-4, info=Non
         L.hmat_blob_free(buf)
     if isinstance(info, dict):
         info.update({k: getattr(inf, k) for k, _ in BuildDeviceInfo._fields_})
+    return out
+
+
+def hmat_form_stats(blob, precision="fp64", c=0) -> dict:
+    """What an upload in `precision` would store (host only): per-segment counts as lists."""
+    L = load()
+    b = np.ascontiguousarray(blob, dtype=np.uint8)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    s = FormStats()
+    _check(L.hmat_form_stats_get(b.ctypes.data, b.nbytes, prec, int(c), C.byref(s)), "hmat_form_stats_get")
+    out = {"segments": s.segments}
+    for k, _ in FormStats._fields_[2:]:
+        out[k] = list(getattr(s, k))[:s.segments]
     return out
 
 

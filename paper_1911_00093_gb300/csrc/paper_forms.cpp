@@ -320,3 +320,46 @@ int combine_blobs(const BlobView *views, int count, CombinedBlob &out, std::stri
 }
 
 }  // namespace hmat_internal
+
+extern "C" int hmat_form_stats_get(const void *blob, size_t blob_bytes, int32_t precision, int32_t method3_c,
+                                   hmat_form_stats *out) {
+    using namespace hmat_internal;
+    if (!blob || !out || precision < HMAT_FP64 || precision > HMAT_M3_DENSE) return HMAT_ERR_ARG;
+    BlobView v;
+    int st = parse_blob(blob, blob_bytes, v);
+    if (st != HMAT_OK) return st;
+    std::memset(out, 0, sizeof(*out));
+    try {
+        DerivedSegment seg[2];
+        Store store[2];
+        int nseg = 1;
+        const BlobView *views[2] = {&v, nullptr};
+        if (precision >= HMAT_M1_SINGLE) {
+            st = derive_table1(v, precision, method3_c, seg, store, &nseg, nullptr);
+            if (st != HMAT_OK) return st;
+            for (int k = 0; k < nseg; ++k) views[k] = &seg[k].view;
+        }
+        out->segments = nseg;
+        for (int k = 0; k < nseg; ++k) {
+            const BlobView &w = *views[k];
+            Layout L;
+            if ((st = build_layout(w, L)) != HMAT_OK || (st = check_layout(L)) != HMAT_OK) return st;
+            out->blocks[k] = w.h->nblocks;
+            for (int64_t b = 0; b < w.h->nblocks; ++b) {
+                const int64_t *e = w.blocks + 8 * b;
+                const int64_t m = e[1] - e[0], n = e[3] - e[2];
+                if (block_is_dense(e)) {
+                    out->dense_entries[k] += m * dense_width(e);
+                    if (e[4] == 2) out->column_subsets[k] += 1;
+                } else {
+                    out->lr_ranks[k] += e[5];
+                    out->lr_entries[k] += e[5] * (m + n);
+                }
+            }
+            out->selected_operands[k] = (int64_t)L.xsel.size();
+        }
+    } catch (const std::bad_alloc &) {
+        return HMAT_ERR_NOMEM;
+    }
+    return HMAT_OK;
+}
