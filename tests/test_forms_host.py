@@ -11,9 +11,10 @@ from blob_util import oracle_blob
 from gpu_util import lib
 
 
-@pytest.fixture(scope="module")
-def case(hcache):
-    mesh = synth.icosphere(3)
+@pytest.fixture(scope="module", params=["icosphere3", "two_spheres3", "cube8"])
+def case(hcache, request):
+    mesh = {"icosphere3": synth.icosphere(3), "two_spheres3": synth.two_spheres(3),
+            "cube8": synth.unit_cube(8)}[request.param]
     H = hcache(mesh)
     return mesh, H, oracle_blob(H)
 
