@@ -290,7 +290,7 @@ typedef struct hmat_solve_info {
     double relres_inner;   /* last recursive ||r_i||_2 / ||b||_2                                */
 } hmat_solve_info;
 
-/* Defaults: tol 1e-8, inner_tol 0, maxit 1000, max_restarts 30, check_every 1, use_graph 1. */
+/* Defaults: tol 1e-8, inner_tol 0, maxit 1000, max_restarts 30, check_every 1, use_graph 2. */
 void hmat_solve_opts_default(hmat_solve_opts *opts);
 
 /*

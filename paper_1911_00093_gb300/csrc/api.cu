@@ -534,7 +534,7 @@ extern "C" void hmat_solve_opts_default(hmat_solve_opts *o) {
     o->maxit = 1000;
     o->max_restarts = 30;
     o->check_every = 1;
-    o->use_graph = 1;
+    o->use_graph = 2;
 }
 
 extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const hmat_solve_opts *opts_in,
