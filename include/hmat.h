@@ -272,7 +272,8 @@ typedef struct hmat_solve_opts {
                               restarts into FP64 iterative refinement of a low-precision solve */
     int32_t maxit;         /* total Algorithm 1 iterations over all runs                        */
     int32_t max_restarts;  /* runs after the first one                                          */
-    int32_t check_every;   /* iterations enqueued between host reads of the stop flag (>= 1)    */
+    int32_t check_every;   /* iterations per graph batch (>= 1): between host reads of the stop
+                              flag (use_graph 1), per body of the device loop (use_graph 2)     */
     int32_t use_graph;     /* 1: replay check_every iterations as one CUDA graph, the host
                               reading the stop flag between replays; 2: a whole run as one graph
                               launch (a conditional WHILE node over those batches; the device
