@@ -27,7 +27,9 @@
  *     assignments of Table 1 for Methods 1, 2 (eq. 11-16) and 3 (eq. 17-20);
  *   - BiCG-STAB, Algorithm 1, with the FP64 true-residual acceptance of
  *     Section 4.1.3 and a restart from the true residual when it fails;
- *   - dense helpers for pins: full matrix, dense product, Gaussian elimination.
+ *   - dense helpers for pins: full matrix, dense product, Gaussian elimination;
+ *     an H-matrix given block by block (or_from_blocks), so that a test can work
+ *     out the products of Table 1 by hand on a few entries.
  *
  * Readings where the paper is silent are marked READING in the comments.
  *
@@ -504,6 +506,44 @@ void or_free(or_hmat *h)
     free(h->bkind); free(h->brank); free(h->bdata); free(h->bforced);
     free(h->perm); free(h->cl);
     free(h);
+}
+
+/* An H-matrix given block by block instead of built from a mesh: the identity
+ * permutation, `nb` blocks with desc6[6b..6b+5] = i_s, i_e, j_s, j_e, kind
+ * (0 dense, 1 low rank), rank, and the blocks' data one after another in the
+ * layout of bdata (dense: A|^m row-major; low rank: V_m then W_m, eq. 3).
+ * No arithmetic: this lets a test write a tiny H-matrix by hand and work out
+ * its products of Table 1 by hand.  Returns NULL on a malformed description. */
+int64_t or_block_size(const or_hmat *h, int64_t b);
+or_hmat *or_from_blocks(int64_t n, int64_t nb, const int64_t *desc6, const double *data)
+{
+    or_hmat *h = (or_hmat *)calloc(1, sizeof(or_hmat));
+    h->n = n;
+    h->perm = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; i++) h->perm[i] = i;
+    h->nb = h->capb = nb;
+    size_t c = (size_t)(nb > 0 ? nb : 1);
+    h->bi_s = (int64_t *)malloc(sizeof(int64_t) * c); h->bi_e = (int64_t *)malloc(sizeof(int64_t) * c);
+    h->bj_s = (int64_t *)malloc(sizeof(int64_t) * c); h->bj_e = (int64_t *)malloc(sizeof(int64_t) * c);
+    h->bkind = (int *)malloc(sizeof(int) * c); h->brank = (int64_t *)malloc(sizeof(int64_t) * c);
+    h->bdata = (double **)calloc(c, sizeof(double *)); h->bforced = (int *)calloc(c, sizeof(int));
+    const double *src = data;
+    for (int64_t b = 0; b < nb; b++) {
+        const int64_t *d = desc6 + 6 * b;
+        h->bi_s[b] = d[0]; h->bi_e[b] = d[1]; h->bj_s[b] = d[2]; h->bj_e[b] = d[3];
+        h->bkind[b] = (int)d[4]; h->brank[b] = h->bkind[b] ? d[5] : 0;
+        if (d[0] < 0 || d[1] > n || d[0] >= d[1] || d[2] < 0 || d[3] > n || d[2] >= d[3] ||
+            (d[4] != 0 && d[4] != 1) || (d[4] == 1 && d[5] < 1)) {
+            h->nb = b;
+            or_free(h);
+            return NULL;
+        }
+        int64_t cnt = or_block_size(h, b);
+        h->bdata[b] = (double *)malloc(sizeof(double) * cnt);
+        memcpy(h->bdata[b], src, sizeof(double) * cnt);
+        src += cnt;
+    }
+    return h;
 }
 
 /* ---- accessors (for the tests' serialisation and structural pins) ---- */

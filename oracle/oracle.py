@@ -43,6 +43,7 @@ def lib():
             "or_admissible_boxes": (I, [P, P, P, P, D]),
             "or_aca_array": (I64, [I64, I64, P, D, I64, P, P]),
             "or_build": (P, [I64, P, P, I64, D, D]),
+            "or_from_blocks": (P, [I64, I64, P, P]),
             "or_free": (None, [P]),
             "or_n": (I64, [P]), "or_nblocks": (I64, [P]), "or_nclusters": (I64, [P]),
             "or_get_perm": (None, [P, P]),
@@ -160,6 +161,30 @@ class HMatrix:
         self._h = lib().or_build(self.n, _p(self._c), _p(self._a), self.leaf, self.eta, self.eps)
         if not self._h:
             raise MemoryError("or_build failed")
+
+    @classmethod
+    def from_blocks(cls, n, blocks):
+        """A hand-written H-matrix (identity permutation): `blocks` is a list of
+        (i_s, i_e, j_s, j_e, A) for a dense block A|^m, or (i_s, i_e, j_s, j_e,
+        (V_m, W_m)) for a low-rank block V_m W_m (eq. 3)."""
+        desc, data = [], []
+        for i_s, i_e, j_s, j_e, d in blocks:
+            if isinstance(d, tuple):
+                V, W = _f64(d[0]), _f64(d[1])
+                desc.append((i_s, i_e, j_s, j_e, 1, V.shape[1]))
+                data += [V.ravel(), W.ravel()]
+            else:
+                desc.append((i_s, i_e, j_s, j_e, 0, 0))
+                data.append(_f64(d).ravel())
+        desc = np.ascontiguousarray(np.array(desc, dtype=np.int64).reshape(-1, 6))
+        flat = _f64(np.concatenate(data) if data else np.zeros(1))
+        self = cls.__new__(cls)
+        self.n = int(n)
+        self.leaf, self.eta, self.eps = 0, 0.0, 0.0
+        self._h = lib().or_from_blocks(self.n, desc.shape[0], _p(desc), _p(flat))
+        if not self._h:
+            raise ValueError("malformed block list")
+        return self
 
     def __del__(self):
         h = getattr(self, "_h", None)

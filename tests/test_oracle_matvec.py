@@ -80,9 +80,12 @@ def _table1():
 @pytest.mark.parametrize("name", ["M1_DOUBLE", "M1_SINGLE", "M1_MIXED", "M2_DOUBLE", "M2_SINGLE", "M2_MIXED"])
 def test_variant_precisions_follow_table1(hcache, oracle_mod, name):
     """The source-vector columns of Table 1 decide whether a perturbation below FP32
-    resolution is seen; the matrix columns decide the error size against FP64."""
+    resolution is seen; the matrix columns decide the error size against FP64; the
+    z_m column decides whether the low-rank sums add FP32 rounding of their own
+    (Method 1) on top of Method 2's with the same source vector (bit-level pins of
+    every cell: test_oracle_table1_cells.py)."""
     cols = _table1()[name]
-    x_dense, x_lr, A_dense, W_lr = cols[2], cols[5], cols[1], cols[4]
+    x_dense, x_lr, A_dense, W_lr, z_lr = cols[2], cols[5], cols[1], cols[4], cols[3]
     assert x_dense == x_lr
     mesh = synth.icosphere(3)
     H = hcache(mesh)
@@ -105,6 +108,13 @@ def test_variant_precisions_follow_table1(hcache, oracle_mod, name):
     else:
         assert 1e-10 <= rel <= 1e-6       # FP32 rounding is present and within the FP32 bound
         assert rel <= 40 * FP32_U
+    if z_lr == "FP32":
+        # the same source and matrix precisions with an FP64 z_m (Method 2's row)
+        twin = _table1()[name.replace("M1", "M2")]
+        assert twin[3] == "FP64" and twin[2] == x_dense and twin[1] == A_dense
+        y2 = H.matvec(x, oracle_mod.VARIANTS[name.replace("M1", "M2")])
+        rel2 = np.linalg.norm(y2 - y64) / np.linalg.norm(y64)
+        assert rel > 2 * rel2             # measured about 4x at level 3
 
 
 def test_method3_limits(hcache, oracle_mod):
