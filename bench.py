@@ -129,17 +129,35 @@ def _dist_setup(args):
 
 def _profiled_traffic(kernel, level):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when
-    there is none for this workload or the kernel source changed since the capture."""
+    there is none for this workload or a product source changed since the capture."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", f"traffic_bf16_icosphere_L{level}.json")
+    path = os.path.join(ROOT, "profiles", f"traffic_icosphere_L{level}.json")
     try:
         rec = json.load(open(path))
-        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        for src, digest in rec["sources"].items():
+            if hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest() != digest:
+                return None
     except (OSError, ValueError, KeyError):
         return None
-    if hashlib.sha256(src).hexdigest() != rec.get("source_sha256"):
-        return None
     return rec.get("dram_bytes_per_launch", {}).get(kernel)
+
+
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
+
+
+def _roofline(table, form, level, peak, peak_kind):
+    """Roofline object of a form's dominant product kernel: algorithmic bytes per
+    launch (stored entries at their element size plus the partial sums written, or
+    plus y written) over the launch's mean CUDA-event time; traffic = ncu DRAM bytes
+    per launch from the committed capture of the same source."""
+    head = table[form]
+    dom = "phase2" if head["kernel_ms"]["phase2"] >= head["kernel_ms"]["phase1"] else "phase1"
+    achieved = head[dom + "_gbs"]
+    kname = f"k_phase2g<{form}>" if dom == "phase2" else f"k_phase1<{form}>"
+    return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+            "algorithmic_bytes": head[dom + "_bytes"], "launch_us": head["kernel_ms"][dom] * 1e3,
+            "traffic": _profiled_traffic(kname, level)}
 
 
 def max_over_ranks(value, dist, device="cuda"):
@@ -173,50 +191,60 @@ def _config(mesh, args, extra=None):
 
 
 def run_reference(args):
-    """The oracle (plain FP64 C, single thread) solving the same workload on the host."""
+    """The oracle (plain FP64 C, OpenMP over the blocks of each product) solving the
+    same workload on the host cores, one whole solve per step."""
     world, rank, _ = _dist_setup(args)
     if rank != 0:
         return
     import oracle
     oracle.build_oracle()
     mesh, b = _workload(args.level)
-    variant, inner = oracle.M1_DOUBLE, 0.0  # the plain FP64 oracle
+    variant = oracle.M1_DOUBLE  # the plain FP64 oracle
     H = oracle.HMatrix(mesh.centroid, mesh.area)
+    threads = oracle.get_threads()
     # warm-up: a few products (a CPU program needs no more)
     for _ in range(max(0, args.warmup)):
         H.matvec(b, variant)
     times, infos = [], []
-    budget = 150.0
     for k in range(args.steps):
         t0 = time.perf_counter()
-        x, info = H.bicgstab(b, variant=variant, tol=1e-8, inner_tol=inner)
+        x, info = H.bicgstab(b, variant=variant, tol=1e-8)
         times.append(time.perf_counter() - t0)
         infos.append(info)
-        if sum(times) > budget:
-            break
     t = statistics.mean(times)
     line = {"metric": METRIC, "value": 1.0 / t, "unit": UNIT, "n_gpus": args.gpus, "steps": len(times),
             "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": _config(mesh, args, {"oracle_variant": "fp64"}),
-            "cpu_baseline": {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{len(times)} whole oracle solves of the benchmark workload "
-                                       f"(iters {infos[-1]['iters']}, true relres {infos[-1]['relres']:.2e})"},
+            "cpu_baseline": {"value": 1.0 / t, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{len(times)} whole oracle solves of the benchmark workload on {threads} "
+                                       f"threads (iters {infos[-1]['iters']}, true relres {infos[-1]['relres']:.2e})"},
             "e2e": {"value": 1.0 / t, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 def cpu_baseline(mesh, b):
-    """The oracle as it stands on this host's cores: one whole FP64 solve of the same workload."""
+    """The oracle as it stands on this host's cores: one whole FP64 solve of the same
+    workload on every core (the reported value), then one on a single thread."""
     import oracle
     oracle.build_oracle()
     H = oracle.HMatrix(mesh.centroid, mesh.area)
+    threads = oracle.get_threads()
     t0 = time.perf_counter()
     x, info = H.bicgstab(b, variant=oracle.M1_DOUBLE, tol=1e-8)
     t = time.perf_counter() - t0
-    return {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one whole FP64 oracle solve of the benchmark workload (iters {info['iters']}, "
-                      f"true relres {info['relres']:.2e}, {t:.1f} s single-threaded; the OpenMP build is untimed)"}
+    try:
+        oracle.set_threads(1)
+        t1 = time.perf_counter()
+        x1, info1 = H.bicgstab(b, variant=oracle.M1_DOUBLE, tol=1e-8)
+        t1 = time.perf_counter() - t1
+    finally:
+        oracle.set_threads(threads)
+    return {"value": 1.0 / t, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"one whole FP64 oracle solve of the benchmark workload on {threads} threads "
+                      f"(iters {info['iters']}, true relres {info['relres']:.2e}, {t:.2f} s)",
+            "single_thread": {"value": 1.0 / t1, "unit": UNIT, "cores": 1,
+                              "sample": f"the same solve on one thread ({t1:.2f} s, the same bits)"}}
 
 
 def _cuda_ms(torch, fn, reps):
@@ -235,7 +263,8 @@ def run_workload(args):
     icosphere_L4 (FP64 correctness size), two_spheres_L7 (BF16 + FP64 refinement,
     N = 655,360), multirhs64 (64 right-hand sides at level 6, tensor-core products),
     batch48 (48 uneven cube / sphere problems in one block-diagonal handle);
-    build_icosphere_L6 / build_batch48 (H-matrix construction, host vs device)."""
+    build_icosphere_L6 / build_batch48 (H-matrix construction, host vs device);
+    matvec_protocol (Section 4.1.3's sets of repeated products, GPU and oracle)."""
     import torch
     import synth
     import paper_1911_00093_gb300 as P
@@ -317,6 +346,48 @@ def run_workload(args):
             P.hmat_destroy(h)
         out["value"] = out["fp32"]["batch_solve_ms"]
         out["speedup_fp32_vs_fp64"] = out["fp64"]["batch_solve_ms"] / out["fp32"]["batch_solve_ms"]
+    elif args.workload == "matvec_protocol":
+        # Section 4.1.3's protocol: sets of repeated products of one source vector,
+        # the median set reported; the GPU forms (1000 products per set) and the FP64
+        # oracle on one thread and on every host core (fewer products per set at
+        # level 6, where one oracle product takes tenths of a second)
+        import oracle
+        oracle.build_oracle()
+        threads = oracle.get_threads()
+        out.update({"metric": "H-matvec time, sets of repeated products (Section 4.1.3)", "unit": "ms per product",
+                    "higher_is_better": False})
+        levels = {}
+        for level, reps_cpu1, reps_cpun in ((4, 1000, 1000), (6, 20, 100)):
+            mesh = synth.icosphere(level)
+            xn = synth.rhs_one_plus_half_z(mesh)
+            blob = P.hmat_build(mesh.centroid, mesh.area)
+            rec = {"n": mesh.n, "sets": 10}
+            xd = torch.from_numpy(xn).cuda()
+            yd = torch.empty_like(xd)
+            for f in ("fp64", "fp32", "bf16", "fp64_dfma"):
+                h = P.hmat_upload(blob, f)
+                for _ in range(20):
+                    P.hmat_matvec(h, xd, yd)
+                sets = [_cuda_ms(torch, lambda: P.hmat_matvec(h, xd, yd), 1000)[0] for _ in range(10)]
+                info = P.hmat_info(h)
+                med = statistics.median(sets)
+                rec["gpu_" + f] = {"ms": med, "products_per_set": 1000, "gbs": info["stored_bytes"] / (med * 1e-3) / 1e9}
+                P.hmat_destroy(h)
+            H = oracle.HMatrix(mesh.centroid, mesh.area)
+            for nt, reps in ((1, reps_cpu1), (threads, reps_cpun)):
+                oracle.set_threads(nt)
+                H.matvec(xn)
+                sets = []
+                for _ in range(10):
+                    t0 = time.perf_counter()
+                    for _ in range(reps):
+                        H.matvec(xn)
+                    sets.append((time.perf_counter() - t0) * 1e3 / reps)
+                rec[f"oracle_{nt}_threads"] = {"ms": statistics.median(sets), "products_per_set": reps}
+            oracle.set_threads(threads)
+            levels[f"icosphere_L{level}"] = rec
+        out.update({"value": levels["icosphere_L6"]["gpu_bf16"]["ms"], "levels": levels, "host_threads": threads,
+                    "config": {"workload": "matvec_protocol icosphere L4 and L6, phi = 1 + z/2"}})
     elif args.workload in ("build_icosphere_L6", "build_batch48"):
         # H-matrix construction: the host builder (OpenMP on the host cores) against
         # the device ACA builder; both produce the same blob (checked here)
@@ -381,7 +452,7 @@ def main():
     ap.add_argument("--matvec-iters", type=int, default=50)
     ap.add_argument("--workload", default="icosphere_L6",
                     choices=["icosphere_L6", "icosphere_L4", "two_spheres_L7", "multirhs64", "batch48",
-                             "build_icosphere_L6", "build_batch48"],
+                             "build_icosphere_L6", "build_batch48", "matvec_protocol"],
                     help="icosphere_L6 is the benchmark; the others print one informative line each")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -464,16 +535,11 @@ def main():
                     "matvec_ms": kt[4], "kernel_ms": {"prep": kt[0], "phase1": kt[1], "reduce": kt[2], "phase2": kt[3]},
                     "matvec_gbs": info["stored_bytes"] / (kt[4] * 1e-3) / 1e9,
                     "phase1_gbs": p1_bytes / (kt[1] * 1e-3) / 1e9, "phase2_gbs": p2_bytes / (kt[3] * 1e-3) / 1e9,
+                    "phase1_bytes": p1_bytes, "phase2_bytes": p2_bytes,
                     "stored_bytes": info["stored_bytes"], "panel_bytes": info["panel_bytes"],
                     "segments": info["segments"]}
-    head = table[args.form]
-    dom = "phase2" if head["kernel_ms"]["phase2"] >= head["kernel_ms"]["phase1"] else "phase1"
-    achieved = head[dom + "_gbs"]
-    # the kernels of the default launch shapes: the row-group expansion and the per-cluster projection
-    kname = f"k_phase2g<{args.form}>" if dom == "phase2" else f"k_phase1<{args.form}>"
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind,
-                "traffic": _profiled_traffic(kname, args.level)}
+    roofline = _roofline(table, args.form, args.level, hbm_peak, peak_kind)
+    roofline_fp64 = _roofline(table, "fp64", args.level, hbm_peak, peak_kind) if "fp64" in table else None
 
     # ---- end to end through the C ABI with pinned host buffers ----
     bh = torch.from_numpy(b_np.copy()).pin_memory()
@@ -502,8 +568,10 @@ def main():
                 "data": "synthetic",
                 "config": _config(mesh, args, {"blob_stats": stats, "host_build_s": round(build_s, 3)}),
                 "fp64_solve_ms": table.get("fp64", {}).get("solve_ms"),
+                "fp32_solve_ms": table.get("fp32", {}).get("solve_ms"),
+                "fp64_dfma_solve_ms": table.get("fp64_dfma", {}).get("solve_ms"),
                 "speedup_vs_fp64_solve": (table["fp64"]["solve_ms"] / ms_per_step) if "fp64" in table else None,
-                "forms": table, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "forms": table, "roofline": roofline, "roofline_fp64": roofline_fp64, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches,
                 "solve_info": {k: infos[-1][k] for k in ("iters", "restarts", "matvecs", "matvecs_fp64", "relres_true")}}
         print(json.dumps(line))

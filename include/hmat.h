@@ -242,10 +242,7 @@ int hmat_form_stats_get(const void *blob, size_t blob_bytes, int32_t precision, 
 int hmat_upload(const void *blob, size_t blob_bytes, int32_t precision, hmat_handle *out);
 
 /* hmat_upload with Method 3's c (eq. 19-20) for HMAT_M3, HMAT_M3_TRUNC and
- * HMAT_M3_DENSE (-1..16, else HMAT_ERR_ARG); ignored by the other forms.
- * Launch shapes (same results): the environment variable HMAT_PHASE2 =
- * cluster | rows | staged selects another expansion shape than the row groups,
- * HMAT_PHASE1 = persistent the persistent projection; read at upload. */
+ * HMAT_M3_DENSE (-1..16, else HMAT_ERR_ARG); ignored by the other forms. */
 int hmat_upload_ex(const void *blob, size_t blob_bytes, int32_t precision, int32_t method3_c, hmat_handle *out);
 
 /* Free every device and host resource of the handle (NULL is accepted). */
@@ -257,7 +254,10 @@ int hmat_destroy(hmat_handle h);
  * overlap.  Asynchronous on `stream` for device pointers.  For a HMAT_BF16
  * handle and nrhs >= 2 the columns go through the tensor-core product, 64 per
  * pass (BF16 panels times x and t split into two BF16 parts, FP32
- * accumulation); it allocates its buffers on first use.
+ * accumulation); it allocates its buffers on first use.  x and y may be host
+ * memory (staged through the handle's buffers) or device memory of the handle's
+ * GPU; device memory of another GPU is rejected (HMAT_ERR_ARG), and so it is for
+ * b and x of the solvers.
  * Errors: HMAT_ERR_ARG, HMAT_ERR_NOMEM, HMAT_ERR_CUDA.
  */
 int hmat_matvec(hmat_handle h, const double *x, double *y, int32_t nrhs, void *stream);
@@ -366,16 +366,17 @@ int hmat_bicgstab_multi(hmat_handle h, const double *b, double *x, int32_t nrhs,
 
 /*
  * hmat_matvec_noalloc -- y = A~ x for one vector, like hmat_matvec, but the call
- * allocates no memory at all.  It is meant for callers that cannot call
- * cudaMalloc when they run the product: code enqueued inside a CUDA stream
- * capture, latency-critical loops that cannot pay for an allocation, and hosts
- * or plugins whose device memory belongs to another allocator or budget.  Such
- * a caller creates the handle once at set-up (hmat_upload allocates then) and
- * afterwards only calls this function.
+ * allocates no memory at all.  The paper has no counterpart: it exists for
+ * callers that cannot call cudaMalloc when they run the product --
+ * latency-critical loops that cannot pay for an allocation (it may synchronise
+ * the device), and hosts or plugins whose device memory belongs to another
+ * allocator or budget.  Such a caller creates the handle once at set-up
+ * (hmat_upload allocates then) and afterwards only calls this function.
  *
  * x and y: device pointers (N doubles, original panel order; host pointers are
  * rejected with HMAT_ERR_ARG because staging them would need buffers), on the
- * handle's device, which must be current.  The product's scratch (source
+ * handle's device, which must be current; device memory of another GPU is
+ * rejected with HMAT_ERR_ARG.  The product's scratch (source
  * operand copy, partial sums, operand buffers) lives in one static device array
  * of HMAT_NOALLOC_SCRATCH_BYTES compiled into the library; every GPU that loads
  * the library holds that array until the process exits.  A handle whose scratch

@@ -37,6 +37,9 @@
  * the not-gpu tests (closed forms, brute force, library routines, invariants).
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -671,12 +674,26 @@ static void hmatvec_perm(const or_hmat *h, int variant, int c3, const double *xp
                 if (fabs(h->bdata[b][k]) > dense_dmax) dense_dmax = fabs(h->bdata[b][k]);
         }
 
+    /* Every block's y^_m is computed on its own (eq. 6-10, 21-24), in parallel
+       over the blocks, into a slice of yall; the slices are then added into y
+       in block order (eq. 25), so the sums are the serial ones at any thread
+       count. */
+    int64_t *yoff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(h->nb + 1));
+    yoff[0] = 0;
+    for (int64_t b = 0; b < h->nb; b++) yoff[b + 1] = yoff[b] + (h->bi_e[b] - h->bi_s[b]);
+    /* zeroed here, on one thread: a calloc'd buffer of this size would take its
+       first-touch page faults inside the parallel loop, where they serialise */
+    const size_t ybytes = sizeof(double) * (size_t)(yoff[h->nb] > 0 ? yoff[h->nb] : 1);
+    double *yall = (double *)malloc(ybytes);
+    memset(yall, 0, ybytes);
+
+#pragma omp parallel for schedule(dynamic, 4)
     for (int64_t b = 0; b < h->nb; b++) {
         int64_t is = h->bi_s[b], js = h->bj_s[b];
         int64_t m = h->bi_e[b] - is, n = h->bj_e[b] - js, r = h->brank[b];
         const double *xm = xp + js;           /* x_m of eq. (6) */
         const float *xm32 = x32 + js;
-        double *yhat = (double *)calloc((size_t)(m > 0 ? m : 1), sizeof(double));  /* y^_m, FP64 in every row of Table 1 */
+        double *yhat = yall + yoff[b];        /* y^_m, FP64 in every row of Table 1 (zero) */
 
         if (h->bkind[b] == 0) {
             const double *A = h->bdata[b];
@@ -826,11 +843,36 @@ static void hmatvec_perm(const or_hmat *h, int variant, int c3, const double *xp
                 free(yhat64); free(yhat32); free(is64); free(Vp); free(Wp); free(d);
             }
         }
+    }
+    for (int64_t b = 0; b < h->nb; b++) {
+        const double *yhat = yall + yoff[b];
+        int64_t is = h->bi_s[b], m = h->bi_e[b] - is;
         for (int64_t i = 0; i < m; i++)
             yp[is + i] = yp[is + i] + yhat[i];                                 /* eq. (25) */
-        free(yhat);
     }
+    free(yall);
+    free(yoff);
     free(x32);
+}
+
+/* Threads of the oracle's parallel loops (block fill, product); n <= 0 keeps
+ * the OpenMP default.  Results do not depend on it. */
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int or_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* y = A~ x with x, y in ORIGINAL order. */

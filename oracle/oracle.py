@@ -60,6 +60,8 @@ def lib():
             "or_gmres": (I, [P, I, I, I64, P, P, D, D, I64, I64, P]),
             "or_gmres_dense": (I, [I64, I64, P, P, P, D, I64, P]),
             "or_round_bf16_pow2": (None, [P, I64, P]),
+            "or_set_threads": (None, [I]),
+            "or_get_threads": (I, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -121,6 +123,16 @@ def aca(A, eps, rmax=None):
     V = np.zeros((max(rmax, 1), n))
     r = lib().or_aca_array(m, n, _p(A), float(eps), rmax, _p(U), _p(V))
     return U[:r].T.copy(), V[:r].T.copy()
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (the block fill of the build and the
+    product); the results are the same bits at any count."""
+    lib().or_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().or_get_threads())
 
 
 def round_bf16_pow2(a):

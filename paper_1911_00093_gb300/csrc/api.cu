@@ -21,14 +21,21 @@ using namespace hmat_internal;
 
 namespace {
 
-bool is_device_pointer(const void *p) {
+// Where a caller's vector lives: *on_device = false for host memory (the call
+// stages it), true for device or managed memory the kernels can read directly.
+// Device memory of another GPU than the handle's is rejected (HMAT_ERR_ARG):
+// the kernels would otherwise read or write a peer's memory.
+int vector_location(const void *p, int device, bool *on_device) {
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        *on_device = false;
+        return HMAT_OK;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeDevice && a.device != device) return HMAT_ERR_ARG;
+    *on_device = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return HMAT_OK;
 }
 
 Store store_of(int precision) {
@@ -53,11 +60,10 @@ namespace {
 // Algorithm 1's inner products in dpart (dotmode 1: r~ . v, v . v; 2: s . t, t . t).
 void enqueue_segments(const HmatSegment *seg, int nseg, const double *x_src, const int32_t *src_perm, double *y,
                       const int32_t *out_perm, const SolverScalars *skipS, int mode, cudaStream_t st,
-                      const double *w = nullptr, int dotmode = 0, double *dpart = nullptr,
-                      const PFold &fold = PFold()) {
+                      const double *w = nullptr, int dotmode = 0, double *dpart = nullptr) {
     if (x_src) launch_prep(seg[0].store, seg[0].ix, x_src, src_perm, seg[0].P.xs, st);
     for (int k = 0; k < nseg; ++k) {
-        launch_phase1(seg[k].store, seg[k].ix, seg[k].P, skipS, mode, st, fold);
+        launch_phase1(seg[k].store, seg[k].ix, seg[k].P, skipS, mode, st);
         launch_reduce(seg[k].store, seg[k].ix, seg[k].P, skipS, mode, st);
     }
     for (int k = 0; k < nseg; ++k) {
@@ -92,7 +98,6 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
     LrDesc *lr = nullptr;
     P2Desc *p2 = nullptr;
     double *tscale = nullptr;
-    RowDesc *rows = nullptr;
     GroupDesc *groups = nullptr;
     int st;
     if ((st = h->upload(&p1, L.p1.data(), sizeof(P1Desc) * L.p1.size())) ||
@@ -105,26 +110,14 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
         (st = h->upload(&red_tasks, L.red_tasks.data(), 4 * L.red_tasks.size())) ||
         (st = h->upload(&p2, L.p2.data(), sizeof(P2Desc) * L.p2.size())) ||
         (st = h->upload(&tscale, L.tscale.data(), 8 * L.tscale.size())) ||
-        (st = h->upload(&rows, L.rows.data(), sizeof(RowDesc) * L.rows.size())) ||
         (st = h->upload(&groups, L.groups.data(), sizeof(GroupDesc) * L.groups.size()))) {
         return st;
     }
     ix.p1 = p1; ix.p1_runs = p1_runs; ix.xdst = xdst; ix.xsel = xsel; ix.lr = lr; ix.gdst = gdst; ix.p2 = p2;
     ix.red_big = red_big; ix.red_tasks = red_tasks;
     ix.tscale = L.tscale.empty() ? nullptr : tscale;
-    ix.rows = rows;
     ix.groups = groups;
     ix.ngroups = (int32_t)L.groups.size();
-    // phase-2 launch shape (phase2_shape): row groups for every store;
-    // HMAT_PHASE2=cluster, =rows, =staged select the others (all are exact)
-    const char *p2env = std::getenv("HMAT_PHASE2");
-    ix.p2_shape = 3;
-    if (p2env && std::strcmp(p2env, "cluster") == 0) ix.p2_shape = 0;
-    if (p2env && std::strcmp(p2env, "rows") == 0) ix.p2_shape = 1;
-    if (p2env && std::strcmp(p2env, "staged") == 0) ix.p2_shape = 2;
-    if (p2env && std::strcmp(p2env, "groups") == 0) ix.p2_shape = 3;
-    const char *p1env = std::getenv("HMAT_PHASE1");
-    ix.p1_persistent = p1env && std::strcmp(p1env, "persistent") == 0;
     int nsm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     ix.nsm = std::max(1, nsm);
@@ -134,7 +127,7 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
                                 sizeof(XDst) * L.xdst.size() + 4 * L.xsel.size() + sizeof(LrDesc) * L.lr.size() +
                                 4 * L.gdst.size() +
                                 sizeof(P2Desc) * L.p2.size() + 4 * (L.red_big.size() + L.red_tasks.size()) +
-                                8 * L.tscale.size() + sizeof(RowDesc) * L.rows.size() +
+                                8 * L.tscale.size() +
                                 sizeof(GroupDesc) * L.groups.size());
     return HMAT_OK;
 }
@@ -249,10 +242,7 @@ int upload_view(const BlobView &v, int32_t precision, int32_t method3_c, const s
         if (st == HMAT_OK) st = check_layout(L);
         if (st != HMAT_OK) return st;
         CK(cudaGetDevice(&h->device));
-        CK(prepare_launches());
         h->precision = precision;
-        const char *fold_env = std::getenv("HMAT_FOLD_P");
-        h->fold_p = fold_env && std::strcmp(fold_env, "1") == 0;
         h->method3_c =
             (precision == HMAT_M3 || precision == HMAT_M3_TRUNC || precision == HMAT_M3_DENSE) ? method3_c : 0;
         h->n = L.n;
@@ -314,7 +304,7 @@ int upload_view(const BlobView &v, int32_t precision, int32_t method3_c, const s
         for (double **pp : vecs)
             if ((st = h->alloc(pp, nb))) return st;
         if ((st = h->alloc(&h->partials, sizeof(double) * 2 * (size_t)vec_blocks(L.n))) ||
-            (st = h->alloc(&h->dpart, sizeof(double) * 2 * (size_t)std::max(L.nleaves, 8 * h->seg[0].ix.nsm))) ||
+            (st = h->alloc(&h->dpart, sizeof(double) * 2 * (size_t)phase2_items(h->seg[0].ix))) ||
             (st = h->alloc(&h->S, sizeof(SolverScalars)))) {
             return st;
         }
@@ -397,7 +387,9 @@ int matvec_impl(hmat_handle h, const double *x, double *y, int32_t nrhs, void *s
     const HmatSegment *seg = fp64 ? &h->seg64 : h->seg;
     const int nseg = fp64 ? 1 : h->nseg;
     const int64_t n = h->n;
-    const bool dx = is_device_pointer(x), dy = is_device_pointer(y);
+    bool dx = false, dy = false;
+    if (int rc_ = vector_location(x, h->device, &dx)) return rc_;
+    if (int rc_ = vector_location(y, h->device, &dy)) return rc_;
     for (int32_t k = 0; k < nrhs; ++k) {
         const double *xk = x + (size_t)k * n;
         double *yk = y + (size_t)k * n;
@@ -419,32 +411,16 @@ int matvec_impl(hmat_handle h, const double *x, double *y, int32_t nrhs, void *s
     return HMAT_OK;
 }
 
-// Whether an iteration folds the p update into the first projection (one
-// segment, HMAT_FOLD_P=1 at upload; measured slower at level 6: the
-// projection's prologue gets one more dependent round).
-bool fold_p_update(const hmat_t *h) { return h->fold_p && h->nseg == 1; }
-
 // One iteration of Algorithm 1 on the device (every kernel returns at once
 // after the run has stopped).
 void enqueue_iteration(hmat_t *h, int iter_limit, cudaStream_t st) {
     const int64_t n = h->n;
     const Store s = h->seg[0].store;
     void *xs = h->seg[0].P.xs;  // operand copy shared by the segments
-    // v = A p, with alpha = rho / (r~ . v); a one-segment operator folds the p
-    // update into its projection (each projection CTA owns its cluster's rows)
-    if (fold_p_update(h)) {
-        PFold fold;
-        fold.r = h->r;
-        fold.p = h->p;
-        fold.v = h->v;
-        fold.S = h->S;
-        enqueue_segments(h->seg, h->nseg, nullptr, nullptr, h->v, nullptr, h->S, 1, st, h->rt, 1, h->dpart, fold);
-    } else {
-        launch_update_p(s, n, h->r, h->p, h->v, xs, h->S, st);
-        enqueue_segments(h->seg, h->nseg, nullptr, nullptr, h->v, nullptr, h->S, 1, st, h->rt, 1, h->dpart);
-    }
-    const HmatSegment &last = h->seg[h->nseg - 1];
-    const int ndp = phase2_items(last.store, last.ix);  // work items of the expansion that leaves the shares
+    // v = A p, with alpha = rho / (r~ . v)
+    launch_update_p(s, n, h->r, h->p, h->v, xs, h->S, st);
+    enqueue_segments(h->seg, h->nseg, nullptr, nullptr, h->v, nullptr, h->S, 1, st, h->rt, 1, h->dpart);
+    const int ndp = phase2_items(h->seg[h->nseg - 1].ix);  // work items of the expansion that leaves the shares
     launch_update_s(s, n, h->r, h->v, h->s, xs, h->S, h->partials, h->dpart, ndp, st);
     // t = A s, with omega = (t . s) / (t . t)
     enqueue_segments(h->seg, h->nseg, nullptr, nullptr, h->t, nullptr, h->S, 2, st, h->s, 2, h->dpart);
@@ -550,14 +526,16 @@ extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const
     std::memset(&inf, 0, sizeof(inf));
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = h->n;
-    const bool db = is_device_pointer(b), dx = is_device_pointer(x);
+    bool db = false, dx = false;
+    if (int rc_ = vector_location(b, h->device, &db)) return rc_;
+    if (int rc_ = vector_location(x, h->device, &dx)) return rc_;
     // kernels per product (source operand, projection, reduction when some block
     // spans several leaf clusters, expansion) and per iteration (p update, two
     // products without operand preparation whose expansions also give alpha and
     // omega, s update, x/r update with the count of the next iteration)
     const int kProductLaunches = product_launches(h->seg, h->nseg);
     const int kProduct64Launches = product_launches(&h->seg64, 1);
-    const int kIterationLaunches = (fold_p_update(h) ? 2 : 3) + 2 * (kProductLaunches - 1);
+    const int kIterationLaunches = 3 + 2 * (kProductLaunches - 1);
     const double *bsrc = b;
     if (!db) {
         CK(cudaMemcpyAsync(h->stage_in, b, 8 * n, cudaMemcpyHostToDevice, st));
@@ -801,7 +779,9 @@ int mrhs_matvec(hmat_t *h, const double *x, double *y, int32_t nrhs, cudaStream_
     auto &m = h->multi;
     const int64_t n = h->n;
     const size_t vb = 8 * (size_t)n * nrhs;
-    const bool dx = is_device_pointer(x), dy = is_device_pointer(y);
+    bool dx = false, dy = false;
+    if (int rc_ = vector_location(x, h->device, &dx)) return rc_;
+    if (int rc_ = vector_location(y, h->device, &dy)) return rc_;
     const double *src = x;
     if (!dx) {
         CK(cudaMemcpyAsync(m.stage, x, vb, cudaMemcpyHostToDevice, st));
@@ -835,7 +815,9 @@ extern "C" int hmat_bicgstab_multi(hmat_handle h, const double *b, double *x, in
     const MultiGrid g = multi_grid(h, nrhs);
     const int64_t n = h->n;
     const size_t vb = 8 * (size_t)n * nrhs;
-    const bool db = is_device_pointer(b), dx = is_device_pointer(x);
+    bool db = false, dx = false;
+    if (int rc_ = vector_location(b, h->device, &db)) return rc_;
+    if (int rc_ = vector_location(x, h->device, &dx)) return rc_;
     // products per iteration: two per column; every launch of a product is counted
     const int per_pass = multi_product_launches(h, h->seg, h->nseg, nrhs);
     const int per_pass64 = multi_product_launches(h, &h->seg64, 1, nrhs);
@@ -981,7 +963,9 @@ extern "C" int hmat_gmres(hmat_handle h, const double *b, double *x, int32_t m, 
     if (rc) return rc;
     auto &g = h->gm;
     const int64_t n = h->n;
-    const bool db = is_device_pointer(b), dx = is_device_pointer(x);
+    bool db = false, dx = false;
+    if (int rc_ = vector_location(b, h->device, &db)) return rc_;
+    if (int rc_ = vector_location(x, h->device, &dx)) return rc_;
     const int per_product = product_launches(h->seg, h->nseg), per_product64 = product_launches(&h->seg64, 1);
     int launches = 0, products = 0;
     // state: zero, then the scratch pointer

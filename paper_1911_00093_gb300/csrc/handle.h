@@ -46,7 +46,6 @@ struct hmat_t {
     int device = 0;
     int precision = 0;
     int method3_c = 0;
-    bool fold_p = false;  // fold Algorithm 1's p update into the projection (one segment; HMAT_FOLD_P=1)
     int64_t n = 0;
     const int32_t *perm = nullptr;  // [n] cluster order -> original index (device)
     HmatSegment seg[2];             // the iterated operator A~ (seg[1] adds into seg[0]'s y)

@@ -20,21 +20,15 @@ namespace hmat_internal {
 // the paper's variants keep x in FP64 (their FP32 copies are made in phase 1)
 static Store operand_store(Store s) { return is_table1(s) ? Store::F64 : s; }
 
-cudaError_t prepare_launches() {
-    cudaError_t e = staged_prepare<Store::BF16>();
-    if (e == cudaSuccess) e = staged_prepare<Store::F32>();
-    return e;
-}
-
 void launch_prep(Store s, const DevIndex &ix, const double *x, const int32_t *src_perm, void *xs, cudaStream_t st) {
     int blocks = grid_for(ix.n, 256, 4096);
     HMAT_DISPATCH(operand_store(s), (k_prep<SS><<<blocks, 256, 0, st>>>(ix.n, x, src_perm, (typename Tr<SS>::Op *)xs)));
 }
 
 void launch_phase1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                   cudaStream_t st, const PFold &fold) {
-    if (is_table1(s)) return launch_phase1_table1(s, ix, P, skipS, mode, st, fold);
-    HMAT_DISPATCH(s, phase1_launch<SS>(ix, P, skipS, mode, st, fold));
+                   cudaStream_t st) {
+    if (is_table1(s)) return launch_phase1_table1(s, ix, P, skipS, mode, st);
+    HMAT_DISPATCH(s, phase1_launch<SS>(ix, P, skipS, mode, st));
 }
 
 void launch_reduce(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,

@@ -21,25 +21,11 @@ struct DevIndex {
     const int32_t *red_big = nullptr, *red_tasks = nullptr;
     const P2Desc *p2 = nullptr;     // [nleaves]
     const double *tscale = nullptr; // per-rank factors of LrDesc::toff (paper's Methods 2 and 3)
-    const RowDesc *rows = nullptr;  // [n] phase-2 rows (cluster order)
     const GroupDesc *groups = nullptr;  // row groups of the row-group expansion
     int32_t ngroups = 0;
-    int32_t p2_shape = 3;           // expansion: 0 per cluster, 1 row-persistent, 2 staged, 3 row groups
-    int32_t nsm = 1;                // SMs of the device (row-persistent grid = nsm x p2w_blocks)
-    int32_t p1_persistent = 0;      // projection: 1 persistent CTAs with staged prologues (HMAT_PHASE1)
+    int32_t nsm = 1;                // SMs of the device (row-group grid = nsm x kP2gBlocks)
     int32_t max_leaf = 0;           // rows of the widest leaf cluster
     int32_t max_ld2 = 0;            // widest phase-2 panel (entries)
-};
-
-// Algorithm 1's p update folded into the next projection: each projection CTA
-// updates the rows of its leaf cluster, p = r + beta (p - omega v) (p = r at a
-// run's first iteration), and projects the new p (null: the operand copy).
-struct SolverScalars;
-struct PFold {
-    const double *r = nullptr;
-    double *p = nullptr;
-    const double *v = nullptr;
-    SolverScalars *S = nullptr;
 };
 
 // One precision copy of the panels plus its work buffers.
@@ -52,42 +38,15 @@ struct DevPanels {
     void *g = nullptr;         // phase-2 operand buffers (glen entries of the operand type)
 };
 
-// CTAs per SM of the row-persistent phase-2 launch (its launch bound).  Four,
-// with two 16-byte vectors per lane and row in flight for 2- and 4-byte panels:
-// BF16 at three CTAs and four vectors measured slower (67.9 vs 57.7 us at L6).
-constexpr int p2w_blocks(Store) { return 4; }
-
-// Phase-2 launch shape of a store: 3 row groups (persistent warps over groups
-// of four rows of one cluster sharing each operand load; the default for every
-// store), 0 one CTA per leaf row cluster (HMAT_PHASE2=cluster; also the 8-byte
-// stores under the two shapes below), 1 row-persistent warps over single rows
-// (HMAT_PHASE2=rows), 2 staged (a persistent CTA per SM streaming through shared
-// memory with bulk copies; BF16 and FP32 panels whose rows fit a slot;
-// HMAT_PHASE2=staged).  Measured at L6: BF16 expansion 51.0 us (groups), 57.7
-// (rows), 61.7 (cluster), 100.5 (staged); double-float 129.1 (groups) vs 133.3
-// (cluster); IEEE FP64 221.6 vs 277.1.
-constexpr int kStagedSlotBytes = 16384;
-constexpr int kStagedSmemMax = 200 * 1024;  // its ring of slots plus two operand slots
-// raise the launch limits the staged expansion needs (once per process and device)
-cudaError_t prepare_launches();
-inline int phase2_shape(Store s, const DevIndex &ix) {
-    if (ix.p2_shape == 0) return 0;
-    if (ix.p2_shape == 3) return 3;
-    if (s == Store::DF || s == Store::F64) return 0;
-    const int esz = s == Store::BF16 ? 2 : 4;
-    if (ix.p2_shape == 2 && (s == Store::BF16 || s == Store::F32) && ix.max_ld2 * esz <= kStagedSlotBytes) return 2;
-    return 1;
-}
-inline bool phase2_rows(Store s, const DevIndex &ix) { return phase2_shape(s, ix) == 1; }
-// Work items whose inner-product shares a solver expansion leaves in dpart.
-inline int phase2_items(Store s, const DevIndex &ix) {
-    switch (phase2_shape(s, ix)) {
-    case 1: return ix.nsm * p2w_blocks(s);
-    case 2: return ix.nsm;
-    case 3: return ix.nsm * 4;
-    default: return ix.nleaves;
-    }
-}
+// The expansion runs as persistent warps over groups of up to four rows of one
+// leaf row cluster (k_phase2g), kP2gBlocks CTAs per SM.  Measured at L6 against
+// the launch shapes it replaced (BF16 expansion): 51.0 us for row groups, 57.7
+// for row-persistent warps, 61.7 for one CTA per leaf row cluster, 100.5 for a
+// bulk-copy pipeline through shared memory.
+constexpr int kP2gBlocks = 4;
+// Work items (CTAs) of the expansion; a solver expansion leaves one pair of
+// inner-product shares per item in dpart.
+inline int phase2_items(const DevIndex &ix) { return ix.nsm * kP2gBlocks; }
 
 // Operand bytes per entry for a store (x and t copies).
 inline size_t operand_bytes(Store s) { return s == Store::F32 || s == Store::BF16 ? 4 : 8; }
@@ -102,20 +61,21 @@ struct SolverScalars;
 // skipS/mode: a solver's product is skipped once its run has stopped (mode 1:
 // flag set; mode 2: flag set or stop at the ||s|| check); mode 0 never skips.
 void launch_phase1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                   cudaStream_t st, const PFold &fold = PFold());
+                   cudaStream_t st);
 // t of the blocks spanning several leaf clusters, scattered into g (no launch when there is none)
 void launch_reduce(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
                    cudaStream_t st);
 // y[p] (cluster order) or y[out_perm[p]] (original order) = (A~ x)_p, or
 // y[.] += (A~ x)_p when accum is set (the second segment of a paper variant);
 // dotmode 1/2 also leaves, per work item k, w . y in dpart[k] and y . y in
-// dpart[nleaves + k] (w = r~ for alpha, w = s for omega of Algorithm 1)
+// dpart[items + k] (items = phase2_items; w = r~ for alpha, w = s for omega of
+// Algorithm 1)
 void launch_phase2(Store s, const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm, int accum,
                    const SolverScalars *skipS, int mode, cudaStream_t st, const double *w = nullptr,
                    int dotmode = 0, double *dpart = nullptr);
 // the same for the paper's stores (kernels_table1.cu)
 void launch_phase1_table1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                          cudaStream_t st, const PFold &fold);
+                          cudaStream_t st);
 void launch_reduce_table1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
                           cudaStream_t st);
 void launch_phase2_table1(Store s, const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm,

@@ -16,8 +16,8 @@ namespace hmat_internal {
     }
 
 void launch_phase1_table1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                          cudaStream_t st, const PFold &fold) {
-    HMAT_T1_DISPATCH(s, phase1_launch<SS>(ix, P, skipS, mode, st, fold));
+                          cudaStream_t st) {
+    HMAT_T1_DISPATCH(s, phase1_launch<SS>(ix, P, skipS, mode, st));
 }
 
 void launch_reduce_table1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,

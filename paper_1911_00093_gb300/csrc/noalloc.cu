@@ -3,12 +3,12 @@
 // allocates no memory.
 //
 // Who needs it: callers that must not allocate device memory at the time they
-// run the product -- code enqueued inside a CUDA stream capture (cudaMalloc is
-// not a capturable operation and stalls or invalidates the capture), real-time
-// or latency-critical loops that cannot pay for an allocation, and host
+// run the product -- real-time or latency-critical loops that cannot pay for a
+// cudaMalloc (it can synchronise the device and take milliseconds), and host
 // programs or plugins whose device memory is owned by another allocator or
-// memory budget they may not touch.  They create the handle once at set-up
-// (hmat_upload allocates then) and afterwards call only this entry point.
+// memory budget (a framework's caching allocator, a fixed reservation) that
+// they may not go around.  They create the handle once at set-up (hmat_upload
+// allocates then) and afterwards call only this entry point.
 //
 // The scratch is the source-vector operand copy, the projection partial sums
 // and the phase-2 operand buffers; the handle's own copies of those buffers are
@@ -48,13 +48,16 @@ int scratch_address(int dev, void **out) {
     return HMAT_OK;
 }
 
-bool on_device(const void *p) {
+// Device (or managed) memory the kernels on `device` may use: device memory of
+// another GPU is refused, the kernels would read or write a peer's memory.
+bool on_device(const void *p, int device) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeDevice) return a.device == device;
+    return a.type == cudaMemoryTypeManaged;
 }
 
 size_t scratch_bytes_for(const hmat_t *h) {
@@ -71,7 +74,7 @@ extern "C" int hmat_matvec_noalloc(hmat_handle h, const double *x, double *y, vo
     int dev = -1;
     CK(cudaGetDevice(&dev));
     if (dev != h->device || dev < 0 || dev >= kMaxDevices) return HMAT_ERR_ARG;
-    if (!on_device(x) || !on_device(y)) return HMAT_ERR_ARG;  // no staging buffers: device pointers only
+    if (!on_device(x, dev) || !on_device(y, dev)) return HMAT_ERR_ARG;  // no staging buffers: this device's memory only
     if (h->nseg != 1) return HMAT_ERR_UNSUPPORTED;            // the paper's two-segment variants
     const size_t need = scratch_bytes_for(h);
     if (need > kNoallocScratchBytes) return HMAT_ERR_UNSUPPORTED;

@@ -91,8 +91,8 @@ __device__ __forceinline__ double df_to_double(DF a) { return (double)a.s + (dou
 __device__ __forceinline__ int4 ld_stream(const void *p) { return __ldcs((const int4 *)p); }
 
 // Algorithm 1's search direction, p = r + beta (p - omega v), or r at a run's
-// first iteration; explicit roundings, so the p-update kernel and the
-// projection that folds it in give the same bits
+// first iteration, with explicit roundings (no contraction choices left to the
+// compiler)
 __device__ __forceinline__ double p_next(bool first, double r, double p, double v, double beta, double omega) {
     return first ? r : __fma_rn(beta, __fma_rn(-omega, v, p), r);
 }
@@ -131,8 +131,7 @@ template <Store S> struct Acc {
 };
 template <> struct Acc<Store::DF> {
     DF a;
-    int n;
-    __device__ void init() { a.s = 0.f; a.c = 0.f; n = 0; }
+    __device__ void init() { a.s = 0.f; a.c = 0.f; }
 };
 template <> struct Acc<Store::F64> {
     double a;
@@ -146,8 +145,7 @@ template <> struct Acc<Store::F32> {
 template <> struct Acc<Store::BF16> {
     DF a;
     float ch;
-    int cnt;
-    __device__ void init() { a.s = 0.f; a.c = 0.f; ch = 0.f; cnt = 0; }
+    __device__ void init() { a.s = 0.f; a.c = 0.f; ch = 0.f; }
 };
 
 // Multiply one 16-byte panel vector by VW operands and accumulate into VW
@@ -443,7 +441,7 @@ __global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc 
                                                         typename Tr<S>::Part *__restrict__ part,
                                                         typename Tr<S>::Op *__restrict__ g,
                                                         const double *__restrict__ tscale, const SolverScalars *S_,
-                                                        int mode, PFold fold) {
+                                                        int mode) {
     using Op = typename Tr<S>::Op;
     __shared__ Op xk[kMaxLeaf];  // x_kappa, broadcast to every thread
     // the cluster's run and dense-operand descriptors, loaded with x_kappa so
@@ -453,32 +451,9 @@ __global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc 
     if (skip_product(S_, mode)) return;
     const P1Desc d = desc[blockIdx.x];
     const bool runs_sm = d.rcnt <= kP1SmemRuns, xd_sm = d.xdcnt <= kP1SmemXd;
-    if (fold.S) {  // Algorithm 1's p update of this cluster's rows, then project the new p
-        SolverScalars *FS = fold.S;
-        const double rho = FS->rho;
-        if (!isfinite(rho) || rho == 0.0) {  // rho_{i-1} = 0: the method fails (every CTA returns)
-            if (blockIdx.x == 0 && threadIdx.x == 0)
-                FS->flag = isfinite(rho) ? HMAT_ERR_BREAKDOWN_RHO : HMAT_ERR_NONFINITE;
-            return;
-        }
-        if (blockIdx.x == 0 && threadIdx.x == 0) FS->nmv += 1;  // v = A p
-        const bool first = FS->iter_in_run == 0;
-        const double beta = first ? 0.0 : (rho / FS->rho_prev) * (FS->alpha / FS->omega);
-        const double omega = FS->omega;
-        for (int j = threadIdx.x; j < d.xlen; j += NT) {
-            const int i = d.xbeg + j;
-            const double pv = p_next(first, fold.r[i], fold.p[i], fold.v[i], beta, omega);
-            fold.p[i] = pv;
-            if constexpr (S == Store::DF) xk[j] = split_double(pv);
-            else if constexpr (S == Store::F64) xk[j] = pv;
-            else if constexpr (is_table1(S)) xk[j] = fp32_source(S) ? (double)__double2float_rn(pv) : pv;
-            else xk[j] = __double2float_rn(pv);
-        }
-    } else {
-        for (int j = threadIdx.x; j < d.xlen; j += NT) {
-            if constexpr (fp32_source(S)) xk[j] = (double)__double2float_rn(xs[d.xbeg + j]);  // Section 3.5
-            else xk[j] = xs[d.xbeg + j];
-        }
+    for (int j = threadIdx.x; j < d.xlen; j += NT) {
+        if constexpr (fp32_source(S)) xk[j] = (double)__double2float_rn(xs[d.xbeg + j]);  // Section 3.5
+        else xk[j] = xs[d.xbeg + j];
     }
     if (runs_sm)
         for (int j = threadIdx.x; j < d.rcnt; j += NT) rs[j] = runs[d.rbeg + j];
@@ -488,78 +463,6 @@ __global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc 
     p1_cluster<S, NT>(d, xk, runs_sm ? rs : nullptr, xd_sm ? xds : nullptr, runs, xdst, xsel, lr, gdst, q1, part, g,
                       tscale);
 }
-
-// asynchronous global -> shared copies (cp.async; 4, 8 or 16 bytes, both
-// addresses aligned to the size), completed by cp_async_wait_all
-template <int B> __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    if constexpr (B == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-    else asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(gmem), "n"(B) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Persistent projection: CTA b takes the clusters b, b + G, b + 2G, ... (G
-// CTAs), and while it works on one cluster the next one's x slice, runs and
-// dense slices are already on their way into the other half of a double
-// buffer (cp.async), the descriptor two clusters ahead into a third slot; so a
-// cluster starts streaming without the two dependent loads of its prologue.
-// The same arithmetic per cluster as k_phase1, so the same bits.
-template <Store S, int NT = p1_threads<S>()>
-__global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1p(
-    int ncl, const P1Desc *__restrict__ desc, const P1Run *__restrict__ runs, const XDst *__restrict__ xdst,
-    const int32_t *__restrict__ xsel, const LrDesc *__restrict__ lr, const int32_t *__restrict__ gdst,
-    const void *__restrict__ q1, const typename Tr<S>::Op *__restrict__ xs, typename Tr<S>::Part *__restrict__ part,
-    typename Tr<S>::Op *__restrict__ g, const double *__restrict__ tscale, const SolverScalars *S_, int mode) {
-    using Op = typename Tr<S>::Op;
-    static_assert(sizeof(P1Desc) == 48 && sizeof(P1Run) == 16 && sizeof(XDst) == 16, "cp.async granules");
-    __shared__ __align__(16) Op xk[2][kMaxLeaf];
-    __shared__ __align__(16) P1Run rs[2][kP1SmemRuns];
-    __shared__ __align__(16) XDst xds[2][kP1SmemXd];
-    __shared__ __align__(16) P1Desc dsm[3];
-    if (skip_product(S_, mode)) return;
-    const int G = gridDim.x;
-    int c = blockIdx.x;
-    if (c >= ncl) return;
-    auto stage_desc = [&](int cl, int slot) {
-        if (threadIdx.x < 3) cp_async<16>(reinterpret_cast<int4 *>(&dsm[slot]) + threadIdx.x,
-                                          reinterpret_cast<const int4 *>(desc + cl) + threadIdx.x);
-    };
-    auto stage_body = [&](const P1Desc &d, int b) {
-        for (int j = threadIdx.x; j < d.xlen; j += NT) cp_async<sizeof(Op)>(&xk[b][j], xs + d.xbeg + j);
-        if (d.rcnt <= kP1SmemRuns)
-            for (int j = threadIdx.x; j < d.rcnt; j += NT) cp_async<16>(&rs[b][j], runs + d.rbeg + j);
-        if (d.xdcnt <= kP1SmemXd)
-            for (int j = threadIdx.x; j < d.xdcnt; j += NT) cp_async<16>(&xds[b][j], xdst + d.xdbeg + j);
-    };
-    // the first cluster's descriptor and body, the second's descriptor
-    stage_desc(c, 0);
-    if (c + G < ncl) stage_desc(c + G, 1);
-    cp_async_commit();
-    cp_async_wait_all();
-    __syncthreads();
-    stage_body(dsm[0], 0);
-    cp_async_commit();
-    int slot = 0, b = 0;
-    for (; c < ncl; c += G) {
-        cp_async_wait_all();  // this cluster's body and the next one's descriptor
-        __syncthreads();      // ... visible to all; the other buffer's last reader is done
-        const P1Desc &d = dsm[slot];
-        if constexpr (fp32_source(S)) {  // Section 3.5: the FP32 copy of x
-            for (int j = threadIdx.x; j < d.xlen; j += NT) xk[b][j] = (double)__double2float_rn(xk[b][j]);
-            __syncthreads();
-        }
-        if (c + G < ncl) stage_body(dsm[(slot + 1) % 3], b ^ 1);
-        if (c + 2 * G < ncl) stage_desc(c + 2 * G, (slot + 2) % 3);
-        cp_async_commit();
-        p1_cluster<S, NT>(d, xk[b], d.rcnt <= kP1SmemRuns ? rs[b] : nullptr, d.xdcnt <= kP1SmemXd ? xds[b] : nullptr,
-                          runs, xdst, xsel, lr, gdst, q1, part, g, tscale);
-        slot = (slot + 1) % 3;
-        b ^= 1;
-    }
-    cp_async_wait_all();
-}
-
 
 // ------------------------------------------------------------------------
 // reduce: t of the blocks spanning several leaf clusters, in a fixed order,
@@ -684,17 +587,9 @@ __device__ __forceinline__ void row_mac(Acc<S> &acc, int4 raw, const GV<S> &gv) 
             acc.a = fma((double)w[e], x[e], acc.a);
     }
 }
-template <>
-__device__ __forceinline__ void row_mac<Store::DF>(Acc<Store::DF> &acc, int4 raw, const GV<Store::DF> &gv) {
-    float4 v = *reinterpret_cast<float4 *>(&raw);
-    const float4 x = gv.v;
-    df_fma(acc.a, v.x, v.y, x.x, x.y);
-    df_fma(acc.a, v.z, v.w, x.z, x.w);
-    if (++acc.n == 4) { renorm(acc.a); acc.n = 0; }
-}
-// row_mac without the per-row fold counter: a caller that advances several rows
-// in step folds them itself (fold<S>) after every kFoldVecs vectors, which
-// gives the same bits as the per-row counters
+// One panel vector of a row: the row-group expansion advances its rows in step
+// and folds the double-float and BF16 accumulators itself (fold<S>) after every
+// kFoldVecs vectors
 constexpr int kFoldVecs = 4;
 template <Store S>
 __device__ __forceinline__ void row_mac_nofold(Acc<S> &acc, int4 raw, const GV<S> &gv) {
@@ -736,21 +631,6 @@ __device__ __forceinline__ void row_mac<Store::F32>(Acc<Store::F32> &acc, int4 r
     c = fmaf(v.w, x.w, c);
     two_sum_acc(acc.a, c);  // one chunk of 4 products
 }
-template <>
-__device__ __forceinline__ void row_mac<Store::BF16>(Acc<Store::BF16> &acc, int4 raw, const GV<Store::BF16> &gv) {
-    const float4 x0 = gv.a, x1 = gv.b;
-    float c = acc.ch;
-    c = fmaf(bf_lo((uint32_t)raw.x), x0.x, c);
-    c = fmaf(bf_hi((uint32_t)raw.x), x0.y, c);
-    c = fmaf(bf_lo((uint32_t)raw.y), x0.z, c);
-    c = fmaf(bf_hi((uint32_t)raw.y), x0.w, c);
-    c = fmaf(bf_lo((uint32_t)raw.z), x1.x, c);
-    c = fmaf(bf_hi((uint32_t)raw.z), x1.y, c);
-    c = fmaf(bf_lo((uint32_t)raw.w), x1.z, c);
-    c = fmaf(bf_hi((uint32_t)raw.w), x1.w, c);
-    acc.ch = c;
-    if (++acc.cnt == 4) { two_sum_acc(acc.a, acc.ch); acc.ch = 0.f; acc.cnt = 0; }  // chunk of 32
-}
 
 // the lane partial of one row as a reduction accumulator
 template <Store S>
@@ -763,228 +643,18 @@ __device__ __forceinline__ typename RedT<S>::T row_partial(Acc<S> &a) {
     }
 }
 
-// Row totals of a phase-2 work item: each warp adds its rows' lane partials with
-// a fixed butterfly; lane 0 writes y (or adds to it, accum).  In a solver product
-// (dotmode != 0, Algorithm 1) the work item also leaves its share of two inner
-// products in dpart -- w . y in dpart[item], y . y in dpart[items + item] (rows
-// in warp-major order, warps in order) -- for the next vector kernel, which adds
-// the shares up in item order (alpha = rho / (r~ . v), omega = (t . s) / (t . t)).
-template <Store S, int MR>
-__device__ __forceinline__ void phase2_epilogue(const P2Desc &d, Acc<S> (&acc)[MR], double *__restrict__ y,
-                                                const int32_t *__restrict__ out_perm, int accum,
-                                                const double (&wv)[MR], int dotmode, double *dpart) {
-    using RT = typename RedT<S>::T;
-    __shared__ double wsum[2][kP2Warps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double dw = 0.0, dy = 0.0;
-#pragma unroll
-    for (int rr = 0; rr < MR; ++rr) {
-        const int i = warp + rr * kP2Warps;
-        if (i < d.ylen) {
-            RT a = row_partial<S>(acc[rr]);
-            for (int m = 16; m >= 1; m >>= 1) a = red_xor<S>(a, m, (lane & m) != 0);  // the canonical row order
-            double out;
-            if constexpr (red_double(S)) out = a;
-            else out = df_to_double(a);
-            if (lane == 0) {
-                const int p = d.ybeg + i;
-                const int q = out_perm ? out_perm[p] : p;
-                if (accum) out = y[q] + out;  // a later segment adds to the earlier ones' rows
-                y[q] = out;
-                if (dotmode != 0) {
-                    dw += wv[rr] * out;
-                    dy += out * out;
-                }
-            }
-        }
-    }
-    if (dotmode == 0) return;
-    if (lane == 0) {
-        wsum[0][warp] = dw;
-        wsum[1][warp] = dy;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int k = 0; k < kP2Warps; ++k) { a += wsum[0][k]; b += wsum[1][k]; }
-        dpart[blockIdx.x] = a;
-        dpart[gridDim.x + blockIdx.x] = b;
-    }
-}
-
-template <Store S, int MR>
-__global__ void __launch_bounds__(kP2Threads, MR == 4 ? 3 : 2) k_phase2(const P2Desc *__restrict__ desc,
-                                                                       const void *__restrict__ p2,
-                                                                       const typename Tr<S>::Op *__restrict__ g,
-                                                                       double *__restrict__ y,
-                                                                       const int32_t *__restrict__ out_perm,
-                                                                       int accum, const SolverScalars *S_, int mode,
-                                                                       const double *__restrict__ w, int dotmode,
-                                                                       double *dpart) {
-    using Op = typename Tr<S>::Op;
-    constexpr int VW = Tr<S>::VW;
-    if (skip_product(S_, mode)) return;
-    const P2Desc d = desc[blockIdx.x];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t esz = 16 / VW;
-    const char *base = (const char *)p2 + (size_t)d.off * esz;
-    const size_t row_bytes = (size_t)d.ld * esz;
-    const Op *gr = g + d.goff;  // operands of this row cluster, read through L1 by every warp
-
-    Acc<S> acc[MR];
-#pragma unroll
-    for (int r = 0; r < MR; ++r) acc[r].init();
-    double wv[MR];  // w of the fused inner products, loaded ahead of the stream
-#pragma unroll
-    for (int r = 0; r < MR; ++r) {
-        const int i = warp + r * kP2Warps;
-        wv[r] = (dotmode != 0 && lane == 0 && i < d.ylen) ? __ldg(w + d.ybeg + i) : 0.0;
-    }
-    const int nv = d.ld / VW;
-    int v = lane;
-    // two vectors per row in flight per iteration
-    for (; v + 32 < nv; v += 64) {
-        int4 ra[MR], rb[MR];
-#pragma unroll
-        for (int rr = 0; rr < MR; ++rr) {
-            const int i = warp + rr * kP2Warps;
-            const char *p = base + (size_t)i * row_bytes + (size_t)v * 16;
-            ra[rr] = i < d.ylen ? ld_stream(p) : make_int4(0, 0, 0, 0);
-            rb[rr] = i < d.ylen ? ld_stream(p + 32 * 16) : make_int4(0, 0, 0, 0);
-        }
-        const GV<S> ga = GV<S>::load(gr + v * VW), gb = GV<S>::load(gr + (v + 32) * VW);
-#pragma unroll
-        for (int rr = 0; rr < MR; ++rr)
-            if (warp + rr * kP2Warps < d.ylen) { row_mac<S>(acc[rr], ra[rr], ga); row_mac<S>(acc[rr], rb[rr], gb); }
-    }
-    if (v < nv) {
-        int4 ra[MR];
-#pragma unroll
-        for (int rr = 0; rr < MR; ++rr) {
-            const int i = warp + rr * kP2Warps;
-            ra[rr] = i < d.ylen ? ld_stream(base + (size_t)i * row_bytes + (size_t)v * 16) : make_int4(0, 0, 0, 0);
-        }
-        const GV<S> ga = GV<S>::load(gr + v * VW);
-#pragma unroll
-        for (int rr = 0; rr < MR; ++rr)
-            if (warp + rr * kP2Warps < d.ylen) row_mac<S>(acc[rr], ra[rr], ga);
-    }
-    phase2_epilogue<S, MR>(d, acc, y, out_perm, accum, wv, dotmode, dpart);
-}
-
-// Row-persistent phase 2: a fixed grid (p2w_blocks CTAs per SM) whose
-// warps each own the rows p = gw, gw + W, gw + 2W, ... (W warps in all), two rows
-// at a time with up to p2w_vec 16-byte vectors per lane and row in flight; no
-// barrier until the CTA's last row.  Each row's lane partials are added by the
-// fixed butterfly and lane 0 writes y (or adds to it, accum); with dotmode set
-// the warp adds its rows' w . y and y . y in row order, and the CTA leaves the
-// sum over its warps, in warp order, in dpart[block] and dpart[grid + block].
-// vectors per lane and row in flight: four for the 8-byte stores, whose rows
-// are twice as many vectors; fewer for the others to stay within 64 registers
-template <Store S> constexpr int p2w_vec() { return Tr<S>::VW == 2 ? 4 : 2; }
-
-template <Store S>
-__device__ __forceinline__ double row_total(Acc<S> &acc) {
-    using RT = typename RedT<S>::T;
-    const int lane = threadIdx.x & 31;
-    RT a = row_partial<S>(acc);
-    for (int m = 16; m >= 1; m >>= 1) a = red_xor<S>(a, m, (lane & m) != 0);  // the canonical row order
-    if constexpr (red_double(S)) return a;
-    else return df_to_double(a);
-}
-
-template <Store S>
-__global__ void __launch_bounds__(kP2Threads, p2w_blocks(S)) k_phase2w(
-    int n, const RowDesc *__restrict__ rows, const void *__restrict__ p2, const typename Tr<S>::Op *__restrict__ g,
-    double *__restrict__ y, const int32_t *__restrict__ out_perm, int accum, const SolverScalars *S_, int mode,
-    const double *__restrict__ w, int dotmode, double *dpart) {
-    constexpr int VW = Tr<S>::VW;
-    constexpr size_t esz = 16 / VW;
-    __shared__ double wsum[2][kP2Warps];
-    if (skip_product(S_, mode)) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int W = gridDim.x * kP2Warps;
-    const RowDesc none{0, 0, 0};
-    double dw = 0.0, dy = 0.0;
-    int p0 = blockIdx.x * kP2Warps + warp;
-    // descriptors of the current row pair; the next pair's are loaded one pair ahead
-    RowDesc c0 = p0 < n ? rows[p0] : none, c1 = p0 + W < n ? rows[p0 + W] : none;
-    for (; p0 < n; p0 += 2 * W) {
-        const RowDesc n0 = p0 + 2 * W < n ? rows[p0 + 2 * W] : none;
-        const RowDesc n1 = p0 + 3 * W < n ? rows[p0 + 3 * W] : none;
-        const char *row0 = (const char *)p2 + (size_t)c0.off * esz, *row1 = (const char *)p2 + (size_t)c1.off * esz;
-        const typename Tr<S>::Op *g0 = g + c0.goff, *g1 = g + c1.goff;
-        const int nv0 = c0.ld / VW, nv1 = c1.ld / VW;
-        // w of the inner products, loaded ahead of the stream
-        const double w0 = (dotmode != 0 && lane == 0) ? __ldg(w + p0) : 0.0;
-        const double w1 = (dotmode != 0 && lane == 0 && nv1) ? __ldg(w + p0 + W) : 0.0;
-        Acc<S> a0, a1;
-        a0.init();
-        a1.init();
-        const int nvmax = max(nv0, nv1);
-        constexpr int NVEC = p2w_vec<S>();
-        for (int c = 0; c < nvmax; c += 32 * NVEC) {
-            int4 ra[NVEC], rb[NVEC];
-#pragma unroll
-            for (int u = 0; u < NVEC; ++u) {
-                const int v = c + lane + 32 * u;
-                ra[u] = v < nv0 ? ld_stream(row0 + (size_t)v * 16) : make_int4(0, 0, 0, 0);
-                rb[u] = v < nv1 ? ld_stream(row1 + (size_t)v * 16) : make_int4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (int u = 0; u < NVEC; ++u) {
-                const int v = c + lane + 32 * u;
-                if (v < nv0) row_mac<S>(a0, ra[u], GV<S>::load(g0 + v * VW));
-                if (v < nv1) row_mac<S>(a1, rb[u], GV<S>::load(g1 + v * VW));
-            }
-        }
-        const double o0 = row_total<S>(a0);
-        const double o1 = nv1 ? row_total<S>(a1) : 0.0;  // warp-uniform condition
-        if (lane == 0) {
-            const int ps[2] = {p0, p0 + W};
-            const double os[2] = {o0, o1}, ws[2] = {w0, w1};
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                if (k == 1 && nv1 == 0) continue;
-                const int p = ps[k];
-                const int q = out_perm ? out_perm[p] : p;
-                double out = os[k];
-                if (accum) out = y[q] + out;  // a later segment adds to the earlier ones' rows
-                y[q] = out;
-                if (dotmode != 0) {
-                    dw += ws[k] * out;
-                    dy += out * out;
-                }
-            }
-        }
-        c0 = n0;
-        c1 = n1;
-    }
-    if (dotmode == 0) return;
-    if (lane == 0) {
-        wsum[0][warp] = dw;
-        wsum[1][warp] = dy;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int k = 0; k < kP2Warps; ++k) { a += wsum[0][k]; b += wsum[1][k]; }
-        dpart[blockIdx.x] = a;
-        dpart[gridDim.x + blockIdx.x] = b;
-    }
-}
-
 // Row-group expansion: persistent warps over groups of up to four consecutive
 // rows of one leaf row cluster, so each 16-byte operand vector g_rho is loaded
-// once for the group's rows (the row-persistent kernel loads it per row).
-template <Store S> constexpr int p2g_blocks() { return 4; }
+// once for the group's rows.
 
 // Totals of a group's four rows from the lanes' partials with 12 shuffles
 // instead of four butterflies of 5: the xor-16 step keeps rows 0-1 in the lower
 // half-warp and rows 2-3 in the upper, the xor-8 step one row per quarter, and
 // xor 4, 2, 1 finish it.  Every pairing adds the lower lane's value first, in
 // the canonical order (16, 8, 4, 2, 1), so lanes 8r..8r+7 hold exactly row r's
-// canonical total.  Rows past the group's end are zero and unused.
+// canonical total (the canonical butterfly: lane partials paired at xor 16, 8,
+// 4, 2, 1, the lower lane's value first).  Rows past the group's end are zero
+// and unused.
 template <Store S>
 __device__ __forceinline__ double group_totals(Acc<S> (&acc)[kGroupRows], int lane) {
     static_assert(kGroupRows == 4, "the transposed reduction is written for four rows");
@@ -1033,7 +703,7 @@ __device__ __forceinline__ GroupDesc group_from_words(int32_t word) {
 }
 
 template <Store S>
-__global__ void __launch_bounds__(kP2Threads, p2g_blocks<S>()) k_phase2g(
+__global__ void __launch_bounds__(kP2Threads, kP2gBlocks) k_phase2g(
     int ng, const GroupDesc *__restrict__ groups, const void *__restrict__ p2, const typename Tr<S>::Op *__restrict__ g,
     double *__restrict__ y, const int32_t *__restrict__ out_perm, int accum, const SolverScalars *S_, int mode,
     const double *__restrict__ w, int dotmode, double *dpart) {
@@ -1123,213 +793,6 @@ __global__ void __launch_bounds__(kP2Threads, p2g_blocks<S>()) k_phase2g(
     }
 }
 
-// ------------------------------------------------------------------------
-// Staged expansion (2- and 4-byte panels): a persistent CTA per SM in which one
-// producer thread streams the row clusters' operands and panel rows into rings
-// of shared-memory slots with bulk copies (cp.async.bulk, completion counted on
-// mbarriers) while eight consumer warps compute rows out of shared memory, so
-// the HBM stream does not wait on the arithmetic or on per-item latencies.
-// Items (leaf row clusters) are dealt round robin; a warp owns rows of a chunk;
-// each row's lane partials are added by the fixed butterfly and lane 0 writes y
-// (deterministic, no atomics).  Every wait is bounded in time: a wait that gives
-// up sets g_stage_abort and the CTA abandons the product (never expected).
-// ------------------------------------------------------------------------
-constexpr int kTsSlots = 8;                    // panel chunk slots
-constexpr int kTsSlot = kStagedSlotBytes;      // bytes per chunk slot (>= one row, checked by phase2_shape)
-constexpr int kTsGSlots = 2;                   // operand slots
-constexpr int kTsConsumers = 8;                // consumer warps
-constexpr int kTsThreads = 32 * (kTsConsumers + 1);
-constexpr long long kTsWaitCycles = 4000000000ll;  // ~2 s at the SM clock
-
-__device__ unsigned int g_stage_abort;
-
-__device__ __forceinline__ uint32_t s_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mb_init(uint64_t *b, int count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(s_addr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mb_arrive(uint64_t *b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(s_addr(b)) : "memory");
-}
-__device__ __forceinline__ void mb_expect_tx(uint64_t *b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(s_addr(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mb_test(uint64_t *b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(s_addr(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Wait for the phase of `parity` to complete; false when this CTA has given up.
-__device__ __forceinline__ bool mb_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag) {
-    const long long t0 = clock64();
-    while (!mb_test(b, parity)) {
-        if (*abort_flag) return false;
-        if (clock64() - t0 > kTsWaitCycles) {
-            *abort_flag = 1;
-            atomicExch(&g_stage_abort, 1u);
-            return false;
-        }
-    }
-    return true;
-}
-__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                     s_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(s_addr(bar))
-                 : "memory");
-}
-
-template <Store S>
-__device__ __forceinline__ GV<S> gv_shared(const typename Tr<S>::Op *p) {
-    GV<S> r;
-    if constexpr (S == Store::BF16) {
-        r.a = reinterpret_cast<const float4 *>(p)[0];
-        r.b = reinterpret_cast<const float4 *>(p)[1];
-    } else {
-        r.v = reinterpret_cast<const float4 *>(p)[0];
-    }
-    return r;
-}
-
-template <Store S>
-__global__ void __launch_bounds__(kTsThreads, 1) k_phase2t(int nitems, const P2Desc *__restrict__ desc,
-                                                          const void *__restrict__ p2,
-                                                          const typename Tr<S>::Op *__restrict__ g,
-                                                          double *__restrict__ y, const int32_t *__restrict__ out_perm,
-                                                          int accum, const SolverScalars *S_, int mode,
-                                                          const double *__restrict__ w, int dotmode, double *dpart,
-                                                          int gslot_bytes) {
-    using Op = typename Tr<S>::Op;
-    constexpr int VW = Tr<S>::VW;
-    constexpr uint32_t esz = 16 / VW;
-    extern __shared__ __align__(128) unsigned char ts_smem[];
-    __shared__ uint64_t full[kTsSlots], empty[kTsSlots], gfull[kTsGSlots], gempty[kTsGSlots];
-    __shared__ int abort_flag;
-    __shared__ uint32_t issued, consumed;
-    __shared__ double wsum[2][kTsConsumers];
-    if (skip_product(S_, mode)) return;
-    unsigned char *data = ts_smem;
-    unsigned char *gbuf = ts_smem + (size_t)kTsSlots * kTsSlot;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kTsSlots; ++s) {
-            mb_init(&full[s], 1);
-            mb_init(&empty[s], kTsConsumers);
-        }
-        for (int s = 0; s < kTsGSlots; ++s) {
-            mb_init(&gfull[s], 1);
-            mb_init(&gempty[s], kTsConsumers);
-        }
-        abort_flag = 0;
-        issued = 0;
-        consumed = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    __syncthreads();
-    if (warp == kTsConsumers) {
-        // producer: one thread issues every copy of this CTA's items in order
-        if (lane == 0) {
-            uint32_t c = 0, gc = 0;
-            bool ok = true;
-            for (int it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
-                const P2Desc d = desc[it];
-                const uint32_t row_bytes = (uint32_t)d.ld * esz;
-                const int k = max(1, kTsSlot / (int)row_bytes);
-                const int gs = gc % kTsGSlots;
-                if (gc >= kTsGSlots && !(ok = mb_wait(&gempty[gs], ((gc / kTsGSlots) - 1) & 1, &abort_flag))) break;
-                mb_expect_tx(&gfull[gs], (uint32_t)d.ld * sizeof(Op));
-                bulk_copy(gbuf + (size_t)gs * gslot_bytes, g + d.goff, (uint32_t)d.ld * sizeof(Op), &gfull[gs]);
-                ++gc;
-                for (int r0 = 0; r0 < d.ylen; r0 += k) {
-                    const uint32_t bytes = (uint32_t)min(k, d.ylen - r0) * row_bytes;
-                    const int s = c % kTsSlots;
-                    if (c >= kTsSlots && !(ok = mb_wait(&empty[s], ((c / kTsSlots) - 1) & 1, &abort_flag))) break;
-                    mb_expect_tx(&full[s], bytes);
-                    bulk_copy(data + (size_t)s * kTsSlot,
-                              (const unsigned char *)p2 + ((size_t)d.off + (size_t)r0 * d.ld) * esz, bytes, &full[s]);
-                    ++c;
-                    issued = c;
-                }
-            }
-        }
-    } else {
-        // consumers: a warp per row of each chunk, operands from the item's slot
-        uint32_t c = 0, gc = 0;
-        double dw = 0.0, dy = 0.0;
-        bool ok = true;
-        for (int it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
-            const P2Desc d = desc[it];
-            const uint32_t row_bytes = (uint32_t)d.ld * esz;
-            const int k = max(1, kTsSlot / (int)row_bytes);
-            const int nv = d.ld / VW;
-            const int gs = gc % kTsGSlots;
-            if (!(ok = mb_wait(&gfull[gs], (gc / kTsGSlots) & 1, &abort_flag))) break;
-            const Op *gsm = reinterpret_cast<const Op *>(gbuf + (size_t)gs * gslot_bytes);
-            for (int r0 = 0; r0 < d.ylen; r0 += k) {
-                const int rows = min(k, d.ylen - r0);
-                const int s = c % kTsSlots;
-                if (!(ok = mb_wait(&full[s], (c / kTsSlots) & 1, &abort_flag))) break;
-                const unsigned char *chunk = data + (size_t)s * kTsSlot;
-                for (int i = warp; i < rows; i += kTsConsumers) {
-                    const int4 *rowp = reinterpret_cast<const int4 *>(chunk + (size_t)i * row_bytes);
-                    Acc<S> a;
-                    a.init();
-                    for (int v = lane; v < nv; v += 32) row_mac<S>(a, rowp[v], gv_shared<S>(gsm + v * VW));
-                    const double o = row_total<S>(a);
-                    if (lane == 0) {
-                        const int p = d.ybeg + r0 + i;
-                        const int q = out_perm ? out_perm[p] : p;
-                        double out = o;
-                        if (accum) out = y[q] + out;
-                        y[q] = out;
-                        if (dotmode != 0) {
-                            dw += __ldg(w + p) * out;
-                            dy += out * out;
-                        }
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mb_arrive(&empty[s]);
-                ++c;
-                if (warp == 0 && lane == 0) consumed = c;
-            }
-            if (!ok) break;
-            __syncwarp();
-            if (lane == 0) mb_arrive(&gempty[gs]);
-            ++gc;
-        }
-        if (lane == 0) {
-            wsum[0][warp] = dw;
-            wsum[1][warp] = dy;
-        }
-    }
-    __syncthreads();
-    if (abort_flag && threadIdx.x == 0) {
-        // a wait gave up: let the copies still in flight land before the CTA exits
-        for (uint32_t q = consumed; q < issued; ++q) {
-            const long long t0 = clock64();
-            while (!mb_test(&full[q % kTsSlots], (q / kTsSlots) & 1) && clock64() - t0 < kTsWaitCycles) {
-            }
-        }
-    }
-    if (dotmode != 0 && threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int k = 0; k < kTsConsumers; ++k) { a += wsum[0][k]; b += wsum[1][k]; }
-        dpart[blockIdx.x] = a;
-        dpart[gridDim.x + blockIdx.x] = b;
-    }
-}
-
-// The staged expansion's shared memory beyond the 48 KB default (set once, at
-// upload, outside any stream capture).
-template <Store SS>
-cudaError_t staged_prepare() {
-    return cudaFuncSetAttribute(k_phase2t<SS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
-}
-
 int grid_for(int64_t n, int threads, int cap) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -1339,20 +802,11 @@ int grid_for(int64_t n, int threads, int cap) {
 
 // launches of one store's product kernels (the dispatchers pick the store)
 template <Store SS>
-void phase1_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st,
-                   const PFold &fold) {
-    if (ix.p1_persistent && !fold.S) {  // (the folded p update runs in the one-CTA-per-cluster form)
-        const int grid = std::min(ix.nleaves, ix.nsm * p1_min_blocks<SS>());
-        k_phase1p<SS><<<grid, p1_threads<SS>(), 0, st>>>(ix.nleaves, ix.p1, ix.p1_runs, ix.xdst, ix.xsel, ix.lr,
-                                                         ix.gdst, P.q1, (const typename Tr<SS>::Op *)P.xs,
-                                                         (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g,
-                                                         ix.tscale, skipS, mode);
-        return;
-    }
+void phase1_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st) {
     k_phase1<SS><<<ix.nleaves, p1_threads<SS>(), 0, st>>>(ix.p1, ix.p1_runs, ix.xdst, ix.xsel, ix.lr, ix.gdst, P.q1,
                                                           (const typename Tr<SS>::Op *)P.xs,
                                                           (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g,
-                                                          ix.tscale, skipS, mode, fold);
+                                                          ix.tscale, skipS, mode);
 }
 
 template <Store SS>
@@ -1368,34 +822,9 @@ template <Store SS>
 void phase2_launch(const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm, int accum,
                    const SolverScalars *skipS, int mode, cudaStream_t st, const double *w, int dotmode,
                    double *dpart) {
-    if constexpr (SS == Store::BF16 || SS == Store::F32) {
-        if (phase2_shape(SS, ix) == 2) {
-            const int gslot = (int)((ix.max_ld2 * sizeof(typename Tr<SS>::Op) + 127) / 128 * 128);
-            const size_t smem = (size_t)kTsSlots * kTsSlot + (size_t)kTsGSlots * gslot;
-            k_phase2t<SS><<<ix.nsm, kTsThreads, smem, st>>>(ix.nleaves, ix.p2, P.p2, (const typename Tr<SS>::Op *)P.g, y,
-                                                            out_perm, accum, skipS, mode, w, dotmode, dpart, gslot);
-            return;
-        }
-    }
-    if (phase2_shape(SS, ix) == 3) {
-        k_phase2g<SS><<<ix.nsm * p2g_blocks<SS>(), kP2Threads, 0, st>>>(ix.ngroups, ix.groups, P.p2,
-                                                                        (const typename Tr<SS>::Op *)P.g, y,
-                                                                        out_perm, accum, skipS, mode, w, dotmode,
-                                                                        dpart);
-        return;
-    }
-    if (phase2_rows(SS, ix)) {
-        k_phase2w<SS><<<ix.nsm * p2w_blocks(SS), kP2Threads, 0, st>>>(ix.n, ix.rows, P.p2,
-                                                                      (const typename Tr<SS>::Op *)P.g, y, out_perm,
-                                                                      accum, skipS, mode, w, dotmode, dpart);
-        return;
-    }
-    if (ix.max_leaf <= 4 * kP2Warps)
-        k_phase2<SS, 4><<<ix.nleaves, kP2Threads, 0, st>>>(ix.p2, P.p2, (const typename Tr<SS>::Op *)P.g, y, out_perm,
-                                                           accum, skipS, mode, w, dotmode, dpart);
-    else
-        k_phase2<SS, kMaxLeaf / kP2Warps><<<ix.nleaves, kP2Threads, 0, st>>>(
-            ix.p2, P.p2, (const typename Tr<SS>::Op *)P.g, y, out_perm, accum, skipS, mode, w, dotmode, dpart);
+    k_phase2g<SS><<<phase2_items(ix), kP2Threads, 0, st>>>(ix.ngroups, ix.groups, P.p2,
+                                                           (const typename Tr<SS>::Op *)P.g, y, out_perm, accum,
+                                                           skipS, mode, w, dotmode, dpart);
 }
 
 }  // namespace

@@ -58,4 +58,18 @@ def test_reference_arm_line():
               "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["steps"] == 2 and d["warmup"] == 1  # every requested step runs
+    assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_roofline_object():
+    """The roofline of a form's dominant kernel: algorithmic bytes over the launch's
+    mean time against the peak, with the per-launch figures it came from."""
+    import bench
+    table = {"bf16": {"kernel_ms": {"phase1": 0.040, "phase2": 0.030}, "phase1_gbs": 3700.0, "phase2_gbs": 5000.0,
+                      "phase1_bytes": 148e6, "phase2_bytes": 150e6}}
+    r = bench._roofline(table, "bf16", 99, 6800.0, "measured")
+    assert r["kernel"] == "k_phase1<bf16>" and r["achieved"] == 3700.0
+    assert r["frac"] == pytest.approx(3700.0 / 6800.0) and r["launch_us"] == pytest.approx(40.0)
+    assert r["traffic"] is None  # no capture for this level

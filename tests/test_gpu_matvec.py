@@ -137,70 +137,3 @@ def test_upload_rejects_bad_blob():
     with pytest.raises(P.HmatError) as e:
         P.hmat_upload(bad, "fp64")
     assert e.value.status == 2
-
-
-
-@pytest.mark.parametrize("shape", ["cluster", "staged", "rows"])
-def test_expansion_launch_shapes_agree(hcache, oracle_mod, monkeypatch, shape):
-    """The other launch shapes of the expansion (one CTA per leaf row cluster; the
-    staged bulk-copy pipeline; single-row persistent warps) against the default
-    row groups: the same rows and operands in the same fixed order per row, so
-    the same bits."""
-    torch = need_gpu()
-    P = lib()
-    for mesh in (synth.icosphere(4), synth.two_spheres(3)):
-        blob = oracle_blob(hcache(mesh))
-        x = np.random.default_rng(31).standard_normal(mesh.n)
-        for form in ("bf16", "fp32", "fp64", "fp64_dfma"):
-            if shape == "staged" and form.startswith("fp64"):
-                continue  # the staged shape takes 2- and 4-byte panels only
-            monkeypatch.delenv("HMAT_PHASE2", raising=False)
-            h0 = P.hmat_upload(blob, form)
-            monkeypatch.setenv("HMAT_PHASE2", shape)
-            h1 = P.hmat_upload(blob, form)
-            try:
-                y0 = _gpu_matvec(P, torch, h0, x)
-                y1 = _gpu_matvec(P, torch, h1, x)
-                assert np.array_equal(y0, y1), (form, shape, rel(y1, y0))
-                # and inside a solve (the expansion also leaves the inner-product shares)
-                b = synth.rhs_one_plus_half_z(mesh)
-                opts = {"inner_tol": {"bf16": 1e-2, "fp32": 1e-4}.get(form, 1e-8)}
-                i0 = P.hmat_bicgstab(h0, b, np.zeros(mesh.n), tol=1e-8, **opts)
-                i1 = P.hmat_bicgstab(h1, b, np.zeros(mesh.n), tol=1e-8, **opts)
-                assert i0["status"] == 0 and i1["status"] == 0 and i1["relres_true"] <= 1e-8
-            finally:
-                P.hmat_destroy(h0)
-                P.hmat_destroy(h1)
-
-
-@pytest.mark.parametrize("form,c", [("bf16", None), ("fp32", None), ("fp64", None), ("fp64_dfma", None),
-                                    ("m2_mixed", None), ("m1_single", None), ("m3_dense", 1)],
-                         ids=lambda v: str(v))
-def test_persistent_projection_agrees(hcache, monkeypatch, form, c):
-    """The persistent projection (HMAT_PHASE1=persistent: CTAs loop over clusters
-    with the next cluster's prologue staged by cp.async) does per cluster what the
-    one-CTA-per-cluster launch does, so the products are the same bits, also for
-    the paper's variants (the FP32 copy of x converted in shared memory) and for
-    a layout with column-subset dense blocks, and the solver agrees."""
-    torch = need_gpu()
-    P = lib()
-    for mesh in (synth.icosphere(4), synth.two_spheres(3)):
-        blob = oracle_blob(hcache(mesh))
-        x = np.random.default_rng(32).standard_normal(mesh.n)
-        monkeypatch.delenv("HMAT_PHASE1", raising=False)
-        h0 = P.hmat_upload(blob, form, c)
-        monkeypatch.setenv("HMAT_PHASE1", "persistent")
-        h1 = P.hmat_upload(blob, form, c)
-        try:
-            y0 = _gpu_matvec(P, torch, h0, x)
-            y1 = _gpu_matvec(P, torch, h1, x)
-            assert np.array_equal(y0, y1), (form, rel(y1, y0))
-            assert np.array_equal(_gpu_matvec(P, torch, h1, x), y1)  # repeatable
-            b = synth.rhs_one_plus_half_z(mesh)
-            opts = {"bf16": {"inner_tol": 1e-2}, "fp32": {"inner_tol": 1e-4}}.get(form, {"inner_tol": 1e-5})
-            i0 = P.hmat_bicgstab(h0, b, np.zeros(mesh.n), tol=1e-8, **opts)
-            i1 = P.hmat_bicgstab(h1, b, np.zeros(mesh.n), tol=1e-8, **opts)
-            assert i1["status"] == 0 and i1["relres_true"] <= 1e-8 and i1["iters"] == i0["iters"]
-        finally:
-            P.hmat_destroy(h0)
-            P.hmat_destroy(h1)

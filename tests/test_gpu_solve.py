@@ -191,32 +191,3 @@ def test_two_spheres_level7_bf16_refinement(oracle_mod):
         assert abs(q1 + q2) <= 1e-3 * abs(q1), (q1, q2)
     finally:
         P.hmat_destroy(h)
-
-
-@pytest.mark.parametrize("form,opts", [("fp64", {}), ("fp64_dfma", {}), ("fp32", {"inner_tol": 1e-4}),
-                                       ("bf16", {"inner_tol": 1e-2}), ("m2_mixed", {"inner_tol": 1e-5}),
-                                       ("m1_single", {"inner_tol": 1e-5})], ids=lambda v: str(v))
-def test_folded_p_update_gives_the_same_bits(hcache, monkeypatch, form, opts):
-    """Algorithm 1's p update folded into the first projection of an iteration
-    (HMAT_FOLD_P=1: each projection CTA updates its cluster's rows) against the
-    separate update kernel (the default): the same p in the same rounding, so the
-    same solution bits and iteration counts."""
-    torch = need_gpu()
-    P = lib()
-    for mesh in (synth.icosphere(4), synth.two_spheres(3)):
-        H = hcache(mesh)
-        blob = oracle_blob(H)
-        b = synth.rhs_one_plus_half_z(mesh)
-        monkeypatch.delenv("HMAT_FOLD_P", raising=False)
-        h0 = P.hmat_upload(blob, form)
-        monkeypatch.setenv("HMAT_FOLD_P", "1")
-        h1 = P.hmat_upload(blob, form)
-        try:
-            x0, i0 = _solve(P, torch, h0, b, tol=1e-8, check_every=4, **opts)
-            x1, i1 = _solve(P, torch, h1, b, tol=1e-8, check_every=4, **opts)
-            assert i0["status"] == 0 and i1["status"] == 0
-            assert np.array_equal(x0, x1) and i0["iters"] == i1["iters"] and i0["matvecs"] == i1["matvecs"]
-            assert i1["launches"] < i0["launches"]
-        finally:
-            P.hmat_destroy(h0)
-            P.hmat_destroy(h1)

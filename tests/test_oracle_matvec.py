@@ -250,3 +250,24 @@ def test_determinism(hcache, oracle_mod):
     x = np.random.default_rng(1).standard_normal(mesh.n)
     for v in range(9):
         assert np.array_equal(H.matvec(x, v, 2), H.matvec(x, v, 2))
+
+
+def test_parallel_product_is_the_serial_one(hcache, oracle_mod):
+    """The oracle's product runs its blocks in parallel and adds their y^_m into y
+    in block order (eq. 25): every variant gives the same bits on one thread and
+    on all of them, and so does a whole solve."""
+    mesh = synth.icosphere(3)
+    H = hcache(mesh)
+    x = np.random.default_rng(47).standard_normal(mesh.n)
+    nt = oracle_mod.get_threads()
+    try:
+        oracle_mod.set_threads(1)
+        ys = [H.matvec(x, v, 2) for v in range(11)]
+        xs, info_s = H.bicgstab(synth.rhs_one_plus_half_z(mesh), tol=1e-8)
+        oracle_mod.set_threads(max(4, nt))
+        for v in range(11):
+            assert np.array_equal(H.matvec(x, v, 2), ys[v]), v
+        xp, info_p = H.bicgstab(synth.rhs_one_plus_half_z(mesh), tol=1e-8)
+        assert np.array_equal(xp, xs) and info_p["iters"] == info_s["iters"]
+    finally:
+        oracle_mod.set_threads(nt)
