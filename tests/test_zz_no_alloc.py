@@ -1,9 +1,10 @@
 """The allocation-free product (hmat_matvec_noalloc) against the ordinary one.
 
-Callers that cannot allocate device memory when they run the product -- inside a
-stream capture, in a latency-critical loop, or under another owner's memory
-budget -- create a handle once and then call hmat_matvec_noalloc, whose scratch
-lives in a static device array of the library.  This file is collected last so
+Callers that cannot allocate device memory when they run the product -- a
+latency-critical loop that cannot pay for a cudaMalloc, or code whose device
+memory belongs to another allocator or budget -- create a handle once and then
+call hmat_matvec_noalloc, whose scratch lives in a static device array of the
+library.  This file is collected last so
 that a run stopping at the first failure has already run every other test; it
 also passes on its own in a fresh process.
 """
