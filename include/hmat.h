@@ -46,7 +46,9 @@ typedef enum hmat_status {
     HMAT_ERR_MAXIT = 7,            /* iteration or restart budget spent before the tolerance   */
     HMAT_ERR_NONFINITE = 8,        /* NaN/Inf in a residual norm or an input vector            */
     HMAT_ERR_RANGE = 9,            /* a panel value cannot be held by the precision form       */
-    HMAT_ERR_UNSUPPORTED = 10      /* valid request outside this build's limits (e.g. leaf>64) */
+    HMAT_ERR_UNSUPPORTED = 10,     /* valid request outside this build's limits (e.g. leaf>64) */
+    HMAT_ERR_TIMEOUT = 11          /* a bounded wait inside a kernel ran out; the kernel gave up
+                                      its work (the result of that product is not valid)        */
 } hmat_status;
 
 /*
@@ -253,8 +255,9 @@ int hmat_destroy(hmat_handle h);
  * original panel order, in the handle's precision form.  x and y must not
  * overlap.  Asynchronous on `stream` for device pointers.  For a HMAT_BF16
  * handle and nrhs >= 2 the columns go through the tensor-core product, 64 per
- * pass (BF16 panels times x and t split into two BF16 parts, FP32
- * accumulation); it allocates its buffers on first use.  x and y may be host
+ * pass (tcgen05 MMAs: BF16 panels times x and t split into two BF16 parts,
+ * FP32 accumulation in tensor memory; one GEMM per column cluster for t, one
+ * per leaf row cluster for y); it allocates its buffers on first use.  x and y may be host
  * memory (staged through the handle's buffers) or device memory of the handle's
  * GPU; device memory of another GPU is rejected (HMAT_ERR_ARG), and so it is for
  * b and x of the solvers.
@@ -389,6 +392,33 @@ int hmat_bicgstab_multi(hmat_handle h, const double *b, double *x, int32_t nrhs,
  * clears what must start at zero and is asynchronous on `stream`.
  */
 int hmat_matvec_noalloc(hmat_handle h, const double *x, double *y, void *stream);
+
+/*
+ * Failure detection of the tensor-core product for many right-hand sides (no
+ * counterpart in the paper; it guards the GPU path).  Its kernels hand shared-
+ * memory buffers between the copy engine, the tensor cores and the threads
+ * through mbarriers; every such wait is bounded (default about one second of SM
+ * clock).  A wait that runs out makes the kernel give up its work, write
+ * HMAT_ERR_TIMEOUT into the handle's status word (host memory the kernel can
+ * write), let the copies and MMAs it issued finish, free its tensor memory and
+ * return; the CUDA context stays usable.  The status is reported, and cleared,
+ * by the next call on the handle (hmat_matvec, the solvers,
+ * hmat_matvec_noalloc, hmat_time_matvec) or by hmat_check.
+ *
+ * hmat_check -- synchronise `stream` and return HMAT_ERR_TIMEOUT if a bounded
+ * wait of one of the handle's kernels ran out since the last report (clearing
+ * it), else HMAT_OK (HMAT_ERR_CUDA if the synchronisation fails).
+ */
+int hmat_check(hmat_handle h, void *stream);
+
+/*
+ * hmat_set_wait_limit -- the bound of those waits, in SM clock cycles (>= 1),
+ * for the products enqueued after the call (a cached solver graph is captured
+ * again).  withhold = 1 makes the projection issue none of its panel copies, so
+ * its waits run out: a test of the timeout path that needs no fault; 0 is
+ * normal operation.  Errors: HMAT_ERR_ARG.
+ */
+int hmat_set_wait_limit(hmat_handle h, int64_t cycles, int32_t withhold);
 
 /* ------------------------------------------------------------------------- */
 /* Introspection                                                              */

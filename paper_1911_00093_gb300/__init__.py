@@ -16,7 +16,8 @@ _LIB_PATH = os.path.join(_HERE, "libhmat.so")
 
 HMAT_OK = 0
 STATUS = {0: "ok", 1: "arg", 2: "bad_layout", 3: "nomem", 4: "cuda", 5: "breakdown_rho",
-          6: "breakdown_omega", 7: "maxit", 8: "nonfinite", 9: "range", 10: "unsupported"}
+          6: "breakdown_omega", 7: "maxit", 8: "nonfinite", 9: "range", 10: "unsupported", 11: "timeout"}
+HMAT_ERR_TIMEOUT = 11
 HMAT_FP64, HMAT_FP64_DFMA, HMAT_FP32, HMAT_BF16 = 0, 1, 2, 3
 HMAT_M1_SINGLE, HMAT_M1_MIXED, HMAT_M2_DOUBLE, HMAT_M2_SINGLE, HMAT_M2_MIXED, HMAT_M3 = 4, 5, 6, 7, 8, 9
 HMAT_M3_TRUNC = 10
@@ -32,7 +33,7 @@ EXPORTS = ("hmat_build", "hmat_blob_free", "hmat_blob_stats_get", "hmat_upload",
            "hmat_matvec", "hmat_matvec_fp64", "hmat_solve_opts_default", "hmat_bicgstab",
            "hmat_bicgstab_ex", "hmat_info", "hmat_time_matvec", "hmat_strerror", "hmat_last_cuda_error",
            "hmat_matvec_noalloc", "hmat_upload_ex", "hmat_upload_batch", "hmat_problems", "hmat_bicgstab_multi",
-           "hmat_gmres", "hmat_build_device", "hmat_form_stats_get")
+           "hmat_gmres", "hmat_build_device", "hmat_form_stats_get", "hmat_check", "hmat_set_wait_limit")
 
 
 class BuildDeviceInfo(C.Structure):
@@ -120,6 +121,8 @@ def load():
         "hmat_build_device": (C.c_int, [I64, P, P, I32, D, D, C.POINTER(C.c_void_p), C.POINTER(SZ),
                                         C.POINTER(BuildDeviceInfo)]),
         "hmat_form_stats_get": (C.c_int, [P, SZ, I32, I32, C.POINTER(FormStats)]),
+        "hmat_check": (C.c_int, [P, P]),
+        "hmat_set_wait_limit": (C.c_int, [P, I64, I32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -313,6 +316,18 @@ def hmat_matvec_noalloc(h, x, y, stream=None):
     py, ky = _ptr(y)
     _check(load().hmat_matvec_noalloc(C.c_void_p(h), px, py, _stream_ptr(stream)), "hmat_matvec_noalloc")
     return y
+
+
+def hmat_check(h, stream=None) -> int:
+    """Synchronise `stream`; the status of the handle's bounded device waits since the
+    last report (HMAT_ERR_TIMEOUT when one ran out, else 0), cleared."""
+    return int(load().hmat_check(C.c_void_p(h), _stream_ptr(stream)))
+
+
+def hmat_set_wait_limit(h, cycles, withhold=False):
+    """Bound of the tensor-core product's waits in SM cycles; withhold=True makes its
+    projection issue no copies, so the waits run out (tests of the timeout path)."""
+    _check(load().hmat_set_wait_limit(C.c_void_p(h), int(cycles), 1 if withhold else 0), "hmat_set_wait_limit")
 
 
 def hmat_solve_opts(**kw) -> SolveOpts:

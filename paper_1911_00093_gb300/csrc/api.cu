@@ -168,19 +168,93 @@ int alloc_panels(hmat_t *h, const BlobView &v, const Layout &L, Store s, DevPane
     return HMAT_OK;
 }
 
-// Indices of the tensor-core product for many right-hand sides (BF16 handles):
-// the U row and power of two feeding every operand slot, the t rows of the
-// low-rank blocks, the reduction tasks of every multi-cluster block.
-int upload_mrhs_index(hmat_t *h, const Layout &L) {
+// Indices of the tensor-core product for many right-hand sides (BF16 handles).
+// The low-rank blocks are grouped by column cluster sigma (in (begin, end)
+// order; blocks in their order) into work items of at most kMrhsMaxRows rank rows; an
+// item's t rows are consecutive in T, and its W tile holds the rank rows of its
+// blocks restricted to sigma -- the BF16 values of the phase-1 panels, W_m / 2^e
+// -- as K-major 8 x 8 core matrices, core (n/8, k/8) at (k/8 * npad/8 + n/8),
+// zero past |sigma| and past the item's rows.  Plus the U row and power of two
+// feeding every operand slot of the expansion.
+int upload_mrhs_index(hmat_t *h, const BlobView &v, const Layout &L) {
     MrhsIndex &mx = h->mx;
-    std::vector<int32_t> tbase(L.lr.size());
-    int64_t trows = 0;
-    for (size_t q = 0; q < L.lr.size(); ++q) {
-        tbase[q] = (int32_t)trows;
-        trows += L.lr[q].rank;
+    const size_t nlr = L.lr.size();
+    // blob block and W exponent of each low-rank block, from its phase-1 slices
+    std::vector<int64_t> blk(nlr, -1);
+    std::vector<int32_t> ew(nlr, 0);
+    for (size_t k = 0; k < L.p1.size(); ++k) {
+        const P1Desc &d = L.p1[k];
+        for (int r = 0; r < d.rcnt; ++r) {
+            const P1Run &run = L.p1_runs[d.rbeg + r];
+            const Layout::Slice &sl = L.p1_slices[L.p1_slice_ptr[k] + r];
+            blk[run.q] = sl.block;
+            ew[run.q] = sl.scale;
+        }
+    }
+    std::vector<std::pair<std::pair<int64_t, int64_t>, int32_t>> order;  // ((begin, end) of sigma, block)
+    order.reserve(nlr);
+    for (size_t q = 0; q < nlr; ++q) {
+        if (blk[q] < 0) return HMAT_ERR_BAD_LAYOUT;
+        const int64_t *e = v.blocks + 8 * blk[q];
+        order.push_back({{e[2], e[3]}, (int32_t)q});
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const auto &a, const auto &b) { return a.first < b.first; });
+    std::vector<int32_t> tbase(nlr, 0);
+    std::vector<MrhsSig> sigs;
+    std::vector<std::pair<size_t, size_t>> members;  // each item's range in `order`
+    int64_t trows = 0, woff = 0;
+    int32_t max_npad = 16;
+    for (size_t a = 0; a < order.size();) {
+        size_t b = a;
+        int32_t R = 0;
+        while (b < order.size() && order[b].first == order[a].first &&
+               R + L.lr[order[b].second].rank <= kMrhsMaxRows) {
+            tbase[order[b].second] = (int32_t)(trows + R);
+            R += L.lr[order[b].second].rank;
+            ++b;
+        }
+        if (b == a) return HMAT_ERR_UNSUPPORTED;  // (a rank above kMrhsMaxRows)
+        MrhsSig sg;
+        sg.woff = woff;
+        sg.xbeg = (int32_t)order[a].first.first;
+        sg.xlen = (int32_t)(order[a].first.second - order[a].first.first);
+        sg.kpad = (sg.xlen + 15) & ~15;
+        sg.npad = (R + 15) & ~15;
+        sg.R = R;
+        sg.tbeg = (int32_t)trows;
+        sigs.push_back(sg);
+        members.push_back({a, b});
+        max_npad = std::max(max_npad, sg.npad);
+        woff += (int64_t)sg.kpad * sg.npad;
+        trows += R;
+        a = b;
     }
     const int64_t zero_row = L.n + trows;
     if (zero_row + 1 > (int64_t(1) << 31) - 16) return HMAT_ERR_UNSUPPORTED;
+    // the device takes the items round robin: largest (K x N) first
+    std::vector<size_t> by_size(sigs.size());
+    for (size_t k = 0; k < by_size.size(); ++k) by_size[k] = k;
+    std::stable_sort(by_size.begin(), by_size.end(), [&](size_t x, size_t y) {
+        return (int64_t)sigs[x].kpad * sigs[x].npad > (int64_t)sigs[y].kpad * sigs[y].npad;
+    });
+    std::vector<uint16_t> wt((size_t)std::max<int64_t>(woff, 8), 0);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t s = 0; s < (int64_t)sigs.size(); ++s) {
+        const MrhsSig &sg = sigs[s];
+        uint16_t *tile = wt.data() + sg.woff;
+        int32_t n = 0;
+        for (size_t o = members[s].first; o < members[s].second; ++o) {
+            const int32_t q = order[o].second;
+            const int64_t *e = v.blocks + 8 * blk[q];
+            const int64_t m = e[1] - e[0], cols = e[3] - e[2], r = e[5];
+            const double *W = v.data + e[6] + m * r;  // W_m, r x cols row-major
+            const double inv = std::ldexp(1.0, -ew[q]);
+            for (int64_t l = 0; l < r; ++l, ++n)
+                for (int64_t k = 0; k < cols; ++k)
+                    tile[((k / 8) * (sg.npad / 8) + n / 8) * 64 + (n % 8) * 8 + (k % 8)] = bf16_bits(W[l * cols + k] * inv);
+        }
+    }
     std::vector<MrhsSrc> src((size_t)L.glen, MrhsSrc{(int32_t)zero_row, 0});
     for (size_t k = 0; k < L.p1.size(); ++k) {
         const P1Desc &d = L.p1[k];
@@ -190,29 +264,33 @@ int upload_mrhs_index(hmat_t *h, const Layout &L) {
                 src[x.goff + j] = MrhsSrc{d.xbeg + (x.sel < 0 ? j : L.xsel[x.sel + j]), x.scale};
         }
     }
-    std::vector<int32_t> tasks;
-    for (size_t q = 0; q < L.lr.size(); ++q) {
+    for (size_t q = 0; q < nlr; ++q) {
         const LrDesc &d = L.lr[q];
         for (int k = 0; k < d.gcnt; ++k)
             for (int l = 0; l < d.rank; ++l)
                 src[L.gdst[d.gbeg + k] + l] = MrhsSrc{(int32_t)(L.n + tbase[q] + l), d.scale};
-        if (d.cnt > 1)
-            for (int l = 0; l < d.rank; ++l) tasks.push_back((int32_t)((q << 6) | l));
     }
     MrhsSrc *dsrc = nullptr;
-    int32_t *dtb = nullptr, *dtasks = nullptr;
+    MrhsSig *dsig = nullptr;
+    uint16_t *dwt = nullptr;
     int st;
+    std::vector<MrhsSig> sorted(sigs.size());
+    for (size_t k = 0; k < by_size.size(); ++k) sorted[k] = sigs[by_size[k]];
     if ((st = h->upload(&dsrc, src.data(), sizeof(MrhsSrc) * src.size())) ||
-        (st = h->upload(&dtb, tbase.data(), 4 * tbase.size())) ||
-        (st = h->upload(&dtasks, tasks.data(), 4 * tasks.size())))
+        (st = h->upload(&dsig, sorted.data(), sizeof(MrhsSig) * sorted.size())) ||
+        (st = h->upload(&dwt, wt.data(), 2 * wt.size())))
         return st;
+    CK(mrhs_prepare());
     mx.src = dsrc;
-    mx.tbase = dtb;
-    mx.tasks = dtasks;
-    mx.ntasks = (int32_t)tasks.size();
+    mx.sigs = dsig;
+    mx.wt = dwt;
+    mx.nsig = (int32_t)sigs.size();
+    mx.max_npad = max_npad;
     mx.urows = zero_row + 1;
-    mx.npart = L.npart;
-    h->index_bytes += (int64_t)(sizeof(MrhsSrc) * src.size() + 4 * (tbase.size() + tasks.size()));
+    mx.ctl.status = h->status_dev;
+    mx.ctl.wait_limit = kDefaultWaitCycles;
+    h->index_bytes += (int64_t)(sizeof(MrhsSrc) * src.size() + sizeof(MrhsSig) * sigs.size());
+    h->panel_bytes_mrhs = 2 * (int64_t)wt.size();
     h->mrhs = true;
     return HMAT_OK;
 }
@@ -242,6 +320,9 @@ int upload_view(const BlobView &v, int32_t precision, int32_t method3_c, const s
         if (st == HMAT_OK) st = check_layout(L);
         if (st != HMAT_OK) return st;
         CK(cudaGetDevice(&h->device));
+        CK(cudaHostAlloc((void **)&h->status_host, sizeof(int32_t), cudaHostAllocMapped));
+        *(volatile int32_t *)h->status_host = 0;
+        CK(cudaHostGetDevicePointer((void **)&h->status_dev, h->status_host, 0));
         h->precision = precision;
         h->method3_c =
             (precision == HMAT_M3 || precision == HMAT_M3_TRUNC || precision == HMAT_M3_DENSE) ? method3_c : 0;
@@ -263,7 +344,7 @@ int upload_view(const BlobView &v, int32_t precision, int32_t method3_c, const s
             h->seg64.ix = g.ix;
             h->seg64.partials_n = g.partials_n;
             h->seg64.glen = g.glen;
-            if (precision == HMAT_BF16 && (st = upload_mrhs_index(h, L))) return st;
+            if (precision == HMAT_BF16 && (st = upload_mrhs_index(h, v, L))) return st;
             if (precision == HMAT_FP64 || precision == HMAT_FP64_DFMA) {
                 h->seg64.store = g.store;
                 h->seg64.P = g.P;
@@ -382,6 +463,7 @@ int mrhs_matvec(hmat_t *h, const double *x, double *y, int32_t nrhs, cudaStream_
 
 int matvec_impl(hmat_handle h, const double *x, double *y, int32_t nrhs, void *stream, bool fp64) {
     if (!h || !x || !y || nrhs < 1) return HMAT_ERR_ARG;
+    if (int e = take_status(h)) return e;  // a wait of an earlier product ran out
     cudaStream_t st = (cudaStream_t)stream;
     if (!fp64 && h->mrhs && nrhs >= 2) return mrhs_matvec(h, x, y, nrhs, st);
     const HmatSegment *seg = fp64 ? &h->seg64 : h->seg;
@@ -513,8 +595,8 @@ extern "C" void hmat_solve_opts_default(hmat_solve_opts *o) {
     o->use_graph = 2;
 }
 
-extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const hmat_solve_opts *opts_in,
-                                void *stream, hmat_solve_info *info) {
+static int bicgstab_ex_impl(hmat_handle h, const double *b, double *x, const hmat_solve_opts *opts_in,
+                            void *stream, hmat_solve_info *info) {
     if (!h || !b || !x) return HMAT_ERR_ARG;
     hmat_solve_opts o;
     hmat_solve_opts_default(&o);
@@ -732,21 +814,18 @@ void multi_products(hmat_t *h, const HmatSegment *seg, int nseg, const double *x
 
 int multi_product_launches(hmat_t *h, const HmatSegment *seg, int nseg, int nrhs) {
     if (seg == h->seg && h->mrhs && h->mx.U && nrhs >= 2)
-        return ((nrhs + kMrhsCols - 1) / kMrhsCols) * (h->mx.ntasks > 0 ? 4 : 3);
+        return ((nrhs + kMrhsCols - 1) / kMrhsCols) * (h->mx.nsig > 0 ? 3 : 2);
     return nrhs * product_launches(seg, nseg);
 }
 
 // buffers of the tensor-core product (first many-right-hand-side solve)
 int mrhs_buffers(hmat_t *h) {
     if (!h->mrhs || h->mx.U) return HMAT_OK;
-    float *U = nullptr, *part = nullptr;
+    float *U = nullptr;
     int st;
-    if ((st = h->alloc(&U, sizeof(float) * kMrhsCols * (size_t)h->mx.urows)) ||
-        (st = h->alloc(&part, sizeof(float) * kMrhsCols * (size_t)std::max<int64_t>(h->mx.npart, 1))))
-        return st;
+    if ((st = h->alloc(&U, sizeof(float) * kMrhsCols * (size_t)h->mx.urows))) return st;
     CK(cudaMemset(U, 0, sizeof(float) * kMrhsCols * (size_t)h->mx.urows));  // the zero row stays zero
     h->mx.U = U;
-    h->mx.part = part;
     return HMAT_OK;
 }
 
@@ -793,14 +872,17 @@ int mrhs_matvec(hmat_t *h, const double *x, double *y, int32_t nrhs, cudaStream_
     launch_mscatter(n, nrhs, h->perm, m.y, dst, st);
     if (!dy) CK(cudaMemcpyAsync(y, m.stage, vb, cudaMemcpyDeviceToHost, st));
     CK(cudaGetLastError());
-    if (!dx || !dy) CK(cudaStreamSynchronize(st));
+    if (!dx || !dy) {
+        CK(cudaStreamSynchronize(st));
+        return take_status(h);  // the call waited for its products
+    }
     return HMAT_OK;
 }
 
 }  // namespace
 
-extern "C" int hmat_bicgstab_multi(hmat_handle h, const double *b, double *x, int32_t nrhs,
-                                   const hmat_solve_opts *opts_in, void *stream, hmat_solve_info *infos) {
+static int bicgstab_multi_impl(hmat_handle h, const double *b, double *x, int32_t nrhs,
+                               const hmat_solve_opts *opts_in, void *stream, hmat_solve_info *infos) {
     if (!h || !b || !x || nrhs < 1) return HMAT_ERR_ARG;
     hmat_solve_opts o;
     hmat_solve_opts_default(&o);
@@ -948,8 +1030,8 @@ int gmres_read(hmat_t *h, cudaStream_t st) {
 
 }  // namespace
 
-extern "C" int hmat_gmres(hmat_handle h, const double *b, double *x, int32_t m, const hmat_solve_opts *opts_in,
-                          void *stream, hmat_solve_info *info) {
+static int gmres_impl(hmat_handle h, const double *b, double *x, int32_t m, const hmat_solve_opts *opts_in,
+                      void *stream, hmat_solve_info *info) {
     if (!h || !b || !x || m < 1 || m > kGmresMaxM) return HMAT_ERR_ARG;
     hmat_solve_opts o;
     hmat_solve_opts_default(&o);
@@ -1093,7 +1175,7 @@ extern "C" int hmat_info(hmat_handle h, hmat_handle_info *out) {
     return HMAT_OK;
 }
 
-extern "C" int hmat_time_matvec(hmat_handle h, int32_t iters, int32_t fp64, void *stream, double *ms_out) {
+static int time_matvec_impl(hmat_handle h, int32_t iters, int32_t fp64, void *stream, double *ms_out) {
     if (!h || !ms_out || iters < 1) return HMAT_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const HmatSegment *seg = fp64 ? &h->seg64 : h->seg;
@@ -1149,6 +1231,7 @@ extern "C" const char *hmat_strerror(int status) {
     case HMAT_ERR_NONFINITE: return "non-finite value";
     case HMAT_ERR_RANGE: return "value out of range for the precision form";
     case HMAT_ERR_UNSUPPORTED: return "unsupported size";
+    case HMAT_ERR_TIMEOUT: return "a bounded wait inside a kernel ran out (the product was abandoned)";
     default: return "unknown status";
     }
 }
@@ -1159,3 +1242,69 @@ std::string &hmat_internal::last_cuda_error() {
 }
 
 extern "C" const char *hmat_last_cuda_error(void) { return hmat_internal::last_cuda_error().c_str(); }
+
+// ---- entry points that report the timeouts of bounded device waits ----
+namespace {
+// a synchronous call's own status, unless one of its products (or an earlier
+// asynchronous product) recorded a timeout: then that product's result was not
+// valid and whatever followed from it is reported as the timeout
+int with_status(hmat_handle h, int rc, hmat_solve_info *info, int ninfo) {
+    const int e = take_status(h);
+    if (e != HMAT_OK) {
+        rc = e;
+        for (int k = 0; info && k < ninfo; ++k) info[k].status = e;
+    }
+    return rc;
+}
+}  // namespace
+
+extern "C" int hmat_bicgstab_ex(hmat_handle h, const double *b, double *x, const hmat_solve_opts *opts_in, void *stream,
+                                hmat_solve_info *info) {
+    if (h)
+        if (int e = take_status(h)) return e;
+    const int rc = bicgstab_ex_impl(h, b, x, opts_in, stream, info);
+    return h ? with_status(h, rc, info, 1) : rc;
+}
+
+extern "C" int hmat_bicgstab_multi(hmat_handle h, const double *b, double *x, int32_t nrhs,
+                                   const hmat_solve_opts *opts_in, void *stream, hmat_solve_info *infos) {
+    if (h)
+        if (int e = take_status(h)) return e;
+    const int rc = bicgstab_multi_impl(h, b, x, nrhs, opts_in, stream, infos);
+    return h ? with_status(h, rc, infos, nrhs > 0 ? nrhs : 0) : rc;
+}
+
+extern "C" int hmat_gmres(hmat_handle h, const double *b, double *x, int32_t m, const hmat_solve_opts *opts_in,
+                          void *stream, hmat_solve_info *info) {
+    if (h)
+        if (int e = take_status(h)) return e;
+    const int rc = gmres_impl(h, b, x, m, opts_in, stream, info);
+    return h ? with_status(h, rc, info, 1) : rc;
+}
+
+extern "C" int hmat_time_matvec(hmat_handle h, int32_t iters, int32_t fp64, void *stream, double *ms_out) {
+    if (h)
+        if (int e = take_status(h)) return e;
+    const int rc = time_matvec_impl(h, iters, fp64, stream, ms_out);
+    return h ? with_status(h, rc, nullptr, 0) : rc;
+}
+
+extern "C" int hmat_check(hmat_handle h, void *stream) {
+    if (!h) return HMAT_ERR_ARG;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return take_status(h);
+}
+
+extern "C" int hmat_set_wait_limit(hmat_handle h, int64_t cycles, int32_t withhold) {
+    if (!h || cycles < 1) return HMAT_ERR_ARG;
+    h->mx.ctl.wait_limit = cycles;
+    h->mx.ctl.withhold = withhold ? 1 : 0;
+    // solver graphs captured the old values: capture them again at their next use
+    if (h->multi.graph) {
+        cudaGraphExecDestroy(h->multi.graph);
+        h->multi.graph = nullptr;
+        h->multi.graph_k = 0;
+        h->multi.graph_limit = -1;
+    }
+    return HMAT_OK;
+}

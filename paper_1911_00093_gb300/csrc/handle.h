@@ -52,6 +52,10 @@ struct hmat_t {
     int nseg = 1;
     HmatSegment seg64;              // the FP64 H-matrix of the true residual (Section 4.1.3)
     std::vector<void *> allocs;
+    // HMAT_ERR_TIMEOUT from a bounded device wait of one of the handle's kernels
+    // (mapped pinned memory: the kernels write it, the host reads it at the
+    // next call or at hmat_check)
+    int32_t *status_host = nullptr, *status_dev = nullptr;
     std::vector<int64_t> prob_off;  // problem p owns [prob_off[p], prob_off[p+1]) (batch handles)
     // GMRES buffers (first GMRES solve; sized for the restart length m)
     struct Gmres {
@@ -92,6 +96,7 @@ struct hmat_t {
     int loop_k = 0, loop_limit = -1;
     // sizes
     int64_t panel_bytes = 0, panel_bytes64 = 0, index_bytes = 0;
+    int64_t panel_bytes_mrhs = 0;  // W tiles of the many-right-hand-side projection (BF16 handles)
     int64_t stored_entries = 0, phase1_entries = 0, phase2_entries = 0, partials_n = 0, rank_sum = 0;
     int64_t phase1_bytes = 0, phase2_bytes = 0;
 
@@ -108,6 +113,7 @@ struct hmat_t {
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (void *a : allocs) cudaFree(a);
         if (S_host) cudaFreeHost(S_host);
+        if (status_host) cudaFreeHost(status_host);
         cudaSetDevice(cur);
     }
 
@@ -144,3 +150,12 @@ struct hmat_t {
     }
 };
 
+// A timeout recorded by a bounded device wait of the handle's kernels, taken
+// (cleared) by the call that reports it; HMAT_OK when there is none.
+inline int take_status(hmat_t *h) {
+    volatile int32_t *s = h->status_host;
+    if (!s || *s == 0) return HMAT_OK;
+    const int e = *s;
+    *s = 0;
+    return e;
+}

@@ -202,6 +202,8 @@ int check_layout(const Layout &L, std::string *why = nullptr);
 enum class Store { F64, DF, F32, BF16, PM, PS, PM1, PS2 };
 size_t store_bytes(Store s);
 void fill_panels(const BlobView &v, const Layout &L, Store s, void *q1, void *p2);
+// the BF16 value the panels store for v (round to nearest, ties to even): its 16 bits
+uint16_t bf16_bits(double v);
 
 // One segment of a paper variant: a derived block list over the cluster tree
 // of the source blob, with its own arrays (`view` points into this object).

@@ -129,20 +129,43 @@ void launch_g_arnoldi(int64_t n, const double *V, int ldv, double *w, GmresState
 void launch_g_finish_cycle(int64_t n, const double *V, int ldv, double *x, GmresState *G, int m, cudaStream_t st);
 
 // ---- product for many right-hand sides on the tensor cores (mrhs.cu, BF16 panels) ----
+// Bounded device waits: a wait that runs out writes HMAT_ERR_TIMEOUT to *status
+// (mapped host memory of the handle) and the kernel gives up its work.
+struct PipeCtl {
+    int32_t *status = nullptr;
+    long long wait_limit = 0;  // SM clock cycles per wait
+    int32_t withhold = 0;      // tests: the projection issues no copies, so its waits run out
+    int32_t pad = 0;
+};
+constexpr long long kDefaultWaitCycles = 2000000000ll;  // about one second at the SM clock
 constexpr int kMrhsCols = 64;  // right-hand sides per pass
 struct MrhsSrc {
     int32_t row;  // row of U feeding this operand slot (x row, t row, or the zero row)
     int32_t exp;  // power of two of the stored array the slot multiplies
 };
+// One column cluster sigma of the projection: the rank rows of every low-rank
+// block whose column cluster is sigma, stacked (R rows), times x_sigma.
+struct MrhsSig {
+    int64_t woff;   // first element of its W tile (BF16, K-major core matrices, kpad x npad)
+    int32_t xbeg;   // first source row (cluster order)
+    int32_t xlen;   // |sigma|
+    int32_t kpad;   // xlen rounded up to 16
+    int32_t npad;   // R rounded up to 16
+    int32_t R;      // rank rows
+    int32_t tbeg;   // first t row (within T) of its rank rows
+};
 struct MrhsIndex {
     const MrhsSrc *src = nullptr;    // [glen]
-    const int32_t *tbase = nullptr;  // [nlr] first t row of each low-rank block (within T)
-    const int32_t *tasks = nullptr;  // (block << 6) | rank of every multi-cluster block
-    int32_t ntasks = 0;
-    int64_t urows = 0, npart = 0;    // rows of U (n + ranks + 1) and of the partials
+    const MrhsSig *sigs = nullptr;   // [nsig]
+    const uint16_t *wt = nullptr;    // W tiles of the column clusters
+    int32_t nsig = 0, max_npad = 16;
+    int64_t urows = 0;               // rows of U (n + ranks + 1)
     float *U = nullptr;              // [urows][64]: x rows, then t rows, then a zero row
-    float *part = nullptr;           // [npart][64]
+    PipeCtl ctl;
 };
+constexpr int kMrhsMaxRows = 128;  // rank rows of one projection item (tensor-memory columns)
+// raise the shared-memory limits of the two kernels (once per device, at upload)
+cudaError_t mrhs_prepare();
 // y(:, k) = A~ x(:, k), k < nrhs <= 64, cluster order, columns ldx / ldy apart
 void launch_mrhs_product(const DevIndex &ix, const MrhsIndex &mx, const DevPanels &P, const double *x, int64_t ldx,
                          double *y, int64_t ldy, int nrhs, cudaStream_t st);

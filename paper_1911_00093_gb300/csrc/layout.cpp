@@ -563,6 +563,8 @@ void fill_panels(const BlobView &v, const Layout &L, Store s, void *q1, void *p2
     }
 }
 
+uint16_t bf16_bits(double v) { return to_bf16(v); }
+
 }  // namespace hmat_internal
 
 extern "C" int hmat_blob_stats_get(const void *blob, size_t blob_bytes, hmat_blob_stats *out) {

@@ -71,6 +71,7 @@ size_t scratch_bytes_for(const hmat_t *h) {
 
 extern "C" int hmat_matvec_noalloc(hmat_handle h, const double *x, double *y, void *stream) {
     if (!h || !x || !y || x == y) return HMAT_ERR_ARG;
+    if (int e = take_status(h)) return e;  // a bounded wait of an earlier product ran out
     int dev = -1;
     CK(cudaGetDevice(&dev));
     if (dev != h->device || dev < 0 || dev >= kMaxDevices) return HMAT_ERR_ARG;
