@@ -391,8 +391,6 @@ def run_workload(args):
     elif args.workload in ("build_icosphere_L6", "build_batch48"):
         # H-matrix construction: the host builder (OpenMP on the host cores) against
         # the device ACA builder; both produce the same blob (checked here)
-        import os
-        import time
         if args.workload == "build_icosphere_L6":
             meshes = [synth.icosphere(6)]
         else:
