@@ -58,18 +58,21 @@ namespace {
 //   out_perm != nullptr: y written in original order
 // The segments' expansions add up in y; the last one also leaves the shares of
 // Algorithm 1's inner products in dpart (dotmode 1: r~ . v, v . v; 2: s . t, t . t).
+// sys != nullptr: the work items of problems whose system sys[problem] has
+// stopped are skipped (their rows of y are left as they were).
 void enqueue_segments(const HmatSegment *seg, int nseg, const double *x_src, const int32_t *src_perm, double *y,
                       const int32_t *out_perm, const SolverScalars *skipS, int mode, cudaStream_t st,
-                      const double *w = nullptr, int dotmode = 0, double *dpart = nullptr) {
+                      const double *w = nullptr, int dotmode = 0, double *dpart = nullptr,
+                      const SysScalars *sys = nullptr) {
     if (x_src) launch_prep(seg[0].store, seg[0].ix, x_src, src_perm, seg[0].P.xs, st);
     for (int k = 0; k < nseg; ++k) {
-        launch_phase1(seg[k].store, seg[k].ix, seg[k].P, skipS, mode, st);
-        launch_reduce(seg[k].store, seg[k].ix, seg[k].P, skipS, mode, st);
+        launch_phase1(seg[k].store, seg[k].ix, seg[k].P, skipS, mode, st, sys);
+        launch_reduce(seg[k].store, seg[k].ix, seg[k].P, skipS, mode, st, sys);
     }
     for (int k = 0; k < nseg; ++k) {
         const bool last = k == nseg - 1;
         launch_phase2(seg[k].store, seg[k].ix, seg[k].P, y, out_perm, k > 0, skipS, mode, st, last ? w : nullptr,
-                      last ? dotmode : 0, dpart);
+                      last ? dotmode : 0, dpart, sys);
     }
 }
 
@@ -100,17 +103,34 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
     double *tscale = nullptr;
     GroupDesc *groups = nullptr;
     int st;
-    if ((st = h->upload(&p1, L.p1.data(), sizeof(P1Desc) * L.p1.size())) ||
+    // the problem of every work item (pad fields): a batch's solver skips the
+    // items of the problems whose systems have stopped
+    std::vector<P1Desc> p1h = L.p1;
+    std::vector<GroupDesc> grh = L.groups;
+    std::vector<LrDesc> lrh = L.lr;
+    auto prob_of = [&](int64_t row) {
+        return (int32_t)(std::upper_bound(h->prob_off.begin(), h->prob_off.end(), row) - h->prob_off.begin() - 1);
+    };
+    for (size_t k = 0; k < p1h.size(); ++k) {
+        p1h[k].pad[0] = prob_of(p1h[k].xbeg);
+        p1h[k].pad[1] = 0;
+        for (int r = 0; r < p1h[k].rcnt; ++r) lrh[L.p1_runs[p1h[k].rbeg + r].q].pad = p1h[k].pad[0];
+    }
+    for (GroupDesc &gd : grh) {
+        gd.pad[0] = prob_of(gd.p0);
+        gd.pad[1] = 0;
+    }
+    if ((st = h->upload(&p1, p1h.data(), sizeof(P1Desc) * p1h.size())) ||
         (st = h->upload(&p1_runs, L.p1_runs.data(), sizeof(P1Run) * L.p1_runs.size())) ||
         (st = h->upload(&xdst, L.xdst.data(), sizeof(XDst) * L.xdst.size())) ||
         (st = h->upload(&xsel, L.xsel.data(), 4 * L.xsel.size())) ||
-        (st = h->upload(&lr, L.lr.data(), sizeof(LrDesc) * L.lr.size())) ||
+        (st = h->upload(&lr, lrh.data(), sizeof(LrDesc) * lrh.size())) ||
         (st = h->upload(&gdst, L.gdst.data(), 4 * L.gdst.size())) ||
         (st = h->upload(&red_big, L.red_big.data(), 4 * L.red_big.size())) ||
         (st = h->upload(&red_tasks, L.red_tasks.data(), 4 * L.red_tasks.size())) ||
         (st = h->upload(&p2, L.p2.data(), sizeof(P2Desc) * L.p2.size())) ||
         (st = h->upload(&tscale, L.tscale.data(), 8 * L.tscale.size())) ||
-        (st = h->upload(&groups, L.groups.data(), sizeof(GroupDesc) * L.groups.size()))) {
+        (st = h->upload(&groups, grh.data(), sizeof(GroupDesc) * grh.size()))) {
         return st;
     }
     ix.p1 = p1; ix.p1_runs = p1_runs; ix.xdst = xdst; ix.xsel = xsel; ix.lr = lr; ix.gdst = gdst; ix.p2 = p2;
@@ -800,16 +820,21 @@ MultiGrid multi_grid(hmat_t *h, int nrhs) {
 }
 
 // y(:, k) = A x(:, k) for every column, cluster order (a block-diagonal batch is one operator)
+// The products of every system's column; skip_stopped (the products inside an
+// iteration): the work items of problems whose system has stopped are skipped,
+// so a batch costs less as its problems converge.
 void multi_products(hmat_t *h, const HmatSegment *seg, int nseg, const double *x, double *y, int nrhs,
-                    cudaStream_t st) {
+                    cudaStream_t st, bool skip_stopped = false) {
     if (seg == h->seg && h->mrhs && h->mx.U && nrhs >= 2) {  // tensor cores, 64 columns per pass
         for (int k0 = 0; k0 < nrhs; k0 += kMrhsCols)
             launch_mrhs_product(h->seg[0].ix, h->mx, h->seg[0].P, x + (size_t)k0 * h->n, h->n, y + (size_t)k0 * h->n,
                                 h->n, std::min(kMrhsCols, nrhs - k0), st);
         return;
     }
+    const size_t count = h->prob_off.size() - 1;  // problems: system (p, k) is k * count + p
     for (int k = 0; k < nrhs; ++k)
-        enqueue_segments(seg, nseg, x + (size_t)k * h->n, nullptr, y + (size_t)k * h->n, nullptr, nullptr, 0, st);
+        enqueue_segments(seg, nseg, x + (size_t)k * h->n, nullptr, y + (size_t)k * h->n, nullptr, nullptr, 0, st,
+                         nullptr, 0, nullptr, skip_stopped ? h->multi.S + (size_t)k * count : nullptr);
 }
 
 int multi_product_launches(hmat_t *h, const HmatSegment *seg, int nseg, int nrhs) {
@@ -833,10 +858,10 @@ void multi_iteration(hmat_t *h, const MultiGrid &g, int nrhs, int iter_limit, cu
     auto &m = h->multi;
     const MultiVecs v{m.x, m.r, m.rt, m.p, m.v, m.s, m.t};
     launch_miteration_vec(g, 0, v, iter_limit, st);  // p
-    multi_products(h, h->seg, h->nseg, m.p, m.v, nrhs, st);
+    multi_products(h, h->seg, h->nseg, m.p, m.v, nrhs, st, true);
     launch_miteration_vec(g, 1, v, iter_limit, st);  // alpha
     launch_miteration_vec(g, 2, v, iter_limit, st);  // s
-    multi_products(h, h->seg, h->nseg, m.s, m.t, nrhs, st);
+    multi_products(h, h->seg, h->nseg, m.s, m.t, nrhs, st, true);
     launch_miteration_vec(g, 3, v, iter_limit, st);  // omega
     launch_miteration_vec(g, 4, v, iter_limit, st);  // x, r
 }

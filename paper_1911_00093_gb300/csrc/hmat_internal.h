@@ -100,7 +100,7 @@ struct P1Desc {
     int32_t xlen;   // rows of kappa
     int32_t xdbeg;  // first XDst (dense-block operand slices fed from x_kappa)
     int32_t xdcnt;
-    int32_t pad[2];
+    int32_t pad[2];  // on the device: pad[0] = the item's problem (batch handles)
 };
 struct P1Run {
     int32_t col0;   // first panel column of the block
@@ -116,7 +116,7 @@ struct LrDesc {
     int32_t gbeg;   // first entry of gdst (one per leaf row cluster of the block)
     int32_t gcnt;
     int32_t toff;   // first per-rank factor d_l of t = d_l z_l (eq. 23), or -1
-    int32_t pad;
+    int32_t pad;    // on the device: the block's problem (batch handles)
 };
 struct XDst {
     int32_t goff;   // operand index of the slice's first entry in g
@@ -150,7 +150,7 @@ struct GroupDesc {
     int32_t ld;     // entries per row
     int32_t p0;     // first row (cluster order)
     int32_t nr;     // rows (1..kGroupRows)
-    int32_t pad[2];
+    int32_t pad[2];  // on the device: pad[0] = the group's problem (batch handles)
 };
 
 constexpr int kMaxScaleExp = 120;  // |e| of every stored power-of-two scale

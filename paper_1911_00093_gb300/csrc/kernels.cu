@@ -26,23 +26,23 @@ void launch_prep(Store s, const DevIndex &ix, const double *x, const int32_t *sr
 }
 
 void launch_phase1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                   cudaStream_t st) {
-    if (is_table1(s)) return launch_phase1_table1(s, ix, P, skipS, mode, st);
-    HMAT_DISPATCH(s, phase1_launch<SS>(ix, P, skipS, mode, st));
+                   cudaStream_t st, const SysScalars *sys) {
+    if (is_table1(s)) return launch_phase1_table1(s, ix, P, skipS, mode, st, sys);
+    HMAT_DISPATCH(s, phase1_launch<SS>(ix, P, skipS, mode, st, sys));
 }
 
 void launch_reduce(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                   cudaStream_t st) {
-    if (is_table1(s)) return launch_reduce_table1(s, ix, P, skipS, mode, st);
-    HMAT_DISPATCH(s, reduce_launch<SS>(ix, P, skipS, mode, st));
+                   cudaStream_t st, const SysScalars *sys) {
+    if (is_table1(s)) return launch_reduce_table1(s, ix, P, skipS, mode, st, sys);
+    HMAT_DISPATCH(s, reduce_launch<SS>(ix, P, skipS, mode, st, sys));
 }
 
 void launch_phase2(Store s, const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm, int accum,
                    const SolverScalars *skipS, int mode, cudaStream_t st, const double *w, int dotmode,
-                   double *dpart) {
+                   double *dpart, const SysScalars *sys) {
     if (is_table1(s))
-        return launch_phase2_table1(s, ix, P, y, out_perm, accum, skipS, mode, st, w, dotmode, dpart);
-    HMAT_DISPATCH(s, phase2_launch<SS>(ix, P, y, out_perm, accum, skipS, mode, st, w, dotmode, dpart));
+        return launch_phase2_table1(s, ix, P, y, out_perm, accum, skipS, mode, st, w, dotmode, dpart, sys);
+    HMAT_DISPATCH(s, phase2_launch<SS>(ix, P, y, out_perm, accum, skipS, mode, st, w, dotmode, dpart, sys));
 }
 
 

@@ -28,6 +28,9 @@ struct DevIndex {
     int32_t max_ld2 = 0;            // widest phase-2 panel (entries)
 };
 
+struct SolverScalars;
+struct SysScalars;
+
 // One precision copy of the panels plus its work buffers.
 struct DevPanels {
     Store store = Store::DF;
@@ -60,11 +63,14 @@ void launch_prep(Store s, const DevIndex &ix, const double *x, const int32_t *sr
 struct SolverScalars;
 // skipS/mode: a solver's product is skipped once its run has stopped (mode 1:
 // flag set; mode 2: flag set or stop at the ||s|| check); mode 0 never skips.
+// sys != nullptr (many-system solver): the work items of a problem whose system
+// sys[problem] has stopped are skipped (the problem index of an item is in the
+// pad fields of its descriptor)
 void launch_phase1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                   cudaStream_t st);
+                   cudaStream_t st, const SysScalars *sys = nullptr);
 // t of the blocks spanning several leaf clusters, scattered into g (no launch when there is none)
 void launch_reduce(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                   cudaStream_t st);
+                   cudaStream_t st, const SysScalars *sys = nullptr);
 // y[p] (cluster order) or y[out_perm[p]] (original order) = (A~ x)_p, or
 // y[.] += (A~ x)_p when accum is set (the second segment of a paper variant);
 // dotmode 1/2 also leaves, per work item k, w . y in dpart[k] and y . y in
@@ -72,15 +78,15 @@ void launch_reduce(Store s, const DevIndex &ix, const DevPanels &P, const Solver
 // Algorithm 1)
 void launch_phase2(Store s, const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm, int accum,
                    const SolverScalars *skipS, int mode, cudaStream_t st, const double *w = nullptr,
-                   int dotmode = 0, double *dpart = nullptr);
+                   int dotmode = 0, double *dpart = nullptr, const SysScalars *sys = nullptr);
 // the same for the paper's stores (kernels_table1.cu)
 void launch_phase1_table1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                          cudaStream_t st);
+                          cudaStream_t st, const SysScalars *sys);
 void launch_reduce_table1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                          cudaStream_t st);
+                          cudaStream_t st, const SysScalars *sys);
 void launch_phase2_table1(Store s, const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm,
                           int accum, const SolverScalars *skipS, int mode, cudaStream_t st, const double *w,
-                          int dotmode, double *dpart);
+                          int dotmode, double *dpart, const SysScalars *sys);
 
 // ---- BiCG-STAB vector kernels (FP64) ----
 struct SolverScalars {

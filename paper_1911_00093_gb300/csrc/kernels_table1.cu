@@ -16,19 +16,19 @@ namespace hmat_internal {
     }
 
 void launch_phase1_table1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                          cudaStream_t st) {
-    HMAT_T1_DISPATCH(s, phase1_launch<SS>(ix, P, skipS, mode, st));
+                          cudaStream_t st, const SysScalars *sys) {
+    HMAT_T1_DISPATCH(s, phase1_launch<SS>(ix, P, skipS, mode, st, sys));
 }
 
 void launch_reduce_table1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
-                          cudaStream_t st) {
-    HMAT_T1_DISPATCH(s, reduce_launch<SS>(ix, P, skipS, mode, st));
+                          cudaStream_t st, const SysScalars *sys) {
+    HMAT_T1_DISPATCH(s, reduce_launch<SS>(ix, P, skipS, mode, st, sys));
 }
 
 void launch_phase2_table1(Store s, const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm,
                           int accum, const SolverScalars *skipS, int mode, cudaStream_t st, const double *w,
-                          int dotmode, double *dpart) {
-    HMAT_T1_DISPATCH(s, phase2_launch<SS>(ix, P, y, out_perm, accum, skipS, mode, st, w, dotmode, dpart));
+                          int dotmode, double *dpart, const SysScalars *sys) {
+    HMAT_T1_DISPATCH(s, phase2_launch<SS>(ix, P, y, out_perm, accum, skipS, mode, st, w, dotmode, dpart, sys));
 }
 
 }  // namespace hmat_internal

@@ -228,6 +228,14 @@ template <> __device__ __forceinline__ float to_part<Store::BF16>(Acc<Store::BF1
     return __fadd_rn(a.a.s, a.a.c);
 }
 
+// the many-system solver: the work item belongs to a problem whose system has
+// stopped (its run ended or it finished), so its products are not needed
+__device__ __forceinline__ bool item_idle(const SysScalars *sys, int prob) {
+    if (sys == nullptr) return false;
+    const SysScalars &q = sys[prob];
+    return q.state != 0 || q.flag != 0;
+}
+
 // skip test of the solver's products: mode 0 never, 1 on a set flag,
 // 2 on a set flag or a stop at the ||s|| check
 __device__ __forceinline__ bool skip_product(const SolverScalars *S, int mode) {
@@ -441,7 +449,7 @@ __global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc 
                                                         typename Tr<S>::Part *__restrict__ part,
                                                         typename Tr<S>::Op *__restrict__ g,
                                                         const double *__restrict__ tscale, const SolverScalars *S_,
-                                                        int mode) {
+                                                        int mode, const SysScalars *sys) {
     using Op = typename Tr<S>::Op;
     __shared__ Op xk[kMaxLeaf];  // x_kappa, broadcast to every thread
     // the cluster's run and dense-operand descriptors, loaded with x_kappa so
@@ -450,6 +458,7 @@ __global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc 
     __shared__ XDst xds[kP1SmemXd];
     if (skip_product(S_, mode)) return;
     const P1Desc d = desc[blockIdx.x];
+    if (item_idle(sys, d.pad[0])) return;  // (pad[0]: the item's problem)
     const bool runs_sm = d.rcnt <= kP1SmemRuns, xd_sm = d.xdcnt <= kP1SmemXd;
     for (int j = threadIdx.x; j < d.xlen; j += NT) {
         if constexpr (fp32_source(S)) xk[j] = (double)__double2float_rn(xs[d.xbeg + j]);  // Section 3.5
@@ -479,13 +488,14 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int ntasks, co
                                                          const typename Tr<S>::Part *__restrict__ part,
                                                          typename Tr<S>::Op *__restrict__ g,
                                                          const double *__restrict__ tscale, const SolverScalars *S_,
-                                                         int mode) {
+                                                         int mode, const SysScalars *sys) {
     using Op = typename Tr<S>::Op;
     using RT = typename RedT<S>::T;
     __shared__ RT red[kRedThreads];
     if (skip_product(S_, mode)) return;
     if ((int)blockIdx.x < nbig) {
         const LrDesc ld = lr[big[blockIdx.x]];
+        if (item_idle(sys, ld.pad)) return;  // (pad: the block's problem; CTA-uniform)
         for (int l0 = 0; l0 < ld.rank; l0 += 32) {
             const int rr = min(32, ld.rank - l0);
             int rp = 1;
@@ -524,6 +534,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int ntasks, co
     if (task >= ntasks) return;
     const int tq = __ldg(tasks + task);
     const LrDesc ld = lr[tq >> 6];
+    if (item_idle(sys, ld.pad)) return;
     const int l = tq & 63;
     const typename Tr<S>::Part *src = part + ld.boff + l;
     RT a;
@@ -706,7 +717,8 @@ template <Store S>
 __global__ void __launch_bounds__(kP2Threads, kP2gBlocks) k_phase2g(
     int ng, const GroupDesc *__restrict__ groups, const void *__restrict__ p2, const typename Tr<S>::Op *__restrict__ g,
     double *__restrict__ y, const int32_t *__restrict__ out_perm, int accum, const SolverScalars *S_, int mode,
-    const double *__restrict__ w, int dotmode, double *dpart) {
+    const double *__restrict__ w, int dotmode, double *dpart,
+    const SysScalars *sys) {
     constexpr int VW = Tr<S>::VW;
     constexpr size_t esz = 16 / VW;
     constexpr int GR = kGroupRows;
@@ -721,10 +733,18 @@ __global__ void __launch_bounds__(kP2Threads, kP2gBlocks) k_phase2g(
     // the next group's descriptor travels as one word per lane (lanes 0..5)
     // while this group streams, then is broadcast: one register, not six
     const int32_t *gwords = reinterpret_cast<const int32_t *>(groups);
-    int32_t word = (lane < 6 && t < ng) ? __ldg(gwords + (size_t)t * 8 + lane) : 0;
+    // (word 6, pad[0], is the group's problem: lane 6 carries it for the skip test)
+    const int nw = sys ? 7 : 6;
+    int32_t word = (lane < nw && t < ng) ? __ldg(gwords + (size_t)t * 8 + lane) : 0;
     GroupDesc cur = group_from_words(word);
+    int prob = sys ? __shfl_sync(0xffffffffu, word, 6) : 0;
     for (; t < ng; t += W) {
-        word = (lane < 6 && t + W < ng) ? __ldg(gwords + (size_t)(t + W) * 8 + lane) : 0;
+        word = (lane < nw && t + W < ng) ? __ldg(gwords + (size_t)(t + W) * 8 + lane) : 0;
+        if (item_idle(sys, prob)) {  // warp-uniform: the group's problem has stopped
+            cur = group_from_words(word);
+            prob = sys ? __shfl_sync(0xffffffffu, word, 6) : 0;
+            continue;
+        }
         const bool own = (lane & 7) == 0 && (lane >> 3) < cur.nr;
         const int p = cur.p0 + (lane >> 3);
         int q = p;
@@ -771,6 +791,7 @@ __global__ void __launch_bounds__(kP2Threads, kP2gBlocks) k_phase2g(
             }
         }
         cur = group_from_words(word);
+        prob = sys ? __shfl_sync(0xffffffffu, word, 6) : 0;
     }
     if (dotmode == 0) return;
     // the warp's share: the owner lanes 0, 8, 16, 24 in lane order
@@ -802,29 +823,31 @@ int grid_for(int64_t n, int threads, int cap) {
 
 // launches of one store's product kernels (the dispatchers pick the store)
 template <Store SS>
-void phase1_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st) {
+void phase1_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st,
+                   const SysScalars *sys) {
     k_phase1<SS><<<ix.nleaves, p1_threads<SS>(), 0, st>>>(ix.p1, ix.p1_runs, ix.xdst, ix.xsel, ix.lr, ix.gdst, P.q1,
                                                           (const typename Tr<SS>::Op *)P.xs,
                                                           (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g,
-                                                          ix.tscale, skipS, mode);
+                                                          ix.tscale, skipS, mode, sys);
 }
 
 template <Store SS>
-void reduce_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st) {
+void reduce_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st,
+                   const SysScalars *sys) {
     const int blocks = ix.nbig + (ix.ntasks + kRedThreads - 1) / kRedThreads;
     if (blocks == 0) return;
     k_reduce<SS><<<blocks, kRedThreads, 0, st>>>(ix.nbig, ix.ntasks, ix.red_big, ix.red_tasks, ix.lr, ix.gdst,
                                                  (const typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g,
-                                                 ix.tscale, skipS, mode);
+                                                 ix.tscale, skipS, mode, sys);
 }
 
 template <Store SS>
 void phase2_launch(const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm, int accum,
                    const SolverScalars *skipS, int mode, cudaStream_t st, const double *w, int dotmode,
-                   double *dpart) {
+                   double *dpart, const SysScalars *sys) {
     k_phase2g<SS><<<phase2_items(ix), kP2Threads, 0, st>>>(ix.ngroups, ix.groups, P.p2,
                                                            (const typename Tr<SS>::Op *)P.g, y, out_perm, accum,
-                                                           skipS, mode, w, dotmode, dpart);
+                                                           skipS, mode, w, dotmode, dpart, sys);
 }
 
 }  // namespace
