@@ -446,6 +446,43 @@ typedef struct hmat_handle_info {
 int hmat_info(hmat_handle h, hmat_handle_info *out);
 
 /*
+ * hmat_autotune -- choose the projection's CTA size per panel-width bucket by
+ * measurement (the paper has no counterpart: it concerns how the GPU runs the
+ * product of eq. 9, not what it computes).  The leaf column clusters are
+ * bucketed by the width of their panels (16-byte column vectors per row: at
+ * most 32, 64, 128, 256, more); each bucket can run with CTAs of 64, 128 or 256
+ * threads.  Starting from one launch over the clusters in cluster order at the
+ * store's default size, the tuner times whole projections (reps launches each,
+ * CUDA events on `stream`) with the work list sorted by bucket and one size per
+ * bucket, changing one bucket at a time while that helps (two passes), and keeps
+ * the sorted plan only if it beats the default by more than 2 %; the plan is
+ * stored in the handle (also for the FP64 operator of the true residuals).  The
+ * products give the same bits under any plan (each column's sum is one thread's
+ * sum in row order).  The paper's variants keep their single launch.  Do not
+ * overlap it with other calls on the handle; cached solver graphs are captured
+ * again.  `out` (may be NULL) receives the report of the iterated operator.
+ * Errors: HMAT_ERR_ARG, HMAT_ERR_NOMEM, HMAT_ERR_CUDA.
+ */
+typedef struct hmat_tune_bucket {
+    int32_t vec_max;   /* the bucket's panels have at most this many column vectors per row (0: no bound) */
+    int32_t clusters;  /* leaf column clusters in the bucket                                            */
+    int32_t threads;   /* the chosen CTA size                                                            */
+    int32_t pad;
+    double us[3];      /* projection microseconds with this bucket at 64, 128, 256 threads (the others
+                          as chosen; 0 if not measured)                                                   */
+} hmat_tune_bucket;
+
+typedef struct hmat_tune_report {
+    int32_t nbuckets;  /* 5                                                                             */
+    int32_t sorted;    /* 1: the projection runs the bucket-sorted work list, one launch per size run    */
+    double default_us; /* one launch over the clusters in cluster order at the default CTA size          */
+    double tuned_us;   /* the plan kept                                                                  */
+    hmat_tune_bucket bucket[5];
+} hmat_tune_report;
+
+int hmat_autotune(hmat_handle h, int32_t reps, void *stream, hmat_tune_report *out);
+
+/*
  * hmat_time_matvec -- enqueue `iters` products of a fixed internal vector on
  * `stream` and time each kernel of the product with CUDA events recorded on
  * that stream; ms_out[0..3] receive the mean milliseconds per launch of the

@@ -33,7 +33,18 @@ EXPORTS = ("hmat_build", "hmat_blob_free", "hmat_blob_stats_get", "hmat_upload",
            "hmat_matvec", "hmat_matvec_fp64", "hmat_solve_opts_default", "hmat_bicgstab",
            "hmat_bicgstab_ex", "hmat_info", "hmat_time_matvec", "hmat_strerror", "hmat_last_cuda_error",
            "hmat_matvec_noalloc", "hmat_upload_ex", "hmat_upload_batch", "hmat_problems", "hmat_bicgstab_multi",
-           "hmat_gmres", "hmat_build_device", "hmat_form_stats_get", "hmat_check", "hmat_set_wait_limit")
+           "hmat_gmres", "hmat_build_device", "hmat_form_stats_get", "hmat_check", "hmat_set_wait_limit",
+           "hmat_autotune")
+
+
+class TuneBucket(C.Structure):
+    _fields_ = [("vec_max", C.c_int32), ("clusters", C.c_int32), ("threads", C.c_int32), ("pad", C.c_int32),
+                ("us", C.c_double * 3)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("nbuckets", C.c_int32), ("sorted", C.c_int32), ("default_us", C.c_double),
+                ("tuned_us", C.c_double), ("bucket", TuneBucket * 5)]
 
 
 class BuildDeviceInfo(C.Structure):
@@ -122,6 +133,7 @@ def load():
                                         C.POINTER(BuildDeviceInfo)]),
         "hmat_form_stats_get": (C.c_int, [P, SZ, I32, I32, C.POINTER(FormStats)]),
         "hmat_check": (C.c_int, [P, P]),
+        "hmat_autotune": (C.c_int, [P, I32, P, C.POINTER(TuneReport)]),
         "hmat_set_wait_limit": (C.c_int, [P, I64, I32]),
     }
     for name, (res, args) in sig.items():
@@ -328,6 +340,16 @@ def hmat_set_wait_limit(h, cycles, withhold=False):
     """Bound of the tensor-core product's waits in SM cycles; withhold=True makes its
     projection issue no copies, so the waits run out (tests of the timeout path)."""
     _check(load().hmat_set_wait_limit(C.c_void_p(h), int(cycles), 1 if withhold else 0), "hmat_set_wait_limit")
+
+
+def hmat_autotune(h, reps=20, stream=None) -> dict:
+    """Choose the projection's CTA size per panel-width bucket by measurement and
+    keep the plan in the handle; returns the report of the iterated operator."""
+    r = TuneReport()
+    _check(load().hmat_autotune(C.c_void_p(h), int(reps), _stream_ptr(stream), C.byref(r)), "hmat_autotune")
+    return {"sorted": bool(r.sorted), "default_us": r.default_us, "tuned_us": r.tuned_us,
+            "buckets": [{"vec_max": b.vec_max, "clusters": b.clusters, "threads": b.threads,
+                         "us_64_128_256": [b.us[0], b.us[1], b.us[2]]} for b in r.bucket[:r.nbuckets]]}
 
 
 def hmat_solve_opts(**kw) -> SolveOpts:

@@ -1333,3 +1333,133 @@ extern "C" int hmat_set_wait_limit(hmat_handle h, int64_t cycles, int32_t withho
     }
     return HMAT_OK;
 }
+
+// ---- the projection's plan, chosen by measurement ----
+namespace {
+
+constexpr int kTuneBuckets = 5;
+constexpr int kBucketVec[kTuneBuckets] = {32, 64, 128, 256, 0};  // column vectors per row (0: no bound)
+constexpr int kTuneSizes[3] = {64, 128, 256};
+
+int bucket_of(int nvec) {
+    for (int b = 0; b < kTuneBuckets - 1; ++b)
+        if (nvec <= kBucketVec[b]) return b;
+    return kTuneBuckets - 1;
+}
+
+// The plan of the sorted work list: one run per stretch of buckets with the same size.
+void sorted_plan(DevIndex &t, const int32_t (&begin)[kTuneBuckets + 1], const int (&nt)[kTuneBuckets]) {
+    t.nruns = 0;
+    for (int b = 0; b < kTuneBuckets; ++b) {
+        const int cnt = begin[b + 1] - begin[b];
+        if (cnt == 0) continue;
+        if (t.nruns > 0 && t.runs[t.nruns - 1].nt == nt[b]) {
+            t.runs[t.nruns - 1].count += cnt;
+        } else {
+            t.runs[t.nruns].begin = begin[b];
+            t.runs[t.nruns].count = cnt;
+            t.runs[t.nruns].nt = nt[b];
+            ++t.nruns;
+        }
+    }
+}
+
+int tune_segment(hmat_t *h, HmatSegment &g, int reps, cudaStream_t st, hmat_tune_report *rep) {
+    DevIndex &ix = g.ix;
+    if (table1_store(g.store) || ix.nleaves == 0) return HMAT_OK;
+    const int VW = g.store == Store::BF16 ? 8 : g.store == Store::F32 ? 4 : 2;
+    std::vector<P1Desc> d((size_t)ix.nleaves);
+    CK(cudaMemcpy(d.data(), ix.p1, sizeof(P1Desc) * d.size(), cudaMemcpyDeviceToHost));
+    // the work list sorted by bucket (stable: cluster order inside a bucket)
+    std::vector<P1Desc> sorted;
+    sorted.reserve(d.size());
+    int32_t begin[kTuneBuckets + 1] = {0};
+    for (int b = 0; b < kTuneBuckets; ++b) {
+        begin[b] = (int32_t)sorted.size();
+        for (const P1Desc &e : d)
+            if (bucket_of(e.ld / VW) == b) sorted.push_back(e);
+    }
+    begin[kTuneBuckets] = (int32_t)sorted.size();
+    P1Desc *dsorted = nullptr;
+    int st2;
+    if ((st2 = h->upload(&dsorted, sorted.data(), sizeof(P1Desc) * sorted.size()))) return st2;
+    DevIndex base = ix;
+    base.nruns = 0;
+    base.p1_sorted = nullptr;
+    const float t_default = time_phase1(g.store, base, g.P, reps, st);
+    if (t_default < 0.f) return HMAT_ERR_CUDA;
+    const int def = phase1_default_threads(g.store);
+    int nt[kTuneBuckets];
+    for (int &v : nt) v = def;
+    double us[kTuneBuckets][3] = {};
+    DevIndex t = base;
+    t.p1_sorted = dsorted;
+    sorted_plan(t, begin, nt);
+    float best = time_phase1(g.store, t, g.P, reps, st);
+    for (int pass = 0; pass < 2; ++pass) {
+        bool changed = false;
+        for (int b = 0; b < kTuneBuckets; ++b) {
+            if (begin[b + 1] == begin[b]) continue;
+            for (int c = 0; c < 3; ++c) {
+                if (kTuneSizes[c] == nt[b]) {
+                    us[b][c] = best;
+                    continue;
+                }
+                int trial[kTuneBuckets];
+                for (int k = 0; k < kTuneBuckets; ++k) trial[k] = nt[k];
+                trial[b] = kTuneSizes[c];
+                sorted_plan(t, begin, trial);
+                const float tt = time_phase1(g.store, t, g.P, reps, st);
+                if (tt < 0.f) return HMAT_ERR_CUDA;
+                us[b][c] = tt;
+                if (tt < best * 0.99f) {
+                    best = tt;
+                    nt[b] = kTuneSizes[c];
+                    changed = true;
+                }
+            }
+        }
+        if (!changed) break;
+    }
+    const bool use_sorted = best < t_default * 0.98f;
+    if (use_sorted) {
+        sorted_plan(ix, begin, nt);
+        ix.p1_sorted = dsorted;
+    } else {
+        ix.nruns = 0;
+        ix.p1_sorted = nullptr;
+    }
+    if (rep) {
+        rep->nbuckets = kTuneBuckets;
+        rep->sorted = use_sorted ? 1 : 0;
+        rep->default_us = t_default;
+        rep->tuned_us = use_sorted ? best : t_default;
+        for (int b = 0; b < kTuneBuckets; ++b) {
+            rep->bucket[b].vec_max = kBucketVec[b];
+            rep->bucket[b].clusters = begin[b + 1] - begin[b];
+            rep->bucket[b].threads = use_sorted ? nt[b] : def;
+            rep->bucket[b].pad = 0;
+            for (int c = 0; c < 3; ++c) rep->bucket[b].us[c] = us[b][c];
+        }
+    }
+    return HMAT_OK;
+}
+
+}  // namespace
+
+extern "C" int hmat_autotune(hmat_handle h, int32_t reps, void *stream, hmat_tune_report *out) {
+    if (!h || reps < 1) return HMAT_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (out) std::memset(out, 0, sizeof(*out));
+    int rc = tune_segment(h, h->seg[0], reps, st, out);
+    if (rc) return rc;
+    const bool fp64_form = h->precision == HMAT_FP64 || h->precision == HMAT_FP64_DFMA;
+    if (fp64_form) h->seg64.ix = h->seg[0].ix;  // the same operator
+    else if ((rc = tune_segment(h, h->seg64, reps, st, nullptr))) return rc;
+    // solver graphs captured the old launches: capture them again at their next use
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; h->graph_k = 0; h->graph_limit = -1; }
+    if (h->loop_graph) { cudaGraphExecDestroy(h->loop_graph); h->loop_graph = nullptr; h->loop_k = 0; h->loop_limit = -1; }
+    if (h->multi.graph) { cudaGraphExecDestroy(h->multi.graph); h->multi.graph = nullptr; h->multi.graph_k = 0; h->multi.graph_limit = -1; }
+    if (h->gm.graph) { cudaGraphExecDestroy(h->gm.graph); h->gm.graph = nullptr; h->gm.graph_m = 0; h->gm.graph_limit = -1; }
+    return HMAT_OK;
+}

@@ -31,6 +31,31 @@ void launch_phase1(Store s, const DevIndex &ix, const DevPanels &P, const Solver
     HMAT_DISPATCH(s, phase1_launch<SS>(ix, P, skipS, mode, st, sys));
 }
 
+float time_phase1(Store s, const DevIndex &ix, const DevPanels &P, int reps, cudaStream_t st) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1.f;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return -1.f;
+    }
+    launch_phase1(s, ix, P, nullptr, 0, st);  // warm-up
+    cudaEventRecord(a, st);
+    for (int k = 0; k < reps; ++k) launch_phase1(s, ix, P, nullptr, 0, st);
+    cudaEventRecord(b, st);
+    float ms = -1.f;
+    if (cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms < 0.f ? -1.f : 1e3f * ms / (float)reps;
+}
+
+int phase1_default_threads(Store s) {
+    switch (s) {
+    case Store::BF16: return p1_threads<Store::BF16>();
+    default: return 256;
+    }
+}
+
 void launch_reduce(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,
                    cudaStream_t st, const SysScalars *sys) {
     if (is_table1(s)) return launch_reduce_table1(s, ix, P, skipS, mode, st, sys);

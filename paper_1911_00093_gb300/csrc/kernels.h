@@ -8,6 +8,13 @@
 
 namespace hmat_internal {
 
+// One launch of the projection over items [begin, begin + count) of its work
+// list with CTAs of nt threads (64, 128 or 256).
+struct P1Plan {
+    int32_t begin = 0, count = 0, nt = 0;
+};
+constexpr int kP1MaxRuns = 8;
+
 // Device-resident packing indices (shared by every precision copy of a handle).
 struct DevIndex {
     int32_t n = 0, nleaves = 0, nlr = 0, nbig = 0, ntasks = 0;
@@ -24,6 +31,12 @@ struct DevIndex {
     const GroupDesc *groups = nullptr;  // row groups of the row-group expansion
     int32_t ngroups = 0;
     int32_t nsm = 1;                // SMs of the device (row-group grid = nsm x kP2gBlocks)
+    // projection plan (hmat_autotune): nruns == 0 is one launch over p1 in cluster
+    // order at the store's default CTA size; else the runs over p1_sorted (the
+    // clusters sorted by panel width) or p1
+    const P1Desc *p1_sorted = nullptr;
+    int32_t nruns = 0;
+    P1Plan runs[kP1MaxRuns];
     int32_t max_leaf = 0;           // rows of the widest leaf cluster
     int32_t max_ld2 = 0;            // widest phase-2 panel (entries)
 };
@@ -55,6 +68,12 @@ inline int phase2_items(const DevIndex &ix) { return ix.nsm * kP2gBlocks; }
 inline size_t operand_bytes(Store s) { return s == Store::F32 || s == Store::BF16 ? 4 : 8; }
 inline size_t partial_bytes(Store s) { return s == Store::F32 || s == Store::BF16 ? 4 : 8; }
 inline bool table1_store(Store s) { return s == Store::PM || s == Store::PS || s == Store::PM1 || s == Store::PS2; }
+
+// Mean microseconds of the projection (every run of ix's plan) over reps
+// launches, CUDA events on st (the autotuner's measurement).
+float time_phase1(Store s, const DevIndex &ix, const DevPanels &P, int reps, cudaStream_t st);
+// default CTA size of a store's projection
+int phase1_default_threads(Store s);
 
 // Source-vector operand from an FP64 vector: src_perm != nullptr gathers
 // x[src_perm[p]] (original order in), otherwise x is already in cluster order.

@@ -347,9 +347,12 @@ template <Store S> __device__ __forceinline__ typename Tr<S>::Part red_to_part(t
 // than 128 threads, and small CTAs let more clusters stream at once), else 256
 template <Store S> constexpr int p1_threads() { return S == Store::BF16 ? 128 : 256; }
 // resident CTAs per SM the register budget is held to: 64 registers a thread
-// (BF16, FP32), 48 for the others
-template <Store S> constexpr int p1_min_blocks() {
-    return S == Store::BF16 ? 8 : S == Store::F32 ? 4 : 5;
+// (BF16, FP32), 51 for the others (8 CTAs of 128 threads for BF16, 4 or 5 of 256
+// for the others; the tuned CTA sizes keep the same budget per thread)
+template <Store S, int NT> constexpr int p1_min_blocks() {
+    return (65536 / (NT * (S == Store::BF16 || S == Store::F32 ? 64 : 51))) < 32
+               ? 65536 / (NT * (S == Store::BF16 || S == Store::F32 ? 64 : 51))
+               : 32;
 }
 constexpr int kP1SmemRuns = 256;  // runs of a cluster staged in shared memory (4 KB)
 constexpr int kP1SmemXd = 64;     // dense-operand slices staged in shared memory
@@ -441,7 +444,8 @@ __device__ __forceinline__ void p1_cluster(const P1Desc &d, const typename Tr<S>
 }
 
 template <Store S, int NT = p1_threads<S>()>
-__global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc *__restrict__ desc, const P1Run *__restrict__ runs,
+__global__ void __launch_bounds__(NT, (p1_min_blocks<S, NT>())) k_phase1(int base, const P1Desc *__restrict__ desc,
+                                                        const P1Run *__restrict__ runs,
                                                         const XDst *__restrict__ xdst, const int32_t *__restrict__ xsel,
                                                         const LrDesc *__restrict__ lr,
                                                         const int32_t *__restrict__ gdst, const void *__restrict__ q1,
@@ -457,7 +461,7 @@ __global__ void __launch_bounds__(NT, p1_min_blocks<S>()) k_phase1(const P1Desc 
     __shared__ P1Run rs[kP1SmemRuns];
     __shared__ XDst xds[kP1SmemXd];
     if (skip_product(S_, mode)) return;
-    const P1Desc d = desc[blockIdx.x];
+    const P1Desc d = desc[base + blockIdx.x];
     if (item_idle(sys, d.pad[0])) return;  // (pad[0]: the item's problem)
     const bool runs_sm = d.rcnt <= kP1SmemRuns, xd_sm = d.xdcnt <= kP1SmemXd;
     for (int j = threadIdx.x; j < d.xlen; j += NT) {
@@ -822,13 +826,36 @@ int grid_for(int64_t n, int threads, int cap) {
 }
 
 // launches of one store's product kernels (the dispatchers pick the store)
+template <Store SS, int NT>
+void phase1_run(const P1Desc *list, int base, int count, const DevIndex &ix, const DevPanels &P,
+                const SolverScalars *skipS, int mode, cudaStream_t st, const SysScalars *sys) {
+    k_phase1<SS, NT><<<count, NT, 0, st>>>(base, list, ix.p1_runs, ix.xdst, ix.xsel, ix.lr, ix.gdst, P.q1,
+                                           (const typename Tr<SS>::Op *)P.xs, (typename Tr<SS>::Part *)P.part,
+                                           (typename Tr<SS>::Op *)P.g, ix.tscale, skipS, mode, sys);
+}
+
+// The projection: one launch per run of the work list (one run over the
+// clusters in order by default; the tuned plan's runs over the list sorted by
+// panel width, each with its CTA size).  The paper's variants keep one CTA size.
 template <Store SS>
 void phase1_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st,
                    const SysScalars *sys) {
-    k_phase1<SS><<<ix.nleaves, p1_threads<SS>(), 0, st>>>(ix.p1, ix.p1_runs, ix.xdst, ix.xsel, ix.lr, ix.gdst, P.q1,
-                                                          (const typename Tr<SS>::Op *)P.xs,
-                                                          (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g,
-                                                          ix.tscale, skipS, mode, sys);
+    if constexpr (is_table1(SS)) {
+        phase1_run<SS, p1_threads<SS>()>(ix.p1, 0, ix.nleaves, ix, P, skipS, mode, st, sys);
+    } else {
+        if (ix.nruns == 0) {
+            phase1_run<SS, p1_threads<SS>()>(ix.p1, 0, ix.nleaves, ix, P, skipS, mode, st, sys);
+            return;
+        }
+        const P1Desc *list = ix.p1_sorted ? ix.p1_sorted : ix.p1;
+        for (int r = 0; r < ix.nruns; ++r) {
+            const P1Plan &u = ix.runs[r];
+            if (u.count <= 0) continue;
+            if (u.nt == 64) phase1_run<SS, 64>(list, u.begin, u.count, ix, P, skipS, mode, st, sys);
+            else if (u.nt == 128) phase1_run<SS, 128>(list, u.begin, u.count, ix, P, skipS, mode, st, sys);
+            else phase1_run<SS, 256>(list, u.begin, u.count, ix, P, skipS, mode, st, sys);
+        }
+    }
 }
 
 template <Store SS>

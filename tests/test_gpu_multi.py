@@ -157,3 +157,34 @@ def test_tensor_core_product_parity(hcache, oracle_mod, mesh, nrhs):
         assert torch.equal(Y2, Yd)
     finally:
         P.hmat_destroy(h)
+
+
+@pytest.mark.parametrize("form", ["bf16", "fp32", "fp64"])
+def test_autotune_keeps_the_bits(hcache, form):
+    """hmat_autotune changes only how the projection is launched (CTA size per
+    panel-width bucket, the work list sorted by bucket): the products, single and
+    batched, give the same bits before and after, and the solves still converge."""
+    torch = need_gpu()
+    P = lib()
+    meshes = [synth.icosphere(4), synth.icosphere(3), synth.two_spheres(3)]
+    blobs = [oracle_blob(hcache(m)) for m in meshes]
+    for h in (P.hmat_upload(blobs[0], form), P.hmat_upload_batch(blobs, form)):
+        try:
+            n = sum(m.n for m in meshes) if len(P.hmat_problems(h)) > 2 else meshes[0].n
+            x = torch.from_numpy(np.random.default_rng(3).standard_normal(n)).cuda()
+            y0, y1 = torch.empty_like(x), torch.empty_like(x)
+            P.hmat_matvec(h, x, y0)
+            rep = P.hmat_autotune(h, reps=5)
+            assert len(rep["buckets"]) == 5 and rep["default_us"] > 0 and rep["tuned_us"] > 0
+            assert sum(b["clusters"] for b in rep["buckets"]) == P.hmat_info(h)["nleaves"]
+            assert all(b["threads"] in (64, 128, 256) for b in rep["buckets"])
+            P.hmat_matvec(h, x, y1)
+            torch.cuda.synchronize()
+            assert torch.equal(y0, y1)
+            b = torch.ones_like(x)
+            xs = torch.zeros_like(x)
+            opts = {"bf16": {"inner_tol": 1e-2}, "fp32": {"inner_tol": 1e-4}}.get(form, {})
+            infos = P.hmat_bicgstab_multi(h, b, xs, 1, tol=1e-8, **opts)
+            assert all(i["status"] == 0 and i["relres_true"] <= 1e-8 for i in infos)
+        finally:
+            P.hmat_destroy(h)
