@@ -55,11 +55,14 @@ struct DevPanels {
 };
 
 // The expansion runs as persistent warps over groups of up to four rows of one
-// leaf row cluster (k_phase2g), kP2gBlocks CTAs per SM.  Measured at L6 against
-// the launch shapes it replaced (BF16 expansion): 51.0 us for row groups, 57.7
-// for row-persistent warps, 61.7 for one CTA per leaf row cluster, 100.5 for a
-// bulk-copy pipeline through shared memory.
-constexpr int kP2gBlocks = 4;
+// leaf row cluster (k_phase2g), kP2gBlocks CTAs per SM, each lane with two
+// vectors of each row in flight.  Measured at L6 against the launch shapes it
+// replaced (BF16 expansion): 51.0 us for row groups, 57.7 for row-persistent
+// warps, 61.7 for one CTA per leaf row cluster, 100.5 for a bulk-copy pipeline
+// through shared memory; two vectors in flight at 3 CTAs per SM against one at
+// 4: FP64 pairs 117.0 against 124.2 us, FP32 60.5 against 63.5, BF16 38.9
+// against 39.2.
+constexpr int kP2gBlocks = 3;
 // Work items (CTAs) of the expansion; a solver expansion leaves one pair of
 // inner-product shares per item in dpart.
 inline int phase2_items(const DevIndex &ix) { return ix.nsm * kP2gBlocks; }

@@ -766,7 +766,38 @@ __global__ void __launch_bounds__(kP2Threads, kP2gBlocks) k_phase2g(
 #pragma unroll
         for (int r = 0; r < GR; ++r) acc[r].init();
         int nf = 0;  // vectors since the rows' last fold (the rows advance in step)
-        for (int v = lane; v < nv; v += 32) {
+        int v = lane;
+        // two vectors per row in flight (v and v + 32), used in order: the same sums
+        for (; v + 32 < nv; v += 64) {
+            int4 raw[GR], raw2[GR];
+#pragma unroll
+            for (int r = 0; r < GR; ++r) {
+                raw[r] = r < nr ? ld_stream(base + (size_t)r * row_bytes + (size_t)v * 16) : make_int4(0, 0, 0, 0);
+                raw2[r] = r < nr ? ld_stream(base + (size_t)r * row_bytes + (size_t)(v + 32) * 16) : make_int4(0, 0, 0, 0);
+            }
+            const GV<S> gv = GV<S>::load(gr + v * VW), gv2 = GV<S>::load(gr + (v + 32) * VW);
+#pragma unroll
+            for (int r = 0; r < GR; ++r)
+                if (r < nr) row_mac_nofold<S>(acc[r], raw[r], gv);
+            if constexpr (row_folds<S>()) {
+                if (++nf == kFoldVecs) {
+#pragma unroll
+                    for (int r = 0; r < GR; ++r) fold<S>(acc[r]);
+                    nf = 0;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < GR; ++r)
+                if (r < nr) row_mac_nofold<S>(acc[r], raw2[r], gv2);
+            if constexpr (row_folds<S>()) {
+                if (++nf == kFoldVecs) {
+#pragma unroll
+                    for (int r = 0; r < GR; ++r) fold<S>(acc[r]);
+                    nf = 0;
+                }
+            }
+        }
+        for (; v < nv; v += 32) {
             int4 raw[GR];
 #pragma unroll
             for (int r = 0; r < GR; ++r)
