@@ -93,9 +93,8 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
     ix.max_leaf = L.max_leaf;
     ix.max_ld2 = L.max_ld2;
     ix.perm = h->perm;
-    int32_t *gdst = nullptr, *red_big = nullptr, *red_tasks = nullptr;
+    int32_t *gdst = nullptr, *red_big = nullptr, *red_tasks = nullptr, *tofs = nullptr;
     P1Desc *p1 = nullptr;
-    P1Run *p1_runs = nullptr;
     XDst *xdst = nullptr;
     int32_t *xsel = nullptr;
     LrDesc *lr = nullptr;
@@ -113,7 +112,6 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
     };
     for (size_t k = 0; k < p1h.size(); ++k) {
         p1h[k].pad[0] = prob_of(p1h[k].xbeg);
-        p1h[k].pad[1] = 0;
         for (int r = 0; r < p1h[k].rcnt; ++r) lrh[L.p1_runs[p1h[k].rbeg + r].q].pad = p1h[k].pad[0];
     }
     for (GroupDesc &gd : grh) {
@@ -121,11 +119,11 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
         gd.pad[1] = 0;
     }
     if ((st = h->upload(&p1, p1h.data(), sizeof(P1Desc) * p1h.size())) ||
-        (st = h->upload(&p1_runs, L.p1_runs.data(), sizeof(P1Run) * L.p1_runs.size())) ||
         (st = h->upload(&xdst, L.xdst.data(), sizeof(XDst) * L.xdst.size())) ||
         (st = h->upload(&xsel, L.xsel.data(), 4 * L.xsel.size())) ||
         (st = h->upload(&lr, lrh.data(), sizeof(LrDesc) * lrh.size())) ||
         (st = h->upload(&gdst, L.gdst.data(), 4 * L.gdst.size())) ||
+        (st = h->upload(&tofs, L.tofs.data(), 4 * L.tofs.size())) ||
         (st = h->upload(&red_big, L.red_big.data(), 4 * L.red_big.size())) ||
         (st = h->upload(&red_tasks, L.red_tasks.data(), 4 * L.red_tasks.size())) ||
         (st = h->upload(&p2, L.p2.data(), sizeof(P2Desc) * L.p2.size())) ||
@@ -133,7 +131,7 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
         (st = h->upload(&groups, grh.data(), sizeof(GroupDesc) * grh.size()))) {
         return st;
     }
-    ix.p1 = p1; ix.p1_runs = p1_runs; ix.xdst = xdst; ix.xsel = xsel; ix.lr = lr; ix.gdst = gdst; ix.p2 = p2;
+    ix.p1 = p1; ix.tofs = tofs; ix.xdst = xdst; ix.xsel = xsel; ix.lr = lr; ix.gdst = gdst; ix.p2 = p2;
     ix.red_big = red_big; ix.red_tasks = red_tasks;
     ix.tscale = L.tscale.empty() ? nullptr : tscale;
     ix.groups = groups;
@@ -143,7 +141,7 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
     ix.nsm = std::max(1, nsm);
     g.partials_n = L.npart;
     g.glen = L.glen;
-    h->index_bytes += (int64_t)(sizeof(P1Desc) * L.p1.size() + sizeof(P1Run) * L.p1_runs.size() +
+    h->index_bytes += (int64_t)(sizeof(P1Desc) * L.p1.size() + 4 * L.tofs.size() +
                                 sizeof(XDst) * L.xdst.size() + 4 * L.xsel.size() + sizeof(LrDesc) * L.lr.size() +
                                 4 * L.gdst.size() +
                                 sizeof(P2Desc) * L.p2.size() + 4 * (L.red_big.size() + L.red_tasks.size()) +

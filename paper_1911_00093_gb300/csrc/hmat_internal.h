@@ -81,11 +81,14 @@ int parse_blob(const void *blob, size_t bytes, BlobView &view, std::string *why 
 // Phase 1, one work item per leaf column cluster kappa: a row-major |kappa| x R
 // panel whose columns are the rank vectors of every W_m (eq. 9/22) whose column
 // cluster contains kappa, restricted to kappa.  Its R dot products with x_kappa
-// are either final (the block's column cluster is kappa) or block-major partial
-// sums that a reduction launch adds up in a fixed order.  Phase 1 and the
-// reduction write every operand phase 2 needs into per-row-cluster operand
-// buffers g: the slices 2^e x_kappa of the dense blocks over kappa, and each
-// block's 2^e t = 2^e W_m x_m for every leaf row cluster of the block.
+// (the contributions t_{m,kappa} = W_m|kappa x_kappa of its blocks, in panel
+// column order) are stored contiguously in the projection output T at tbeg.  A
+// reduction launch then forms every block's t_m = sum over the leaf clusters
+// kappa of its column cluster of t_{m,kappa}, in cluster order (one term when the
+// column cluster is a leaf).  Phase 1 and the reduction write every operand
+// phase 2 needs into per-row-cluster operand buffers g: the slices 2^e x_kappa
+// of the dense blocks over kappa (phase 1), and each block's 2^e t for every leaf
+// row cluster of the block (the reduction).
 //
 // Phase 2, one work item per leaf row cluster rho: a row-major |rho| x K panel
 // holding the rows over rho of every dense block (eq. 21) and of every V_m
@@ -100,16 +103,17 @@ struct P1Desc {
     int32_t xlen;   // rows of kappa
     int32_t xdbeg;  // first XDst (dense-block operand slices fed from x_kappa)
     int32_t xdcnt;
-    int32_t pad[2];  // on the device: pad[0] = the item's problem (batch handles)
+    int32_t tbeg;    // first entry of the cluster's projection output in T (ld entries)
+    int32_t pad[1];  // on the device: pad[0] = the item's problem (batch handles)
 };
-struct P1Run {
+struct P1Run {      // one low-rank block of a phase-1 panel (host side)
     int32_t col0;   // first panel column of the block
     int32_t len;    // rank r
     int32_t q;      // low-rank block index (LrDesc)
-    int32_t poff;   // first partial of this kappa's row of the block, or -1 when final
+    int32_t pad;
 };
 struct LrDesc {
-    int32_t boff;   // first partial (block-major: cnt rows of rank values), -1 if single cluster
+    int32_t boff;   // first of its cnt entries of tofs: where t_{m,kappa} starts in T, kappa in cluster order
     int32_t cnt;    // leaf clusters inside the column cluster
     int32_t rank;
     int32_t scale;  // exponent e of 2^e t
@@ -171,10 +175,11 @@ struct Layout {
     std::vector<int32_t> gdst;
     std::vector<P2Desc> p2;
     int64_t p1_elems = 0, p2_elems = 0;
-    int64_t npart = 0, glen = 0;
+    int64_t npart = 0, glen = 0;     // entries of T (the phase-1 panels' ld summed) and of g
+    std::vector<int32_t> tofs;       // LrDesc::boff: T offsets of each block's per-cluster projections
     std::vector<double> tscale;      // per-rank factors referenced by LrDesc::toff
     std::vector<int32_t> red_big;    // multi-cluster blocks over >= kRedBigCnt clusters (a CTA each)
-    std::vector<int32_t> red_tasks;  // (block << 6) | rank of the other multi-cluster blocks (a lane each)
+    std::vector<int32_t> red_tasks;  // (block << 6) | rank of the other low-rank blocks (a lane each)
     int32_t max_ld2 = 0, max_ld1 = 0, max_runs1 = 0, max_leaf = 0;
     int64_t stored_entries = 0, phase1_entries = 0, phase2_entries = 0, rank_sum = 0;
     // source of each packed entry, used to fill typed panels without

@@ -20,7 +20,7 @@ struct DevIndex {
     int32_t n = 0, nleaves = 0, nlr = 0, nbig = 0, ntasks = 0;
     const int32_t *perm = nullptr;  // [n]
     const P1Desc *p1 = nullptr;     // [nleaves]
-    const P1Run *p1_runs = nullptr;
+    const int32_t *tofs = nullptr;  // LrDesc::boff: T offsets of each block's per-cluster projections
     const XDst *xdst = nullptr;
     const int32_t *xsel = nullptr;  // local indices of the column-subset operand slices
     const LrDesc *lr = nullptr;     // [nlr]

@@ -330,7 +330,7 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
     // low-rank descriptors: operand destinations in every leaf row cluster of the block
     std::vector<int64_t> kfirst(nb, 0), kcnt(nb, 0);
     L.lr.resize(nlr);
-    int64_t npart = 0;
+    int64_t ntofs = 0;
     for (int64_t q = 0; q < nlr; ++q) {
         const int64_t b = lr_blocks[q];
         const int64_t *e = v.blocks + 8 * b;
@@ -340,17 +340,14 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
         d.rank = (int32_t)e[5];
         d.cnt = (int32_t)kcnt[b];
         d.scale = eU[b] + eV[b];
-        if (kcnt[b] > 1) {
-            d.boff = (int32_t)npart;
-            npart += kcnt[b] * e[5];
-            if (kcnt[b] >= kRedBigCnt) {
-                L.red_big.push_back((int32_t)q);
-            } else {
-                if (q >= (int64_t(1) << 25) || e[5] > 63) { if (why) *why = "reduction task out of range"; return HMAT_ERR_UNSUPPORTED; }
-                for (int64_t l = 0; l < e[5]; ++l) L.red_tasks.push_back((int32_t)((q << 6) | l));
-            }
+        d.boff = (int32_t)ntofs;  // filled with the phase-1 panels below
+        ntofs += kcnt[b];
+        if (ntofs > (int64_t(1) << 31) - 16) { if (why) *why = "too many projection terms"; return HMAT_ERR_UNSUPPORTED; }
+        if (kcnt[b] >= kRedBigCnt) {
+            L.red_big.push_back((int32_t)q);
         } else {
-            d.boff = -1;
+            if (q >= (int64_t(1) << 25) || e[5] > 63) { if (why) *why = "reduction task out of range"; return HMAT_ERR_UNSUPPORTED; }
+            for (int64_t l = 0; l < e[5]; ++l) L.red_tasks.push_back((int32_t)((q << 6) | l));
         }
         d.gbeg = (int32_t)L.gdst.size();
         for (int64_t rho = leaf_index(e[0]); rho < leaf_index(e[1]); ++rho) {
@@ -367,8 +364,7 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
             L.tscale.insert(L.tscale.end(), v.tval + v.toff[b], v.tval + v.toff[b] + e[5]);
         }
     }
-    if (npart > (int64_t(1) << 31) - 16) { if (why) *why = "too many partials"; return HMAT_ERR_UNSUPPORTED; }
-    L.npart = npart;
+    L.tofs.assign((size_t)ntofs, -1);
 
     // phase 1: low-rank blocks per leaf column cluster (block order), and the
     // dense-block operand slices each leaf column cluster feeds
@@ -385,6 +381,7 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
     L.p1.resize(nleaves);
     L.p1_slice_ptr.assign(nleaves + 1, 0);
     off = 0;
+    int64_t tbeg = 0;
     for (int64_t k = 0; k < nleaves; ++k) {
         P1Desc &d = L.p1[k];
         d.xbeg = (int32_t)v.leaf_begin[k];
@@ -399,7 +396,8 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
             run.col0 = (int32_t)col;
             run.len = (int32_t)r;
             run.q = lrq[b];
-            run.poff = ld.boff >= 0 ? (int32_t)(ld.boff + (k - kfirst[b]) * r) : -1;
+            run.pad = 0;
+            L.tofs[ld.boff + (k - kfirst[b])] = (int32_t)(tbeg + col);
             L.p1_runs.push_back(run);
             L.p1_slices.push_back({b, (int32_t)col, (int32_t)r, (int32_t)(d.xbeg - e[2]), 1, eV[b]});
             col += r;
@@ -409,6 +407,9 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
         d.ld = (int32_t)roundup(std::max<int64_t>(col, 1), kPadElems);
         d.off = off;
         off += (int64_t)d.ld * d.xlen;
+        d.tbeg = (int32_t)tbeg;
+        tbeg += d.ld;
+        if (tbeg > (int64_t(1) << 31) - 16) { if (why) *why = "too many projections"; return HMAT_ERR_UNSUPPORTED; }
         d.xdbeg = (int32_t)L.xdst.size();
         for (int64_t b : dense_by_col[k]) {
             const int64_t *e = v.blocks + 8 * b;
@@ -431,13 +432,14 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
             }
         }
         d.xdcnt = (int32_t)L.xdst.size() - d.xdbeg;
-        d.pad[0] = d.pad[1] = 0;
+        d.pad[0] = 0;
         L.phase1_entries += col * d.xlen;
         L.max_ld1 = std::max(L.max_ld1, d.ld);
         L.max_runs1 = std::max(L.max_runs1, d.rcnt);
         L.p1_slice_ptr[k + 1] = (int64_t)L.p1_slices.size();
     }
     L.p1_elems = off;
+    L.npart = tbeg;
     return HMAT_OK;
 }
 
@@ -456,8 +458,9 @@ int check_layout(const Layout &L, std::string *why) {
     }
     for (const LrDesc &d : L.lr) {
         if (d.rank < 1 || d.cnt < 1 || std::abs(d.scale) > kMaxScaleExp) return bad("lr desc");
-        if (d.cnt > 1 ? (d.boff < 0 || (int64_t)d.boff + (int64_t)d.cnt * d.rank > L.npart) : d.boff != -1)
-            return bad("lr partials");
+        if (d.boff < 0 || (int64_t)d.boff + d.cnt > (int64_t)L.tofs.size()) return bad("lr projections");
+        for (int k = 0; k < d.cnt; ++k)
+            if (L.tofs[d.boff + k] < 0 || (int64_t)L.tofs[d.boff + k] + d.rank > L.npart) return bad("lr projection range");
         if (d.gbeg < 0 || d.gcnt < 1 || (int64_t)d.gbeg + d.gcnt > (int64_t)L.gdst.size()) return bad("lr dst");
         if (d.toff < -1 || (d.toff >= 0 && (int64_t)d.toff + d.rank > (int64_t)L.tscale.size())) return bad("lr factors");
         for (int k = 0; k < d.gcnt; ++k) {
@@ -473,6 +476,7 @@ int check_layout(const Layout &L, std::string *why) {
         if (d.xlen < 1 || d.xlen > kMaxLeaf || d.xbeg < 0 || (int64_t)d.xbeg + d.xlen > L.n) return bad("p1 rows");
         if (d.R < 0 || d.ld < d.R || d.ld % kPadElems || d.off % kPadElems) return bad("p1 stride");
         if (d.off < 0 || d.off + (int64_t)d.xlen * d.ld > L.p1_elems) return bad("p1 extent");
+        if (d.tbeg < 0 || d.tbeg % kPadElems || (int64_t)d.tbeg + d.ld > L.npart) return bad("p1 projection output");
         if (d.rbeg < 0 || d.rcnt < 0 || (int64_t)d.rbeg + d.rcnt > (int64_t)L.p1_runs.size()) return bad("p1 runs");
         if (d.R > 0 && d.rcnt < 1) return bad("p1 empty runs");
         int64_t at = 0;
@@ -481,9 +485,9 @@ int check_layout(const Layout &L, std::string *why) {
             if (u.col0 != at || u.len < 1 || u.q < 0 || u.q >= (int32_t)L.lr.size()) return bad("p1 runs do not tile");
             const LrDesc &ld = L.lr[u.q];
             if (u.len != ld.rank) return bad("p1 run rank");
-            if (ld.cnt > 1 ? (u.poff < ld.boff || (int64_t)u.poff + u.len > (int64_t)ld.boff + (int64_t)ld.cnt * ld.rank)
-                           : u.poff != -1)
-                return bad("p1 run partial");
+            bool listed = false;  // the block finds this cluster's projection where it is written
+            for (int k = 0; k < ld.cnt && !listed; ++k) listed = L.tofs[ld.boff + k] == d.tbeg + u.col0;
+            if (!listed) return bad("p1 run projection");
             at += u.len;
         }
         if (at != d.R) return bad("p1 runs do not cover R");
@@ -507,13 +511,13 @@ int check_layout(const Layout &L, std::string *why) {
         if (!gw[k]) return bad("operand slot never written");
     size_t multi = 0, multi_ranks = 0;
     for (const LrDesc &d : L.lr)
-        if (d.cnt > 1 && d.cnt < kRedBigCnt) multi_ranks += d.rank;
+        if (d.cnt < kRedBigCnt) multi_ranks += d.rank;
         else if (d.cnt >= kRedBigCnt) ++multi;
     if (multi != L.red_big.size() || multi_ranks != L.red_tasks.size()) return bad("reduction lists");
     for (int32_t q : L.red_big) if (q < 0 || q >= (int32_t)L.lr.size() || L.lr[q].cnt < kRedBigCnt) return bad("red big");
     for (int32_t t : L.red_tasks) {
         const int32_t q = t >> 6, l = t & 63;
-        if (q < 0 || q >= (int32_t)L.lr.size() || L.lr[q].cnt < 2 || L.lr[q].cnt >= kRedBigCnt || l >= L.lr[q].rank)
+        if (q < 0 || q >= (int32_t)L.lr.size() || L.lr[q].cnt >= kRedBigCnt || l >= L.lr[q].rank)
             return bad("red task");
     }
     if ((int64_t)L.rows.size() != L.n) return bad("rows size");

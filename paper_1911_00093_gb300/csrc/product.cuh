@@ -354,24 +354,22 @@ template <Store S, int NT> constexpr int p1_min_blocks() {
                ? 65536 / (NT * (S == Store::BF16 || S == Store::F32 ? 64 : 51))
                : 32;
 }
-constexpr int kP1SmemRuns = 256;  // runs of a cluster staged in shared memory (4 KB)
 constexpr int kP1SmemXd = 64;     // dense-operand slices staged in shared memory
 
-// One leaf column cluster of the projection, its x slice, runs and dense
-// slices already staged in shared memory (rs / xds null: read them from global
-// memory): the column vectors' dot products with x_kappa and their
-// destinations, then the dense-block operand slices.
+// One leaf column cluster of the projection, its x slice and dense slices
+// already staged in shared memory (xds null: read them from global memory):
+// the column vectors' dot products with x_kappa, stored in panel column order
+// at T + d.tbeg (each thread its VW consecutive sums: 16 or 32 contiguous bytes,
+// a warp 512 or 1024), then the dense-block operand slices.
 template <Store S, int NT>
-__device__ __forceinline__ void p1_cluster(const P1Desc &d, const typename Tr<S>::Op *xk, const P1Run *rs,
-                                           const XDst *xds, const P1Run *__restrict__ runs,
+__device__ __forceinline__ void p1_cluster(const P1Desc &d, const typename Tr<S>::Op *xk, const XDst *xds,
                                            const XDst *__restrict__ xdst, const int32_t *__restrict__ xsel,
-                                           const LrDesc *__restrict__ lr, const int32_t *__restrict__ gdst,
                                            const void *__restrict__ q1, typename Tr<S>::Part *__restrict__ part,
-                                           typename Tr<S>::Op *__restrict__ g, const double *__restrict__ tscale) {
-    using Op = typename Tr<S>::Op;
+                                           typename Tr<S>::Op *__restrict__ g) {
     using Part = typename Tr<S>::Part;
     constexpr int VW = Tr<S>::VW;
-    const int nvec = d.ld / VW, xlen = d.xlen, R = d.R, rcnt = d.rcnt;
+    static_assert(sizeof(Part) * VW % 16 == 0, "a thread's sums are whole 16-byte vectors");
+    const int nvec = d.ld / VW, xlen = d.xlen;
     const char *base = (const char *)q1 + (size_t)d.off * (16 / VW);
     const size_t row_bytes = (size_t)d.ld * (16 / VW);
 
@@ -405,32 +403,16 @@ __device__ __forceinline__ void p1_cluster(const P1Desc &d, const typename Tr<S>
                 Cols<S>::mac(acc, raw[u], xk[j + u]);
             }
         }
-        const int c0 = vc * VW;
-        if (c0 >= R) continue;
-        const P1Run *rk = rs ? rs : runs + d.rbeg;  // generic pointer: shared or global
-        int lo = 0, hi = rcnt - 1;  // run holding column c0
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (rk[mid].col0 <= c0) lo = mid;
-            else hi = mid - 1;
-        }
-        P1Run rn = rk[lo];
+        // t_{m,kappa} of the vector's VW columns (zero past R: the panel's padding)
+        Part out[VW];
 #pragma unroll
-        for (int e = 0; e < VW; ++e) {
-            const int c = c0 + e;
-            if (c < R) {
-                while (c >= rn.col0 + rn.len) rn = rk[++lo];
-                const int l = c - rn.col0;
-                const Part pv = to_part<S>(acc[e]);
-                if (rn.poff >= 0) {
-                    part[rn.poff + l] = pv;
-                } else {  // final: 2^e t to every leaf row cluster of the block
-                    const LrDesc ld = lr[rn.q];
-                    const Op o = apply_d<S>(part_to_op<S>(pv, ld.scale), ld, l, tscale);
-                    for (int k = 0; k < ld.gcnt; ++k) g[gdst[ld.gbeg + k] + l] = o;
-                }
-            }
-        }
+        for (int e = 0; e < VW; ++e) out[e] = to_part<S>(acc[e]);
+        uint32_t w[sizeof(out) / 4];
+        memcpy(w, out, sizeof(out));
+        int4 *dst = reinterpret_cast<int4 *>(part + d.tbeg + (size_t)vc * VW);
+#pragma unroll
+        for (int u = 0; u < (int)(sizeof(out) / 16); ++u)
+            dst[u] = make_int4((int)w[4 * u], (int)w[4 * u + 1], (int)w[4 * u + 2], (int)w[4 * u + 3]);
     }
 
     // the dense-block operands fed by x_kappa (eq. 21 inputs), scaled by 2^e: a
@@ -445,43 +427,38 @@ __device__ __forceinline__ void p1_cluster(const P1Desc &d, const typename Tr<S>
 
 template <Store S, int NT = p1_threads<S>()>
 __global__ void __launch_bounds__(NT, (p1_min_blocks<S, NT>())) k_phase1(int base, const P1Desc *__restrict__ desc,
-                                                        const P1Run *__restrict__ runs,
                                                         const XDst *__restrict__ xdst, const int32_t *__restrict__ xsel,
-                                                        const LrDesc *__restrict__ lr,
-                                                        const int32_t *__restrict__ gdst, const void *__restrict__ q1,
+                                                        const void *__restrict__ q1,
                                                         const typename Tr<S>::Op *__restrict__ xs,
                                                         typename Tr<S>::Part *__restrict__ part,
-                                                        typename Tr<S>::Op *__restrict__ g,
-                                                        const double *__restrict__ tscale, const SolverScalars *S_,
+                                                        typename Tr<S>::Op *__restrict__ g, const SolverScalars *S_,
                                                         int mode, const SysScalars *sys) {
     using Op = typename Tr<S>::Op;
     __shared__ Op xk[kMaxLeaf];  // x_kappa, broadcast to every thread
-    // the cluster's run and dense-operand descriptors, loaded with x_kappa so
-    // that the epilogue's lookups stay on chip (global reads past the limits)
-    __shared__ P1Run rs[kP1SmemRuns];
+    // the cluster's dense-operand descriptors, loaded with x_kappa so that the
+    // slice loop's lookups stay on chip (global reads past the limit)
     __shared__ XDst xds[kP1SmemXd];
     if (skip_product(S_, mode)) return;
     const P1Desc d = desc[base + blockIdx.x];
     if (item_idle(sys, d.pad[0])) return;  // (pad[0]: the item's problem)
-    const bool runs_sm = d.rcnt <= kP1SmemRuns, xd_sm = d.xdcnt <= kP1SmemXd;
+    const bool xd_sm = d.xdcnt <= kP1SmemXd;
     for (int j = threadIdx.x; j < d.xlen; j += NT) {
         if constexpr (fp32_source(S)) xk[j] = (double)__double2float_rn(xs[d.xbeg + j]);  // Section 3.5
         else xk[j] = xs[d.xbeg + j];
     }
-    if (runs_sm)
-        for (int j = threadIdx.x; j < d.rcnt; j += NT) rs[j] = runs[d.rbeg + j];
     if (xd_sm)
         for (int j = threadIdx.x; j < d.xdcnt; j += NT) xds[j] = xdst[d.xdbeg + j];
     __syncthreads();
-    p1_cluster<S, NT>(d, xk, runs_sm ? rs : nullptr, xd_sm ? xds : nullptr, runs, xdst, xsel, lr, gdst, q1, part, g,
-                      tscale);
+    p1_cluster<S, NT>(d, xk, xd_sm ? xds : nullptr, xdst, xsel, q1, part, g);
 }
 
 // ------------------------------------------------------------------------
-// reduce: t of the blocks spanning several leaf clusters, in a fixed order,
-// scattered to the operand buffers.  Blocks over >= kRedBigCnt clusters get a
-// whole CTA (kernel blocks [0, nbig)); the others are split into one task per
-// rank, one lane each.
+// reduce: every block's t_m = sum of its per-cluster projections
+// t_{m,kappa} (eq. 9), in a fixed order, scaled by 2^e (and d_l, eq. 23) and
+// scattered to the operand buffers of its leaf row clusters.  Blocks over
+// >= kRedBigCnt leaf clusters get a whole CTA (kernel blocks [0, nbig)); the
+// others are split into one task per rank, one lane each (one term and no sum
+// when the column cluster is a leaf).
 // ------------------------------------------------------------------------
 constexpr int kRedThreads = 256;
 
@@ -489,6 +466,7 @@ template <Store S>
 __global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int ntasks, const int32_t *__restrict__ big,
                                                          const int32_t *__restrict__ tasks,
                                                          const LrDesc *__restrict__ lr, const int32_t *__restrict__ gdst,
+                                                         const int32_t *__restrict__ tofs,
                                                          const typename Tr<S>::Part *__restrict__ part,
                                                          typename Tr<S>::Op *__restrict__ g,
                                                          const double *__restrict__ tscale, const SolverScalars *S_,
@@ -508,9 +486,10 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int ntasks, co
             RT a;
             red_zero<S>(a);
             if (l < rr) {
-                const typename Tr<S>::Part *src = part + ld.boff + l0 + l;
+                const typename Tr<S>::Part *src = part + l0 + l;
+                const int32_t *to = tofs + ld.boff;
 #pragma unroll 4
-                for (int k = gi; k < ld.cnt; k += G) red_add_part<S>(a, src[(size_t)k * ld.rank]);
+                for (int k = gi; k < ld.cnt; k += G) red_add_part<S>(a, src[__ldg(to + k)]);
             }
             red[threadIdx.x] = a;
             __syncthreads();
@@ -540,12 +519,19 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int ntasks, co
     const LrDesc ld = lr[tq >> 6];
     if (item_idle(sys, ld.pad)) return;
     const int l = tq & 63;
-    const typename Tr<S>::Part *src = part + ld.boff + l;
-    RT a;
-    red_zero<S>(a);
+    const typename Tr<S>::Part *src = part + l;
+    const int32_t *to = tofs + ld.boff;
+    typename Tr<S>::Part t;
+    if (ld.cnt == 1) {  // the column cluster is a leaf: t_m is its one projection
+        t = src[__ldg(to)];
+    } else {
+        RT a;
+        red_zero<S>(a);
 #pragma unroll 4
-    for (int k = 0; k < ld.cnt; ++k) red_add_part<S>(a, src[(size_t)k * ld.rank]);
-    const Op o = apply_d<S>(part_to_op<S>(red_to_part<S>(a), ld.scale), ld, l, tscale);
+        for (int k = 0; k < ld.cnt; ++k) red_add_part<S>(a, src[__ldg(to + k)]);
+        t = red_to_part<S>(a);
+    }
+    const Op o = apply_d<S>(part_to_op<S>(t, ld.scale), ld, l, tscale);
     for (int k = 0; k < ld.gcnt; ++k) g[gdst[ld.gbeg + k] + l] = o;
 }
 
@@ -860,9 +846,9 @@ int grid_for(int64_t n, int threads, int cap) {
 template <Store SS, int NT>
 void phase1_run(const P1Desc *list, int base, int count, const DevIndex &ix, const DevPanels &P,
                 const SolverScalars *skipS, int mode, cudaStream_t st, const SysScalars *sys) {
-    k_phase1<SS, NT><<<count, NT, 0, st>>>(base, list, ix.p1_runs, ix.xdst, ix.xsel, ix.lr, ix.gdst, P.q1,
-                                           (const typename Tr<SS>::Op *)P.xs, (typename Tr<SS>::Part *)P.part,
-                                           (typename Tr<SS>::Op *)P.g, ix.tscale, skipS, mode, sys);
+    k_phase1<SS, NT><<<count, NT, 0, st>>>(base, list, ix.xdst, ix.xsel, P.q1, (const typename Tr<SS>::Op *)P.xs,
+                                           (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g, skipS, mode,
+                                           sys);
 }
 
 // The projection: one launch per run of the work list (one run over the
@@ -895,7 +881,8 @@ void reduce_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *
     const int blocks = ix.nbig + (ix.ntasks + kRedThreads - 1) / kRedThreads;
     if (blocks == 0) return;
     k_reduce<SS><<<blocks, kRedThreads, 0, st>>>(ix.nbig, ix.ntasks, ix.red_big, ix.red_tasks, ix.lr, ix.gdst,
-                                                 (const typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g,
+                                                 ix.tofs, (const typename Tr<SS>::Part *)P.part,
+                                                 (typename Tr<SS>::Op *)P.g,
                                                  ix.tscale, skipS, mode, sys);
 }
 
