@@ -22,7 +22,8 @@ static Store operand_store(Store s) { return is_table1(s) ? Store::F64 : s; }
 
 void launch_prep(Store s, const DevIndex &ix, const double *x, const int32_t *src_perm, void *xs, cudaStream_t st) {
     int blocks = grid_for(ix.n, 256, 4096);
-    HMAT_DISPATCH(operand_store(s), (k_prep<SS><<<blocks, 256, 0, st>>>(ix.n, x, src_perm, (typename Tr<SS>::Op *)xs)));
+    HMAT_DISPATCH(operand_store(s),
+                  launch_pdl(k_prep<SS>, dim3(blocks), dim3(256), st, ix.n, x, src_perm, (typename Tr<SS>::Op *)xs));
 }
 
 void launch_phase1(Store s, const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode,

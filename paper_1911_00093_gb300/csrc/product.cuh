@@ -4,14 +4,15 @@
 //
 // Product (Section 2.1, eq. 5-10 and 21-25), in three launches:
 //   phase 1  one CTA per leaf column cluster kappa (128 threads for BF16 panels,
-//            else 256): t-partials = Q_kappa^T x_kappa, Q_kappa the rows of every
+//            else 256): T_kappa = Q_kappa^T x_kappa, Q_kappa the rows of every
 //            W_m^T (eq. 9/22) whose column cluster contains kappa, row-major; each
 //            thread owns one 16-byte column vector and walks the |kappa| rows
 //            (coalesced 128-bit loads, x from shared memory, no cross-thread
-//            reduction);
-//   reduce   t = 2^e sum_kappa partials of the blocks over several leaf clusters,
-//            in a fixed order: a lane per (block, rank), a CTA per block over 32 or
-//            more clusters (deterministic, no atomics on values);
+//            reduction) and stores its sums as whole vectors, so T_kappa is
+//            written contiguously;
+//   reduce   t = 2^e sum_kappa T_kappa entries of every block, in a fixed order: a
+//            lane per (block, rank), a CTA per block over 32 or more clusters
+//            (deterministic, no atomics on values), scattered to the operands;
 //   phase 2  y_rho = P_rho g_rho with P_rho the rows of the dense blocks (eq. 21)
 //            and of the V_m (eq. 10/24) over rho, g_rho the matching pieces of x
 //            and t; a warp per row, each row of y written once by its owner (eq. 25
@@ -32,6 +33,7 @@
 #include <cmath>
 #include <cstddef>
 #include <cstdint>
+#include <cstring>
 
 #include "hmat.h"
 #include "kernels.h"
@@ -251,6 +253,8 @@ __device__ __forceinline__ bool skip_product(const SolverScalars *S, int mode) {
 template <Store S>
 __global__ void k_prep(int n, const double *__restrict__ x, const int32_t *__restrict__ src_perm,
                        typename Tr<S>::Op *__restrict__ xs) {
+    pdl_trigger();
+    pdl_wait();
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         double v = x[src_perm ? src_perm[p] : p];
         if constexpr (S == Store::DF) xs[p] = split_double(v);
@@ -438,16 +442,17 @@ __global__ void __launch_bounds__(NT, (p1_min_blocks<S, NT>())) k_phase1(int bas
     // the cluster's dense-operand descriptors, loaded with x_kappa so that the
     // slice loop's lookups stay on chip (global reads past the limit)
     __shared__ XDst xds[kP1SmemXd];
-    if (skip_product(S_, mode)) return;
+    pdl_trigger();
     const P1Desc d = desc[base + blockIdx.x];
-    if (item_idle(sys, d.pad[0])) return;  // (pad[0]: the item's problem)
     const bool xd_sm = d.xdcnt <= kP1SmemXd;
+    if (xd_sm)
+        for (int j = threadIdx.x; j < d.xdcnt; j += NT) xds[j] = xdst[d.xdbeg + j];
+    pdl_wait();  // x, the flags and the outputs belong to earlier kernels
+    if (skip_product(S_, mode) || item_idle(sys, d.pad[0])) return;  // (pad[0]: the item's problem)
     for (int j = threadIdx.x; j < d.xlen; j += NT) {
         if constexpr (fp32_source(S)) xk[j] = (double)__double2float_rn(xs[d.xbeg + j]);  // Section 3.5
         else xk[j] = xs[d.xbeg + j];
     }
-    if (xd_sm)
-        for (int j = threadIdx.x; j < d.xdcnt; j += NT) xds[j] = xdst[d.xdbeg + j];
     __syncthreads();
     p1_cluster<S, NT>(d, xk, xd_sm ? xds : nullptr, xdst, xsel, q1, part, g);
 }
@@ -456,11 +461,38 @@ __global__ void __launch_bounds__(NT, (p1_min_blocks<S, NT>())) k_phase1(int bas
 // reduce: every block's t_m = sum of its per-cluster projections
 // t_{m,kappa} (eq. 9), in a fixed order, scaled by 2^e (and d_l, eq. 23) and
 // scattered to the operand buffers of its leaf row clusters.  Blocks over
-// >= kRedBigCnt leaf clusters get a whole CTA (kernel blocks [0, nbig)); the
-// others are split into one task per rank, one lane each (one term and no sum
-// when the column cluster is a leaf).
+// >= kRedBigCnt leaf clusters get a whole CTA (kernel blocks [0, nbig)), their
+// T offsets and destinations staged in shared memory; the others are split into
+// one task per rank, kRedTasks tasks per thread (one term and no sum when the
+// column cluster is a leaf).
 // ------------------------------------------------------------------------
-constexpr int kRedThreads = 256;
+constexpr int kRedThreads = 128;
+constexpr int kRedTasks = 1;     // independent tasks per thread of the small blocks
+constexpr int kRedStage = 256;   // T offsets / destinations of a big block staged on chip
+
+template <Store S>
+__device__ __forceinline__ void reduce_task(int l, const LrDesc &ld, const int32_t *__restrict__ gdst,
+                                            const int32_t *__restrict__ tofs,
+                                            const typename Tr<S>::Part *__restrict__ part,
+                                            typename Tr<S>::Op *__restrict__ g, const double *__restrict__ tscale,
+                                            const SysScalars *sys) {
+    using RT = typename RedT<S>::T;
+    if (item_idle(sys, ld.pad)) return;
+    const typename Tr<S>::Part *src = part + l;
+    const int32_t *to = tofs + ld.boff;
+    typename Tr<S>::Part t;
+    if (ld.cnt == 1) {  // the column cluster is a leaf: t_m is its one projection
+        t = src[__ldg(to)];
+    } else {
+        RT a;
+        red_zero<S>(a);
+#pragma unroll 4
+        for (int k = 0; k < ld.cnt; ++k) red_add_part<S>(a, src[__ldg(to + k)]);
+        t = red_to_part<S>(a);
+    }
+    const typename Tr<S>::Op o = apply_d<S>(part_to_op<S>(t, ld.scale), ld, l, tscale);
+    for (int k = 0; k < ld.gcnt; ++k) g[gdst[ld.gbeg + k] + l] = o;
+}
 
 template <Store S>
 __global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int ntasks, const int32_t *__restrict__ big,
@@ -471,13 +503,22 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int ntasks, co
                                                          typename Tr<S>::Op *__restrict__ g,
                                                          const double *__restrict__ tscale, const SolverScalars *S_,
                                                          int mode, const SysScalars *sys) {
-    using Op = typename Tr<S>::Op;
     using RT = typename RedT<S>::T;
     __shared__ RT red[kRedThreads];
-    if (skip_product(S_, mode)) return;
+    __shared__ int32_t sto[kRedStage], sgd[kRedStage];
+    pdl_trigger();
     if ((int)blockIdx.x < nbig) {
         const LrDesc ld = lr[big[blockIdx.x]];
-        if (item_idle(sys, ld.pad)) return;  // (pad: the block's problem; CTA-uniform)
+        const bool st_to = ld.cnt <= kRedStage, st_gd = ld.gcnt <= kRedStage;
+        if (st_to)
+            for (int k = threadIdx.x; k < ld.cnt; k += kRedThreads) sto[k] = __ldg(tofs + ld.boff + k);
+        if (st_gd)
+            for (int k = threadIdx.x; k < ld.gcnt; k += kRedThreads) sgd[k] = __ldg(gdst + ld.gbeg + k);
+        pdl_wait();  // T, the flags and g belong to earlier kernels
+        if (skip_product(S_, mode) || item_idle(sys, ld.pad)) return;  // (pad: the block's problem; CTA-uniform)
+        __syncthreads();
+        const int32_t *to = st_to ? sto : tofs + ld.boff;  // generic pointers: shared or global
+        const int32_t *gd = st_gd ? sgd : gdst + ld.gbeg;
         for (int l0 = 0; l0 < ld.rank; l0 += 32) {
             const int rr = min(32, ld.rank - l0);
             int rp = 1;
@@ -487,9 +528,8 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int ntasks, co
             red_zero<S>(a);
             if (l < rr) {
                 const typename Tr<S>::Part *src = part + l0 + l;
-                const int32_t *to = tofs + ld.boff;
-#pragma unroll 4
-                for (int k = gi; k < ld.cnt; k += G) red_add_part<S>(a, src[__ldg(to + k)]);
+#pragma unroll 8
+                for (int k = gi; k < ld.cnt; k += G) red_add_part<S>(a, src[to[k]]);
             }
             red[threadIdx.x] = a;
             __syncthreads();
@@ -504,8 +544,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int ntasks, co
             // every thread scatters: destination k, rank l
             for (int idx = threadIdx.x; idx < ld.gcnt * rr; idx += kRedThreads) {
                 const int k = idx / rr, ll = idx - k * rr;
-                g[gdst[ld.gbeg + k] + l0 + ll] =
-                    apply_d<S>(part_to_op<S>(red_to_part<S>(red[ll]), ld.scale), ld, l0 + ll, tscale);
+                g[gd[k] + l0 + ll] = apply_d<S>(part_to_op<S>(red_to_part<S>(red[ll]), ld.scale), ld, l0 + ll, tscale);
             }
             __syncthreads();
         }
@@ -513,26 +552,20 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int ntasks, co
     }
     // the other blocks: one lane per (block, rank), a sequential sum over the
     // block's leaf clusters (independent loads) and the scatter of that rank
-    const int task = ((int)blockIdx.x - nbig) * kRedThreads + threadIdx.x;
-    if (task >= ntasks) return;
-    const int tq = __ldg(tasks + task);
-    const LrDesc ld = lr[tq >> 6];
-    if (item_idle(sys, ld.pad)) return;
-    const int l = tq & 63;
-    const typename Tr<S>::Part *src = part + l;
-    const int32_t *to = tofs + ld.boff;
-    typename Tr<S>::Part t;
-    if (ld.cnt == 1) {  // the column cluster is a leaf: t_m is its one projection
-        t = src[__ldg(to)];
-    } else {
-        RT a;
-        red_zero<S>(a);
-#pragma unroll 4
-        for (int k = 0; k < ld.cnt; ++k) red_add_part<S>(a, src[__ldg(to + k)]);
-        t = red_to_part<S>(a);
+    const int t0 = ((int)blockIdx.x - nbig) * kRedThreads * kRedTasks + threadIdx.x;
+    int tq[kRedTasks];
+    LrDesc ld[kRedTasks];
+#pragma unroll
+    for (int u = 0; u < kRedTasks; ++u) {
+        const int task = t0 + u * kRedThreads;
+        tq[u] = task < ntasks ? __ldg(tasks + task) : -1;
+        if (tq[u] >= 0) ld[u] = lr[tq[u] >> 6];
     }
-    const Op o = apply_d<S>(part_to_op<S>(t, ld.scale), ld, l, tscale);
-    for (int k = 0; k < ld.gcnt; ++k) g[gdst[ld.gbeg + k] + l] = o;
+    pdl_wait();  // T, the flags and g belong to earlier kernels
+    if (skip_product(S_, mode)) return;
+#pragma unroll
+    for (int u = 0; u < kRedTasks; ++u)
+        if (tq[u] >= 0) reduce_task<S>(tq[u] & 63, ld[u], gdst, tofs, part, g, tscale, sys);
 }
 
 // ------------------------------------------------------------------------
@@ -713,6 +746,8 @@ __global__ void __launch_bounds__(kP2Threads, kP2gBlocks) k_phase2g(
     constexpr size_t esz = 16 / VW;
     constexpr int GR = kGroupRows;
     __shared__ double wsum[2][kP2Warps];
+    pdl_trigger();
+    pdl_wait();  // g, y, w and the flags belong to earlier kernels
     if (skip_product(S_, mode)) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int W = gridDim.x * kP2Warps;
@@ -846,9 +881,9 @@ int grid_for(int64_t n, int threads, int cap) {
 template <Store SS, int NT>
 void phase1_run(const P1Desc *list, int base, int count, const DevIndex &ix, const DevPanels &P,
                 const SolverScalars *skipS, int mode, cudaStream_t st, const SysScalars *sys) {
-    k_phase1<SS, NT><<<count, NT, 0, st>>>(base, list, ix.xdst, ix.xsel, P.q1, (const typename Tr<SS>::Op *)P.xs,
-                                           (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g, skipS, mode,
-                                           sys);
+    launch_pdl(k_phase1<SS, NT>, dim3(count), dim3(NT), st, base, list, ix.xdst, ix.xsel, P.q1,
+               (const typename Tr<SS>::Op *)P.xs, (typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g, skipS,
+               mode, sys);
 }
 
 // The projection: one launch per run of the work list (one run over the
@@ -878,21 +913,19 @@ void phase1_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *
 template <Store SS>
 void reduce_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st,
                    const SysScalars *sys) {
-    const int blocks = ix.nbig + (ix.ntasks + kRedThreads - 1) / kRedThreads;
+    const int blocks = ix.nbig + (ix.ntasks + kRedThreads * kRedTasks - 1) / (kRedThreads * kRedTasks);
     if (blocks == 0) return;
-    k_reduce<SS><<<blocks, kRedThreads, 0, st>>>(ix.nbig, ix.ntasks, ix.red_big, ix.red_tasks, ix.lr, ix.gdst,
-                                                 ix.tofs, (const typename Tr<SS>::Part *)P.part,
-                                                 (typename Tr<SS>::Op *)P.g,
-                                                 ix.tscale, skipS, mode, sys);
+    launch_pdl(k_reduce<SS>, dim3(blocks), dim3(kRedThreads), st, ix.nbig, ix.ntasks, ix.red_big, ix.red_tasks, ix.lr,
+               ix.gdst, ix.tofs, (const typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g, ix.tscale, skipS,
+               mode, sys);
 }
 
 template <Store SS>
 void phase2_launch(const DevIndex &ix, const DevPanels &P, double *y, const int32_t *out_perm, int accum,
                    const SolverScalars *skipS, int mode, cudaStream_t st, const double *w, int dotmode,
                    double *dpart, const SysScalars *sys) {
-    k_phase2g<SS><<<phase2_items(ix), kP2Threads, 0, st>>>(ix.ngroups, ix.groups, P.p2,
-                                                           (const typename Tr<SS>::Op *)P.g, y, out_perm, accum,
-                                                           skipS, mode, w, dotmode, dpart, sys);
+    launch_pdl(k_phase2g<SS>, dim3(phase2_items(ix)), dim3(kP2Threads), st, ix.ngroups, ix.groups, P.p2,
+               (const typename Tr<SS>::Op *)P.g, y, out_perm, accum, skipS, mode, w, dotmode, dpart, sys);
 }
 
 }  // namespace
