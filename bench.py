@@ -472,6 +472,9 @@ def main():
     ap.add_argument("--forms", default=DEFAULT_FORMS, help="forms measured beside the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--matvec-iters", type=int, default=50)
+    ap.add_argument("--use-graph", type=int, default=2, choices=[0, 1, 2],
+                    help="graph mode of the solves: 2 one conditional-loop graph per run (default); 1 a graph "
+                         "per batch of iterations, whose kernels ncu profiles one by one; 0 stream launches")
     ap.add_argument("--workload", default="icosphere_L6",
                     choices=["icosphere_L6", "icosphere_L4", "two_spheres_L7", "multirhs64", "batch48",
                              "build_icosphere_L6", "build_batch48", "matvec_protocol"],
@@ -511,7 +514,7 @@ def main():
     def solve(form):
         x.zero_()
         return P.hmat_bicgstab(handles[form], b, x, tol=1e-8, maxit=2000, stream=stream, check_every=CHECK_EVERY,
-                               **FORM_OPTS[form])
+                               use_graph=args.use_graph, **FORM_OPTS[form])
 
     def timed(form, steps, warmup, clk=None, tag=None):
         for _ in range(warmup):
@@ -549,7 +552,7 @@ def main():
     for f in forms:
         fms, finf = timed(f, max(3, args.steps // 2), 2)
         info = P.hmat_info(handles[f])
-        with _nvtx(torch, f"products_{f}"):
+        with _nvtx(torch, "products"):
             kt = P.hmat_time_matvec(handles[f], args.matvec_iters, False, stream)
         # algorithmic bytes: stored entries at their element size, plus the partial
         # sums written (projection) and y written once per segment (expansion)
@@ -591,7 +594,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": {"bf16": "bf16+f64", "fp64": "f64", "fp64_dfma": "f64", "m2_double": "f64"}.get(args.form, "f32+f64"),
                 "data": "synthetic",
-                "config": _config(mesh, args, {"blob_stats": stats, "host_build_s": round(build_s, 3)}),
+                "config": _config(mesh, args, {"blob_stats": stats, "host_build_s": round(build_s, 3),
+                                               "solve_graph_mode": args.use_graph}),
                 "fp64_solve_ms": table.get("fp64", {}).get("solve_ms"),
                 "fp32_solve_ms": table.get("fp32", {}).get("solve_ms"),
                 "fp64_dfma_solve_ms": table.get("fp64_dfma", {}).get("solve_ms"),
