@@ -319,32 +319,42 @@ def run_workload(args):
         mesh = synth.icosphere(6)
         nrhs = 64
         blob = P.hmat_build(mesh.centroid, mesh.area)
-        h = P.hmat_upload(blob, "bf16")
         B = torch.from_numpy(np.ascontiguousarray(synth.rhs_normal_columns(mesh.n, nrhs).T)).cuda()
         X = torch.zeros_like(B)
-        def multi():
-            X.zero_()
-            return P.hmat_bicgstab_multi(h, B, X, nrhs, tol=1e-8, maxit=3000, inner_tol=1e-2, check_every=CHECK_EVERY)
-        multi()
-        ms, infos = _cuda_ms(torch, multi, 2)
-        x1 = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
-        def single():
-            x1.zero_()
-            return P.hmat_bicgstab(h, B[0].contiguous(), x1, tol=1e-8, maxit=3000, inner_tol=1e-2,
-                                   check_every=CHECK_EVERY)
-        single()
-        ms1, info1 = _cuda_ms(torch, single, 3)
-        Y = torch.empty_like(B)
-        with _nvtx(torch, "product64"):
-            mv_ms, _ = _cuda_ms(torch, lambda: P.hmat_matvec(h, B, Y, nrhs), 10)
-        assert all(i["status"] == 0 for i in infos[-1])
-        out.update({"unit": "ms per 64 solves", "value": ms, "config": {"workload": "icosphere_L6_64rhs_N(0,1)",
-                    "n": mesh.n, "nrhs": nrhs, "form": "bf16 + FP64 refinement"},
-                    "iters_min_max": [min(i["iters"] for i in infos[-1]), max(i["iters"] for i in infos[-1])],
-                    "single_rhs_solve_ms": ms1, "single_rhs_iters": info1[-1]["iters"],
-                    "tensor_core_product_ms_64_columns": mv_ms,
-                    "single_column_product_ms": P.hmat_time_matvec(h, 10)[4]})
-        P.hmat_destroy(h)
+        res = {}
+        for form, itol in (("bf16", 1e-2), ("fp32", 1e-4)):
+            h = P.hmat_upload(blob, form)
+            def multi():
+                X.zero_()
+                return P.hmat_bicgstab_multi(h, B, X, nrhs, tol=1e-8, maxit=3000, inner_tol=itol,
+                                             check_every=CHECK_EVERY)
+            multi()
+            ms, infos = _cuda_ms(torch, multi, 2)
+            x1 = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
+            def single():
+                x1.zero_()
+                return P.hmat_bicgstab(h, B[0].contiguous(), x1, tol=1e-8, maxit=3000, inner_tol=itol,
+                                       check_every=CHECK_EVERY)
+            single()
+            ms1, info1 = _cuda_ms(torch, single, 3)
+            Y = torch.empty_like(B)
+            with _nvtx(torch, "product64" if form == "bf16" else "product64_fp32"):
+                mv_ms, _ = _cuda_ms(torch, lambda: P.hmat_matvec(h, B, Y, nrhs), 10)
+            assert all(i["status"] == 0 for i in infos[-1])
+            res[form] = {"solves_ms": ms, "iters_min_max": [min(i["iters"] for i in infos[-1]),
+                                                            max(i["iters"] for i in infos[-1])],
+                         "single_rhs_solve_ms": ms1, "single_rhs_iters": info1[-1]["iters"],
+                         "tensor_core_product_ms_64_columns": mv_ms,
+                         "single_column_product_ms": P.hmat_time_matvec(h, 10)[4]}
+            P.hmat_destroy(h)
+        out.update({"unit": "ms per 64 solves", "value": res["bf16"]["solves_ms"],
+                    "config": {"workload": "icosphere_L6_64rhs_N(0,1)", "n": mesh.n, "nrhs": nrhs,
+                               "form": "bf16 + FP64 refinement (fp32 beside it)"},
+                    "iters_min_max": res["bf16"]["iters_min_max"],
+                    "single_rhs_solve_ms": res["bf16"]["single_rhs_solve_ms"],
+                    "single_rhs_iters": res["bf16"]["single_rhs_iters"],
+                    "tensor_core_product_ms_64_columns": res["bf16"]["tensor_core_product_ms_64_columns"],
+                    "single_column_product_ms": res["bf16"]["single_column_product_ms"], "fp32": res["fp32"]})
     elif args.workload == "batch48":
         specs = synth.uneven_batch_specs(48)
         meshes = [synth.mesh_from_spec(sp) for sp in specs]

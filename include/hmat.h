@@ -253,11 +253,15 @@ int hmat_destroy(hmat_handle h);
 /*
  * hmat_matvec -- y = A~ x (overwrite) for nrhs vectors, column-major N x nrhs,
  * original panel order, in the handle's precision form.  x and y must not
- * overlap.  Asynchronous on `stream` for device pointers.  For a HMAT_BF16
- * handle and nrhs >= 2 the columns go through the tensor-core product, 64 per
- * pass (tcgen05 MMAs: BF16 panels times x and t split into two BF16 parts,
- * FP32 accumulation in tensor memory; one GEMM per column cluster for t, one
- * per leaf row cluster for y); it allocates its buffers on first use.  x and y may be host
+ * overlap.  Asynchronous on `stream` for device pointers.  For a HMAT_BF16 or
+ * HMAT_FP32 handle and nrhs >= 2 the columns go through the tensor-core
+ * product, 64 per pass (tcgen05 MMAs, FP32 accumulation in tensor memory; one
+ * GEMM per column cluster for t, one per leaf row cluster for y): BF16 panels
+ * (kind::f16) times x and t split into two BF16 parts, within 2e-5 of the same
+ * panels' exact product; FP32 panels and operands each split into two TF32
+ * parts (kind::tf32, two MMAs per step), within 1e-5 -- the tensor cores' FP32
+ * accumulation, where one column at a time (nrhs = 1) keeps the FP32 form's
+ * 2e-7.  It allocates its buffers on first use.  x and y may be host
  * memory (staged through the handle's buffers) or device memory of the handle's
  * GPU; device memory of another GPU is rejected (HMAT_ERR_ARG), and so it is for
  * b and x of the solvers.

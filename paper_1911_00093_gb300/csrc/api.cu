@@ -194,7 +194,20 @@ int alloc_panels(hmat_t *h, const BlobView &v, const Layout &L, Store s, DevPane
 // -- as K-major 8 x 8 core matrices, core (n/8, k/8) at (k/8 * npad/8 + n/8),
 // zero past |sigma| and past the item's rows.  Plus the U row and power of two
 // feeding every operand slot of the expansion.
-int upload_mrhs_index(hmat_t *h, const BlobView &v, const Layout &L) {
+// FP32 -> TF32 on the host as the device's cvt.rna does it: round to nearest,
+// ties away from zero, the low 13 bits cleared (finite values of pow2-scaled panels)
+uint32_t tf32_bits(float v) {
+    uint32_t b;
+    std::memcpy(&b, &v, 4);
+    return (b + 0x1000u) & ~0x1FFFu;
+}
+float bits_float(uint32_t b) {
+    float v;
+    std::memcpy(&v, &b, 4);
+    return v;
+}
+
+int upload_mrhs_index(hmat_t *h, const BlobView &v, const Layout &L, bool tf32) {
     MrhsIndex &mx = h->mx;
     const size_t nlr = L.lr.size();
     // blob block and W exponent of each low-rank block, from its phase-1 slices
@@ -244,7 +257,7 @@ int upload_mrhs_index(hmat_t *h, const BlobView &v, const Layout &L) {
         sigs.push_back(sg);
         members.push_back({a, b});
         max_npad = std::max(max_npad, sg.npad);
-        woff += (int64_t)sg.kpad * sg.npad;
+        woff += (int64_t)sg.kpad * sg.npad * (tf32 ? 2 : 1);
         trows += R;
         a = b;
     }
@@ -256,11 +269,14 @@ int upload_mrhs_index(hmat_t *h, const BlobView &v, const Layout &L) {
     std::stable_sort(by_size.begin(), by_size.end(), [&](size_t x, size_t y) {
         return (int64_t)sigs[x].kpad * sigs[x].npad > (int64_t)sigs[y].kpad * sigs[y].npad;
     });
-    std::vector<uint16_t> wt((size_t)std::max<int64_t>(woff, 8), 0);
+    // BF16 tiles: core (n/8, k/8) at (k/8 * npad/8 + n/8); TF32 (FP32 panels):
+    // per 32-entry K chunk a high-part tile, core (n/8, kk/4) at (kk/4 * npad/8 +
+    // n/8), then the remainders' tile of the same chunk
+    std::vector<uint16_t> wt(tf32 ? 8 : (size_t)std::max<int64_t>(woff, 8), 0);
+    std::vector<uint32_t> wt32(tf32 ? (size_t)std::max<int64_t>(woff, 8) : 8, 0);
 #pragma omp parallel for schedule(dynamic, 8)
     for (int64_t s = 0; s < (int64_t)sigs.size(); ++s) {
         const MrhsSig &sg = sigs[s];
-        uint16_t *tile = wt.data() + sg.woff;
         int32_t n = 0;
         for (size_t o = members[s].first; o < members[s].second; ++o) {
             const int32_t q = order[o].second;
@@ -269,8 +285,20 @@ int upload_mrhs_index(hmat_t *h, const BlobView &v, const Layout &L) {
             const double *W = v.data + e[6] + m * r;  // W_m, r x cols row-major
             const double inv = std::ldexp(1.0, -ew[q]);
             for (int64_t l = 0; l < r; ++l, ++n)
-                for (int64_t k = 0; k < cols; ++k)
-                    tile[((k / 8) * (sg.npad / 8) + n / 8) * 64 + (n % 8) * 8 + (k % 8)] = bf16_bits(W[l * cols + k] * inv);
+                for (int64_t k = 0; k < cols; ++k) {
+                    if (!tf32) {
+                        wt[sg.woff + ((k / 8) * (sg.npad / 8) + n / 8) * 64 + (n % 8) * 8 + (k % 8)] =
+                            bf16_bits(W[l * cols + k] * inv);
+                        continue;
+                    }
+                    const float w = (float)(W[l * cols + k] * inv);  // the FP32 panel's value
+                    const uint32_t hi = tf32_bits(w), lo = tf32_bits(w - bits_float(hi));
+                    const int64_t c = k / 32, kk = k % 32, kc = std::min<int64_t>(32, sg.kpad - c * 32);
+                    const int64_t at = sg.woff + c * 32 * 2 * sg.npad + ((kk / 4) * (sg.npad / 8) + n / 8) * 32 +
+                                       (n % 8) * 4 + (kk % 4);
+                    wt32[at] = hi;
+                    wt32[at + kc * sg.npad] = lo;
+                }
         }
     }
     std::vector<MrhsSrc> src((size_t)L.glen, MrhsSrc{(int32_t)zero_row, 0});
@@ -290,25 +318,26 @@ int upload_mrhs_index(hmat_t *h, const BlobView &v, const Layout &L) {
     }
     MrhsSrc *dsrc = nullptr;
     MrhsSig *dsig = nullptr;
-    uint16_t *dwt = nullptr;
+    void *dwt = nullptr;
     int st;
     std::vector<MrhsSig> sorted(sigs.size());
     for (size_t k = 0; k < by_size.size(); ++k) sorted[k] = sigs[by_size[k]];
     if ((st = h->upload(&dsrc, src.data(), sizeof(MrhsSrc) * src.size())) ||
         (st = h->upload(&dsig, sorted.data(), sizeof(MrhsSig) * sorted.size())) ||
-        (st = h->upload(&dwt, wt.data(), 2 * wt.size())))
+        (st = tf32 ? h->upload(&dwt, wt32.data(), 4 * wt32.size()) : h->upload(&dwt, wt.data(), 2 * wt.size())))
         return st;
     CK(mrhs_prepare());
     mx.src = dsrc;
     mx.sigs = dsig;
     mx.wt = dwt;
+    mx.tf32 = tf32;
     mx.nsig = (int32_t)sigs.size();
     mx.max_npad = max_npad;
     mx.urows = zero_row + 1;
     mx.ctl.status = h->status_dev;
     mx.ctl.wait_limit = kDefaultWaitCycles;
     h->index_bytes += (int64_t)(sizeof(MrhsSrc) * src.size() + sizeof(MrhsSig) * sigs.size());
-    h->panel_bytes_mrhs = 2 * (int64_t)wt.size();
+    h->panel_bytes_mrhs = tf32 ? 4 * (int64_t)wt32.size() : 2 * (int64_t)wt.size();
     h->mrhs = true;
     return HMAT_OK;
 }
@@ -362,7 +391,9 @@ int upload_view(const BlobView &v, int32_t precision, int32_t method3_c, const s
             h->seg64.ix = g.ix;
             h->seg64.partials_n = g.partials_n;
             h->seg64.glen = g.glen;
-            if (precision == HMAT_BF16 && (st = upload_mrhs_index(h, v, L))) return st;
+            if ((precision == HMAT_BF16 || precision == HMAT_FP32) &&
+                (st = upload_mrhs_index(h, v, L, precision == HMAT_FP32)))
+                return st;
             if (precision == HMAT_FP64 || precision == HMAT_FP64_DFMA) {
                 h->seg64.store = g.store;
                 h->seg64.P = g.P;

@@ -205,7 +205,7 @@ struct MrhsSrc {
 // One column cluster sigma of the projection: the rank rows of every low-rank
 // block whose column cluster is sigma, stacked (R rows), times x_sigma.
 struct MrhsSig {
-    int64_t woff;   // first element of its W tile (BF16, K-major core matrices, kpad x npad)
+    int64_t woff;   // first element of its W tile (K-major core matrices, kpad x npad; TF32: two per chunk)
     int32_t xbeg;   // first source row (cluster order)
     int32_t xlen;   // |sigma|
     int32_t kpad;   // xlen rounded up to 16
@@ -216,8 +216,9 @@ struct MrhsSig {
 struct MrhsIndex {
     const MrhsSrc *src = nullptr;    // [glen]
     const MrhsSig *sigs = nullptr;   // [nsig]
-    const uint16_t *wt = nullptr;    // W tiles of the column clusters
+    const void *wt = nullptr;        // W tiles of the column clusters (BF16, or TF32 high/low pairs)
     int32_t nsig = 0, max_npad = 16;
+    bool tf32 = false;               // FP32 panels: kind::tf32 MMAs on TF32 high/low parts
     int64_t urows = 0;               // rows of U (n + ranks + 1)
     float *U = nullptr;              // [urows][64]: x rows, then t rows, then a zero row
     PipeCtl ctl;
