@@ -21,12 +21,13 @@ SHORT = 200_000            # SM cycles: about 0.1 ms
 DEFAULT = 2_000_000_000    # the library's default bound (about one second)
 
 
-def test_tensor_core_timeout_is_reported_and_the_handle_recovers(hcache, oracle_mod):
+@pytest.mark.parametrize("form,data,tol", [("bf16", "DATA_BF16", 2e-5), ("fp32", "DATA_FP32", 1e-5)])
+def test_tensor_core_timeout_is_reported_and_the_handle_recovers(hcache, oracle_mod, form, data, tol):
     torch = need_gpu()
     P = lib()
     mesh = synth.icosphere(4)
     H = hcache(mesh)
-    h = P.hmat_upload(oracle_blob(H), "bf16")
+    h = P.hmat_upload(oracle_blob(H), form)
     try:
         nrhs = 3
         X = synth.rhs_normal_columns(mesh.n, nrhs, seed=7)
@@ -53,7 +54,7 @@ def test_tensor_core_timeout_is_reported_and_the_handle_recovers(hcache, oracle_
         assert P.hmat_check(h) == 0
         Y = Yd.cpu().numpy().T
         for k in range(nrhs):
-            assert rel(Y[:, k], H.matvec(X[:, k], oracle_mod.DATA_BF16)) <= 2e-5
+            assert rel(Y[:, k], H.matvec(X[:, k], getattr(oracle_mod, data))) <= tol
     finally:
         P.hmat_destroy(h)
 
