@@ -709,24 +709,28 @@ static int bicgstab_ex_impl(hmat_handle h, const double *b, double *x, const hma
             launches += kProductLaunches + 1;
         }
         CK(cudaGetLastError());
+        // the state a run starts from is read from the device only when the host
+        // does not know it already: ||r_0||^2 is ||b||^2 for x_0 = 0, and a restart
+        // starts from the true residual just read (a start that fails -- budget --
+        // leaves every kernel of the run a no-op, and the flag shows at the end)
+        bool start_known = x0_zero;
+        double start_rnorm2 = bnorm2;
         for (;;) {
             // a run: its stop threshold, then batches of iterations until its flag is set
-            // (a run whose start already failed -- budget, non-finite -- goes straight on)
-            if ((rc = read_scalars(h, st))) return rc;
-            if (h->S_host->flag == 0) {
-                double stop2 = std::max(o.tol * o.tol * bnorm2, o.inner_tol * o.inner_tol * h->S_host->rnorm2);
+            int start_flag = 0;
+            if (!start_known) {
+                if ((rc = read_scalars(h, st))) return rc;
+                start_flag = h->S_host->flag;
+                start_rnorm2 = h->S_host->rnorm2;
+            }
+            bool read_after_run = false;
+            if (start_flag == 0) {
+                double stop2 = std::max(o.tol * o.tol * bnorm2, o.inner_tol * o.inner_tol * start_rnorm2);
                 CK(cudaMemcpyAsync(&h->S->stop2, &stop2, sizeof(double), cudaMemcpyHostToDevice, st));
                 if (o.use_graph == 2) {  // the whole run on the device
                     if ((rc = ensure_loop_graph(h, o.check_every, o.maxit))) return rc;
                     CK(cudaMemsetAsync(&h->S->loops, 0, sizeof(int32_t), st));
                     CK(cudaGraphLaunch(h->loop_graph, st));
-                    if ((rc = read_scalars(h, st))) return rc;
-                    launches += h->S_host->loops * (o.check_every * kIterationLaunches + 1);
-                    if (h->S_host->flag == 0) {  // the loop bound ended it: count it as the budget
-                        const int32_t maxit_flag = HMAT_ERR_MAXIT;
-                        CK(cudaMemcpyAsync(&h->S->flag, &maxit_flag, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-                        if ((rc = read_scalars(h, st))) return rc;
-                    }
                 }
                 for (; o.use_graph != 2;) {
                     launches += o.check_every * kIterationLaunches;
@@ -738,18 +742,26 @@ static int bicgstab_ex_impl(hmat_handle h, const double *b, double *x, const hma
                         CK(cudaGetLastError());
                     }
                     if ((rc = read_scalars(h, st))) return rc;
+                    read_after_run = true;
                     if (h->S_host->flag != 0) break;
                 }
             }
-            const int flag = h->S_host->flag;
-            inf.relres_inner = std::sqrt(h->S_host->rnorm2 / bnorm2);
-            inf.iters = h->S_host->iters;
-            // true residual with the FP64 H-matrix (Section 4.1.3); r~ = r for a restart
+            // true residual with the FP64 H-matrix (Section 4.1.3); r~ = r for a
+            // restart; the residual kernel first keeps the run's flag and ||r||^2
             enqueue_segments(&h->seg64, 1, h->x, nullptr, h->y, nullptr, nullptr, 0, st);
             launch_residual(n, h->b, h->y, h->r, h->rt, h->S, h->partials, -1, st);
             launches += kProduct64Launches + 1;
             inf.matvecs_fp64 += 1;
             if ((rc = read_scalars(h, st))) return rc;
+            int flag = h->S_host->run_flag;
+            if (start_flag == 0 && o.use_graph == 2) {
+                launches += h->S_host->loops * (o.check_every * kIterationLaunches + 1);
+                if (flag == 0) flag = HMAT_ERR_MAXIT;  // the loop bound ended it: count it as the budget
+            } else if (start_flag != 0 && !read_after_run) {
+                flag = start_flag;
+            }
+            inf.relres_inner = std::sqrt(h->S_host->run_rnorm2 / bnorm2);
+            inf.iters = h->S_host->iters;
             const double rel = std::sqrt(h->S_host->rnorm2 / bnorm2);
             inf.relres_true = rel;
             if (flag != 1) { status = flag; break; }
@@ -759,6 +771,8 @@ static int bicgstab_ex_impl(hmat_handle h, const double *b, double *x, const hma
             inf.restarts += 1;
             launch_count_iter(h->S, o.maxit, st);  // the restarted run starts
             launches += 1;
+            start_known = true;
+            start_rnorm2 = h->S_host->rnorm2;
         }
     }
     // products with the iterated operator: r_0, then two per iteration except a stop at ||s||

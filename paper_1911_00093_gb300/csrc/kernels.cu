@@ -278,6 +278,10 @@ __global__ void __launch_bounds__(kVecThreads) k_residual(int n, const double *_
         a[0] += rv * rv;
     }
     if (grid_reduce<1>(a, partials, S, sh) && threadIdx.x == 0) {
+        if (iter_limit < 0) {  // a true residual: keep the state of the run it follows
+            S->run_flag = S->flag;
+            S->run_rnorm2 = S->rnorm2;
+        }
         S->rnorm2 = a[0];
         S->rho = a[0];
         S->iter_in_run = 0;

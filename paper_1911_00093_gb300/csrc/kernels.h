@@ -152,7 +152,8 @@ struct SolverScalars {
     unsigned int ticket;  // last-block counter of the fused reductions
     int32_t nmv;          // products with the iterated operator, excluding r_0
     int32_t loops;        // batches of iterations the device loop of a run has replayed
-    int32_t pad_;
+    int32_t run_flag;     // the flag of the run a true residual follows (kept by that residual)
+    double run_rnorm2;    // its ||r||^2 at the end of the run
 };
 
 constexpr int kVecThreads = 256;
