@@ -682,13 +682,13 @@ static int bicgstab_ex_impl(hmat_handle h, const double *b, double *x, const hma
     launch_gather(n, h->perm, xsrc, h->x, st);
     CK(cudaMemsetAsync(h->S, 0, sizeof(SolverScalars), st));
     // ||x_0|| (a zero initial guess needs no product for r_0 = b), then ||b||
+    // ||x_0||^2, then ||b||^2 (the second keeps the first in run_rnorm2): one read
     launch_residual(n, h->x, nullptr, h->r, h->rt, h->S, h->partials, -1, st);
-    int rc = read_scalars(h, st);
-    if (rc) return rc;
-    const bool x0_zero = h->S_host->rnorm2 == 0.0;
     launch_residual(n, h->b, nullptr, h->r, h->rt, h->S, h->partials, -1, st);
     launches += 3;
-    if ((rc = read_scalars(h, st))) return rc;
+    int rc = read_scalars(h, st);
+    if (rc) return rc;
+    const bool x0_zero = h->S_host->run_rnorm2 == 0.0;
     const double bnorm2 = h->S_host->rnorm2;
     int status = HMAT_OK;
     if (!std::isfinite(bnorm2)) {
