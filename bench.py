@@ -564,8 +564,8 @@ def main():
         info = P.hmat_info(handles[f])
         with _nvtx(torch, "products"):
             kt = P.hmat_time_matvec(handles[f], args.matvec_iters, False, stream)
-        # algorithmic bytes: stored entries at their element size, plus the partial
-        # sums written (projection) and y written once per segment (expansion)
+        # algorithmic bytes: stored entries at their element size, plus the
+        # projections T written (projection) and y written once per segment (expansion)
         p1_bytes = info["phase1_bytes"] + info["partials"] * PART_BYTES.get(f, 8)
         p2_bytes = info["phase2_bytes"] + 8 * info["n"] * info["segments"]
         table[f] = {"solve_ms": fms / max(3, args.steps // 2), "iters": finf[-1]["iters"],

@@ -437,7 +437,7 @@ typedef struct hmat_handle_info {
     int64_t stored_entries;      /* dense_entries + lr_entries of the blob                                  */
     int64_t phase1_entries;      /* entries streamed by the projection t = W x                              */
     int64_t phase2_entries;      /* entries streamed by the expansion y = D x + V t                         */
-    int64_t partials;            /* partial sums of blocks spanning several leaf clusters                   */
+    int64_t partials;            /* projection outputs T (per leaf column cluster, padded), summed per block */
     int64_t rank_sum;
     int64_t stored_bytes;        /* stored entries times their element bytes (no padding): the bytes one   */
                                  /* product must read at least                                              */
