@@ -329,7 +329,8 @@ def run_workload(args):
                 return P.hmat_bicgstab_multi(h, B, X, nrhs, tol=1e-8, maxit=3000, inner_tol=itol,
                                              check_every=CHECK_EVERY)
             multi()
-            ms, infos = _cuda_ms(torch, multi, 2)
+            with _nvtx(torch, "solves64" if form == "bf16" else "solves64_fp32"):
+                ms, infos = _cuda_ms(torch, multi, 2)
             x1 = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
             def single():
                 x1.zero_()
