@@ -322,14 +322,14 @@ def run_workload(args):
         B = torch.from_numpy(np.ascontiguousarray(synth.rhs_normal_columns(mesh.n, nrhs).T)).cuda()
         X = torch.zeros_like(B)
         res = {}
-        for form, itol in (("bf16", 1e-2), ("fp32", 1e-4)):
+        for form, itol in (("bf16", 1e-2), ("fp32", 1e-4), ("fp64", 0.0)):
             h = P.hmat_upload(blob, form)
             def multi():
                 X.zero_()
                 return P.hmat_bicgstab_multi(h, B, X, nrhs, tol=1e-8, maxit=3000, inner_tol=itol,
                                              check_every=CHECK_EVERY)
             multi()
-            with _nvtx(torch, "solves64" if form == "bf16" else "solves64_fp32"):
+            with _nvtx(torch, "solves64" if form == "bf16" else "solves64_" + form):
                 ms, infos = _cuda_ms(torch, multi, 2)
             x1 = torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
             def single():
@@ -339,14 +339,20 @@ def run_workload(args):
             single()
             ms1, info1 = _cuda_ms(torch, single, 3)
             Y = torch.empty_like(B)
-            with _nvtx(torch, "product64" if form == "bf16" else "product64_fp32"):
+            with _nvtx(torch, "product64" if form == "bf16" else "product64_" + form):
                 mv_ms, _ = _cuda_ms(torch, lambda: P.hmat_matvec(h, B, Y, nrhs), 10)
             assert all(i["status"] == 0 for i in infos[-1])
             res[form] = {"solves_ms": ms, "iters_min_max": [min(i["iters"] for i in infos[-1]),
                                                             max(i["iters"] for i in infos[-1])],
+                         "true_residual_products": sum(i["matvecs_fp64"] for i in infos[-1]),
                          "single_rhs_solve_ms": ms1, "single_rhs_iters": info1[-1]["iters"],
-                         "tensor_core_product_ms_64_columns": mv_ms,
+                         ("double_float_product_ms_64_columns" if form == "fp64"
+                          else "tensor_core_product_ms_64_columns"): mv_ms,
                          "single_column_product_ms": P.hmat_time_matvec(h, 10)[4]}
+            if form == "bf16":  # the FP64 copy of the true residuals, 64 columns at once
+                with _nvtx(torch, "product64_fp64_copy"):
+                    res[form]["fp64_copy_product_ms_64_columns"], _ = _cuda_ms(
+                        torch, lambda: P.hmat_matvec(h, B, Y, nrhs, fp64=True), 10)
             P.hmat_destroy(h)
         out.update({"unit": "ms per 64 solves", "value": res["bf16"]["solves_ms"],
                     "config": {"workload": "icosphere_L6_64rhs_N(0,1)", "n": mesh.n, "nrhs": nrhs,
@@ -355,7 +361,11 @@ def run_workload(args):
                     "single_rhs_solve_ms": res["bf16"]["single_rhs_solve_ms"],
                     "single_rhs_iters": res["bf16"]["single_rhs_iters"],
                     "tensor_core_product_ms_64_columns": res["bf16"]["tensor_core_product_ms_64_columns"],
-                    "single_column_product_ms": res["bf16"]["single_column_product_ms"], "fp32": res["fp32"]})
+                    "single_column_product_ms": res["bf16"]["single_column_product_ms"],
+                    "fp64_copy_product_ms_64_columns": res["bf16"]["fp64_copy_product_ms_64_columns"],
+                    "true_residual_products": res["bf16"]["true_residual_products"],
+                    "fp32": res["fp32"], "fp64": res["fp64"],
+                    "speedup_bf16_vs_fp64": res["fp64"]["solves_ms"] / res["bf16"]["solves_ms"]})
     elif args.workload == "batch48":
         specs = synth.uneven_batch_specs(48)
         meshes = [synth.mesh_from_spec(sp) for sp in specs]

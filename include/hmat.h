@@ -261,7 +261,12 @@ int hmat_destroy(hmat_handle h);
  * panels' exact product; FP32 panels and operands each split into two TF32
  * parts (kind::tf32, two MMAs per step), within 1e-5 -- the tensor cores' FP32
  * accumulation, where one column at a time (nrhs = 1) keeps the FP32 form's
- * 2e-7.  It allocates its buffers on first use.  x and y may be host
+ * 2e-7.  For a double-float operator (an HMAT_FP64 handle, and the FP64 copy
+ * that hmat_matvec_fp64 applies for HMAT_FP64, HMAT_BF16 and HMAT_FP32
+ * handles) and nrhs >= 2 the columns go through the many-column double-float
+ * product, 16 per pass: each panel vector loaded is applied to several columns,
+ * and every column's result is bit for bit that of a one-column product.  The
+ * many-column products allocate their buffers on first use.  x and y may be host
  * memory (staged through the handle's buffers) or device memory of the handle's
  * GPU; device memory of another GPU is rejected (HMAT_ERR_ARG), and so it is for
  * b and x of the solvers.
@@ -354,7 +359,12 @@ int hmat_problems(hmat_handle h, int32_t *count, int64_t *offsets);
  * one product launch sequence per right-hand side and iteration serves every
  * problem, the vector kernels run over all systems at once with per-system
  * inner products, and every decision (stop, breakdown, true residual with the
- * FP64 H-matrix, restart from it) is taken per system on the device.
+ * FP64 H-matrix, restart from it) is taken per system on the device.  The
+ * products of several columns go through the many-column products of
+ * hmat_matvec; the work of a system whose run has stopped is skipped inside the
+ * iterations and, where the FP64 copy is double-float (every form but the
+ * paper's Table 1 variants), that of a system already accepted in the true
+ * residuals.
  * b, x: N_total x nrhs column-major (N_total = the handle's N), host or device;
  * x holds the initial guess and receives the solution.  `opts` as for
  * hmat_bicgstab_ex (NULL: defaults).  infos (may be NULL): count x nrhs entries,

@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 
 CXX_SOURCES = ["builder.cpp", "layout.cpp", "paper_forms.cpp"]
 CU_SOURCES = ["kernels.cu", "kernels_table1.cu", "multi.cu", "mrhs.cu", "gmres.cu", "api.cu", "noalloc.cu",
-              "aca_device.cu"]
+              "aca_device.cu", "multi_df.cu"]
 # per-file flags: the device builder reproduces the host builder's rounding (no FMA contraction)
 CU_FLAGS = {"aca_device.cu": ["-fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

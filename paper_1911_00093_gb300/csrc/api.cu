@@ -508,15 +508,17 @@ extern "C" int hmat_destroy(hmat_handle h) {
 
 namespace {
 
-int mrhs_matvec(hmat_t *h, const double *x, double *y, int32_t nrhs, cudaStream_t st);
+int multi_matvec(hmat_t *h, const HmatSegment *seg, int nseg, const double *x, double *y, int32_t nrhs,
+                 cudaStream_t st);
 
 int matvec_impl(hmat_handle h, const double *x, double *y, int32_t nrhs, void *stream, bool fp64) {
     if (!h || !x || !y || nrhs < 1) return HMAT_ERR_ARG;
     if (int e = take_status(h)) return e;  // a wait of an earlier product ran out
     cudaStream_t st = (cudaStream_t)stream;
-    if (!fp64 && h->mrhs && nrhs >= 2) return mrhs_matvec(h, x, y, nrhs, st);
     const HmatSegment *seg = fp64 ? &h->seg64 : h->seg;
     const int nseg = fp64 ? 1 : h->nseg;
+    if (nrhs >= 2 && ((!fp64 && h->mrhs) || (nseg == 1 && seg->store == Store::DF)))
+        return multi_matvec(h, seg, nseg, x, y, nrhs, st);
     const int64_t n = h->n;
     bool dx = false, dy = false;
     if (int rc_ = vector_location(x, h->device, &dx)) return rc_;
@@ -862,12 +864,21 @@ MultiGrid multi_grid(hmat_t *h, int nrhs) {
     return g;
 }
 
+// The many-column double-float product serves a one-segment double-float
+// operator (the FP64 handle's own, every handle's FP64 copy but the Table 1
+// variants') once its buffers exist.
+bool mdf_serves(const hmat_t *h, const HmatSegment *seg, int nseg, int nrhs) {
+    return nrhs >= 2 && nseg == 1 && seg->store == Store::DF && h->mdf.cap > 0;
+}
+
 // y(:, k) = A x(:, k) for every column, cluster order (a block-diagonal batch is one operator)
-// The products of every system's column; skip_stopped (the products inside an
+// The products of every system's column.  sysmode 1 (the products inside an
 // iteration): the work items of problems whose system has stopped are skipped,
-// so a batch costs less as its problems converge.
+// so a batch costs less as its problems converge; 2 (true residuals, the
+// many-column double-float product only): those of systems already accepted or
+// finished.
 void multi_products(hmat_t *h, const HmatSegment *seg, int nseg, const double *x, double *y, int nrhs,
-                    cudaStream_t st, bool skip_stopped = false) {
+                    cudaStream_t st, int sysmode = 0) {
     if (seg == h->seg && h->mrhs && h->mx.U && nrhs >= 2) {  // tensor cores, 64 columns per pass
         for (int k0 = 0; k0 < nrhs; k0 += kMrhsCols)
             launch_mrhs_product(h->seg[0].ix, h->mx, h->seg[0].P, x + (size_t)k0 * h->n, h->n, y + (size_t)k0 * h->n,
@@ -875,15 +886,42 @@ void multi_products(hmat_t *h, const HmatSegment *seg, int nseg, const double *x
         return;
     }
     const size_t count = h->prob_off.size() - 1;  // problems: system (p, k) is k * count + p
+    if (mdf_serves(h, seg, nseg, nrhs)) {  // double-float panels, kMdfCols columns per pass
+        launch_mdf_product(seg->ix, seg->P, h->mdf, x, h->n, y, h->n, nrhs, sysmode ? h->multi.S : nullptr, sysmode,
+                           (int)count, st);
+        return;
+    }
     for (int k = 0; k < nrhs; ++k)
         enqueue_segments(seg, nseg, x + (size_t)k * h->n, nullptr, y + (size_t)k * h->n, nullptr, nullptr, 0, st,
-                         nullptr, 0, nullptr, skip_stopped ? h->multi.S + (size_t)k * count : nullptr);
+                         nullptr, 0, nullptr, sysmode == 1 ? h->multi.S + (size_t)k * count : nullptr);
 }
 
 int multi_product_launches(hmat_t *h, const HmatSegment *seg, int nseg, int nrhs) {
     if (seg == h->seg && h->mrhs && h->mx.U && nrhs >= 2)
         return ((nrhs + kMrhsCols - 1) / kMrhsCols) * (h->mx.nsig > 0 ? 3 : 2);
+    if (mdf_serves(h, seg, nseg, nrhs)) return mdf_launches(seg->ix, nrhs);
     return nrhs * product_launches(seg, nseg);
+}
+
+// buffers of the many-column double-float product (first use), sized by the
+// FP64 copy's index (the handle's own double-float segment shares it); column
+// strides are multiples of 32 entries (16-byte vector access)
+int mdf_buffers(hmat_t *h) {
+    auto &b = h->mdf;
+    if (b.cap > 0 || h->seg64.store != Store::DF) return HMAT_OK;
+    auto up = [](int64_t v) { return (std::max<int64_t>(v, 1) + 31) / 32 * 32; };
+    const int64_t ld[3] = {up(h->n), up(h->seg64.partials_n), up(h->seg64.glen)};
+    void **buf[3] = {&b.xs, &b.part, &b.g};
+    for (int k = 0; k < 3; ++k) {
+        const size_t bytes = 8 * (size_t)kMdfCols * ld[k];
+        if (int st = h->alloc(buf[k], bytes)) return st;
+        CK(cudaMemset(*buf[k], 0, bytes));  // the operands' padding columns stay zero
+    }
+    b.ldxs = ld[0];
+    b.ldt = ld[1];
+    b.ldg = ld[2];
+    b.cap = kMdfCols;
+    return HMAT_OK;
 }
 
 // buffers of the tensor-core product (first many-right-hand-side solve)
@@ -901,10 +939,10 @@ void multi_iteration(hmat_t *h, const MultiGrid &g, int nrhs, int iter_limit, cu
     auto &m = h->multi;
     const MultiVecs v{m.x, m.r, m.rt, m.p, m.v, m.s, m.t};
     launch_miteration_vec(g, 0, v, iter_limit, st);  // p
-    multi_products(h, h->seg, h->nseg, m.p, m.v, nrhs, st, true);
+    multi_products(h, h->seg, h->nseg, m.p, m.v, nrhs, st, 1);
     launch_miteration_vec(g, 1, v, iter_limit, st);  // alpha
     launch_miteration_vec(g, 2, v, iter_limit, st);  // s
-    multi_products(h, h->seg, h->nseg, m.s, m.t, nrhs, st, true);
+    multi_products(h, h->seg, h->nseg, m.s, m.t, nrhs, st, 1);
     launch_miteration_vec(g, 3, v, iter_limit, st);  // omega
     launch_miteration_vec(g, 4, v, iter_limit, st);  // x, r
 }
@@ -918,11 +956,13 @@ int multi_read(hmat_t *h, int nsys, cudaStream_t st, bool *running) {
     return HMAT_OK;
 }
 
-// Several columns through the tensor-core product: original order in and out,
-// host or device pointers.
-int mrhs_matvec(hmat_t *h, const double *x, double *y, int32_t nrhs, cudaStream_t st) {
+// Several columns through the tensor-core product (seg = the handle's
+// operator) or the many-column double-float product (a double-float operator):
+// original order in and out, host or device pointers.
+int multi_matvec(hmat_t *h, const HmatSegment *seg, int nseg, const double *x, double *y, int32_t nrhs,
+                 cudaStream_t st) {
     int rc;
-    if ((rc = multi_ensure(h, nrhs)) || (rc = mrhs_buffers(h))) return rc;
+    if ((rc = multi_ensure(h, nrhs)) || (rc = mrhs_buffers(h)) || (rc = mdf_buffers(h))) return rc;
     auto &m = h->multi;
     const int64_t n = h->n;
     const size_t vb = 8 * (size_t)n * nrhs;
@@ -935,7 +975,7 @@ int mrhs_matvec(hmat_t *h, const double *x, double *y, int32_t nrhs, cudaStream_
         src = m.stage;
     }
     launch_mgather(n, nrhs, h->perm, src, m.x, st);
-    multi_products(h, h->seg, h->nseg, m.x, m.y, nrhs, st);
+    multi_products(h, seg, nseg, m.x, m.y, nrhs, st);
     double *dst = dy ? y : m.stage;
     launch_mscatter(n, nrhs, h->perm, m.y, dst, st);
     if (!dy) CK(cudaMemcpyAsync(y, m.stage, vb, cudaMemcpyDeviceToHost, st));
@@ -960,7 +1000,7 @@ static int bicgstab_multi_impl(hmat_handle h, const double *b, double *x, int32_
     cudaStream_t st = (cudaStream_t)stream;
     int rc = multi_ensure(h, nrhs);
     if (rc) return rc;
-    if (nrhs >= 2 && (rc = mrhs_buffers(h))) return rc;
+    if (nrhs >= 2 && ((rc = mrhs_buffers(h)) || (rc = mdf_buffers(h)))) return rc;
     auto &m = h->multi;
     const MultiGrid g = multi_grid(h, nrhs);
     const int64_t n = h->n;
@@ -1020,7 +1060,7 @@ static int bicgstab_multi_impl(hmat_handle h, const double *b, double *x, int32_
             if ((rc = multi_read(h, g.nsys, st, &running))) return rc;
         }
         // every system has stopped: true residuals with the FP64 H-matrix decide
-        multi_products(h, &h->seg64, 1, m.x, m.y, nrhs, st);
+        multi_products(h, &h->seg64, 1, m.x, m.y, nrhs, st, 2);
         launch_mresidual(g, 2, m.b, m.y, m.x, m.r, m.rt, o.tol, o.inner_tol, o.maxit, o.max_restarts, st);
         launches += per_pass64 + 1;
         if ((rc = multi_read(h, g.nsys, st, &running))) return rc;

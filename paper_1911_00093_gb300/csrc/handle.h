@@ -9,6 +9,7 @@
 #include "hmat.h"
 #include "hmat_internal.h"
 #include "kernels.h"
+#include "mdf.h"
 
 namespace hmat_internal {
 
@@ -67,6 +68,7 @@ struct hmat_t {
         int graph_m = 0, graph_limit = -1;
         std::vector<void *> mine;
     } gm;
+    hmat_internal::MdfBufs mdf;     // many-column double-float product (first use)
     bool mrhs = false;              // BF16 handle with the many-right-hand-side tensor-core product
     hmat_internal::MrhsIndex mx;    // its indices (upload) and buffers (first use)
     // buffers of the many-system solver, sized for `cap` right-hand sides

@@ -198,3 +198,39 @@ def test_autotune_keeps_the_bits(hcache, form):
             assert all(i["status"] == 0 and i["relres_true"] <= 1e-8 for i in infos)
         finally:
             P.hmat_destroy(h)
+
+
+@pytest.mark.parametrize("form,fp64", [("fp64", False), ("bf16", True), ("fp32", True)])
+@pytest.mark.parametrize("nrhs", [2, 5, 19])
+def test_double_float_many_columns_bits(hcache, oracle_mod, form, fp64, nrhs):
+    """Several columns of a double-float operator (the FP64 handle's own, the
+    FP64 copy of a BF16 or FP32 handle) go through the many-column product: each
+    CTA or warp applies its panel loads to several columns.  Every column keeps
+    the one-column product's summation order, so the bits are the same; 19
+    columns take two passes of 16, and a batch handle covers the problem index
+    of every work item."""
+    torch = need_gpu()
+    P = lib()
+    meshes = [synth.icosphere(3), synth.two_spheres(3)]
+    Hs = [hcache(m) for m in meshes]
+    for h, H in ((P.hmat_upload(oracle_blob(Hs[0]), form), Hs[0]),
+                 (P.hmat_upload_batch([oracle_blob(x) for x in Hs], form), None)):
+        try:
+            n = P.hmat_info(h)["n"]
+            X = synth.rhs_normal_columns(n, nrhs, seed=7 + nrhs)
+            Xd = torch.from_numpy(np.ascontiguousarray(X.T)).cuda()
+            Yd = torch.empty_like(Xd)
+            P.hmat_matvec(h, Xd, Yd, nrhs, fp64=fp64)
+            Yh = np.zeros(n * nrhs)  # host buffers, staged: flat column-major
+            P.hmat_matvec(h, X.ravel(order="F").copy(), Yh, nrhs, fp64=fp64)
+            torch.cuda.synchronize()
+            assert np.array_equal(Yd.cpu().numpy(), Yh.reshape(nrhs, n))
+            for k in range(nrhs):
+                y1 = torch.empty(n, dtype=torch.float64, device="cuda")
+                P.hmat_matvec(h, Xd[k].contiguous(), y1, 1, fp64=fp64)
+                torch.cuda.synchronize()
+                assert torch.equal(Yd[k], y1), k
+                if H is not None and k in (0, nrhs - 1):
+                    assert rel(Yd[k].cpu().numpy(), H.matvec(X[:, k])) <= 1e-13
+        finally:
+            P.hmat_destroy(h)
