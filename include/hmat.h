@@ -361,10 +361,13 @@ int hmat_problems(hmat_handle h, int32_t *count, int64_t *offsets);
  * inner products, and every decision (stop, breakdown, true residual with the
  * FP64 H-matrix, restart from it) is taken per system on the device.  The
  * products of several columns go through the many-column products of
- * hmat_matvec; the work of a system whose run has stopped is skipped inside the
- * iterations and, where the FP64 copy is double-float (every form but the
- * paper's Table 1 variants), that of a system already accepted in the true
- * residuals.
+ * hmat_matvec, and the work of a system whose run has stopped is skipped
+ * inside the iterations.  With nrhs >= 2 and a double-float FP64 copy (every
+ * form but the paper's Table 1 variants) the true residuals of the systems
+ * whose run stopped are taken at the next host read (every check_every
+ * iterations), over those systems' columns only, and a system that restarts
+ * iterates on with the others; otherwise they are taken once no system
+ * iterates.  A system's results do not depend on the other systems'.
  * b, x: N_total x nrhs column-major (N_total = the handle's N), host or device;
  * x holds the initial guess and receives the solution.  `opts` as for
  * hmat_bicgstab_ex (NULL: defaults).  infos (may be NULL): count x nrhs entries,

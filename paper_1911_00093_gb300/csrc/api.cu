@@ -816,6 +816,10 @@ int multi_ensure(hmat_t *h, int nrhs) {
         cudaFreeHost(m.S_host);
         m.S_host = nullptr;
     }
+    if (m.cols_host) {
+        cudaFreeHost(m.cols_host);
+        m.cols_host = nullptr;
+    }
     m.cap = 0;
     const int nprob = (int)h->prob_off.size() - 1;
     const int nsys = nprob * nrhs;
@@ -833,6 +837,8 @@ int multi_ensure(hmat_t *h, int nrhs) {
     m.mine.push_back(m.partials);
     if ((st = h->alloc(&m.S, sizeof(SysScalars) * (size_t)nsys))) return st;
     m.mine.push_back(m.S);
+    if ((st = h->alloc(&m.cols, sizeof(int32_t) * (size_t)nrhs))) return st;
+    m.mine.push_back(m.cols);
     std::vector<SysDesc> sys(nsys);
     for (int k = 0; k < nrhs; ++k)
         for (int p = 0; p < nprob; ++p) {
@@ -847,6 +853,7 @@ int multi_ensure(hmat_t *h, int nrhs) {
     CK(cudaMemset(m.p, 0, vb));
     CK(cudaMemset(m.v, 0, vb));
     CK(cudaHostAlloc((void **)&m.S_host, sizeof(SysScalars) * (size_t)nsys, cudaHostAllocDefault));
+    CK(cudaHostAlloc((void **)&m.cols_host, sizeof(int32_t) * (size_t)nrhs, cudaHostAllocDefault));
     m.cap = nrhs;
     return HMAT_OK;
 }
@@ -872,13 +879,11 @@ bool mdf_serves(const hmat_t *h, const HmatSegment *seg, int nseg, int nrhs) {
 }
 
 // y(:, k) = A x(:, k) for every column, cluster order (a block-diagonal batch is one operator)
-// The products of every system's column.  sysmode 1 (the products inside an
+// The products of every system's column; skip_stopped (the products inside an
 // iteration): the work items of problems whose system has stopped are skipped,
-// so a batch costs less as its problems converge; 2 (true residuals, the
-// many-column double-float product only): those of systems already accepted or
-// finished.
+// so a batch costs less as its problems converge.
 void multi_products(hmat_t *h, const HmatSegment *seg, int nseg, const double *x, double *y, int nrhs,
-                    cudaStream_t st, int sysmode = 0) {
+                    cudaStream_t st, bool skip_stopped = false) {
     if (seg == h->seg && h->mrhs && h->mx.U && nrhs >= 2) {  // tensor cores, 64 columns per pass
         for (int k0 = 0; k0 < nrhs; k0 += kMrhsCols)
             launch_mrhs_product(h->seg[0].ix, h->mx, h->seg[0].P, x + (size_t)k0 * h->n, h->n, y + (size_t)k0 * h->n,
@@ -887,13 +892,13 @@ void multi_products(hmat_t *h, const HmatSegment *seg, int nseg, const double *x
     }
     const size_t count = h->prob_off.size() - 1;  // problems: system (p, k) is k * count + p
     if (mdf_serves(h, seg, nseg, nrhs)) {  // double-float panels, kMdfCols columns per pass
-        launch_mdf_product(seg->ix, seg->P, h->mdf, x, h->n, y, h->n, nrhs, sysmode ? h->multi.S : nullptr, sysmode,
-                           (int)count, st);
+        launch_mdf_product(seg->ix, seg->P, h->mdf, x, h->n, y, h->n, nrhs, nullptr,
+                           skip_stopped ? h->multi.S : nullptr, 1, (int)count, st);
         return;
     }
     for (int k = 0; k < nrhs; ++k)
         enqueue_segments(seg, nseg, x + (size_t)k * h->n, nullptr, y + (size_t)k * h->n, nullptr, nullptr, 0, st,
-                         nullptr, 0, nullptr, sysmode == 1 ? h->multi.S + (size_t)k * count : nullptr);
+                         nullptr, 0, nullptr, skip_stopped ? h->multi.S + (size_t)k * count : nullptr);
 }
 
 int multi_product_launches(hmat_t *h, const HmatSegment *seg, int nseg, int nrhs) {
@@ -939,20 +944,61 @@ void multi_iteration(hmat_t *h, const MultiGrid &g, int nrhs, int iter_limit, cu
     auto &m = h->multi;
     const MultiVecs v{m.x, m.r, m.rt, m.p, m.v, m.s, m.t};
     launch_miteration_vec(g, 0, v, iter_limit, st);  // p
-    multi_products(h, h->seg, h->nseg, m.p, m.v, nrhs, st, 1);
+    multi_products(h, h->seg, h->nseg, m.p, m.v, nrhs, st, true);
     launch_miteration_vec(g, 1, v, iter_limit, st);  // alpha
     launch_miteration_vec(g, 2, v, iter_limit, st);  // s
-    multi_products(h, h->seg, h->nseg, m.s, m.t, nrhs, st, 1);
+    multi_products(h, h->seg, h->nseg, m.s, m.t, nrhs, st, true);
     launch_miteration_vec(g, 3, v, iter_limit, st);  // omega
     launch_miteration_vec(g, 4, v, iter_limit, st);  // x, r
 }
 
-int multi_read(hmat_t *h, int nsys, cudaStream_t st, bool *running) {
+// The systems' scalars to the host: whether a system still iterates, and the
+// columns (right-hand sides) with a system whose run has stopped and that
+// awaits its true residual (ncols of them in multi.cols_host).
+int multi_read(hmat_t *h, int nsys, int nrhs, cudaStream_t st, bool *running, int *ncols) {
     CK(cudaMemcpyAsync(h->multi.S_host, h->multi.S, sizeof(SysScalars) * (size_t)nsys, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     *running = false;
-    for (int k = 0; k < nsys; ++k)
-        if (h->multi.S_host[k].state == 0 && h->multi.S_host[k].flag == 0) *running = true;
+    *ncols = 0;
+    const int count = nsys / nrhs;  // problems: system (p, k) is k * count + p
+    for (int k = 0; k < nrhs; ++k) {
+        bool waits = false;
+        for (int p = 0; p < count; ++p) {
+            const SysScalars &q = h->multi.S_host[(size_t)k * count + p];
+            if (q.state == 0 && q.flag == 0) *running = true;
+            if (q.state == 0 && q.flag != 0) waits = true;
+        }
+        if (waits) h->multi.cols_host[(*ncols)++] = k;
+    }
+    return HMAT_OK;
+}
+
+// The true residuals (Section 4.1.3) of the systems whose run has stopped, in
+// the ncols columns listed by multi_read: FP64 products of those columns, then
+// acceptance, the run's error, or a restart from the true residual, decided per
+// system on the device; the other systems are left as they are.
+int multi_true_residuals(hmat_t *h, const MultiGrid &g, int ncols, const hmat_solve_opts &o, cudaStream_t st,
+                         int *launches) {
+    auto &m = h->multi;
+    const HmatSegment *seg = &h->seg64;
+    const int count = (int)(h->prob_off.size() - 1);
+    // the many-column product over the list (its work items of the other
+    // systems skipped), or one column at a time when a single right-hand side of
+    // a one-problem handle is listed (the same bits, no unused column batch)
+    if (seg->store == Store::DF && h->mdf.cap > 0 && (ncols >= 2 || count > 1)) {
+        CK(cudaMemcpyAsync(m.cols, m.cols_host, sizeof(int32_t) * (size_t)ncols, cudaMemcpyHostToDevice, st));
+        launch_mdf_product(seg->ix, seg->P, h->mdf, m.x, h->n, m.y, h->n, ncols, m.cols, m.S, 2, count, st);
+        *launches += mdf_launches(seg->ix, ncols);
+    } else {
+        for (int j = 0; j < ncols; ++j) {
+            const size_t k = (size_t)m.cols_host[j] * h->n;
+            enqueue_segments(seg, 1, m.x + k, nullptr, m.y + k, nullptr, nullptr, 0, st);
+        }
+        *launches += ncols * product_launches(seg, 1);
+    }
+    launch_mresidual(g, 2, m.b, m.y, m.x, m.r, m.rt, o.tol, o.inner_tol, o.maxit, o.max_restarts, st);
+    *launches += 1;
+    CK(cudaGetLastError());
     return HMAT_OK;
 }
 
@@ -1010,7 +1056,6 @@ static int bicgstab_multi_impl(hmat_handle h, const double *b, double *x, int32_
     if (int rc_ = vector_location(x, h->device, &dx)) return rc_;
     // products per iteration: two per column; every launch of a product is counted
     const int per_pass = multi_product_launches(h, h->seg, h->nseg, nrhs);
-    const int per_pass64 = multi_product_launches(h, &h->seg64, 1, nrhs);
     int launches = 0;
     const double *bsrc = b;
     if (!db) {
@@ -1029,42 +1074,50 @@ static int bicgstab_multi_impl(hmat_handle h, const double *b, double *x, int32_
     launch_mresidual(g, 1, m.b, m.y, m.x, m.r, m.rt, o.tol, o.inner_tol, o.maxit, o.max_restarts, st);
     launches += 4 + per_pass;
     CK(cudaGetLastError());
+    // Each host read (after every batch of check_every iterations) lists the
+    // systems whose run has stopped since.  With several right-hand sides and a
+    // double-float FP64 copy their true residuals decide at once (accept, finish
+    // on an error, or restart from the true residual) while the other systems
+    // keep iterating, so no system waits for the slowest one; otherwise they
+    // wait until no system iterates.  Either way every system goes through the
+    // same steps: only the time at which its next run starts differs.
+    const bool early = nrhs >= 2 && h->seg64.store == Store::DF && h->mdf.cap > 0;
     bool running = false;
-    for (;;) {
-        if ((rc = multi_read(h, g.nsys, st, &running))) return rc;
-        while (running) {
-            if (o.use_graph) {
-                if (!(m.graph && m.graph_k == o.check_every && m.graph_limit == o.maxit && m.graph_nrhs == nrhs)) {
-                    if (m.graph) {
-                        cudaGraphExecDestroy(m.graph);
-                        m.graph = nullptr;
-                    }
-                    cudaGraph_t gr = nullptr;
-                    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-                    for (int i = 0; i < o.check_every; ++i) multi_iteration(h, g, nrhs, o.maxit, h->cap_stream);
-                    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &gr);
-                    if (!hmat_internal::cuda_ok(e, "cudaStreamEndCapture")) return HMAT_ERR_CUDA;
-                    e = cudaGraphInstantiate(&m.graph, gr, 0);
-                    cudaGraphDestroy(gr);
-                    if (!hmat_internal::cuda_ok(e, "cudaGraphInstantiate")) return HMAT_ERR_CUDA;
-                    m.graph_k = o.check_every;
-                    m.graph_limit = o.maxit;
-                    m.graph_nrhs = nrhs;
-                }
-                CK(cudaGraphLaunch(m.graph, st));
-            } else {
-                for (int i = 0; i < o.check_every; ++i) multi_iteration(h, g, nrhs, o.maxit, st);
-                CK(cudaGetLastError());
+    int nwait = 0;
+    if ((rc = multi_read(h, g.nsys, nrhs, st, &running, &nwait))) return rc;
+    while (running || nwait > 0) {
+        if (nwait > 0 && (early || !running)) {
+            if ((rc = multi_true_residuals(h, g, nwait, o, st, &launches))) return rc;
+            if (!running) {  // nothing iterates: the read tells which systems restarted
+                if ((rc = multi_read(h, g.nsys, nrhs, st, &running, &nwait))) return rc;
+                continue;
             }
-            launches += o.check_every * (5 + 2 * per_pass);
-            if ((rc = multi_read(h, g.nsys, st, &running))) return rc;
         }
-        // every system has stopped: true residuals with the FP64 H-matrix decide
-        multi_products(h, &h->seg64, 1, m.x, m.y, nrhs, st, 2);
-        launch_mresidual(g, 2, m.b, m.y, m.x, m.r, m.rt, o.tol, o.inner_tol, o.maxit, o.max_restarts, st);
-        launches += per_pass64 + 1;
-        if ((rc = multi_read(h, g.nsys, st, &running))) return rc;
-        if (!running) break;  // no system restarted
+        if (o.use_graph) {
+            if (!(m.graph && m.graph_k == o.check_every && m.graph_limit == o.maxit && m.graph_nrhs == nrhs)) {
+                if (m.graph) {
+                    cudaGraphExecDestroy(m.graph);
+                    m.graph = nullptr;
+                }
+                cudaGraph_t gr = nullptr;
+                CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+                for (int i = 0; i < o.check_every; ++i) multi_iteration(h, g, nrhs, o.maxit, h->cap_stream);
+                cudaError_t e = cudaStreamEndCapture(h->cap_stream, &gr);
+                if (!hmat_internal::cuda_ok(e, "cudaStreamEndCapture")) return HMAT_ERR_CUDA;
+                e = cudaGraphInstantiate(&m.graph, gr, 0);
+                cudaGraphDestroy(gr);
+                if (!hmat_internal::cuda_ok(e, "cudaGraphInstantiate")) return HMAT_ERR_CUDA;
+                m.graph_k = o.check_every;
+                m.graph_limit = o.maxit;
+                m.graph_nrhs = nrhs;
+            }
+            CK(cudaGraphLaunch(m.graph, st));
+        } else {
+            for (int i = 0; i < o.check_every; ++i) multi_iteration(h, g, nrhs, o.maxit, st);
+            CK(cudaGetLastError());
+        }
+        launches += o.check_every * (5 + 2 * per_pass);
+        if ((rc = multi_read(h, g.nsys, nrhs, st, &running, &nwait))) return rc;
     }
     double *xo = dx ? x : m.stage;
     launch_mscatter(n, nrhs, h->perm, m.x, xo, st);

@@ -78,6 +78,7 @@ struct hmat_t {
                *t = nullptr, *y = nullptr, *stage = nullptr, *partials = nullptr;
         hmat_internal::SysDesc *sys = nullptr;
         hmat_internal::SysScalars *S = nullptr, *S_host = nullptr;
+        int32_t *cols = nullptr, *cols_host = nullptr;  // the columns of a true-residual pass (device, pinned)
         cudaGraphExec_t graph = nullptr;
         int graph_k = 0, graph_limit = -1, graph_nrhs = 0;
         std::vector<void *> mine;
@@ -111,6 +112,7 @@ struct hmat_t {
         if (gm.graph) cudaGraphExecDestroy(gm.graph);
         if (gm.G_host) cudaFreeHost(gm.G_host);
         if (multi.S_host) cudaFreeHost(multi.S_host);
+        if (multi.cols_host) cudaFreeHost(multi.cols_host);
         if (loop_graph) cudaGraphExecDestroy(loop_graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (void *a : allocs) cudaFree(a);

@@ -16,17 +16,19 @@ struct MdfBufs {
     int64_t ldxs = 0, ldt = 0, ldg = 0;                   // entries per column
 };
 
-// y(:, k) = A x(:, k) for k < ncols with the double-float panels of (ix, P),
-// x and y in cluster order, columns ldx and ldy apart.  Every column's result
-// is bit for bit the one-column product's (enqueue of prep, phase 1, reduce and
+// y(:, k) = A x(:, k) for the columns k = cols[j], j < ncols (k = j when cols
+// is null; cols is a device array) with the double-float panels of (ix, P), x
+// and y in cluster order, columns ldx and ldy apart.  Every column's result is
+// bit for bit the one-column product's (enqueue of prep, phase 1, reduce and
 // phase 2 with Store::DF).
 // sys != nullptr (many-system solver; sys[k * nprob + p] is system (p, k)):
 //   sysmode 1 skips the work of a system whose run has stopped (state or flag
-//   set), sysmode 2 that of a system already accepted or finished (state set);
-//   the skipped rows of y are left as they were.
+//   set); sysmode 2 keeps only that of a system awaiting its true residual
+//   (its run stopped: flag set, state not); the skipped rows of y are left as
+//   they were.
 void launch_mdf_product(const DevIndex &ix, const DevPanels &P, const MdfBufs &b, const double *x, int64_t ldx,
-                        double *y, int64_t ldy, int ncols, const SysScalars *sys, int sysmode, int nprob,
-                        cudaStream_t st);
+                        double *y, int64_t ldy, int ncols, const int32_t *cols, const SysScalars *sys, int sysmode,
+                        int nprob, cudaStream_t st);
 // kernel launches of one such product of ncols columns
 int mdf_launches(const DevIndex &ix, int ncols);
 

@@ -94,7 +94,8 @@ __device__ void start_run(SysScalars &S, double rn, double tol, double inner_tol
 // mode 0: ||b||^2 of every system (state reset);
 // mode 1: r = b - y, r~ = r and a run starts (y = A~ x, the iterated operator);
 // mode 2: the true residual r = b - y (y = the FP64 H-matrix times x) decides
-//         acceptance (Section 4.1.3), the run's error, or a restart from r.
+//         acceptance (Section 4.1.3), the run's error, or a restart from r, for
+//         every system whose run has stopped (the others keep iterating).
 __global__ void __launch_bounds__(kT) k_mresidual(const SysDesc *__restrict__ sys, SysScalars *Sa, int mode,
                                                   const double *__restrict__ b, const double *__restrict__ y,
                                                   double *__restrict__ x, double *__restrict__ r,
@@ -103,6 +104,7 @@ __global__ void __launch_bounds__(kT) k_mresidual(const SysDesc *__restrict__ sy
     __shared__ double sh[kT];
     SysScalars &S = Sa[blockIdx.y];
     if (mode != 0 && S.state != 0) return;
+    if (mode == 2 && S.flag == 0) return;  // its run goes on: no true residual yet
     SYS_RANGE;
     if (mode == 2 && S.bnorm2 == 0.0) {  // b = 0: x = 0 is the solution
         for (int i = first; i < sd.n; i += stride) x[i0 + i] = 0.0;

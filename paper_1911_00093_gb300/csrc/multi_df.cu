@@ -33,20 +33,25 @@ static_assert(kMdfCols % kMdfP1Cols == 0 && kMdfCols % kMdfP2Cols == 0,
               "a pass's column batches stay inside the buffers");
 
 struct MdfArgs {
-    const double *x;
+    const double *x;          // column 0 of x and y
     double *y;
-    float2 *xs, *part, *g;
+    float2 *xs, *part, *g;    // the pass's buffers (column c of the pass at c * ld..)
     int64_t ldx, ldy, ldxs, ldt, ldg;
     int ncols;                // columns of this pass (<= kMdfCols)
-    const SysScalars *sys;    // system of (problem 0, column 0 of this pass), or null
+    int cbase;                // column c of the pass is column cbase + c of x and y ...
+    const int32_t *cols;      // ... or cols[c] when the pass runs over a list
+    const SysScalars *sys;    // system (problem 0, column 0), or null
     int sysmode, nprob;
 };
 
+// the x / y column (and system column) of the pass's column c
+__device__ __forceinline__ int col_of(const MdfArgs &a, int c) { return a.cols ? __ldg(a.cols + c) : a.cbase + c; }
+
 // the column's system does not need this product (see launch_mdf_product)
-__device__ __forceinline__ bool col_idle(const MdfArgs &a, int col, int prob) {
+__device__ __forceinline__ bool col_idle(const MdfArgs &a, int c, int prob) {
     if (a.sys == nullptr || a.sysmode == 0) return false;
-    const SysScalars &q = a.sys[(size_t)col * a.nprob + prob];
-    return a.sysmode == 1 ? (q.state != 0 || q.flag != 0) : q.state != 0;
+    const SysScalars &q = a.sys[(size_t)col_of(a, c) * a.nprob + prob];
+    return a.sysmode == 1 ? (q.state != 0 || q.flag != 0) : (q.state != 0 || q.flag == 0);
 }
 
 // bit c: column c0 + c is in the pass and its system needs the product
@@ -64,7 +69,7 @@ __device__ __forceinline__ int4 ld_panel(const char *p) { return __ldg(reinterpr
 // operand copies: every column's x split into double-float pairs
 __global__ void k_mdf_prep(MdfArgs a, int n) {
     const int c = blockIdx.y;
-    const double *x = a.x + (size_t)c * a.ldx;
+    const double *x = a.x + (size_t)col_of(a, c) * a.ldx;
     float2 *xs = a.xs + (size_t)c * a.ldxs;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) xs[p] = split_double(x[p]);
 }
@@ -265,7 +270,7 @@ __global__ void __launch_bounds__(kMdfP2Threads, kMdfP2Blocks) k_mdf_phase2(MdfA
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const double tot = group_totals<Store::DF>(acc[c], lane);  // lanes 8r..8r+7: row r
-            if (own && ((mask >> c) & 1u)) a.y[(size_t)(c0 + c) * a.ldy + p] = tot;
+            if (own && ((mask >> c) & 1u)) a.y[(size_t)col_of(a, c0 + c) * a.ldy + p] = tot;
         }
     }
 }
@@ -278,12 +283,12 @@ int mdf_launches(const DevIndex &ix, int ncols) {
 }
 
 void launch_mdf_product(const DevIndex &ix, const DevPanels &P, const MdfBufs &b, const double *x, int64_t ldx,
-                        double *y, int64_t ldy, int ncols, const SysScalars *sys, int sysmode, int nprob,
-                        cudaStream_t st) {
+                        double *y, int64_t ldy, int ncols, const int32_t *cols, const SysScalars *sys, int sysmode,
+                        int nprob, cudaStream_t st) {
     for (int k0 = 0; k0 < ncols; k0 += kMdfCols) {
         MdfArgs a;
-        a.x = x + (size_t)k0 * ldx;
-        a.y = y + (size_t)k0 * ldy;
+        a.x = x;
+        a.y = y;
         a.xs = (float2 *)b.xs;
         a.part = (float2 *)b.part;
         a.g = (float2 *)b.g;
@@ -293,7 +298,9 @@ void launch_mdf_product(const DevIndex &ix, const DevPanels &P, const MdfBufs &b
         a.ldt = b.ldt;
         a.ldg = b.ldg;
         a.ncols = std::min(kMdfCols, ncols - k0);
-        a.sys = sys ? sys + (size_t)k0 * nprob : nullptr;
+        a.cbase = k0;
+        a.cols = cols ? cols + k0 : nullptr;
+        a.sys = sys;
         a.sysmode = sys ? sysmode : 0;
         a.nprob = nprob;
         const int prep_x = grid_for(ix.n, 256, 4 * ix.nsm);

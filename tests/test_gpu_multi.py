@@ -234,3 +234,36 @@ def test_double_float_many_columns_bits(hcache, oracle_mod, form, fp64, nrhs):
                     assert rel(Yd[k].cpu().numpy(), H.matvec(X[:, k])) <= 1e-13
         finally:
             P.hmat_destroy(h)
+
+
+@pytest.mark.parametrize("form,opts", [("fp64", {}), ("bf16", {"inner_tol": 1e-2}), ("fp32", {"inner_tol": 1e-4})])
+def test_multi_rhs_systems_independent(hcache, form, opts):
+    """A system's result does not depend on the other systems solved with it:
+    the true residual of a system whose run has stopped is taken at the next
+    host read and the system restarts while the others iterate, so changing the
+    other right-hand sides changes when runs end around it, but not one bit of
+    its own iterates, counts or residuals."""
+    torch = need_gpu()
+    P = lib()
+    mesh = synth.icosphere(3)
+    H = hcache(mesh)
+    nrhs = 8
+    B1 = synth.rhs_normal_columns(mesh.n, nrhs, seed=11)
+    B2 = synth.rhs_normal_columns(mesh.n, nrhs, seed=12)
+    B2[:, 0] = B1[:, 0]
+    B2[:, 3] *= 1e3  # a column far from the others in scale
+    h = P.hmat_upload(oracle_blob(H), form)
+    try:
+        out = []
+        for B in (B1, B2):
+            Bd = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+            Xd = torch.zeros_like(Bd)
+            infos = P.hmat_bicgstab_multi(h, Bd, Xd, nrhs, tol=1e-8, maxit=500, check_every=2, **opts)
+            torch.cuda.synchronize()
+            assert all(i["status"] == 0 and i["relres_true"] <= 1e-8 for i in infos), infos
+            out.append((Xd[0].cpu().numpy(), infos[0]))
+        assert np.array_equal(out[0][0], out[1][0])
+        for key in ("iters", "restarts", "matvecs", "matvecs_fp64", "relres_true", "relres_inner"):
+            assert out[0][1][key] == out[1][1][key], key
+    finally:
+        P.hmat_destroy(h)
