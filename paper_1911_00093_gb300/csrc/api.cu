@@ -78,7 +78,7 @@ void enqueue_segments(const HmatSegment *seg, int nseg, const double *x_src, con
 
 int product_launches(const HmatSegment *seg, int nseg) {
     int n = 1;  // operand copy
-    for (int k = 0; k < nseg; ++k) n += (seg[k].ix.nbig + seg[k].ix.ntasks) ? 3 : 2;
+    for (int k = 0; k < nseg; ++k) n += (seg[k].ix.nbig + seg[k].ix.ntasks + seg[k].ix.ndirect) ? 3 : 2;
     return n;
 }
 
@@ -90,6 +90,7 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
     ix.nlr = (int32_t)L.lr.size();
     ix.nbig = (int32_t)L.red_big.size();
     ix.ntasks = (int32_t)L.red_tasks.size();
+    ix.ndirect = (int32_t)L.red_direct.size();
     ix.max_leaf = L.max_leaf;
     ix.max_ld2 = L.max_ld2;
     ix.perm = h->perm;
@@ -101,6 +102,7 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
     P2Desc *p2 = nullptr;
     double *tscale = nullptr;
     GroupDesc *groups = nullptr;
+    RedDirect *red_direct = nullptr;
     int st;
     // the problem of every work item (pad fields): a batch's solver skips the
     // items of the problems whose systems have stopped
@@ -118,6 +120,8 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
         gd.pad[0] = prob_of(gd.p0);
         gd.pad[1] = 0;
     }
+    std::vector<RedDirect> rdh = L.red_direct;
+    for (size_t k = 0; k < rdh.size(); ++k) rdh[k].prob = lrh[L.red_direct_q[k]].pad;
     if ((st = h->upload(&p1, p1h.data(), sizeof(P1Desc) * p1h.size())) ||
         (st = h->upload(&xdst, L.xdst.data(), sizeof(XDst) * L.xdst.size())) ||
         (st = h->upload(&xsel, L.xsel.data(), 4 * L.xsel.size())) ||
@@ -126,13 +130,14 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
         (st = h->upload(&tofs, L.tofs.data(), 4 * L.tofs.size())) ||
         (st = h->upload(&red_big, L.red_big.data(), 4 * L.red_big.size())) ||
         (st = h->upload(&red_tasks, L.red_tasks.data(), 4 * L.red_tasks.size())) ||
+        (st = h->upload(&red_direct, rdh.data(), sizeof(RedDirect) * rdh.size())) ||
         (st = h->upload(&p2, L.p2.data(), sizeof(P2Desc) * L.p2.size())) ||
         (st = h->upload(&tscale, L.tscale.data(), 8 * L.tscale.size())) ||
         (st = h->upload(&groups, grh.data(), sizeof(GroupDesc) * grh.size()))) {
         return st;
     }
     ix.p1 = p1; ix.tofs = tofs; ix.xdst = xdst; ix.xsel = xsel; ix.lr = lr; ix.gdst = gdst; ix.p2 = p2;
-    ix.red_big = red_big; ix.red_tasks = red_tasks;
+    ix.red_big = red_big; ix.red_tasks = red_tasks; ix.red_direct = red_direct;
     ix.tscale = L.tscale.empty() ? nullptr : tscale;
     ix.groups = groups;
     ix.ngroups = (int32_t)L.groups.size();
@@ -145,6 +150,7 @@ int upload_index(hmat_t *h, const Layout &L, HmatSegment &g) {
                                 sizeof(XDst) * L.xdst.size() + 4 * L.xsel.size() + sizeof(LrDesc) * L.lr.size() +
                                 4 * L.gdst.size() +
                                 sizeof(P2Desc) * L.p2.size() + 4 * (L.red_big.size() + L.red_tasks.size()) +
+                                sizeof(RedDirect) * L.red_direct.size() +
                                 8 * L.tscale.size() +
                                 sizeof(GroupDesc) * L.groups.size());
     return HMAT_OK;

@@ -122,6 +122,15 @@ struct LrDesc {
     int32_t toff;   // first per-rank factor d_l of t = d_l z_l (eq. 23), or -1
     int32_t pad;    // on the device: the block's problem (batch handles)
 };
+// One rank of a low-rank block whose column cluster is a leaf and whose row
+// cluster is a leaf: its t_m entry is its one projection, and it feeds one
+// operand slot, so the reduction copies it without the block's descriptor.
+struct RedDirect {
+    int32_t tsrc;   // entry of T holding t_{m,kappa} of this rank
+    int32_t gdst;   // operand slot in g
+    int32_t scale;  // exponent e of 2^e t
+    int32_t prob;   // on the device: the block's problem (batch handles)
+};
 struct XDst {
     int32_t goff;   // operand index of the slice's first entry in g
     int32_t scale;  // exponent e
@@ -179,7 +188,9 @@ struct Layout {
     std::vector<int32_t> tofs;       // LrDesc::boff: T offsets of each block's per-cluster projections
     std::vector<double> tscale;      // per-rank factors referenced by LrDesc::toff
     std::vector<int32_t> red_big;    // multi-cluster blocks over >= kRedBigCnt clusters (a CTA each)
-    std::vector<int32_t> red_tasks;  // (block << 6) | rank of the other low-rank blocks (a lane each)
+    std::vector<int32_t> red_tasks;  // (block << 6) | rank of the other low-rank blocks (a lane each) ...
+    std::vector<RedDirect> red_direct;  // ... but the ranks of single-leaf blocks without factors d_l
+    std::vector<int32_t> red_direct_q;  // (host) the low-rank block of each red_direct entry
     int32_t max_ld2 = 0, max_ld1 = 0, max_runs1 = 0, max_leaf = 0;
     int64_t stored_entries = 0, phase1_entries = 0, phase2_entries = 0, rank_sum = 0;
     // source of each packed entry, used to fill typed panels without

@@ -26,6 +26,8 @@ struct DevIndex {
     const LrDesc *lr = nullptr;     // [nlr]
     const int32_t *gdst = nullptr;
     const int32_t *red_big = nullptr, *red_tasks = nullptr;
+    const RedDirect *red_direct = nullptr;  // [ndirect]
+    int32_t ndirect = 0;
     const P2Desc *p2 = nullptr;     // [nleaves]
     const double *tscale = nullptr; // per-rank factors of LrDesc::toff (paper's Methods 2 and 3)
     const GroupDesc *groups = nullptr;  // row groups of the row-group expansion

@@ -331,6 +331,7 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
     std::vector<int64_t> kfirst(nb, 0), kcnt(nb, 0);
     L.lr.resize(nlr);
     int64_t ntofs = 0;
+    std::vector<int64_t> direct_q;
     for (int64_t q = 0; q < nlr; ++q) {
         const int64_t b = lr_blocks[q];
         const int64_t *e = v.blocks + 8 * b;
@@ -343,12 +344,6 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
         d.boff = (int32_t)ntofs;  // filled with the phase-1 panels below
         ntofs += kcnt[b];
         if (ntofs > (int64_t(1) << 31) - 16) { if (why) *why = "too many projection terms"; return HMAT_ERR_UNSUPPORTED; }
-        if (kcnt[b] >= kRedBigCnt) {
-            L.red_big.push_back((int32_t)q);
-        } else {
-            if (q >= (int64_t(1) << 25) || e[5] > 63) { if (why) *why = "reduction task out of range"; return HMAT_ERR_UNSUPPORTED; }
-            for (int64_t l = 0; l < e[5]; ++l) L.red_tasks.push_back((int32_t)((q << 6) | l));
-        }
         d.gbeg = (int32_t)L.gdst.size();
         for (int64_t rho = leaf_index(e[0]); rho < leaf_index(e[1]); ++rho) {
             int32_t c = column_in(rho, b);
@@ -362,6 +357,18 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
             if (L.tscale.size() + e[5] > (size_t(1) << 31) - 16) { if (why) *why = "too many rank factors"; return HMAT_ERR_UNSUPPORTED; }
             d.toff = (int32_t)L.tscale.size();
             L.tscale.insert(L.tscale.end(), v.tval + v.toff[b], v.tval + v.toff[b] + e[5]);
+        }
+        // the reduction's work: a CTA for a block over many leaf clusters; a
+        // direct copy per rank for a block inside one leaf column cluster and one
+        // leaf row cluster (its records follow once T is laid out); else a lane
+        // per rank
+        if (kcnt[b] >= kRedBigCnt) {
+            L.red_big.push_back((int32_t)q);
+        } else if (kcnt[b] == 1 && d.gcnt == 1 && d.toff < 0) {
+            direct_q.push_back(q);
+        } else {
+            if (q >= (int64_t(1) << 25) || e[5] > 63) { if (why) *why = "reduction task out of range"; return HMAT_ERR_UNSUPPORTED; }
+            for (int64_t l = 0; l < e[5]; ++l) L.red_tasks.push_back((int32_t)((q << 6) | l));
         }
     }
     L.tofs.assign((size_t)ntofs, -1);
@@ -440,6 +447,13 @@ int build_layout(const BlobView &v, Layout &L, std::string *why) {
     }
     L.p1_elems = off;
     L.npart = tbeg;
+    for (int64_t q : direct_q) {
+        const LrDesc &d = L.lr[q];
+        for (int32_t l = 0; l < d.rank; ++l) {
+            L.red_direct.push_back({L.tofs[d.boff] + l, L.gdst[d.gbeg] + l, d.scale, 0});
+            L.red_direct_q.push_back((int32_t)q);
+        }
+    }
     return HMAT_OK;
 }
 
@@ -513,7 +527,20 @@ int check_layout(const Layout &L, std::string *why) {
     for (const LrDesc &d : L.lr)
         if (d.cnt < kRedBigCnt) multi_ranks += d.rank;
         else if (d.cnt >= kRedBigCnt) ++multi;
-    if (multi != L.red_big.size() || multi_ranks != L.red_tasks.size()) return bad("reduction lists");
+    if (multi != L.red_big.size() || multi_ranks != L.red_tasks.size() + L.red_direct.size() ||
+        L.red_direct_q.size() != L.red_direct.size())
+        return bad("reduction lists");
+    for (size_t k = 0; k < L.red_direct.size(); ++k) {  // the block's own projection and slot, one per rank
+        const RedDirect &r = L.red_direct[k];
+        const int32_t q = L.red_direct_q[k];
+        if (q < 0 || q >= (int32_t)L.lr.size()) return bad("red direct block");
+        const LrDesc &d = L.lr[q];
+        const int64_t l = (int64_t)r.tsrc - L.tofs[d.boff];
+        if (d.cnt != 1 || d.gcnt != 1 || d.toff >= 0 || r.scale != d.scale || l < 0 || l >= d.rank ||
+            (int64_t)r.gdst != (int64_t)L.gdst[d.gbeg] + l || r.tsrc < 0 || r.tsrc >= L.npart || r.gdst < 0 ||
+            r.gdst >= L.glen)
+            return bad("red direct");
+    }
     for (int32_t q : L.red_big) if (q < 0 || q >= (int32_t)L.lr.size() || L.lr[q].cnt < kRedBigCnt) return bad("red big");
     for (int32_t t : L.red_tasks) {
         const int32_t q = t >> 6, l = t & 63;

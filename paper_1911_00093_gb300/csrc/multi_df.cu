@@ -161,9 +161,10 @@ __global__ void __launch_bounds__(kMdfP1Threads, kMdfP1Blocks) k_mdf_phase1(MdfA
 
 // reduce: CTA row blockIdx.y = one column; the one-column reduction's work
 // split and order (k_reduce)
-__global__ void __launch_bounds__(kRedThreads) k_mdf_reduce(MdfArgs a, int nbig, int ntasks,
+__global__ void __launch_bounds__(kRedThreads) k_mdf_reduce(MdfArgs a, int nbig, int ntasks, int ndirect,
                                                             const int32_t *__restrict__ big,
                                                             const int32_t *__restrict__ tasks,
+                                                            const RedDirect *__restrict__ direct,
                                                             const LrDesc *__restrict__ lr,
                                                             const int32_t *__restrict__ gdst,
                                                             const int32_t *__restrict__ tofs,
@@ -205,6 +206,15 @@ __global__ void __launch_bounds__(kRedThreads) k_mdf_reduce(MdfArgs a, int nbig,
             }
             __syncthreads();
         }
+        return;
+    }
+    const int task_blocks = (ntasks + kRedThreads - 1) / kRedThreads;
+    if ((int)blockIdx.x >= nbig + task_blocks) {  // a rank of a single-leaf block: t_m = 2^e T entry
+        const int i = ((int)blockIdx.x - nbig - task_blocks) * kRedThreads + threadIdx.x;
+        if (i >= ndirect) return;
+        const int4 r = __ldg(reinterpret_cast<const int4 *>(direct) + i);  // (tsrc, gdst, scale, prob)
+        if (col_idle(a, c, r.w)) return;
+        g[r.y] = part_to_op<Store::DF>(part[r.x], r.z);
         return;
     }
     const int task = ((int)blockIdx.x - nbig) * kRedThreads + threadIdx.x;
@@ -279,7 +289,7 @@ __global__ void __launch_bounds__(kMdfP2Threads, kMdfP2Blocks) k_mdf_phase2(MdfA
 
 int mdf_launches(const DevIndex &ix, int ncols) {
     const int passes = (ncols + kMdfCols - 1) / kMdfCols;
-    return passes * ((ix.nbig + ix.ntasks) ? 4 : 3);
+    return passes * ((ix.nbig + ix.ntasks + ix.ndirect) ? 4 : 3);
 }
 
 void launch_mdf_product(const DevIndex &ix, const DevPanels &P, const MdfBufs &b, const double *x, int64_t ldx,
@@ -308,10 +318,12 @@ void launch_mdf_product(const DevIndex &ix, const DevPanels &P, const MdfBufs &b
         const int ncb1 = (a.ncols + kMdfP1Cols - 1) / kMdfP1Cols;
         k_mdf_phase1<kMdfP1Cols><<<(unsigned)ix.nleaves * ncb1, kMdfP1Threads, 0, st>>>(a, ix.p1, ix.xdst, ix.xsel,
                                                                                      P.q1);
-        const int rblocks = ix.nbig + (ix.ntasks + kRedThreads - 1) / kRedThreads;
+        const int rblocks = ix.nbig + (ix.ntasks + kRedThreads - 1) / kRedThreads +
+                            (ix.ndirect + kRedThreads - 1) / kRedThreads;
         if (rblocks > 0)
-            k_mdf_reduce<<<dim3(rblocks, a.ncols), kRedThreads, 0, st>>>(a, ix.nbig, ix.ntasks, ix.red_big,
-                                                                         ix.red_tasks, ix.lr, ix.gdst, ix.tofs,
+            k_mdf_reduce<<<dim3(rblocks, a.ncols), kRedThreads, 0, st>>>(a, ix.nbig, ix.ntasks, ix.ndirect, ix.red_big,
+                                                                         ix.red_tasks, ix.red_direct, ix.lr, ix.gdst,
+                                                                         ix.tofs,
                                                                          ix.tscale);
         k_mdf_phase2<kMdfP2Cols><<<ix.nsm * kMdfP2Blocks, kMdfP2Threads, 0, st>>>(a, ix.ngroups, ix.groups, P.p2);
     }

@@ -464,7 +464,9 @@ __global__ void __launch_bounds__(NT, (p1_min_blocks<S, NT>())) k_phase1(int bas
 // >= kRedBigCnt leaf clusters get a whole CTA (kernel blocks [0, nbig)), their
 // T offsets and destinations staged in shared memory; the others are split into
 // one task per rank, kRedTasks tasks per thread (one term and no sum when the
-// column cluster is a leaf).
+// column cluster is a leaf), except the ranks of blocks inside one leaf column
+// cluster and one leaf row cluster (no factors d_l): those are direct copies
+// from T to their operand slot, one record each (the last kernel blocks).
 // ------------------------------------------------------------------------
 constexpr int kRedThreads = 128;
 constexpr int kRedTasks = 1;     // independent tasks per thread of the small blocks
@@ -494,9 +496,15 @@ __device__ __forceinline__ void reduce_task(int l, const LrDesc &ld, const int32
     for (int k = 0; k < ld.gcnt; ++k) g[gdst[ld.gbeg + k] + l] = o;
 }
 
+static_assert(sizeof(RedDirect) == 16 && offsetof(RedDirect, gdst) == 4 && offsetof(RedDirect, scale) == 8 &&
+                  offsetof(RedDirect, prob) == 12,
+              "RedDirect is read as one int4 (tsrc, gdst, scale, prob)");
+
 template <Store S>
-__global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int ntasks, const int32_t *__restrict__ big,
+__global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int ntasks, int ndirect,
+                                                         const int32_t *__restrict__ big,
                                                          const int32_t *__restrict__ tasks,
+                                                         const RedDirect *__restrict__ direct,
                                                          const LrDesc *__restrict__ lr, const int32_t *__restrict__ gdst,
                                                          const int32_t *__restrict__ tofs,
                                                          const typename Tr<S>::Part *__restrict__ part,
@@ -548,6 +556,16 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int nbig, int ntasks, co
             }
             __syncthreads();
         }
+        return;
+    }
+    const int task_blocks = (ntasks + kRedThreads * kRedTasks - 1) / (kRedThreads * kRedTasks);
+    if ((int)blockIdx.x >= nbig + task_blocks) {  // a rank of a single-leaf block: t_m = 2^e T entry
+        const int i = ((int)blockIdx.x - nbig - task_blocks) * kRedThreads + threadIdx.x;
+        int4 r = make_int4(0, 0, 0, 0);  // (tsrc, gdst, scale, prob) of RedDirect
+        if (i < ndirect) r = __ldg(reinterpret_cast<const int4 *>(direct) + i);
+        pdl_wait();  // T, the flags and g belong to earlier kernels
+        if (i >= ndirect || skip_product(S_, mode) || item_idle(sys, r.w)) return;
+        g[r.y] = part_to_op<S>(part[r.x], r.z);
         return;
     }
     // the other blocks: one lane per (block, rank), a sequential sum over the
@@ -913,9 +931,11 @@ void phase1_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *
 template <Store SS>
 void reduce_launch(const DevIndex &ix, const DevPanels &P, const SolverScalars *skipS, int mode, cudaStream_t st,
                    const SysScalars *sys) {
-    const int blocks = ix.nbig + (ix.ntasks + kRedThreads * kRedTasks - 1) / (kRedThreads * kRedTasks);
+    const int blocks = ix.nbig + (ix.ntasks + kRedThreads * kRedTasks - 1) / (kRedThreads * kRedTasks) +
+                       (ix.ndirect + kRedThreads - 1) / kRedThreads;
     if (blocks == 0) return;
-    launch_pdl(k_reduce<SS>, dim3(blocks), dim3(kRedThreads), st, ix.nbig, ix.ntasks, ix.red_big, ix.red_tasks, ix.lr,
+    launch_pdl(k_reduce<SS>, dim3(blocks), dim3(kRedThreads), st, ix.nbig, ix.ntasks, ix.ndirect, ix.red_big,
+               ix.red_tasks, ix.red_direct, ix.lr,
                ix.gdst, ix.tofs, (const typename Tr<SS>::Part *)P.part, (typename Tr<SS>::Op *)P.g, ix.tscale, skipS,
                mode, sys);
 }
