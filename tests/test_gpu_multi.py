@@ -8,7 +8,7 @@ import pytest
 
 import synth
 from blob_util import oracle_blob
-from gpu_util import lib, need_gpu, rel
+from gpu_util import lib, maxrel, need_gpu, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -265,5 +265,35 @@ def test_multi_rhs_systems_independent(hcache, form, opts):
         assert np.array_equal(out[0][0], out[1][0])
         for key in ("iters", "restarts", "matvecs", "matvecs_fp64", "relres_true", "relres_inner"):
             assert out[0][1][key] == out[1][1][key], key
+    finally:
+        P.hmat_destroy(h)
+
+
+def test_double_float_many_columns_full_size(oracle_mod):
+    """Icosphere level 6 (N = 81,920), 18 columns (a full pass of 16 and a ragged
+    one of 2) of the FP64 handle: sampled rows against the oracle's own H-matrix
+    for two columns, and three columns bit for bit the one-column product."""
+    torch = need_gpu()
+    P = lib()
+    mesh = synth.icosphere(6)
+    blob = P.hmat_build(mesh.centroid, mesh.area)
+    H = oracle_mod.HMatrix(mesh.centroid, mesh.area)
+    nrhs = 18
+    X = synth.rhs_normal_columns(mesh.n, nrhs, seed=18)
+    rows = np.random.default_rng(8).choice(mesh.n, 300, replace=False)
+    h = P.hmat_upload(blob, "fp64")
+    try:
+        Xd = torch.from_numpy(np.ascontiguousarray(X.T)).cuda()
+        Yd = torch.empty_like(Xd)
+        P.hmat_matvec(h, Xd, Yd, nrhs)
+        torch.cuda.synchronize()
+        for k in (0, 17):
+            ref = H.matvec_rows(X[:, k], rows)
+            assert maxrel(Yd[k].cpu().numpy()[rows], ref) <= 1e-13, k
+        for k in (0, 15, 17):
+            y1 = torch.empty(mesh.n, dtype=torch.float64, device="cuda")
+            P.hmat_matvec(h, Xd[k].contiguous(), y1, 1)
+            torch.cuda.synchronize()
+            assert torch.equal(Yd[k], y1), k
     finally:
         P.hmat_destroy(h)
