@@ -297,3 +297,33 @@ def test_double_float_many_columns_full_size(oracle_mod):
             assert torch.equal(Yd[k], y1), k
     finally:
         P.hmat_destroy(h)
+
+
+@pytest.mark.parametrize("form,opts", [("fp64", {}), ("bf16", {"inner_tol": 1e-2})])
+def test_batch_several_rhs(hcache, form, opts):
+    """A block-diagonal batch of three problems with three right-hand sides each:
+    nine systems whose true residuals are taken as their runs stop, over the
+    listed columns, with the work items of the other problems of a column
+    skipped.  Every system converges against its own problem's oracle
+    H-matrix."""
+    torch = need_gpu()
+    P = lib()
+    meshes = [synth.icosphere(3), synth.two_spheres(3), synth.cube_sphere(12)]
+    Hs = [hcache(m) for m in meshes]
+    nrhs = 3
+    h = P.hmat_upload_batch([oracle_blob(H) for H in Hs], form)
+    try:
+        off = P.hmat_problems(h)
+        n = off[-1]
+        B = synth.rhs_normal_columns(n, nrhs, seed=33)
+        X = np.zeros((n, nrhs), order="F")
+        infos = P.hmat_bicgstab_multi(h, B, X, nrhs, tol=1e-8, maxit=800, check_every=2, **opts)
+        cnt = len(off) - 1
+        assert len(infos) == cnt * nrhs
+        assert all(i["status"] == 0 and i["relres_true"] <= 1e-8 for i in infos), infos
+        for p, H in enumerate(Hs):
+            sl = slice(off[p], off[p + 1])
+            for k in range(nrhs):
+                assert _true_rel(H, B[sl, k], X[sl, k]) <= 1.05e-8, (p, k)
+    finally:
+        P.hmat_destroy(h)
