@@ -22,11 +22,12 @@
 // descriptors' leading (K) stride is R/8 * 128 bytes and the stride (M/N) one
 // 128 bytes.  K runs in chunks of 64 through one buffer per CTA: a chunk's MMAs
 // finish before the next chunk is staged over it, and the other CTAs on the SM
-// (4 or 8, as many as its tensor memory serves) fill the gap.  The projection's W tiles are stored in
-// that layout (packed at upload) and arrive by one bulk copy per chunk; the
-// expansion's panel rows arrive by 16-byte cp.async.  Every wait is bounded: a
-// wait that runs out records HMAT_ERR_TIMEOUT in *ctl.status, the CTA stops
-// issuing work, lets what it issued finish, frees its tensor memory and returns.
+// (4 or 8, as many as its tensor memory serves) fill the gap.  The projection's
+// W tiles are stored in that layout (packed at upload) and arrive by one bulk
+// copy per chunk; the expansion's panel rows arrive by 16-byte cp.async.
+// Every wait is bounded: a wait that runs out records HMAT_ERR_TIMEOUT in
+// *ctl.status, the CTA stops issuing work, lets what it issued finish, frees its
+// tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
