@@ -327,3 +327,34 @@ def test_batch_several_rhs(hcache, form, opts):
                 assert _true_rel(H, B[sl, k], X[sl, k]) <= 1.05e-8, (p, k)
     finally:
         P.hmat_destroy(h)
+
+
+@pytest.mark.parametrize("form,opts", [("fp64", {}), ("bf16", {"inner_tol": 1e-2})])
+def test_multi_rhs_read_interval_same_bits(hcache, form, opts):
+    """How often the host reads the systems' state (check_every) and whether the
+    iterations replay as a graph only move the time at which a stopped system's
+    true residual is taken and its next run starts, never its arithmetic: the
+    same bits, counts and residuals for every system."""
+    torch = need_gpu()
+    P = lib()
+    mesh = synth.icosphere(3)
+    H = hcache(mesh)
+    nrhs = 6
+    B = synth.rhs_normal_columns(mesh.n, nrhs, seed=21)
+    Bd = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    h = P.hmat_upload(oracle_blob(H), form)
+    try:
+        runs = []
+        for ce, ug in ((2, 1), (1, 0), (5, 1)):
+            Xd = torch.zeros_like(Bd)
+            infos = P.hmat_bicgstab_multi(h, Bd, Xd, nrhs, tol=1e-8, maxit=500, check_every=ce, use_graph=ug, **opts)
+            torch.cuda.synchronize()
+            assert all(i["status"] == 0 for i in infos), infos
+            runs.append((Xd.cpu().numpy(), infos))
+        for X, infos in runs[1:]:
+            assert np.array_equal(X, runs[0][0])
+            for a, b in zip(infos, runs[0][1]):
+                for key in ("iters", "restarts", "matvecs", "matvecs_fp64", "relres_true", "relres_inner"):
+                    assert a[key] == b[key], key
+    finally:
+        P.hmat_destroy(h)
